@@ -1,0 +1,318 @@
+"""TEST INFRASTRUCTURE ONLY: ctypes binding of the CPU oracle (gs_oracle.c).
+
+Only tests/, the smoke check in __graft_entry__ and the CPU-baseline leg of
+bench.py may import this module.  It never touches the CUDA library.
+
+Conventions: parameters arrive as the float32 arrays of a scene; the FP32
+specification path takes them as they are, the FP64 path takes them widened
+to float64 (exact).  Images are [3, H, W]; per-pixel maps are [H, W].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+SRC = HERE / "gs_oracle.c"
+BUILD_DIR = HERE / "_build"
+LIB_PATH = BUILD_DIR / "libgs_oracle.so"
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc: -O2, IEEE arithmetic, no FP contraction."""
+    BUILD_DIR.mkdir(exist_ok=True)
+    if not force and LIB_PATH.exists() and LIB_PATH.stat().st_mtime >= SRC.stat().st_mtime:
+        return LIB_PATH
+    tmp = LIB_PATH.with_suffix(f".so.tmp{os.getpid()}")
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-o", str(tmp), str(SRC), "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class OrcCam(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int), ("H", ctypes.c_int),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3),
+                ("campos", ctypes.c_float * 3), ("znear", ctypes.c_float),
+                ("bg", ctypes.c_float * 3)]
+
+
+def _p(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype)) if a is not None else None
+
+
+F32 = ctypes.c_float
+F64 = ctypes.c_double
+I32 = ctypes.c_int
+U32 = ctypes.c_uint
+I64 = ctypes.c_longlong
+U8 = ctypes.c_ubyte
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(str(LIB_PATH))
+        P = ctypes.POINTER
+        L.orc_exp_spec.restype = F32
+        L.orc_exp_spec.argtypes = [F32]
+        L.orc_keypath_f32.argtypes = [P(OrcCam), I32, P(F32), P(F32), P(F32), P(F32), P(F32),
+                                      P(F32), P(I32), P(I32), P(I32), P(I32)]
+        L.orc_tile_list.restype = I64
+        L.orc_tile_list.argtypes = [I32, P(I32), P(I32), P(F32), I32, I32, P(U32), I64]
+        L.orc_tile_counts.argtypes = [P(OrcCam), I32, P(I32), P(I32), P(I64)]
+        L.orc_sh_basis.argtypes = [F64, F64, F64, P(F64), P(F64)]
+        L.orc_project_f64.argtypes = [P(OrcCam), I32] + [P(F64)] * 5 + [P(I32)] + [P(F64)] * 5
+        L.orc_render_fwd.restype = I64
+        L.orc_render_fwd.argtypes = ([P(OrcCam), I32, P(I32), P(I32), P(F32)] + [P(F64)] * 4 +
+                                     [I32] * 4 + [F64, F64, P(F64), P(F64), P(I32), P(U8)])
+        L.orc_render_bwd.argtypes = ([P(OrcCam), I32, P(I32), P(I32), P(F32)] + [P(F64)] * 4 +
+                                     [I32] * 4 + [P(F64), P(F64)])
+        L.orc_project_bwd.argtypes = [P(OrcCam), I32] + [P(F64)] * 5 + [P(I32), P(F64), P(F64)]
+        L.orc_l1.restype = F64
+        L.orc_l1.argtypes = [I64, P(F64), P(F64), P(F64)]
+        L.orc_adam.argtypes = [I64, P(F64), P(F64), P(F64), P(F64), P(F64), F64, F64, F64, I32]
+        L.orc_mlp_fwd.argtypes = [I32] + [P(F64)] * 6
+        L.orc_mlp_loss_grad.restype = F64
+        L.orc_mlp_loss_grad.argtypes = [I32] + [P(F64)] * 7
+        L.orc_tile_features.argtypes = [P(OrcCam), I32, P(I32), P(I32), P(F32), P(F64), P(F64),
+                                        I32, I32, I64, P(F64)]
+        L.orc_set_threads.argtypes = [I32]
+        L.orc_get_threads.restype = I32
+        _lib = L
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def cam_struct(cam) -> OrcCam:
+    c = OrcCam()
+    c.W, c.H = int(cam.W), int(cam.H)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    for k, v in enumerate(np.asarray(cam.R, np.float32).ravel()):
+        c.R[k] = float(v)
+    for k, v in enumerate(np.asarray(cam.t, np.float32).ravel()):
+        c.t[k] = float(v)
+    for k, v in enumerate(np.asarray(cam.campos, np.float32).ravel()):
+        c.campos[k] = float(v)
+    c.znear = float(cam.znear)
+    for k, v in enumerate(cam.bg):
+        c.bg[k] = float(v)
+    return c
+
+
+def exp_spec(x: float) -> float:
+    return float(lib().orc_exp_spec(float(x)))
+
+
+def _c32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def keypath(cam, scene) -> dict:
+    """FP32 specification path: depth, mean2d, cov2d, radius, rect, touched."""
+    n = scene.n
+    means, ls, q = _c32(scene.means), _c32(scene.log_scales), _c32(scene.quats)
+    out = dict(depth=np.zeros(n, np.float32), mean2d=np.zeros((n, 2), np.float32),
+               cov2d=np.zeros((n, 3), np.float32), radius=np.zeros(n, np.int32),
+               rect=np.zeros((n, 4), np.int32), touched=np.zeros(n, np.int32),
+               status=np.zeros(n, np.int32))
+    c = cam_struct(cam)
+    lib().orc_keypath_f32(ctypes.byref(c), n, _p(means, F32), _p(ls, F32), _p(q, F32),
+                          _p(out["depth"], F32), _p(out["mean2d"], F32), _p(out["cov2d"], F32),
+                          _p(out["radius"], I32), _p(out["rect"], I32), _p(out["touched"], I32),
+                          _p(out["status"], I32))
+    return out
+
+
+def tile_list(kp: dict, tx: int, ty: int) -> np.ndarray:
+    n = kp["depth"].shape[0]
+    L = lib()
+    cnt = L.orc_tile_list(n, _p(kp["rect"], I32), _p(kp["touched"], I32), _p(kp["depth"], F32),
+                          tx, ty, None, 0)
+    ids = np.zeros(max(cnt, 1), np.uint32)
+    L.orc_tile_list(n, _p(kp["rect"], I32), _p(kp["touched"], I32), _p(kp["depth"], F32),
+                    tx, ty, _p(ids, U32), cnt)
+    return ids[:cnt]
+
+
+def tile_counts(cam, kp: dict) -> np.ndarray:
+    c = cam_struct(cam)
+    out = np.zeros(cam.n_tiles, np.int64)
+    lib().orc_tile_counts(ctypes.byref(c), kp["depth"].shape[0], _p(kp["rect"], I32),
+                          _p(kp["touched"], I32), _p(out, I64))
+    return out
+
+
+def sh_basis(x: float, y: float, z: float):
+    Y = np.zeros(16, np.float64)
+    G = np.zeros((16, 3), np.float64)
+    lib().orc_sh_basis(float(x), float(y), float(z), _p(Y, F64), _p(G, F64))
+    return Y, G
+
+
+def project(cam, scene, kp: dict, params64: dict | None = None) -> dict:
+    """FP64 projection.  params64 overrides the scene's parameters (float64
+    arrays with keys means, log_scales, quats, opacity_logits, sh)."""
+    n = scene.n
+    p = params64 or {}
+    means = _c64(p.get("means", scene.means))
+    ls = _c64(p.get("log_scales", scene.log_scales))
+    q = _c64(p.get("quats", scene.quats))
+    lg = _c64(p.get("opacity_logits", scene.opacity_logits))
+    sh = _c64(p.get("sh", scene.sh)).reshape(n, 48)
+    out = dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), opac=np.zeros(n),
+               rgb=np.zeros((n, 3)), rgb_pre=np.zeros((n, 3)))
+    c = cam_struct(cam)
+    lib().orc_project_f64(ctypes.byref(c), n, _p(means, F64), _p(ls, F64), _p(q, F64),
+                          _p(lg, F64), _p(sh, F64), _p(kp["touched"], I32),
+                          _p(out["mean2d"], F64), _p(out["conic"], F64), _p(out["opac"], F64),
+                          _p(out["rgb"], F64), _p(out["rgb_pre"], F64))
+    return out
+
+
+def _window(cam, window):
+    if window is None:
+        return 0, 0, cam.W, cam.H
+    return tuple(int(v) for v in window)
+
+
+def render(cam, kp: dict, proj: dict, window=None, margin_alpha: float = 1e-4,
+           margin_T: float = 1e-3) -> dict:
+    """FP64 forward blend over the pixel window (x0, y0, x1, y1)."""
+    x0, y0, x1, y1 = _window(cam, window)
+    n = kp["depth"].shape[0]
+    W, H = cam.W, cam.H
+    img = np.zeros((3, H, W))
+    T = np.zeros((H, W))
+    nproc = np.zeros((H, W), np.int32)
+    flag = np.zeros((H, W), np.uint8)
+    c = cam_struct(cam)
+    m2, co, op, rgb = (_c64(proj[k]) for k in ("mean2d", "conic", "opac", "rgb"))
+    pairs = lib().orc_render_fwd(ctypes.byref(c), n, _p(kp["rect"], I32), _p(kp["touched"], I32),
+                                 _p(kp["depth"], F32), _p(m2, F64), _p(co, F64), _p(op, F64),
+                                 _p(rgb, F64), x0, y0, x1, y1, margin_alpha, margin_T,
+                                 _p(img, F64), _p(T, F64), _p(nproc, I32), _p(flag, U8))
+    return dict(img=img, T_final=T, n_proc=nproc, flag=flag, pairs=int(pairs))
+
+
+def render_bwd(cam, kp: dict, proj: dict, dL_dimg: np.ndarray, window=None) -> np.ndarray:
+    """Gradient with respect to (u, v, A, B, C, opacity, r, g, b) per Gaussian."""
+    x0, y0, x1, y1 = _window(cam, window)
+    n = kp["depth"].shape[0]
+    g = np.zeros((n, 9))
+    c = cam_struct(cam)
+    m2, co, op, rgb = (_c64(proj[k]) for k in ("mean2d", "conic", "opac", "rgb"))
+    d = _c64(dL_dimg)
+    lib().orc_render_bwd(ctypes.byref(c), n, _p(kp["rect"], I32), _p(kp["touched"], I32),
+                         _p(kp["depth"], F32), _p(m2, F64), _p(co, F64), _p(op, F64), _p(rgb, F64),
+                         x0, y0, x1, y1, _p(d, F64), _p(g, F64))
+    return g
+
+
+def project_bwd(cam, scene, kp: dict, grad2d: np.ndarray, params64: dict | None = None) -> np.ndarray:
+    """Gradient of the 59 parameters, grouped [means|log_scales|quats|logits|sh]."""
+    n = scene.n
+    p = params64 or {}
+    means = _c64(p.get("means", scene.means))
+    ls = _c64(p.get("log_scales", scene.log_scales))
+    q = _c64(p.get("quats", scene.quats))
+    lg = _c64(p.get("opacity_logits", scene.opacity_logits))
+    sh = _c64(p.get("sh", scene.sh)).reshape(n, 48)
+    out = np.zeros(59 * n)
+    g2 = _c64(grad2d)
+    c = cam_struct(cam)
+    lib().orc_project_bwd(ctypes.byref(c), n, _p(means, F64), _p(ls, F64), _p(q, F64),
+                          _p(lg, F64), _p(sh, F64), _p(kp["touched"], I32), _p(g2, F64),
+                          _p(out, F64))
+    return out
+
+
+def split_params(flat: np.ndarray, n: int) -> dict:
+    """View a grouped 59 n buffer as its named parameter groups."""
+    o = 0
+    out = {}
+    for name, w in (("means", 3), ("log_scales", 3), ("quats", 4), ("opacity_logits", 1), ("sh", 48)):
+        out[name] = flat[o:o + w * n].reshape((n, w) if w > 1 else (n,))
+        o += w * n
+    out["sh"] = out["sh"].reshape(n, 16, 3)
+    return out
+
+
+def l1(img: np.ndarray, tgt: np.ndarray):
+    a, b = _c64(img).ravel(), _c64(tgt).ravel()
+    d = np.zeros_like(a)
+    loss = lib().orc_l1(a.size, _p(a, F64), _p(b, F64), _p(d, F64))
+    return float(loss), d.reshape(np.shape(img))
+
+
+def adam(p, g, m, v, lr, b1=0.9, b2=0.999, eps=1e-15, step=1):
+    """One Adam step in FP64; returns new (p, m, v).  lr is per entry."""
+    p, g, m, v = (_c64(x).copy() for x in (p, g, m, v))
+    lr = _c64(np.broadcast_to(lr, p.shape))
+    lib().orc_adam(p.size, _p(p, F64), _p(g, F64), _p(m, F64), _p(v, F64), _p(lr, F64),
+                   b1, b2, eps, int(step))
+    return p, m, v
+
+
+def mlp_fwd(feats, W1, b1, W2, b2) -> np.ndarray:
+    f = _c64(feats)
+    n = f.shape[0]
+    y = np.zeros(n)
+    lib().orc_mlp_fwd(n, _p(f, F64), _p(_c64(W1), F64), _p(_c64(b1), F64), _p(_c64(W2), F64),
+                      _p(_c64(np.atleast_1d(b2)), F64), _p(y, F64))
+    return y
+
+
+def mlp_loss_grad(feats, target, W1, b1, W2, b2):
+    f = _c64(feats)
+    n = f.shape[0]
+    g = np.zeros(321)
+    loss = lib().orc_mlp_loss_grad(n, _p(f, F64), _p(_c64(target), F64), _p(_c64(W1), F64),
+                                   _p(_c64(b1), F64), _p(_c64(W2), F64),
+                                   _p(_c64(np.atleast_1d(b2)), F64), _p(g, F64))
+    return float(loss), g
+
+
+def tile_features(cam, kp: dict, proj: dict, tx: int, ty: int, cap: int = 4096) -> np.ndarray:
+    """The eight per-tile cost features of tile (tx, ty)."""
+    n = kp["depth"].shape[0]
+    cov = proj["conic"]
+    # det of the dilated Sigma' from its inverse: det(Sigma') = 1 / det(conic)
+    dconic = cov[:, 0] * cov[:, 2] - cov[:, 1] ** 2
+    det = np.where(dconic > 0, 1.0 / np.where(dconic > 0, dconic, 1.0), 0.0)
+    f = np.zeros(8)
+    c = cam_struct(cam)
+    lib().orc_tile_features(ctypes.byref(c), n, _p(kp["rect"], I32), _p(kp["touched"], I32),
+                            _p(kp["depth"], F32), _p(_c64(proj["opac"]), F64), _p(_c64(det), F64),
+                            tx, ty, cap, _p(f, F64))
+    return f
+
+
+def forward(cam, scene, window=None, margin_alpha=1e-4, margin_T=1e-3) -> dict:
+    """Key path + FP64 projection + render, in one call."""
+    kp = keypath(cam, scene)
+    proj = project(cam, scene, kp)
+    r = render(cam, kp, proj, window, margin_alpha, margin_T)
+    r.update(kp=kp, proj=proj)
+    return r

@@ -1,0 +1,547 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every test here runs on the CPU.  Each one checks the oracle against something
+other than itself: closed forms of special cases (Sec. II-A's G(x), Sigma' and
+blending equations), invariants of front-to-back blending, textbook tables,
+scipy's spherical harmonics, brute-force enumeration written independently in
+numpy, and central finite differences of the oracle's own forward.
+"""
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2510_14564_gb300 import scenes as S
+
+GOLDEN = Path(__file__).resolve().parent / "golden"
+Y00 = 0.5 / math.sqrt(math.pi)
+
+
+def one_scene(means, log_scales, quats, logits, sh):
+    n = len(means)
+    f = lambda a, s: np.ascontiguousarray(np.asarray(a, np.float64).reshape(s), np.float32)
+    return S.Scene(f(means, (n, 3)), f(log_scales, (n, 3)), f(quats, (n, 4)),
+                   f(logits, (n,)), f(sh, (n, 16, 3)))
+
+
+def dc_sh(rgb):
+    """SH block whose DC term gives colour `rgb` (0.5 + Y00 k = rgb)."""
+    sh = np.zeros((16, 3))
+    sh[0] = (np.asarray(rgb, np.float64) - 0.5) / Y00
+    return sh
+
+
+def sigmoid(x):
+    return 1.0 / (1.0 + math.exp(-x))
+
+
+def f32(x):
+    """The float32 value a scene stores for x."""
+    return float(np.float32(x))
+
+
+def s32(s):
+    """The scale a float32-stored log-scale of log(s) decodes to."""
+    return math.exp(f32(math.log(s)))
+
+
+# ---------------------------------------------------------------------------
+# Single isotropic Gaussian on the optical axis: closed form
+# ---------------------------------------------------------------------------
+
+def test_single_isotropic_gaussian_closed_form():
+    cam = S.front_camera(64, 64)
+    s, logit, rgb = 0.05, 0.5, (0.7, 0.3, 0.55)
+    sc = one_scene([[0, 0, 0]], [[math.log(s)] * 3], [[1, 0, 0, 0]], [logit], [dc_sh(rgb)])
+    r = O.forward(cam, sc)
+    kp = r["kp"]
+    z = 3.0
+    f = float(np.float32(cam.fx))
+    var = (f * s32(s) / z) ** 2 + 0.3
+    rad = math.ceil(3 * math.sqrt(var))
+    assert kp["radius"][0] == rad == 4
+    # rect: floor((u - r)/16), floor((u + r + 15)/16) with u = 32
+    assert list(kp["rect"][0]) == [1, 1, 3, 3] and kp["touched"][0] == 4
+    o = sigmoid(f32(logit))
+    rgb_exp = 0.5 + Y00 * sc.sh[0, 0].astype(np.float64)      # float32-stored DC term
+    ys, xs = np.mgrid[0:64, 0:64]
+    rho2 = (xs + 0.5 - 32.0) ** 2 + (ys + 0.5 - 32.0) ** 2
+    alpha = np.minimum(0.99, o * np.exp(-0.5 * rho2 / var))
+    inside = (xs >= 16) & (xs < 48) & (ys >= 16) & (ys < 48)      # the two-by-two tile block
+    keep = inside & (alpha >= 1 / 255)
+    expect = np.where(keep[None], alpha[None] * rgb_exp[:, None, None], 0.0)
+    assert np.allclose(r["img"], expect, rtol=0, atol=1e-12)
+    assert np.allclose(r["T_final"], np.where(keep, 1 - alpha, 1.0), atol=1e-12)
+    assert np.array_equal(r["n_proc"], keep.astype(np.int32))
+    assert r["flag"].sum() == 0
+
+
+def test_single_gaussian_alpha_clamp():
+    cam = S.front_camera(64, 64)
+    s, logit = 0.5, 6.0
+    sc = one_scene([[0, 0, 0]], [[math.log(s)] * 3], [[1, 0, 0, 0]], [logit], [dc_sh((1, 1, 1))])
+    r = O.forward(cam, sc, window=(30, 30, 34, 34))
+    var = (float(np.float32(cam.fx)) * s32(s) / 3.0) ** 2 + 0.3
+    a0 = sigmoid(f32(logit)) * math.exp(-0.5 * 0.5 / var)     # pixel (31, 31): rho^2 = 0.5
+    assert a0 > 0.99
+    c0 = 0.5 + Y00 * float(sc.sh[0, 0, 0])
+    assert r["img"][0, 31, 31] == pytest.approx(0.99 * c0, abs=1e-12)
+    assert r["T_final"][31, 31] == pytest.approx(0.01, abs=1e-12)
+
+
+def test_single_gaussian_skip_threshold():
+    """A Gaussian whose alpha is below 1/255 at a pixel leaves it untouched."""
+    cam = S.front_camera(64, 64)
+    s, logit = 0.05, -4.0         # o = 0.018
+    sc = one_scene([[0, 0, 0]], [[math.log(s)] * 3], [[1, 0, 0, 0]], [logit], [dc_sh((1, 1, 1))])
+    r = O.forward(cam, sc)
+    o = sigmoid(f32(logit))
+    var = (float(np.float32(cam.fx)) * s32(s) / 3.0) ** 2 + 0.3
+    ys, xs = np.mgrid[0:64, 0:64]
+    a = o * np.exp(-0.5 * ((xs + 0.5 - 32) ** 2 + (ys + 0.5 - 32) ** 2) / var)
+    inside = (xs >= 16) & (xs < 48) & (ys >= 16) & (ys < 48)
+    touched = inside & (a >= 1 / 255)
+    assert touched.sum() > 0 and (inside & ~touched).sum() > 0
+    assert np.all(r["img"][0][~touched] == 0.0)
+    c0 = 0.5 + Y00 * float(sc.sh[0, 0, 0])
+    assert np.allclose(r["img"][0][touched], c0 * a[touched], atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Two Gaussians: blending order follows depth
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("swap", [False, True])
+def test_two_gaussians_order(swap):
+    cam = S.front_camera(64, 64)
+    z1, z2 = (0.0, 0.5) if not swap else (0.5, 0.0)
+    s, l1, l2 = 0.08, 0.3, 1.2
+    c1, c2 = (0.9, 0.2, 0.1), (0.1, 0.3, 0.8)
+    sc = one_scene([[0, 0, z1], [0, 0, z2]], [[math.log(s)] * 3] * 2, [[1, 0, 0, 0]] * 2,
+                   [l1, l2], [dc_sh(c1), dc_sh(c2)])
+    r = O.forward(cam, sc, window=(31, 31, 32, 32))
+    f = float(np.float32(cam.fx))
+
+    def alpha(zw, logit):
+        var = (f * s32(s) / (3.0 + f32(zw))) ** 2 + 0.3
+        return sigmoid(f32(logit)) * math.exp(-0.5 * 0.5 / var)
+
+    a1, a2 = alpha(z1, l1), alpha(z2, l2)
+    col = 0.5 + Y00 * sc.sh[:, 0, :].astype(np.float64)        # float32-stored DC terms
+    front, back = ((a1, col[0]), (a2, col[1])) if z1 < z2 else ((a2, col[1]), (a1, col[0]))
+    expect = front[1] * front[0] + back[1] * back[0] * (1 - front[0])
+    assert np.allclose(r["img"][:, 31, 31], expect, atol=1e-12)
+    assert r["T_final"][31, 31] == pytest.approx((1 - a1) * (1 - a2), abs=1e-12)
+    assert r["n_proc"][31, 31] == 2
+
+
+# ---------------------------------------------------------------------------
+# Transmittance identity: with unit colours, img = (1 - T_final) + T_final bg
+# ---------------------------------------------------------------------------
+
+def test_transmittance_identity():
+    sc = S.uniform_scene(3000, seed=11)
+    sc.sh[:] = 0.0
+    sc.sh[:, 0, :] = 0.5 / Y00
+    cam = S.front_camera(96, 80)
+    cam.bg = (0.25, 0.5, 0.75)
+    r = O.forward(cam, sc)
+    T = r["T_final"]
+    col = r["proj"]["rgb"][r["kp"]["touched"] > 0][0]      # every Gaussian has this colour
+    assert np.all(np.abs(col - 1.0) < 1e-6)
+    for ch in range(3):
+        assert np.allclose(r["img"][ch], col[ch] * (1 - T) + T * cam.bg[ch], atol=1e-12)
+    assert (T < 0.5).mean() > 0.05          # the scene does cover pixels
+    # the stop rule: nothing ends below 1e-4
+    assert T.min() >= 1e-4
+
+
+def test_transmittance_stop_rule():
+    """Ten identical opaque Gaussians: stop before T would fall below 1e-4."""
+    cam = S.front_camera(64, 64)
+    n = 10
+    sc = one_scene([[0, 0, 0.01 * k] for k in range(n)], [[math.log(0.5)] * 3] * n,
+                   [[1, 0, 0, 0]] * n, [1.5] * n, [dc_sh((1, 1, 1))] * n)
+    r = O.forward(cam, sc, window=(31, 31, 32, 32))
+    f = float(np.float32(cam.fx))
+    T, k_last = 1.0, 0
+    for k in range(n):
+        var = (f * s32(0.5) / (3.0 + f32(0.01 * k))) ** 2 + 0.3
+        a = min(0.99, sigmoid(f32(1.5)) * math.exp(-0.5 * 0.5 / var))
+        if T * (1 - a) < 1e-4:
+            break
+        T *= 1 - a
+        k_last = k + 1
+    assert k_last < n                     # the rule fired
+    assert r["n_proc"][31, 31] == k_last
+    assert r["T_final"][31, 31] == pytest.approx(T, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Sigma' = J W Sigma W^T J^T (+0.3 I): special cases
+# ---------------------------------------------------------------------------
+
+def test_cov2d_axis_aligned_and_rotated():
+    cam = S.front_camera(64, 64)
+    f = float(np.float32(cam.fx))
+    sx, sy, sz = 0.05, 0.02, 0.07
+    th = 0.6
+    sc = one_scene([[0, 0, 0], [0, 0, 0]], [[math.log(sx), math.log(sy), math.log(sz)]] * 2,
+                   [[1, 0, 0, 0], [math.cos(th / 2), 0, 0, math.sin(th / 2)]], [0, 0],
+                   [np.zeros((16, 3))] * 2)
+    kp = O.keypath(cam, sc)
+    pr = O.project(cam, sc, kp)
+    D = np.diag([(f * s32(sx) / 3) ** 2, (f * s32(sy) / 3) ** 2])
+    for i, ang in enumerate([0.0, 2 * math.atan2(float(sc.quats[1, 3]), float(sc.quats[1, 0]))]):
+        Rz = np.array([[math.cos(ang), -math.sin(ang)], [math.sin(ang), math.cos(ang)]])
+        S2 = Rz @ D @ Rz.T + 0.3 * np.eye(2)
+        K = np.linalg.inv(S2)
+        A, B, C = pr["conic"][i]
+        assert np.allclose([A, B, C], [K[0, 0], K[0, 1], K[1, 1]], rtol=1e-12)
+        # FP32 key path agrees with FP64 to float precision
+        assert np.allclose(kp["cov2d"][i], [S2[0, 0], S2[0, 1], S2[1, 1]], rtol=2e-6, atol=1e-6)
+
+
+def test_cov2d_off_axis_jacobian():
+    """Off-axis isotropic Gaussian: Sigma' = s^2 J J^T + 0.3 I with the third
+    column of J = -f x / z^2 (pins the projective Jacobian)."""
+    cam = S.front_camera(64, 64)
+    f = float(np.float32(cam.fx))
+    s, x, y = 0.03, 0.7, -0.4
+    sc = one_scene([[x, y, 0.0]], [[math.log(s)] * 3], [[1, 0, 0, 0]], [0], [np.zeros((16, 3))])
+    kp = O.keypath(cam, sc)
+    pr = O.project(cam, sc, kp)
+    z = 3.0
+    x, y = f32(x), f32(y)
+    J = np.array([[f / z, 0, -f * x / z ** 2], [0, f / z, -f * y / z ** 2]])
+    S2 = s32(s) ** 2 * J @ J.T + 0.3 * np.eye(2)
+    K = np.linalg.inv(S2)
+    assert np.allclose(pr["conic"][0], [K[0, 0], K[0, 1], K[1, 1]], rtol=1e-12)
+    assert np.allclose(pr["mean2d"][0], [f * x / z + 32, f * y / z + 32], rtol=1e-12)
+
+
+def test_keypath_culling_and_status():
+    cam = S.front_camera(64, 64)
+    sc = one_scene([[0, 0, -2.9], [0, 0, -4.0], [50, 0, 0], [0, 0, 0], [0, float("nan"), 0]],
+                   [[-3] * 3] * 5, [[1, 0, 0, 0]] * 5, [0] * 5, [np.zeros((16, 3))] * 5)
+    kp = O.keypath(cam, sc)
+    # z = 0.1 (< znear), z = -1 (behind), far off-screen, visible, NaN
+    assert list(kp["touched"] > 0) == [False, False, False, True, False]
+    assert list(kp["status"]) == [0, 0, 0, 0, 1]
+
+
+def test_exp_spec_accuracy():
+    xs = np.linspace(-20, 20, 4001, dtype=np.float32)
+    got = np.array([O.exp_spec(float(x)) for x in xs], np.float64)
+    ref = np.exp(xs.astype(np.float64))
+    assert np.max(np.abs(got - ref) / ref) < 4 * 2.0 ** -23
+
+
+# ---------------------------------------------------------------------------
+# Spherical harmonics
+# ---------------------------------------------------------------------------
+
+def _sphere_quadrature(nz=24, nphi=48):
+    zs, wz = np.polynomial.legendre.leggauss(nz)
+    phis = 2 * np.pi * np.arange(nphi) / nphi
+    pts, w = [], []
+    for z, wzz in zip(zs, wz):
+        r = math.sqrt(1 - z * z)
+        for ph in phis:
+            pts.append((r * math.cos(ph), r * math.sin(ph), z))
+            w.append(wzz * 2 * np.pi / nphi)
+    return np.array(pts), np.array(w)
+
+
+def test_sh_orthonormal_by_quadrature():
+    pts, w = _sphere_quadrature()
+    Y = np.array([O.sh_basis(*p)[0] for p in pts])
+    G = (Y * w[:, None]).T @ Y
+    assert np.allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_sh_matches_textbook_table():
+    rows = [l.split(None, 3) for l in (GOLDEN / "real_sh_degree3.txt").read_text().splitlines()
+            if l.strip() and not l.startswith("#")]
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        v = rng.normal(size=3)
+        x, y, z = v / np.linalg.norm(v)
+        Y, _ = O.sh_basis(x, y, z)
+        for idx, l, m, expr in rows:
+            val = eval(expr, {"sqrt": math.sqrt, "pi": math.pi, "x": x, "y": y, "z": z})
+            assert Y[int(idx)] == pytest.approx(val, abs=1e-13), (l, m)
+
+
+def test_sh_matches_scipy_complex_harmonics():
+    sp = pytest.importorskip("scipy.special")
+    if not hasattr(sp, "sph_harm_y"):
+        pytest.skip("scipy without sph_harm_y")
+    rng = np.random.default_rng(6)
+    for _ in range(10):
+        v = rng.normal(size=3)
+        x, y, z = v / np.linalg.norm(v)
+        theta, phi = math.acos(z), math.atan2(y, x)
+        Y, _ = O.sh_basis(x, y, z)
+        for l in range(4):
+            for m in range(-l, l + 1):
+                c = sp.sph_harm_y(l, abs(m), theta, phi)
+                if m == 0:
+                    ref = c.real
+                elif m > 0:
+                    ref = math.sqrt(2) * (-1) ** m * c.real
+                else:
+                    ref = math.sqrt(2) * (-1) ** m * c.imag
+                assert Y[l * l + l + m] == pytest.approx(ref, abs=1e-12)
+
+
+def test_sh_gradient_central_differences():
+    rng = np.random.default_rng(7)
+    h = 1e-6
+    for _ in range(5):
+        p = rng.normal(size=3)
+        _, G = O.sh_basis(*p)
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = h
+            fd = (O.sh_basis(*(p + e))[0] - O.sh_basis(*(p - e))[0]) / (2 * h)
+            assert np.allclose(G[:, k], fd, atol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# Tile lists: brute force in numpy
+# ---------------------------------------------------------------------------
+
+def test_tile_lists_brute_force():
+    sc = S.uniform_scene(400, seed=3)
+    sc.log_scales += 1.0
+    cam = S.front_camera(72, 40)    # ragged: 5 x 3 tiles, partial last column and row
+    kp = O.keypath(cam, sc)
+    TX = cam.tiles_x
+    trip = []
+    for i in range(sc.n):
+        if kp["touched"][i] <= 0:
+            continue
+        x0, y0, x1, y1 = kp["rect"][i]
+        assert (x1 - x0) * (y1 - y0) == kp["touched"][i]
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                trip.append((ty * TX + tx, int(kp["depth"][i:i + 1].view(np.uint32)[0]), i))
+    trip = np.array(trip, dtype=np.int64)
+    order = np.lexsort((trip[:, 2], trip[:, 1], trip[:, 0]))
+    trip = trip[order]
+    counts = O.tile_counts(cam, kp)
+    assert counts.sum() == len(trip) == kp["touched"].sum()
+    start = 0
+    for t in range(cam.n_tiles):
+        ids = O.tile_list(kp, t % TX, t // TX)
+        assert len(ids) == counts[t]
+        assert np.array_equal(ids, trip[start:start + counts[t], 2])
+        start += counts[t]
+
+
+def test_tile_list_depth_ties_by_index():
+    cam = S.front_camera(32, 32)
+    sc = one_scene([[0, 0, 0]] * 3, [[-3] * 3] * 3, [[1, 0, 0, 0]] * 3, [0] * 3,
+                   [np.zeros((16, 3))] * 3)
+    kp = O.keypath(cam, sc)
+    assert np.array_equal(O.tile_list(kp, 0, 0), [0, 1, 2])
+
+
+# ---------------------------------------------------------------------------
+# Gradients: central differences of the FP64 forward
+# ---------------------------------------------------------------------------
+
+def _grad_scene(seed):
+    rng = np.random.default_rng(seed)
+    n = 12
+    means = np.c_[rng.uniform(-0.5, 0.5, n), rng.uniform(-0.5, 0.5, n), rng.uniform(-0.3, 0.3, n)]
+    ls = rng.normal(-1.6, 0.25, (n, 3))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    logits = rng.normal(-0.5, 0.6, n)
+    sh = rng.normal(0, 0.2, (n, 16, 3))
+    sh[0, 0, 1] = -4.0            # a colour clamped at 0 (zero SH gradient)
+    logits[1] = 7.0               # an opacity clamped at 0.99 near its centre
+    return one_scene(means, ls, q, logits, sh)
+
+
+def _loss(cam, sc, kp, p64, dimg):
+    pr = O.project(cam, sc, kp, p64)
+    r = O.render(cam, kp, pr)
+    return float(np.sum(r["img"] * dimg)), r
+
+
+@pytest.fixture(scope="module")
+def grad_case():
+    cam = S.front_camera(32, 32)
+    for seed in range(50):
+        sc = _grad_scene(seed)
+        kp = O.keypath(cam, sc)
+        pr = O.project(cam, sc, kp)
+        r = O.render(cam, kp, pr, margin_alpha=1e-3, margin_T=1e-2)
+        ok = (r["flag"].sum() == 0 and (kp["touched"] > 0).all()
+              and np.all(np.abs(pr["rgb_pre"]) > 1e-3))
+        if ok:
+            dimg = S.random_cotangent((3, 32, 32), seed=seed)
+            return cam, sc, kp, pr, dimg
+    pytest.fail("no threshold-free gradient scene found")
+
+
+def test_render_bwd_central_differences(grad_case):
+    cam, sc, kp, pr, dimg = grad_case
+    g = O.render_bwd(cam, kp, pr, dimg)
+    h = 1e-6
+    fields = [("mean2d", 0), ("mean2d", 1), ("conic", 0), ("conic", 1), ("conic", 2),
+              ("opac", None), ("rgb", 0), ("rgb", 1), ("rgb", 2)]
+    for i in range(sc.n):
+        for q, (name, col) in enumerate(fields):
+            vals = []
+            for sgn in (+1, -1):
+                p2 = {k: v.copy() for k, v in pr.items()}
+                if col is None:
+                    p2[name][i] += sgn * h
+                else:
+                    p2[name][i, col] += sgn * h
+                vals.append(float(np.sum(O.render(cam, kp, p2)["img"] * dimg)))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert g[i, q] == pytest.approx(fd, rel=1e-5, abs=1e-8), (i, name, col)
+
+
+def test_full_gradient_central_differences(grad_case):
+    cam, sc, kp, pr, dimg = grad_case
+    g2 = O.render_bwd(cam, kp, pr, dimg)
+    g = O.project_bwd(cam, sc, kp, g2)
+    base = {"means": sc.means.astype(np.float64), "log_scales": sc.log_scales.astype(np.float64),
+            "quats": sc.quats.astype(np.float64),
+            "opacity_logits": sc.opacity_logits.astype(np.float64),
+            "sh": sc.sh.astype(np.float64).reshape(sc.n, 48)}
+    h = 1e-6
+    off = 0
+    for name, w in (("means", 3), ("log_scales", 3), ("quats", 4), ("opacity_logits", 1), ("sh", 48)):
+        for i in range(sc.n):
+            for k in range(w):
+                vals = []
+                for sgn in (+1, -1):
+                    p = {kk: vv.copy() for kk, vv in base.items()}
+                    if w == 1:
+                        p[name][i] += sgn * h
+                    else:
+                        p[name][i, k] += sgn * h
+                    vals.append(_loss(cam, sc, kp, p, dimg)[0])
+                fd = (vals[0] - vals[1]) / (2 * h)
+                got = g[off + i * w + k]
+                assert got == pytest.approx(fd, rel=1e-5, abs=1e-8), (name, i, k)
+        off += w * sc.n
+    # the clamped colour channel has no SH gradient; the clamped opacity
+    # Gaussian still has colour gradients
+    dsh = g[11 * sc.n:].reshape(sc.n, 16, 3)
+    assert np.all(dsh[0, :, 1] == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# L1, Adam, MLP, features
+# ---------------------------------------------------------------------------
+
+def test_l1_closed_form():
+    img = np.array([0.5, 0.2, 0.9, 0.4])
+    tgt = np.array([0.5, 0.3, 0.1, 0.4])
+    loss, d = O.l1(img, tgt)
+    assert loss == pytest.approx((0.1 + 0.8) / 4, abs=1e-15)
+    assert list(d) == [0.0, -0.25, 0.25, 0.0]
+
+
+def test_adam_constant_gradient_closed_form():
+    rng = np.random.default_rng(1)
+    n = 64
+    p0 = rng.normal(size=n)
+    g = rng.normal(size=n)
+    g[0] = 0.0
+    lr = np.full(n, 1e-3)
+    p, m, v = p0.copy(), np.zeros(n), np.zeros(n)
+    for t in range(1, 6):
+        p, m, v = O.adam(p, g, m, v, lr, step=t)
+        # bias-corrected moments of a constant gradient are g and g^2 exactly
+        expect = p0 - t * lr * g / (np.abs(g) + 1e-15)
+        assert np.allclose(p, expect, rtol=0, atol=1e-13)
+
+
+def test_adam_two_steps_closed_form():
+    g1, g2 = np.array([0.3, -2.0]), np.array([-0.1, 4.0])
+    lr = np.array([0.01, 0.02])
+    p, m, v = O.adam(np.zeros(2), g1, np.zeros(2), np.zeros(2), lr, step=1)
+    p, m, v = O.adam(p, g2, m, v, lr, step=2)
+    m2 = 0.09 * g1 + 0.1 * g2
+    v2 = 0.999 * 0.001 * g1 ** 2 + 0.001 * g2 ** 2
+    step1 = lr * g1 / (np.abs(g1) + 1e-15)
+    step2 = lr * (m2 / (1 - 0.81)) / (np.sqrt(v2 / (1 - 0.999 ** 2)) + 1e-15)
+    assert np.allclose(p, -step1 - step2, rtol=1e-13)
+
+
+def test_mlp_forward_hand_case():
+    W1 = np.zeros((32, 8)); b1 = np.zeros(32); W2 = np.zeros(32)
+    W1[0, 0] = 2.0; W1[1, 1] = -1.0; b1[1] = 0.5; W2[0] = 3.0; W2[1] = 4.0
+    f = np.zeros((2, 8)); f[0, 0] = 1.5; f[0, 1] = 0.25; f[1, 1] = 2.0
+    y = O.mlp_fwd(f, W1, b1, W2, 0.1)
+    # row 0: relu(3) * 3 + relu(0.25) * 4 + 0.1; row 1: relu(-1.5) = 0 -> 0.1
+    assert np.allclose(y, [9.0 + 1.0 + 0.1, 0.1], atol=1e-15)
+
+
+def test_mlp_gradient_central_differences():
+    rng = np.random.default_rng(2)
+    n = 40
+    f = rng.normal(size=(n, 8))
+    tgt = rng.normal(size=n)
+    W = rng.normal(0, 0.4, 321)
+    unpack = lambda w: (w[:256].reshape(32, 8), w[256:288], w[288:320], w[320:321])
+    loss, g = O.mlp_loss_grad(f, tgt, *unpack(W))
+    h = 1e-6
+    for k in range(321):
+        e = np.zeros(321); e[k] = h
+        fd = (O.mlp_loss_grad(f, tgt, *unpack(W + e))[0] - O.mlp_loss_grad(f, tgt, *unpack(W - e))[0]) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    y = O.mlp_fwd(f, *unpack(W))
+    assert loss == pytest.approx(np.mean((y - tgt) ** 2), rel=1e-13)
+
+
+def test_tile_features_single_gaussian_and_edge():
+    cam = S.front_camera(40, 40)         # 3 x 3 tiles, last row and column 8 px
+    s, logit = 0.05, 0.4
+    sc = one_scene([[0, 0, 0]], [[math.log(s)] * 3], [[1, 0, 0, 0]], [logit], [np.zeros((16, 3))])
+    kp = O.keypath(cam, sc)
+    pr = O.project(cam, sc, kp)
+    f = O.tile_features(cam, kp, pr, 1, 1)
+    o = sigmoid(f32(logit))
+    var = (float(np.float32(cam.fx)) * s32(s) / 3) ** 2 + 0.3
+    cov = min(1.0, math.pi * var / 256)
+    assert f[0] == pytest.approx(math.log(2))
+    assert f[1] == pytest.approx(o) and f[2] == pytest.approx(o)
+    assert f[3] == pytest.approx(cov, rel=1e-12)
+    assert f[4] == pytest.approx(math.log1p(o * cov), rel=1e-12)
+    assert f[5] == pytest.approx(math.log(2), rel=1e-12)       # sum of Th = Th_0 = 1
+    assert f[6] == 1.0
+    assert f[7] == pytest.approx(math.log1p(1600) / 16)
+    fe = O.tile_features(cam, kp, pr, 2, 2)
+    assert fe[6] == pytest.approx(64 / 256) and fe[0] == 0.0
+
+
+def test_tile_features_saturation_sum():
+    """f5 sums the expected transmittance while it stays at or above 1e-4."""
+    cam = S.front_camera(32, 32)
+    n = 30
+    sc = one_scene([[0, 0, 0.001 * k] for k in range(n)], [[math.log(0.4)] * 3] * n,
+                   [[1, 0, 0, 0]] * n, [3.0] * n, [np.zeros((16, 3))] * n)
+    kp = O.keypath(cam, sc)
+    pr = O.project(cam, sc, kp)
+    f = O.tile_features(cam, kp, pr, 0, 0)
+    Th, acc = 1.0, 0.0
+    for k in range(n):
+        if Th < 1e-4:
+            break
+        acc += Th
+        dconic = pr["conic"][k, 0] * pr["conic"][k, 2] - pr["conic"][k, 1] ** 2
+        cov = min(1.0, math.pi * math.sqrt(1 / dconic) / 256)
+        Th *= 1 - min(0.99, pr["opac"][k] * cov)
+    assert f[5] == pytest.approx(math.log1p(acc), rel=1e-12)
