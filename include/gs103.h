@@ -1,0 +1,271 @@
+/*
+ * gs103.h -- C ABI of the GB300 (sm_103a) 3D Gaussian Splatting training hot path.
+ *
+ * Method: BalanceGS (arXiv 2510.14564).  Sec. II-A of the paper defines what is
+ * computed: a Gaussian's influence G(x) = exp(-1/2 (x-mu)^T Sigma^-1 (x-mu)),
+ * its screen covariance Sigma' = J W Sigma W^T J^T, and front-to-back
+ * blending C = sum_i c_i alpha_i prod_{j<i} (1 - alpha_j) over the Gaussians
+ * of a pixel sorted by depth, rendered in 16x16 pixel blocks (Sec. IV-C1).
+ * Readings the paper leaves to the 3DGS renderer it builds on: Sigma' gets a
+ * +0.3 I dilation; a Gaussian covers the tiles of its 3-sigma square
+ * (radius ceil(3 sqrt(lambda_max))); alpha = min(0.99, o G); alpha < 1/255 is
+ * skipped; a pixel stops before the Gaussian that would take its
+ * transmittance below 1e-4; colour = max(0, 0.5 + sum_lm Y_lm(d) k_lm) with
+ * real degree-3 SH and d the unit vector from the camera centre to mu.
+ *
+ * Conventions shared by every call:
+ *   - Pointers named d_* (and every array argument unless stated) are DEVICE
+ *     pointers owned by the caller; the library never allocates or frees.
+ *     Host arrays are marked "host".
+ *   - Every call is asynchronous on the given CUDA stream (0 = legacy default
+ *     stream) and returns a gs_status for host-side argument checks and launch
+ *     errors.  Errors found by kernels are OR-ed as GS_EW_* bits into the
+ *     caller's device word *err_word (read it after the stream synchronises).
+ *   - A batch holds n_views cameras (host array); Gaussians are per view,
+ *     view-major: record v*N + i belongs to view v, Gaussian i.
+ *   - Tiles are 16x16 pixels; view v has TX_v = ceil(W/16) x TY_v = ceil(H/16)
+ *     tiles, numbered row-major, and the batch numbers its tiles globally as
+ *     tile_base_v + ty*TX_v + tx (tile_base = running sum over earlier views).
+ *   - Pixels: view v's image occupies [3, H_v, W_v] floats (planar RGB) at float
+ *     offset 3*pix_base_v, pix_base_v = running sum of W*H over earlier views;
+ *     per-pixel maps (T_final, n_proc) use offset pix_base_v.
+ *   - Parameters of N Gaussians sit in one grouped FP32 buffer of 59 N floats:
+ *     [means 3N | log_scales 3N | quats 4N (w,x,y,z) | opacity_logits N |
+ *      sh 48N ([N,16,3], coefficient-major, RGB innermost)].  Gradients and
+ *     Adam moments use the same layout.
+ */
+#ifndef GS103_H
+#define GS103_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *gs_stream_t; /* = cudaStream_t */
+
+#define GS_TILE 16
+#define GS_MAX_VIEWS 64
+#define GS_PARAM_FLOATS 59
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_ARG = 1,       /* null / misaligned pointer, bad size or dtype */
+    GS_ERR_CAPACITY = 2,  /* an output buffer is too small; see the call */
+    GS_ERR_CUDA = 3,      /* a CUDA launch or copy failed */
+    GS_ERR_TIMEOUT = 4,   /* a persistent kernel ran out of its time budget */
+    GS_ERR_NONFINITE = 5  /* non-finite input (host-detected) */
+} gs_status;
+
+/* Bits OR-ed into *err_word by kernels. */
+#define GS_EW_NONFINITE 0x1u /* a Gaussian had a non-finite parameter; it was culled */
+#define GS_EW_CAPACITY 0x2u  /* instance count exceeded the capacity given */
+#define GS_EW_TIMEOUT 0x4u   /* a persistent render kernel exceeded its budget */
+#define GS_EW_BOUNDS 0x8u    /* an index check failed; the access was skipped */
+
+typedef enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype;
+
+/* Pinhole camera.  world -> camera: p_cam = R p + t (R row-major); the camera
+ * looks along +z_cam; pixel (px, py) has its centre at (px + 0.5, py + 0.5);
+ * u = fx x/z + cx, v = fy y/z + cy.  Gaussians with z <= znear are culled.
+ * campos = -R^T t (the SH view direction origin); bg is added as T_final*bg. */
+typedef struct {
+    int W, H;
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float campos[3];
+    float znear;
+    float bg[3];
+} gs_camera;
+
+/* Screen-space splat record written by gs_project and read by the renderer.
+ * Geometry is FP32; the conic and opacity are stored pre-scaled for exp2:
+ *   e = lo + Ap dx^2 + Bp dx dy + Cp dy^2,  alpha = min(0.99, 2^e)
+ * with Ap = -A/2 log2(e), Bp = -B log2(e), Cp = -C/2 log2(e), lo = log2(o),
+ * (A, B; B, C) = Sigma'^-1, d = pixel centre - (u, v).
+ * GS_F32 colour: record of 48 bytes  {u, v, Ap, Bp}, {Cp, lo, r, g}, {b, 0, 0, 0}.
+ * GS_BF16 / GS_F16 colour: 32 bytes  {u, v, Ap, Bp}, {Cp, lo, rg, b0} where rg
+ * packs r (low half) and g (high half), b0 packs b (low half). */
+#define GS_SPLAT_BYTES_F32 48
+#define GS_SPLAT_BYTES_HALF 32
+
+/* ------------------------------------------------------------------------ */
+
+/* Library version, and a human-readable message for a gs_status. */
+int gs_version(void);
+const char *gs_strerror(int status);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (a host-side counter; thread-safe). */
+long long gs_launch_count(void);
+
+/* a1. Projection and SH colour (Sec. II-A projection equation).
+ * In:  N Gaussians' parameters (grouped layout above; d_sh may instead be a
+ *      separate [N,16,3] array of dtype sh_dtype = GS_F32, GS_BF16 or GS_F16).
+ * Out, per (view, Gaussian), V*N entries each:
+ *   d_splats  records of colour dtype rgb_dtype (size above, 16-B aligned)
+ *   d_depth   camera-space z (FP32), the sort key
+ *   d_rect    int16 [V*N, 4] tile rectangle (xmin, ymin, xmax, ymax), local to the view
+ *   d_touched int32 tiles covered = (xmax-xmin)(ymax-ymin); 0 = culled
+ *   d_radius  int32 radius in pixels (may be NULL)
+ * Depth, radius, rectangle and culling are computed in FP32 with IEEE-rounded
+ * + - * / sqrt in a fixed order (no FMA contraction), so they are reproducible
+ * bit for bit by any IEEE implementation of the same order.
+ * d_quats, d_sh and d_splats must be 16-byte aligned and d_rect 8-byte
+ * aligned (in the grouped layout: N a multiple of 4), else GS_ERR_ARG.
+ * Non-finite parameters cull the Gaussian and set GS_EW_NONFINITE. */
+int gs_project(const gs_camera *cams, int n_views, int N, const float *d_means,
+               const float *d_log_scales, const float *d_quats, const float *d_opacity_logits,
+               const void *d_sh, int sh_dtype, void *d_splats, int rgb_dtype, float *d_depth,
+               int16_t *d_rect, int32_t *d_touched, int32_t *d_radius, int *d_err_word,
+               gs_stream_t stream);
+
+/* a2. Tile binning and the (tile, depth) sort.
+ * gs_bin_sort_workspace gives the scratch bytes gs_bin_sort needs for V*N
+ * Gaussians, an instance capacity and T total tiles.
+ * gs_bin_sort emits one instance per (Gaussian, covered tile) and sorts them
+ * by the 64-bit key (global tile id << 32 | FP32 depth bits), ties by
+ * record index (v*N + i); the order is exactly that of a stable sort of that
+ * key over index-ordered input.
+ * Out: d_vals [capacity] u32 record index per sorted instance;
+ *      d_tile_ranges [T, 2] u32 [start, end) into d_vals per global tile;
+ *      d_keys [capacity] u64 (optional, NULL = not written) the sorted keys;
+ *      d_n_instances (device, 1 x int64) the instance count.
+ * If the count exceeds capacity, nothing past the capacity is written,
+ * GS_EW_CAPACITY is set and *d_n_instances still holds the count needed.
+ * d_workspace must be 256-byte aligned. */
+int gs_bin_sort_workspace(int n_views, int N, long long capacity, const gs_camera *cams,
+                          size_t *bytes);
+int gs_bin_sort(const gs_camera *cams, int n_views, int N, const float *d_depth,
+                const int16_t *d_rect, const int32_t *d_touched, long long capacity,
+                uint32_t *d_vals, uint32_t *d_tile_ranges, uint64_t *d_keys,
+                long long *d_n_instances, void *d_workspace, size_t workspace_bytes,
+                int *d_err_word, gs_stream_t stream);
+
+/* Work schedule for the render kernels (a8).  mode GS_SCHED_RASTER: one CTA
+ * per tile in tile order.  GS_SCHED_ORDER: persistent CTAs take tiles from
+ * d_order (a permutation of the T global tiles) through an atomic queue
+ * (d_queue: one device int, zeroed by the call); the image does not depend
+ * on the order.  budget_ns > 0 bounds a CTA's time: a CTA past it takes no
+ * new tile and sets GS_EW_TIMEOUT (unrendered tiles are then left as they
+ * were). */
+#define GS_SCHED_RASTER 0
+#define GS_SCHED_ORDER 1
+typedef struct {
+    int mode;
+    const int32_t *d_order;
+    int *d_queue;
+    long long budget_ns;
+} gs_schedule;
+
+/* a3. Forward blending (Sec. II-A blending equation), one CTA per 16x16 tile.
+ * Out: d_img [3, H, W] per view; d_T_final per pixel (transmittance left);
+ *      d_n_proc per pixel: entries of the tile list processed up to and
+ *      including the last Gaussian blended (0 if none);
+ *      d_tile_nproc [T] the maximum of d_n_proc over the tile;
+ *      d_tile_ns [T] u64 nanoseconds the tile took (NULL = not measured).
+ * sched may be NULL (raster). */
+int gs_render_fwd(const gs_camera *cams, int n_views, const uint32_t *d_tile_ranges,
+                  const uint32_t *d_vals, const void *d_splats, int rgb_dtype,
+                  const gs_schedule *sched, float *d_img, float *d_T_final, int32_t *d_n_proc,
+                  int32_t *d_tile_nproc, uint64_t *d_tile_ns, int *d_err_word,
+                  gs_stream_t stream);
+
+/* a4. L1 loss over n floats: *d_loss (device float, overwritten)
+ * = mean |img - tgt|; d_dimg = sign(img - tgt)/n with sign(0) = 0. */
+int gs_l1_loss(long long n, const float *d_img, const float *d_tgt, float *d_loss,
+               float *d_dimg, gs_stream_t stream);
+
+/* a5. Reverse mode of the blending.  Walks each pixel's list back to front
+ * from d_n_proc, recovering the transmittance in front of each Gaussian as
+ * T <- T / (1 - alpha) from T_final (nothing per Gaussian is stored).
+ * Accumulates (adds) into d_grad2d [V*N, 12] FP32 per record: dL/d(u, v, A,
+ * B, C, opacity, r, g, b) in entries 0..8 (A, B, C the conic entries, power =
+ * -1/2 (A dx^2 + C dy^2) - B dx dy); entries 9..11 are padding.  The caller
+ * zeroes d_grad2d before the first accumulation. */
+int gs_render_bwd(const gs_camera *cams, int n_views, const uint32_t *d_tile_ranges,
+                  const uint32_t *d_vals, const void *d_splats, int rgb_dtype,
+                  const gs_schedule *sched, const float *d_dimg, const float *d_T_final,
+                  const int32_t *d_n_proc, const int32_t *d_tile_nproc, float *d_grad2d,
+                  int *d_err_word, gs_stream_t stream);
+
+/* a6. Chain d_grad2d through the projection to the 59 parameters of each
+ * Gaussian, summed over views, WRITTEN (not added) into d_dparams (grouped
+ * layout, 16-byte aligned; N must be a multiple of 4 so that every group
+ * stays 16-byte aligned).  Same parameter inputs as gs_project. */
+int gs_project_bwd(const gs_camera *cams, int n_views, int N, const float *d_means,
+                   const float *d_log_scales, const float *d_quats,
+                   const float *d_opacity_logits, const void *d_sh, int sh_dtype,
+                   const int32_t *d_touched, const float *d_grad2d, float *d_dparams,
+                   gs_stream_t stream);
+
+/* a7. One bias-corrected Adam step (Kingma & Ba) over the grouped buffers of
+ * N Gaussians (59 N floats each, 16-B aligned), step t >= 1:
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   p -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)
+ * lr (host, 6 floats) per group: means, log_scales, quats, logits, SH DC
+ * (coefficient 0), SH rest.  If d_sh_shadow != NULL, the updated SH group is
+ * also written there as [N,16,3] in shadow_dtype (GS_BF16 or GS_F16). */
+int gs_adam_step(int N, float *d_params, const float *d_grads, float *d_m, float *d_v,
+                 const float *lr, float b1, float b2, float eps, int t, void *d_sh_shadow,
+                 int shadow_dtype, gs_stream_t stream);
+
+/* Plain Adam over n floats with one learning rate (used for the MLP). */
+int gs_adam_flat(long long n, float *d_p, const float *d_g, float *d_m, float *d_v, float lr,
+                 float b1, float b2, float eps, int t, gs_stream_t stream);
+
+/* a8. Learned tile-cost scheduler.  The paper balances rendering work by a
+ * region density rho = active Gaussians / pixels (Sec. IV-C2); here a small
+ * MLP predicts each tile's render cost from eight tile statistics and the
+ * renderer takes tiles longest-predicted first (GS_SCHED_ORDER).
+ *
+ * gs_tile_features: eight FP32 features per global tile into d_feats [T, 8],
+ * from the first min(count, cap) entries of the tile's list:
+ *   f0 log1p(count), f1 mean opacity, f2 max opacity,
+ *   f3 mean coverage cov = min(1, pi sqrt(det Sigma') / 256),
+ *   f4 log1p(sum o cov),
+ *   f5 log1p(sum of Th_j over entries with Th_j >= 1e-4), where Th_0 = 1 and
+ *      Th_{j+1} = Th_j (1 - min(0.99, o_j cov_j)) (expected transmittance),
+ *   f6 fraction of the tile's pixels inside the image, f7 log1p(W H) / 16. */
+int gs_tile_features(const gs_camera *cams, int n_views, const uint32_t *d_tile_ranges,
+                     const uint32_t *d_vals, const void *d_splats, int rgb_dtype, int cap,
+                     float *d_feats, gs_stream_t stream);
+
+/* MLP 8 -> 32 (ReLU) -> 1.  Weights are 321 values in the order W1 [32, 8]
+ * (row-major), b1 [32], W2 [32], b2 [1].  gs_mlp_predict reads FP16 weights
+ * (d_w16, 321 halves) and accumulates in FP32: d_pred[i] = W2 relu(W1 f_i +
+ * b1) + b2 for n rows of d_feats [n, 8]. */
+int gs_mlp_predict(const void *d_w16, const float *d_feats, int n, float *d_pred,
+                   gs_stream_t stream);
+
+/* Mean squared error of the FP32-weight MLP (d_w32) against targets and its
+ * gradient: target_i = d_target[i] if d_target != NULL, else
+ * log(max(d_tile_ns[i], 1)).  Writes d_grad [321] and *d_loss (device). */
+int gs_mlp_grad(const float *d_w32, const float *d_feats, const uint64_t *d_tile_ns,
+                const float *d_target, int n, float *d_grad, float *d_loss, gs_stream_t stream);
+
+/* gs_mlp_grad, then one Adam step (b1 0.9, b2 0.999, eps 1e-8, step t) on the
+ * FP32 weights with moments d_m, d_v [321], then the FP16 copy d_w16. */
+int gs_mlp_train_step(float *d_w32, void *d_w16, float *d_m, float *d_v, int t, float lr,
+                      const float *d_feats, const uint64_t *d_tile_ns, const float *d_target, int n,
+                      float *d_grad, float *d_loss, gs_stream_t stream);
+
+/* d_cost[i] = (float) d_counts[i] for n entries. */
+int gs_int_cost(const int32_t *d_counts, int n, float *d_cost, gs_stream_t stream);
+
+/* d_cost[t] = entries in tile t's list (from d_tile_ranges [T, 2]). */
+int gs_range_cost(const uint32_t *d_tile_ranges, int T, float *d_cost, gs_stream_t stream);
+
+/* A work order: d_order = the n indices sorted by d_cost descending (ties by
+ * index).  d_workspace (256-byte aligned) of gs_sched_order_workspace bytes. */
+int gs_sched_order_workspace(int n, size_t *bytes);
+int gs_sched_order(const float *d_cost, int n, int32_t *d_order, void *d_workspace,
+                   size_t workspace_bytes, gs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS103_H */

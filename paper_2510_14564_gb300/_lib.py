@@ -1,0 +1,277 @@
+"""ctypes binding of libgs103.so: the C ABI declared in include/gs103.h.
+
+Every function here has the name of the C entry point it calls and only
+marshals arguments: torch tensors become device pointers, cameras become a
+gs_camera array, the current torch stream becomes the cudaStream_t.  All the
+arithmetic runs in the CUDA library.  There is no fallback: if the library is
+missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+PKG = Path(__file__).resolve().parent
+LIB_PATH = PKG / "_build" / "libgs103.so"
+
+GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_NONFINITE = range(6)
+GS_F32, GS_BF16, GS_F16 = 0, 1, 2
+GS_EW_NONFINITE, GS_EW_CAPACITY, GS_EW_TIMEOUT, GS_EW_BOUNDS = 1, 2, 4, 8
+GS_SCHED_RASTER, GS_SCHED_ORDER = 0, 1
+GS_MAX_VIEWS = 64
+SPLAT_BYTES = {GS_F32: 48, GS_BF16: 32, GS_F16: 32}
+
+# Every symbol include/gs103.h declares.
+EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort",
+           "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_project_bwd", "gs_adam_step",
+           "gs_adam_flat", "gs_tile_features", "gs_mlp_predict", "gs_mlp_grad",
+           "gs_mlp_train_step", "gs_int_cost", "gs_range_cost", "gs_sched_order_workspace", "gs_sched_order"]
+
+
+class GsError(RuntimeError):
+    pass
+
+
+class GsCamera(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int), ("H", ctypes.c_int),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3),
+                ("campos", ctypes.c_float * 3), ("znear", ctypes.c_float),
+                ("bg", ctypes.c_float * 3)]
+
+
+class GsSchedule(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("d_order", ctypes.c_void_p),
+                ("d_queue", ctypes.c_void_p), ("budget_ns", ctypes.c_longlong)]
+
+
+_lib = None
+VP = ctypes.c_void_p
+I32 = ctypes.c_int
+I64 = ctypes.c_longlong
+F32 = ctypes.c_float
+SZ = ctypes.c_size_t
+
+
+def lib():
+    """Load the CUDA library (built by paper_2510_14564_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise GsError(f"CUDA library not built: {LIB_PATH} is missing "
+                          "(run python -m paper_2510_14564_gb300.build)")
+        L = ctypes.CDLL(str(LIB_PATH))
+        P = ctypes.POINTER
+        L.gs_version.restype = I32
+        L.gs_launch_count.restype = I64
+        L.gs_strerror.restype = ctypes.c_char_p
+        L.gs_strerror.argtypes = [I32]
+        L.gs_project.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, VP, VP, I32, VP, I32, VP, VP, VP,
+                                 VP, VP, VP]
+        L.gs_bin_sort_workspace.argtypes = [I32, I32, I64, P(GsCamera), P(SZ)]
+        L.gs_bin_sort.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, I64, VP, VP, VP, VP, VP, SZ, VP, VP]
+        L.gs_render_fwd.argtypes = [P(GsCamera), I32, VP, VP, VP, I32, P(GsSchedule), VP, VP, VP, VP,
+                                    VP, VP, VP]
+        L.gs_l1_loss.argtypes = [I64, VP, VP, VP, VP, VP]
+        L.gs_render_bwd.argtypes = [P(GsCamera), I32, VP, VP, VP, I32, P(GsSchedule), VP, VP, VP, VP,
+                                    VP, VP, VP]
+        L.gs_project_bwd.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, VP, VP, I32, VP, VP, VP, VP]
+        L.gs_adam_step.argtypes = [I32, VP, VP, VP, VP, P(F32), F32, F32, F32, I32, VP, I32, VP]
+        L.gs_adam_flat.argtypes = [I64, VP, VP, VP, VP, F32, F32, F32, F32, I32, VP]
+        L.gs_tile_features.argtypes = [P(GsCamera), I32, VP, VP, VP, I32, I32, VP, VP]
+        L.gs_mlp_predict.argtypes = [VP, VP, I32, VP, VP]
+        L.gs_mlp_grad.argtypes = [VP, VP, VP, VP, I32, VP, VP, VP]
+        L.gs_mlp_train_step.argtypes = [VP, VP, VP, VP, I32, F32, VP, VP, VP, I32, VP, VP, VP]
+        L.gs_int_cost.argtypes = [VP, I32, VP, VP]
+        L.gs_range_cost.argtypes = [VP, I32, VP, VP]
+        L.gs_sched_order_workspace.argtypes = [I32, P(SZ)]
+        L.gs_sched_order.argtypes = [VP, I32, VP, VP, SZ, VP]
+        for name in EXPORTS:
+            if name not in ("gs_version", "gs_strerror", "gs_launch_count"):
+                getattr(L, name).restype = I32
+        _lib = L
+    return _lib
+
+
+def check(rc: int, what: str) -> None:
+    if rc != GS_OK:
+        msg = lib().gs_strerror(int(rc)).decode()
+        raise GsError(f"{what}: {msg} (status {rc})")
+
+
+def ptr(t) -> int | None:
+    """Device pointer of a tensor (None for None)."""
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def stream_ptr(stream=None) -> int | None:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or None
+
+
+def camera_array(cams) -> ctypes.Array:
+    """gs_camera[] from scenes.Camera objects (host memory)."""
+    if len(cams) < 1 or len(cams) > GS_MAX_VIEWS:
+        raise GsError(f"need 1..{GS_MAX_VIEWS} views, got {len(cams)}")
+    arr = (GsCamera * len(cams))()
+    for c, cam in zip(arr, cams):
+        c.W, c.H = int(cam.W), int(cam.H)
+        c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+        for k, v in enumerate(np.asarray(cam.R, np.float32).ravel()):
+            c.R[k] = float(v)
+        for k, v in enumerate(np.asarray(cam.t, np.float32).ravel()):
+            c.t[k] = float(v)
+        for k, v in enumerate(np.asarray(cam.campos, np.float32).ravel()):
+            c.campos[k] = float(v)
+        c.znear = float(cam.znear)
+        for k, v in enumerate(cam.bg):
+            c.bg[k] = float(v)
+    return arr
+
+
+# ---------------------------------------------------------------------------
+# Entry points (argument marshalling only)
+# ---------------------------------------------------------------------------
+
+def gs_version() -> int:
+    return int(lib().gs_version())
+
+
+def gs_strerror(status: int) -> str:
+    return lib().gs_strerror(int(status)).decode()
+
+
+def gs_launch_count() -> int:
+    return int(lib().gs_launch_count())
+
+
+def gs_project(cams, N, means, log_scales, quats, opacity_logits, sh, sh_dtype, splats, rgb_dtype,
+               depth, rect, touched, radius, err_word, stream=None):
+    ca = camera_array(cams)
+    check(lib().gs_project(ca, len(cams), int(N), ptr(means), ptr(log_scales), ptr(quats),
+                           ptr(opacity_logits), ptr(sh), int(sh_dtype), ptr(splats), int(rgb_dtype),
+                           ptr(depth), ptr(rect), ptr(touched), ptr(radius), ptr(err_word),
+                           stream_ptr(stream)), "gs_project")
+
+
+def gs_bin_sort_workspace(cams, N, capacity) -> int:
+    ca = camera_array(cams)
+    out = SZ(0)
+    check(lib().gs_bin_sort_workspace(len(cams), int(N), int(capacity), ca, ctypes.byref(out)),
+          "gs_bin_sort_workspace")
+    return int(out.value)
+
+
+def gs_bin_sort(cams, N, depth, rect, touched, capacity, vals, tile_ranges, keys, n_instances,
+                workspace, err_word, stream=None):
+    ca = camera_array(cams)
+    check(lib().gs_bin_sort(ca, len(cams), int(N), ptr(depth), ptr(rect), ptr(touched),
+                            int(capacity), ptr(vals), ptr(tile_ranges), ptr(keys), ptr(n_instances),
+                            ptr(workspace), workspace.numel() * workspace.element_size(),
+                            ptr(err_word), stream_ptr(stream)), "gs_bin_sort")
+
+
+def _sched(sched):
+    if sched is None:
+        return None
+    s = GsSchedule()
+    s.mode = int(sched.get("mode", GS_SCHED_RASTER))
+    s.d_order = ptr(sched.get("order"))
+    s.d_queue = ptr(sched.get("queue"))
+    s.budget_ns = int(sched.get("budget_ns", 0))
+    return ctypes.byref(s), s
+
+
+def gs_render_fwd(cams, tile_ranges, vals, splats, rgb_dtype, sched, img, T_final, n_proc,
+                  tile_nproc, tile_ns, err_word, stream=None):
+    ca = camera_array(cams)
+    sp = _sched(sched)
+    check(lib().gs_render_fwd(ca, len(cams), ptr(tile_ranges), ptr(vals), ptr(splats), int(rgb_dtype),
+                              sp[0] if sp else None, ptr(img), ptr(T_final), ptr(n_proc),
+                              ptr(tile_nproc), ptr(tile_ns), ptr(err_word), stream_ptr(stream)),
+          "gs_render_fwd")
+
+
+def gs_l1_loss(n, img, tgt, loss, dimg, stream=None):
+    check(lib().gs_l1_loss(int(n), ptr(img), ptr(tgt), ptr(loss), ptr(dimg), stream_ptr(stream)),
+          "gs_l1_loss")
+
+
+def gs_render_bwd(cams, tile_ranges, vals, splats, rgb_dtype, sched, dimg, T_final, n_proc,
+                  tile_nproc, grad2d, err_word, stream=None):
+    ca = camera_array(cams)
+    sp = _sched(sched)
+    check(lib().gs_render_bwd(ca, len(cams), ptr(tile_ranges), ptr(vals), ptr(splats), int(rgb_dtype),
+                              sp[0] if sp else None, ptr(dimg), ptr(T_final), ptr(n_proc),
+                              ptr(tile_nproc), ptr(grad2d), ptr(err_word), stream_ptr(stream)),
+          "gs_render_bwd")
+
+
+def gs_project_bwd(cams, N, means, log_scales, quats, opacity_logits, sh, sh_dtype, touched, grad2d,
+                   dparams, stream=None):
+    ca = camera_array(cams)
+    check(lib().gs_project_bwd(ca, len(cams), int(N), ptr(means), ptr(log_scales), ptr(quats),
+                               ptr(opacity_logits), ptr(sh), int(sh_dtype), ptr(touched), ptr(grad2d),
+                               ptr(dparams), stream_ptr(stream)), "gs_project_bwd")
+
+
+def gs_adam_step(N, params, grads, m, v, lr6, b1, b2, eps, t, sh_shadow=None, shadow_dtype=GS_BF16,
+                 stream=None):
+    lr = (F32 * 6)(*[float(x) for x in lr6])
+    check(lib().gs_adam_step(int(N), ptr(params), ptr(grads), ptr(m), ptr(v), lr, float(b1), float(b2),
+                             float(eps), int(t), ptr(sh_shadow), int(shadow_dtype), stream_ptr(stream)),
+          "gs_adam_step")
+
+
+def gs_adam_flat(n, p, g, m, v, lr, b1, b2, eps, t, stream=None):
+    check(lib().gs_adam_flat(int(n), ptr(p), ptr(g), ptr(m), ptr(v), float(lr), float(b1), float(b2),
+                             float(eps), int(t), stream_ptr(stream)), "gs_adam_flat")
+
+
+def gs_tile_features(cams, tile_ranges, vals, splats, rgb_dtype, cap, feats, stream=None):
+    ca = camera_array(cams)
+    check(lib().gs_tile_features(ca, len(cams), ptr(tile_ranges), ptr(vals), ptr(splats),
+                                 int(rgb_dtype), int(cap), ptr(feats), stream_ptr(stream)),
+          "gs_tile_features")
+
+
+def gs_mlp_predict(w16, feats, n, pred, stream=None):
+    check(lib().gs_mlp_predict(ptr(w16), ptr(feats), int(n), ptr(pred), stream_ptr(stream)),
+          "gs_mlp_predict")
+
+
+def gs_mlp_grad(w32, feats, tile_ns, target, n, grad, loss, stream=None):
+    check(lib().gs_mlp_grad(ptr(w32), ptr(feats), ptr(tile_ns), ptr(target), int(n), ptr(grad),
+                            ptr(loss), stream_ptr(stream)), "gs_mlp_grad")
+
+
+def gs_mlp_train_step(w32, w16, m, v, t, lr, feats, tile_ns, target, n, grad, loss, stream=None):
+    check(lib().gs_mlp_train_step(ptr(w32), ptr(w16), ptr(m), ptr(v), int(t), float(lr), ptr(feats),
+                                  ptr(tile_ns), ptr(target), int(n), ptr(grad), ptr(loss),
+                                  stream_ptr(stream)), "gs_mlp_train_step")
+
+
+def gs_int_cost(counts, n, cost, stream=None):
+    check(lib().gs_int_cost(ptr(counts), int(n), ptr(cost), stream_ptr(stream)), "gs_int_cost")
+
+
+def gs_range_cost(tile_ranges, T, cost, stream=None):
+    check(lib().gs_range_cost(ptr(tile_ranges), int(T), ptr(cost), stream_ptr(stream)), "gs_range_cost")
+
+
+def gs_sched_order_workspace(n) -> int:
+    out = SZ(0)
+    check(lib().gs_sched_order_workspace(int(n), ctypes.byref(out)), "gs_sched_order_workspace")
+    return int(out.value)
+
+
+def gs_sched_order(cost, n, order, workspace, stream=None):
+    check(lib().gs_sched_order(ptr(cost), int(n), ptr(order), ptr(workspace),
+                               workspace.numel() * workspace.element_size(), stream_ptr(stream)),
+          "gs_sched_order")

@@ -1,0 +1,562 @@
+// binsort.cu -- a2 tile binning and the (tile, depth) sort (sm_103a).
+//
+// Sec. II-A blends the Gaussians of a pixel "sorted by depth", per 16x16
+// block (Sec. IV-C1).  The order defined here is that of a stable sort of the
+// 64-bit key (global tile id << 32 | FP32 depth bits) over instances emitted
+// in record-index order.  It is produced without ever sorting 64-bit keys:
+//   1. a stable LSD radix sort of the records by depth bits (V*N keys);
+//   2. an exclusive scan of the per-record tile counts in that order;
+//   3. warp-cooperative emission of (tile id, record) pairs in depth order;
+//   4. a stable LSD radix sort of the pairs by tile id alone
+//      (ceil(log2 T) bits, 8 bits per pass).
+// Stability carries the depth order (and the index order of equal depths)
+// through step 4, so the result equals the 64-bit sort.  Tile ranges come
+// from the boundaries of the sorted tile ids.
+#include "gs_common.cuh"
+
+namespace gs {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys per CTA
+constexpr int kRadix = 256;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t read_count(const uint32_t *d_count, uint32_t host_count) {
+    return d_count ? *d_count : host_count;
+}
+
+// Per-CTA digit histogram of keys [b*4096, b*4096+4096) below count.
+// Writes hist[d * nb + b] for every digit (zeros past the count).
+__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
+                                                                const uint32_t *d_count, uint32_t host_count,
+                                                                int shift, uint32_t mask,
+                                                                uint32_t *__restrict__ hist, int nb) {
+    __shared__ uint32_t s_h[8][kRadix];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < 8 * kRadix; k += kSortThreads) (&s_h[0][0])[k] = 0;
+    __syncthreads();
+    const uint32_t count = read_count(d_count, host_count);
+    const long long base = (long long)blockIdx.x * kSortTile + w * (kSortItems * 32);
+#pragma unroll 4
+    for (int it = 0; it < kSortItems; ++it) {
+        long long idx = base + it * 32 + l;
+        bool valid = idx < (long long)count;
+        uint32_t d = valid ? ((__ldg(keys + idx) >> shift) & mask) : kRadix;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (peers & lanemask_lt()) == 0) s_h[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int ww = 0; ww < 8; ++ww) s += s_h[ww][d];
+        hist[(long long)d * nb + blockIdx.x] = s;
+    }
+}
+
+// Exclusive scan of 256 values held one per thread (blockDim = 256).
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *s_warp /*[8]*/) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += t;
+    }
+    if (l == 31) s_warp[w] = inc;
+    __syncthreads();
+    uint32_t off = 0;
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) off += (ww < w) ? s_warp[ww] : 0;
+    return off + inc - v;
+}
+
+// Stable scatter of keys/values by digit, given the scanned histogram matrix.
+__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, const uint32_t *__restrict__ offs, const uint32_t *d_count,
+    uint32_t host_count, int shift, uint32_t mask, int nb, int write_keys) {
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t s_wh[8][kRadix];
+    __shared__ uint32_t s_dstart[kRadix];
+    __shared__ uint32_t s_goff[kRadix];
+    __shared__ uint32_t s_warp[8];
+    const uint32_t count = read_count(d_count, host_count);
+    const long long bbase = (long long)blockIdx.x * kSortTile;
+    if (bbase >= (long long)count) return;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < 8 * kRadix; k += kSortThreads) (&s_wh[0][0])[k] = 0;
+    __syncthreads();
+    uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
+    const long long base = bbase + w * (kSortItems * 32);
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        long long idx = base + it * 32 + l;
+        bool valid = idx < (long long)count;
+        key[it] = valid ? __ldg(kin + idx) : 0u;
+        val[it] = valid ? __ldg(vin + idx) : 0u;
+        uint32_t d = valid ? ((key[it] >> shift) & mask) : kRadix;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned rank = __popc(peers & lanemask_lt());
+        uint32_t before = valid ? s_wh[w][d] : 0u;
+        __syncwarp();
+        if (valid && rank == 0) s_wh[w][d] = before + __popc(peers);
+        __syncwarp();
+        loc[it] = valid ? before + rank : 0xffffffffu;
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, block total, block-local start
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < 8; ++ww) {
+            uint32_t c = s_wh[ww][d];
+            s_wh[ww][d] = run;
+            run += c;
+        }
+        uint32_t start = block_excl_scan_256(run, s_warp);
+        s_dstart[d] = start;
+        s_goff[d] = __ldg(offs + (long long)d * nb + blockIdx.x);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        if (loc[it] != 0xffffffffu) {
+            uint32_t d = (key[it] >> shift) & mask;
+            uint32_t pos = s_dstart[d] + s_wh[w][d] + loc[it];
+            s_keys[pos] = key[it];
+            s_vals[pos] = val[it];
+        }
+    }
+    __syncthreads();
+    const int n_local = (int)min((long long)kSortTile, (long long)count - bbase);
+    for (int s = threadIdx.x; s < n_local; s += kSortThreads) {
+        uint32_t k = s_keys[s];
+        uint32_t d = (k >> shift) & mask;
+        uint32_t g = s_goff[d] + (uint32_t)(s - s_dstart[d]);
+        if (write_keys) kout[g] = k;
+        vout[g] = s_vals[s];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan (device-wide, three kernels)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *s_tmp /*[8]*/) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) s_tmp[w] = v;
+    __syncthreads();
+    T s = 0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < kScanThreads / 32; ++k) s += s_tmp[k];
+        s_tmp[0] = s;
+    }
+    __syncthreads();
+    s = s_tmp[0];
+    __syncthreads();
+    return s;
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(const Tin *__restrict__ in, long long n,
+                                                                Tout *__restrict__ partials) {
+    __shared__ Tout s_tmp[8];
+    long long base = (long long)blockIdx.x * kScanChunk;
+    Tout acc = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        long long i = base + (long long)k * kScanThreads + threadIdx.x;
+        if (i < n) acc += (Tout)in[i];
+    }
+    Tout s = block_sum(acc, s_tmp);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// One CTA of 1024 threads: exclusive scan of the partials in place; total out.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_scan_top(T *partials, int np, T *total) {
+    __shared__ T s_w[32];
+    const int per = (np + 1023) / 1024;
+    const int b = threadIdx.x * per;
+    T loc = 0;
+    for (int k = 0; k < per; ++k)
+        if (b + k < np) loc += partials[b + k];
+    // block exclusive scan of loc
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    T inc = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += t;
+    }
+    if (l == 31) s_w[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        T v = s_w[l];
+        T iv = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T t = __shfl_up_sync(0xffffffffu, iv, o);
+            if (l >= o) iv += t;
+        }
+        s_w[l] = iv - v;
+        if (l == 31 && total) *total = iv;
+    }
+    __syncthreads();
+    T run = s_w[w] + inc - loc;
+    for (int k = 0; k < per; ++k)
+        if (b + k < np) {
+            T v = partials[b + k];
+            partials[b + k] = run;
+            run += v;
+        }
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const Tin *__restrict__ in, long long n,
+                                                             const Tout *__restrict__ partials,
+                                                             Tout *__restrict__ out) {
+    __shared__ Tout s_v[kScanChunk];
+    __shared__ Tout s_w[8];
+    const long long base = (long long)blockIdx.x * kScanChunk;
+    for (int k = 0; k < kScanItems; ++k) {
+        int j = k * kScanThreads + threadIdx.x;
+        long long i = base + j;
+        s_v[j] = i < n ? (Tout)in[i] : (Tout)0;
+    }
+    __syncthreads();
+    Tout loc[kScanItems];
+    Tout sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        loc[k] = s_v[threadIdx.x * kScanItems + k];
+        sum += loc[k];
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    Tout inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        Tout t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += t;
+    }
+    if (l == 31) s_w[w] = inc;
+    __syncthreads();
+    Tout off = partials[blockIdx.x];
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) off += (ww < w) ? s_w[ww] : 0;
+    Tout run = off + inc - sum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        s_v[threadIdx.x * kScanItems + k] = run;
+        run += loc[k];
+    }
+    __syncthreads();
+    for (int k = 0; k < kScanItems; ++k) {
+        int j = k * kScanThreads + threadIdx.x;
+        long long i = base + j;
+        if (i < n) out[i] = s_v[j];
+    }
+}
+
+template <typename Tin, typename Tout>
+static void exclusive_scan(const Tin *in, Tout *out, long long n, Tout *partials, Tout *total,
+                           cudaStream_t st) {
+    int nbk = cdiv(n, kScanChunk);
+    { k_scan_partials<Tin, Tout><<<nbk, kScanThreads, 0, st>>>(in, n, partials); count_launches(1); }
+    { k_scan_top<Tout><<<1, 1024, 0, st>>>(partials, nbk, total); count_launches(1); }
+    { k_scan_apply<Tin, Tout><<<nbk, kScanThreads, 0, st>>>(in, n, partials, out); count_launches(1); }
+}
+
+// ---------------------------------------------------------------------------
+// Binning kernels
+// ---------------------------------------------------------------------------
+__global__ void k_depth_keys(const float *__restrict__ depth, const int *__restrict__ touched,
+                             long long n, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    keys[j] = touched[j] > 0 ? __float_as_uint(depth[j]) : 0xffffffffu;
+    vals[j] = (uint32_t)j;
+}
+
+__global__ void k_gather_counts(const uint32_t *__restrict__ order, const int *__restrict__ touched,
+                                long long n, uint32_t *__restrict__ out) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int t = touched[order[j]];
+    out[j] = t > 0 ? (uint32_t)t : 0u;
+}
+
+// Clamp the instance count to the capacity; flag an overflow.
+__global__ void k_finish_count(const unsigned long long *total, long long cap, long long *n_inst,
+                               uint32_t *count, int *err_word) {
+    unsigned long long t = *total;
+    if (n_inst) *n_inst = (long long)t;
+    if ((long long)t > cap) {
+        set_err(err_word, GS_EW_CAPACITY);
+        *count = (uint32_t)cap;
+    } else {
+        *count = (uint32_t)t;
+    }
+}
+
+// One warp per 32 depth-ordered records; the warp writes each record's
+// tiles (row-major over its rectangle) to consecutive slots, lanes striding
+// the slots so the stores coalesce.
+__global__ void __launch_bounds__(256) k_emit(TileBatch tb, int N, long long VN,
+                                              const uint32_t *__restrict__ order,
+                                              const unsigned long long *__restrict__ offs,
+                                              const short4 *__restrict__ rect,
+                                              const int *__restrict__ touched, long long cap,
+                                              uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = threadIdx.x & 31;
+    bool valid = j < VN;
+    uint32_t g = valid ? __ldg(order + j) : 0u;
+    int cnt = valid ? __ldg(touched + g) : 0;
+    if (cnt < 0) cnt = 0;
+    unsigned long long off = valid ? __ldg(offs + j) : 0ull;
+    short4 rc = valid ? __ldg(rect + g) : make_short4(0, 0, 0, 0);
+    int v = (int)(g / (uint32_t)N);
+    int tbase = tb.v[v].tile_base, TX = tb.v[v].TX;
+    unsigned has = __ballot_sync(0xffffffffu, cnt > 0);
+    while (has) {
+        int o = __ffs(has) - 1;
+        has &= has - 1;
+        int c = __shfl_sync(0xffffffffu, cnt, o);
+        unsigned long long b = __shfl_sync(0xffffffffu, off, o);
+        int x0 = __shfl_sync(0xffffffffu, (int)rc.x, o);
+        int y0 = __shfl_sync(0xffffffffu, (int)rc.y, o);
+        int x1 = __shfl_sync(0xffffffffu, (int)rc.z, o);
+        int base_t = __shfl_sync(0xffffffffu, tbase, o);
+        int tx_n = __shfl_sync(0xffffffffu, TX, o);
+        uint32_t gid = __shfl_sync(0xffffffffu, g, o);
+        int w = x1 - x0;
+        for (int k = l; k < c; k += 32) {
+            int ty = y0 + k / w, tx = x0 + k % w;
+            unsigned long long pos = b + (unsigned long long)k;
+            if ((long long)pos < cap) {
+                keys[pos] = (uint32_t)(base_t + ty * tx_n + tx);
+                vals[pos] = gid;
+            }
+        }
+    }
+}
+
+__global__ void k_tile_ranges(const uint32_t *__restrict__ keys, const uint32_t *d_count,
+                              uint2 *__restrict__ ranges) {
+    const uint32_t count = *d_count;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
+    if (i == (long long)count - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+}
+
+__global__ void k_keys64(const uint32_t *__restrict__ tkeys, const uint32_t *__restrict__ vals,
+                         const float *__restrict__ depth, const uint32_t *d_count,
+                         unsigned long long *__restrict__ out) {
+    const uint32_t count = *d_count;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    out[i] = ((unsigned long long)tkeys[i] << 32) | __float_as_uint(depth[vals[i]]);
+}
+
+// ---------------------------------------------------------------------------
+// Workspace plan
+// ---------------------------------------------------------------------------
+struct Plan {
+    size_t dk0, dk1, dv0, dv1, cnt, offs, tk0, tk1, tvs, hist, part, misc, bytes;
+    int nb_max;
+};
+
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Plan make_plan(long long VN, long long cap) {
+    Plan p;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
+    p.dk0 = take(4 * VN); p.dk1 = take(4 * VN); p.dv0 = take(4 * VN); p.dv1 = take(4 * VN);
+    p.cnt = take(4 * VN);
+    p.offs = take(8 * VN);
+    p.tk0 = take(4 * cap); p.tk1 = take(4 * cap); p.tvs = take(4 * cap);
+    long long nbc = (cap + kSortTile - 1) / kSortTile, nbv = (VN + kSortTile - 1) / kSortTile;
+    p.nb_max = (int)(nbc > nbv ? nbc : nbv);
+    if (p.nb_max < 1) p.nb_max = 1;
+    p.hist = take(4 * (size_t)kRadix * p.nb_max);
+    long long maxscan = (long long)kRadix * p.nb_max > VN ? (long long)kRadix * p.nb_max : VN;
+    p.part = take(8 * (size_t)((maxscan + kScanChunk - 1) / kScanChunk + 1));
+    p.misc = take(64);
+    p.bytes = o;
+    return p;
+}
+
+// One stable LSD pass over `count` keys (device or host count).
+static void radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+                       const uint32_t *d_count, uint32_t host_count, long long cap_keys, int shift,
+                       int bits, bool write_keys, uint32_t *hist, uint32_t *part, cudaStream_t st) {
+    int nb = cdiv(cap_keys, kSortTile);
+    if (nb < 1) nb = 1;
+    uint32_t mask = (bits >= 32) ? 0xffffffffu : ((1u << bits) - 1u);
+    { k_radix_upsweep<<<nb, kSortThreads, 0, st>>>(kin, d_count, host_count, shift, mask, hist, nb); count_launches(1); }
+    exclusive_scan<uint32_t, uint32_t>(hist, hist, (long long)kRadix * nb, part, (uint32_t *)nullptr, st);
+    { k_radix_downsweep<<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, hist, d_count, host_count,
+                                                   shift, mask, nb, write_keys ? 1 : 0); count_launches(1); }
+}
+
+size_t radix_sort_workspace(long long n) {
+    long long nb = (n + kSortTile - 1) / kSortTile;
+    if (nb < 1) nb = 1;
+    long long scan = (long long)kRadix * nb;
+    return 4 * al(4 * (size_t)n) + al(4 * (size_t)kRadix * nb) +
+           al(8 * (size_t)((scan + kScanChunk - 1) / kScanChunk + 1));
+}
+
+// Stable LSD sort of n (key, value) pairs on the low `bits` key bits.  k0/v0
+// (caller memory, clobbered) hold the input; the sorted values land in vout.
+// scratch is what radix_sort_workspace(n) counts past the first two arrays.
+void radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *vout, long long n, int bits, void *scratch,
+                      cudaStream_t st) {
+    char *ws = reinterpret_cast<char *>(scratch);
+    size_t a = al(4 * (size_t)n);
+    uint32_t *k1 = (uint32_t *)ws, *v1 = (uint32_t *)(ws + a);
+    uint32_t *hist = (uint32_t *)(ws + 2 * a);
+    long long nb = (n + kSortTile - 1) / kSortTile;
+    if (nb < 1) nb = 1;
+    uint32_t *part = (uint32_t *)(ws + 2 * a + al(4 * (size_t)kRadix * nb));
+    int passes = (bits + 7) / 8;
+    uint32_t *K[2] = {k0, k1}, *V[2] = {v0, v1};
+    int done = 0;
+    for (int p = 0; p < passes; ++p) {
+        int b = (bits - done + (passes - p) - 1) / (passes - p);
+        uint32_t *vo = (p == passes - 1) ? vout : V[(p + 1) % 2];
+        radix_pass(K[p % 2], V[p % 2], K[(p + 1) % 2], vo, nullptr, (uint32_t)n, n, done, b,
+                   p != passes - 1, hist, part, st);
+        done += b;
+    }
+}
+
+int make_tile_batch(const gs_camera *cams, int n_views, TileBatch *out) {
+    if (!cams || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_ARG;
+    out->n = n_views;
+    long long tiles = 0, pix = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const gs_camera &c = cams[v];
+        if (c.W <= 0 || c.H <= 0 || c.W > 32767 * GS_TILE || c.H > 32767 * GS_TILE) return GS_ERR_ARG;
+        ViewTiles &t = out->v[v];
+        t.W = c.W; t.H = c.H;
+        t.TX = (c.W + GS_TILE - 1) / GS_TILE;
+        t.TY = (c.H + GS_TILE - 1) / GS_TILE;
+        t.tile_base = (int)tiles;
+        t.pix_base = pix;
+        for (int k = 0; k < 3; ++k) t.bg[k] = c.bg[k];
+        tiles += (long long)t.TX * t.TY;
+        pix += (long long)c.W * c.H;
+        if (tiles > (1ll << 30)) return GS_ERR_ARG;
+    }
+    out->total_tiles = (int)tiles;
+    out->total_pix = pix;
+    return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" int gs_bin_sort_workspace(int n_views, int N, long long capacity, const gs_camera *cams,
+                                     size_t *bytes) {
+    (void)cams;
+    if (!bytes || n_views < 1 || n_views > GS_MAX_VIEWS || N < 0 || capacity < 0 ||
+        capacity > 0xF0000000ll)
+        return GS_ERR_ARG;
+    long long VN = (long long)n_views * N;
+    *bytes = make_plan(VN, capacity).bytes;
+    return GS_OK;
+}
+
+extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const float *d_depth,
+                           const int16_t *d_rect, const int32_t *d_touched, long long capacity,
+                           uint32_t *d_vals, uint32_t *d_tile_ranges, uint64_t *d_keys,
+                           long long *d_n_instances, void *d_workspace, size_t workspace_bytes,
+                           int *d_err_word, gs_stream_t stream) {
+    TileBatch tb;
+    if (make_tile_batch(cams, n_views, &tb) != GS_OK) return GS_ERR_ARG;
+    if (N < 0 || capacity < 0 || capacity > 0xF0000000ll) return GS_ERR_ARG;
+    if (!d_depth || !d_rect || !d_touched || !d_vals || !d_tile_ranges || !d_n_instances ||
+        !d_workspace)
+        return GS_ERR_ARG;
+    if (!aligned(d_workspace, 256) || !aligned(d_rect, 8) || !aligned(d_tile_ranges, 8))
+        return GS_ERR_ARG;
+    const long long VN = (long long)n_views * N;
+    Plan p = make_plan(VN, capacity);
+    if (workspace_bytes < p.bytes) return GS_ERR_CAPACITY;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(d_workspace);
+    uint32_t *dk0 = (uint32_t *)(ws + p.dk0), *dk1 = (uint32_t *)(ws + p.dk1);
+    uint32_t *dv0 = (uint32_t *)(ws + p.dv0), *dv1 = (uint32_t *)(ws + p.dv1);
+    uint32_t *cnt = (uint32_t *)(ws + p.cnt);
+    unsigned long long *offs = (unsigned long long *)(ws + p.offs);
+    uint32_t *tk0 = (uint32_t *)(ws + p.tk0), *tk1 = (uint32_t *)(ws + p.tk1);
+    uint32_t *tvs = (uint32_t *)(ws + p.tvs);
+    uint32_t *hist = (uint32_t *)(ws + p.hist);
+    void *part = (void *)(ws + p.part);
+    unsigned long long *total = (unsigned long long *)(ws + p.misc);
+    uint32_t *count = (uint32_t *)(ws + p.misc + 8);
+
+    cudaMemsetAsync(d_tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)tb.total_tiles, st);
+    if (VN == 0) {
+        cudaMemsetAsync(d_n_instances, 0, sizeof(long long), st);
+        return launch_status();
+    }
+    // 1. depth order of the records (stable, 4 x 8 bits)
+    { k_depth_keys<<<cdiv(VN, 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0); count_launches(1); }
+    uint32_t *ka = dk0, *kb = dk1, *va = dv0, *vb = dv1;
+    for (int pass = 0; pass < 4; ++pass) {
+        radix_pass(ka, va, kb, vb, nullptr, (uint32_t)VN, VN, 8 * pass, 8, true, hist, (uint32_t *)part, st);
+        uint32_t *t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+    }
+    const uint32_t *order = va;
+    // 2. offsets of each record's instances in depth order
+    { k_gather_counts<<<cdiv(VN, 256), 256, 0, st>>>(order, d_touched, VN, cnt); count_launches(1); }
+    exclusive_scan<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, total, st);
+    { k_finish_count<<<1, 1, 0, st>>>(total, capacity, d_n_instances, count, d_err_word); count_launches(1); }
+    if (capacity == 0) return launch_status();
+    // 3. emission in depth order; 4. stable sort by tile id
+    int bits = 1;
+    while ((1ll << bits) < tb.total_tiles) ++bits;
+    int passes = (bits + 7) / 8;
+    uint32_t *K[2] = {tk0, tk1};
+    uint32_t *V[2];
+    V[passes % 2] = d_vals;
+    V[(passes + 1) % 2] = tvs;
+    { k_emit<<<cdiv(VN, 256), 256, 0, st>>>(tb, N, VN, order, offs, reinterpret_cast<const short4 *>(d_rect),
+                                         d_touched, capacity, K[0], V[0]); count_launches(1); }
+    int done = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        int b = (bits - done + (passes - pass) - 1) / (passes - pass);
+        radix_pass(K[pass % 2], V[pass % 2], K[(pass + 1) % 2], V[(pass + 1) % 2], count, 0, capacity,
+                   done, b, true, hist, (uint32_t *)part, st);
+        done += b;
+    }
+    const uint32_t *tkeys = K[passes % 2];
+    { k_tile_ranges<<<cdiv(capacity, 256), 256, 0, st>>>(tkeys, count, reinterpret_cast<uint2 *>(d_tile_ranges)); count_launches(1); }
+    if (d_keys)
+        { k_keys64<<<cdiv(capacity, 256), 256, 0, st>>>(tkeys, d_vals, d_depth, count,
+                                                     reinterpret_cast<unsigned long long *>(d_keys)); count_launches(1); }
+    return launch_status();
+}

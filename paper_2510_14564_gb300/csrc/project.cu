@@ -1,0 +1,562 @@
+// project.cu -- a1 projection + SH colour, a6 projection backward (sm_103a).
+//
+// Sec. II-A: Sigma = R S S^T R^T is carried to the image plane as
+// Sigma' = J W Sigma W^T J^T (+0.3 I dilation), the splat's conic is its
+// inverse, opacity is sigmoid(logit) and colour is the degree-3 real SH
+// expansion evaluated in the direction from the camera centre to the mean.
+//
+// The depth, screen mean, Sigma', radius and tile rectangle are the discrete
+// path: computed with IEEE-rounded intrinsics in a fixed order (no FMA
+// contraction), so that an independent IEEE implementation written to the
+// same order reproduces tile keys and counts bit for bit.
+#include "gs_common.cuh"
+
+namespace gs {
+
+// ---------------------------------------------------------------------------
+// FP32 arithmetic of the discrete path (no contraction)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float m_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float a_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float s_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float d_(float a, float b) { return __fdiv_rn(a, b); }
+
+// e^x for the discrete path: Cody-Waite reduction x = k ln2 + r with ln2
+// split into a 15-bit head and a tail, the degree-7 Taylor polynomial of e^r
+// in Horner form, and an exact scaling by 2^k built from its exponent bits.
+__device__ __forceinline__ float exp_spec(float x) {
+    x = fminf(fmaxf(x, -87.0f), 88.0f);
+    float k = rintf(m_(x, 1.44269504089f));
+    float r = s_(s_(x, m_(k, 0.693145751953125f)), m_(k, 1.428606820309417e-06f));
+    float p = 1.0f / 5040.0f;
+    p = a_(m_(p, r), 1.0f / 720.0f);
+    p = a_(m_(p, r), 1.0f / 120.0f);
+    p = a_(m_(p, r), 1.0f / 24.0f);
+    p = a_(m_(p, r), 1.0f / 6.0f);
+    p = a_(m_(p, r), 0.5f);
+    p = a_(m_(p, r), 1.0f);
+    p = a_(m_(p, r), 1.0f);
+    int ki = (int)k;
+    return m_(p, __int_as_float((ki + 127) << 23));
+}
+
+// Real orthonormal SH to degree 3 at a unit vector (x, y, z); index l*l+l+m.
+// Constants: N_lm = sqrt((2l+1)/(4pi) (l-|m|)!/(l+|m|)!), times sqrt2 for
+// m != 0, folded with the polynomial's integer factors.
+#define SH_C0 0.28209479177387814f   // 1/(2 sqrt(pi))
+#define SH_C1 0.48860251190291992f   // sqrt(3/(4 pi))
+#define SH_C2A 1.0925484305920792f   // sqrt(15/pi)/2
+#define SH_C2B 0.31539156525252005f  // sqrt(5/pi)/4
+#define SH_C2C 0.54627421529603959f  // sqrt(15/pi)/4
+#define SH_C3A 0.59004358992664352f  // sqrt(35/(2 pi))/4
+#define SH_C3B 2.8906114426405538f   // sqrt(105/pi)/2
+#define SH_C3C 0.45704579946446572f  // sqrt(21/(2 pi))/4
+#define SH_C3D 0.3731763325901154f   // sqrt(7/pi)/4
+#define SH_C3E 1.4453057213202769f   // sqrt(105/pi)/4
+
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16]) {
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = SH_C0;
+    Y[1] = SH_C1 * y;
+    Y[2] = SH_C1 * z;
+    Y[3] = SH_C1 * x;
+    Y[4] = SH_C2A * x * y;
+    Y[5] = SH_C2A * y * z;
+    Y[6] = SH_C2B * (3.0f * zz - 1.0f);
+    Y[7] = SH_C2A * x * z;
+    Y[8] = SH_C2C * (xx - yy);
+    Y[9] = SH_C3A * y * (3.0f * xx - yy);
+    Y[10] = SH_C3B * x * y * z;
+    Y[11] = SH_C3C * y * (5.0f * zz - 1.0f);
+    Y[12] = SH_C3D * z * (5.0f * zz - 3.0f);
+    Y[13] = SH_C3C * x * (5.0f * zz - 1.0f);
+    Y[14] = SH_C3E * (xx - yy) * z;
+    Y[15] = SH_C3A * x * (xx - 3.0f * yy);
+}
+
+// Gradient of each polynomial above in (x, y, z) (off the sphere too).
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float G[16][3]) {
+    float xx = x * x, yy = y * y, zz = z * z;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) G[j][0] = G[j][1] = G[j][2] = 0.0f;
+    G[1][1] = SH_C1;
+    G[2][2] = SH_C1;
+    G[3][0] = SH_C1;
+    G[4][0] = SH_C2A * y; G[4][1] = SH_C2A * x;
+    G[5][1] = SH_C2A * z; G[5][2] = SH_C2A * y;
+    G[6][2] = SH_C2B * 6.0f * z;
+    G[7][0] = SH_C2A * z; G[7][2] = SH_C2A * x;
+    G[8][0] = SH_C2C * 2.0f * x; G[8][1] = -SH_C2C * 2.0f * y;
+    G[9][0] = SH_C3A * 6.0f * x * y; G[9][1] = SH_C3A * 3.0f * (xx - yy);
+    G[10][0] = SH_C3B * y * z; G[10][1] = SH_C3B * x * z; G[10][2] = SH_C3B * x * y;
+    G[11][1] = SH_C3C * (5.0f * zz - 1.0f); G[11][2] = SH_C3C * 10.0f * y * z;
+    G[12][2] = SH_C3D * (15.0f * zz - 3.0f);
+    G[13][0] = SH_C3C * (5.0f * zz - 1.0f); G[13][2] = SH_C3C * 10.0f * x * z;
+    G[14][0] = SH_C3E * 2.0f * x * z; G[14][1] = -SH_C3E * 2.0f * y * z; G[14][2] = SH_C3E * (xx - yy);
+    G[15][0] = SH_C3A * 3.0f * (xx - yy); G[15][1] = -SH_C3A * 6.0f * x * y;
+}
+
+// SH coefficients of one Gaussian as FP32 [16][3].
+template <int SDT>
+__device__ __forceinline__ void load_sh(const void *sh, long long i, float k[48]) {
+    if (SDT == GS_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(sh) + i * 12;
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+            float4 v = __ldg(p + j);
+            k[4 * j] = v.x; k[4 * j + 1] = v.y; k[4 * j + 2] = v.z; k[4 * j + 3] = v.w;
+        }
+    } else {
+        const uint4 *p = reinterpret_cast<const uint4 *>(sh) + i * 6;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            uint4 v = __ldg(p + j);
+            float2 a = unpack2(v.x, SDT), b = unpack2(v.y, SDT), c = unpack2(v.z, SDT),
+                   d = unpack2(v.w, SDT);
+            k[8 * j] = a.x; k[8 * j + 1] = a.y; k[8 * j + 2] = b.x; k[8 * j + 3] = b.y;
+            k[8 * j + 4] = c.x; k[8 * j + 5] = c.y; k[8 * j + 6] = d.x; k[8 * j + 7] = d.y;
+        }
+    }
+}
+
+struct Discrete {
+    float x, y, z, u, v, ca, cb, cc;
+    float Rq[9], s[3];
+    bool visible;
+    int rad, x0, y0, x1, y1;
+};
+
+// The discrete path (see file header).  Returns visibility.
+__device__ __forceinline__ void discrete_path(const ViewGeom &cam, float mx, float my, float mz,
+                                              const float ls[3], const float q[4], Discrete &o) {
+    const float *R = cam.R;
+    o.visible = false;
+    o.rad = o.x0 = o.y0 = o.x1 = o.y1 = 0;
+    o.ca = o.cb = o.cc = 0.0f;
+    o.x = a_(a_(a_(m_(R[0], mx), m_(R[1], my)), m_(R[2], mz)), cam.t[0]);
+    o.y = a_(a_(a_(m_(R[3], mx), m_(R[4], my)), m_(R[5], mz)), cam.t[1]);
+    o.z = a_(a_(a_(m_(R[6], mx), m_(R[7], my)), m_(R[8], mz)), cam.t[2]);
+    const float x = o.x, y = o.y, z = o.z;
+    o.u = o.v = 0.0f;
+    if (!(z > cam.znear)) return;
+    o.u = a_(d_(m_(cam.fx, x), z), cam.cx);
+    o.v = a_(d_(m_(cam.fy, y), z), cam.cy);
+    float qq = a_(a_(a_(m_(q[0], q[0]), m_(q[1], q[1])), m_(q[2], q[2])), m_(q[3], q[3]));
+    if (!(qq > 0.0f)) return;
+    float qn = __fsqrt_rn(qq);
+    float w = d_(q[0], qn), qa = d_(q[1], qn), qb = d_(q[2], qn), qc = d_(q[3], qn);
+    float *Rq = o.Rq;
+    Rq[0] = s_(1.0f, m_(2.0f, a_(m_(qb, qb), m_(qc, qc))));
+    Rq[1] = m_(2.0f, s_(m_(qa, qb), m_(w, qc)));
+    Rq[2] = m_(2.0f, a_(m_(qa, qc), m_(w, qb)));
+    Rq[3] = m_(2.0f, a_(m_(qa, qb), m_(w, qc)));
+    Rq[4] = s_(1.0f, m_(2.0f, a_(m_(qa, qa), m_(qc, qc))));
+    Rq[5] = m_(2.0f, s_(m_(qb, qc), m_(w, qa)));
+    Rq[6] = m_(2.0f, s_(m_(qa, qc), m_(w, qb)));
+    Rq[7] = m_(2.0f, a_(m_(qb, qc), m_(w, qa)));
+    Rq[8] = s_(1.0f, m_(2.0f, a_(m_(qa, qa), m_(qb, qb))));
+    o.s[0] = exp_spec(ls[0]);
+    o.s[1] = exp_spec(ls[1]);
+    o.s[2] = exp_spec(ls[2]);
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) M[3 * r + k] = m_(Rq[3 * r + k], o.s[k]);
+    float S[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            S[3 * r + c] = a_(a_(m_(M[3 * r], M[3 * c]), m_(M[3 * r + 1], M[3 * c + 1])),
+                              m_(M[3 * r + 2], M[3 * c + 2]));
+    float zz = m_(z, z);
+    float j00 = d_(cam.fx, z), j11 = d_(cam.fy, z);
+    float j02 = -d_(m_(cam.fx, x), zz);
+    float j12 = -d_(m_(cam.fy, y), zz);
+    float T[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T[k] = a_(m_(j00, R[k]), m_(j02, R[6 + k]));
+        T[3 + k] = a_(m_(j11, R[3 + k]), m_(j12, R[6 + k]));
+    }
+    float U[6];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            U[3 * r + k] = a_(a_(m_(T[3 * r], S[k]), m_(T[3 * r + 1], S[3 + k])),
+                              m_(T[3 * r + 2], S[6 + k]));
+    float ca = a_(a_(a_(m_(U[0], T[0]), m_(U[1], T[1])), m_(U[2], T[2])), 0.3f);
+    float cb = a_(a_(m_(U[0], T[3]), m_(U[1], T[4])), m_(U[2], T[5]));
+    float cc = a_(a_(a_(m_(U[3], T[3]), m_(U[4], T[4])), m_(U[5], T[5])), 0.3f);
+    o.ca = ca; o.cb = cb; o.cc = cc;
+    float det = s_(m_(ca, cc), m_(cb, cb));
+    if (!(det > 0.0f)) return;
+    float mid = m_(0.5f, a_(ca, cc));
+    float lam = a_(mid, __fsqrt_rn(fmaxf(0.0f, s_(m_(mid, mid), det))));
+    float rad = ceilf(m_(3.0f, __fsqrt_rn(lam)));
+    const float TX = (float)cam.TX, TY = (float)cam.TY;
+    int x0 = (int)fminf(fmaxf(floorf(d_(s_(o.u, rad), 16.0f)), 0.0f), TX);
+    int x1 = (int)fminf(fmaxf(floorf(d_(a_(a_(o.u, rad), 15.0f), 16.0f)), 0.0f), TX);
+    int y0 = (int)fminf(fmaxf(floorf(d_(s_(o.v, rad), 16.0f)), 0.0f), TY);
+    int y1 = (int)fminf(fmaxf(floorf(d_(a_(a_(o.v, rad), 15.0f), 16.0f)), 0.0f), TY);
+    if ((x1 - x0) * (y1 - y0) <= 0) return;
+    o.rad = (int)rad;
+    o.x0 = x0; o.y0 = y0; o.x1 = x1; o.y1 = y1;
+    o.visible = true;
+}
+
+__device__ __forceinline__ bool finite_params(float mx, float my, float mz, const float ls[3],
+                                              const float q[4]) {
+    bool f = isfinite(mx) && isfinite(my) && isfinite(mz);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f = f && isfinite(ls[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f = f && isfinite(q[k]);
+    return f;
+}
+
+template <int SDT, int RDT>
+__global__ void __launch_bounds__(128) k_project(GeomBatch views, int N, const float *__restrict__ means,
+                                                 const float *__restrict__ log_scales,
+                                                 const float *__restrict__ quats,
+                                                 const float *__restrict__ logits,
+                                                 const void *__restrict__ sh, void *__restrict__ splats,
+                                                 float *__restrict__ depth, short4 *__restrict__ rect,
+                                                 int *__restrict__ touched, int *__restrict__ radius,
+                                                 int *err_word) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (long long)views.n * N) return;
+    int vi = (int)(r / N);
+    long long i = r - (long long)vi * N;
+    const ViewGeom &cam = views.v[vi];
+    float mx = __ldg(means + 3 * i), my = __ldg(means + 3 * i + 1), mz = __ldg(means + 3 * i + 2);
+    float ls[3] = {__ldg(log_scales + 3 * i), __ldg(log_scales + 3 * i + 1), __ldg(log_scales + 3 * i + 2)};
+    float4 q4 = __ldg(reinterpret_cast<const float4 *>(quats) + i);
+    float q[4] = {q4.x, q4.y, q4.z, q4.w};
+    Discrete d;
+    bool fin = finite_params(mx, my, mz, ls, q);
+    if (fin) {
+        discrete_path(cam, mx, my, mz, ls, q, d);
+    } else {
+        d.visible = false;
+        d.z = 0.0f;
+        d.rad = d.x0 = d.y0 = d.x1 = d.y1 = 0;
+        if (vi == 0) set_err(err_word, GS_EW_NONFINITE);
+    }
+    depth[r] = d.z;
+    rect[r] = make_short4((short)d.x0, (short)d.y0, (short)d.x1, (short)d.y1);
+    touched[r] = d.visible ? (d.x1 - d.x0) * (d.y1 - d.y0) : 0;
+    if (radius) radius[r] = d.rad;
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0;
+    if (d.visible) {
+        float det = d.ca * d.cc - d.cb * d.cb;
+        float A = d.cc / det, B = -d.cb / det, C = d.ca / det;
+        float lg = __ldg(logits + i);
+        float o = 1.0f / (1.0f + expf(-lg));
+        float lo = log2f(o);
+        // colour: max(0, 0.5 + sum_j Y_j(dir) k_j)
+        float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
+        float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float Y[16];
+        sh_basis(dx * inv, dy * inv, dz * inv, Y);
+        float k[48];
+        load_sh<SDT>(sh, i, k);
+        float c[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc = fmaf(Y[j], k[3 * j + ch], acc);
+            c[ch] = fmaxf(acc, 0.0f);
+        }
+        g0 = make_float4(d.u, d.v, -0.5f * kLog2e * A, -kLog2e * B);
+        if (RDT == GS_F32) {
+            g1 = make_float4(-0.5f * kLog2e * C, lo, c[0], c[1]);
+            g2 = make_float4(c[2], 0.f, 0.f, 0.f);
+        } else {
+            g1 = make_float4(-0.5f * kLog2e * C, lo, __uint_as_float(pack2(c[0], c[1], RDT)),
+                             __uint_as_float(pack2(c[2], 0.0f, RDT)));
+        }
+    }
+    if (RDT == GS_F32) {
+        SplatF32 *p = reinterpret_cast<SplatF32 *>(splats) + r;
+        p->g0 = g0; p->g1 = g1; p->g2 = g2;
+    } else {
+        SplatHalf *p = reinterpret_cast<SplatHalf *>(splats) + r;
+        p->g0 = g0; p->g1 = g1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a6: projection backward (reverse mode of k_project, continuous part)
+// ---------------------------------------------------------------------------
+template <int SDT>
+__global__ void __launch_bounds__(128) k_project_bwd(GeomBatch views, int N, const float *__restrict__ means,
+                                                     const float *__restrict__ log_scales,
+                                                     const float *__restrict__ quats,
+                                                     const float *__restrict__ logits,
+                                                     const void *__restrict__ sh,
+                                                     const int *__restrict__ touched,
+                                                     const float *__restrict__ grad2d,
+                                                     float *__restrict__ dparams) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float mx = __ldg(means + 3 * i), my = __ldg(means + 3 * i + 1), mz = __ldg(means + 3 * i + 2);
+    float ls[3] = {__ldg(log_scales + 3 * i), __ldg(log_scales + 3 * i + 1), __ldg(log_scales + 3 * i + 2)};
+    float4 q4 = __ldg(reinterpret_cast<const float4 *>(quats) + i);
+    float q[4] = {q4.x, q4.y, q4.z, q4.w};
+    float lg = __ldg(logits + i);
+    float dmean[3] = {0, 0, 0}, dls[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dlog = 0.0f;
+    float dsh[48];
+#pragma unroll
+    for (int j = 0; j < 48; ++j) dsh[j] = 0.0f;
+    bool any = false;
+    float k[48];
+    for (int vi = 0; vi < views.n; ++vi) {
+        long long r = (long long)vi * N + i;
+        if (__ldg(touched + r) <= 0) continue;
+        const float4 *gp = reinterpret_cast<const float4 *>(grad2d + 12 * r);
+        float4 ga = __ldg(gp), gb = __ldg(gp + 1), gc = __ldg(gp + 2);
+        float g[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
+        if (!any) { load_sh<SDT>(sh, i, k); any = true; }
+        const ViewGeom &cam = views.v[vi];
+        const float *R = cam.R;
+        const float fx = cam.fx, fy = cam.fy;
+        // forward quantities (same values as k_project)
+        Discrete d;
+        discrete_path(cam, mx, my, mz, ls, q, d);
+        const float x = d.x, y = d.y, z = d.z;
+        float M[9], Sg[9];
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) M[3 * rr + kk] = d.Rq[3 * rr + kk] * d.s[kk];
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc)
+                Sg[3 * rr + cc] = M[3 * rr] * M[3 * cc] + M[3 * rr + 1] * M[3 * cc + 1] + M[3 * rr + 2] * M[3 * cc + 2];
+        float iz = 1.0f / z, iz2 = iz * iz;
+        float J[6] = {fx * iz, 0.0f, -fx * x * iz2, 0.0f, fy * iz, -fy * y * iz2};
+        float T[6];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk)
+                T[3 * rr + kk] = J[3 * rr] * R[kk] + J[3 * rr + 1] * R[3 + kk] + J[3 * rr + 2] * R[6 + kk];
+        const float a = d.ca, b = d.cb, c = d.cc;
+        float D = a * c - b * b, iD = 1.0f / D, iD2 = iD * iD;
+        // conic (A, B, C) = (c, -b, a) / D
+        float gA = g[2], gB = g[3], gC = g[4];
+        float ga_ = gA * (-c * c * iD2) + gB * (b * c * iD2) + gC * (iD - a * c * iD2);
+        float gb_ = gA * (2.0f * b * c * iD2) + gB * (-iD - 2.0f * b * b * iD2) + gC * (2.0f * a * b * iD2);
+        float gc_ = gA * (iD - a * c * iD2) + gB * (a * b * iD2) + gC * (-a * a * iD2);
+        float G2[4] = {ga_, 0.5f * gb_, 0.5f * gb_, gc_};
+        float TS[6];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk)
+                TS[3 * rr + kk] = T[3 * rr] * Sg[kk] + T[3 * rr + 1] * Sg[3 + kk] + T[3 * rr + 2] * Sg[6 + kk];
+        float dT[6];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk)
+                dT[3 * rr + kk] = 2.0f * (G2[2 * rr] * TS[kk] + G2[2 * rr + 1] * TS[3 + kk]);
+        float dS[9];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                float t0 = G2[0] * T[kk] + G2[1] * T[3 + kk];
+                float t1 = G2[2] * T[kk] + G2[3] * T[3 + kk];
+                dS[3 * j + kk] = T[j] * t0 + T[3 + j] * t1;
+            }
+        float dJ[6];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                dJ[3 * rr + j] = dT[3 * rr] * R[3 * j] + dT[3 * rr + 1] * R[3 * j + 1] + dT[3 * rr + 2] * R[3 * j + 2];
+        float dp0 = dJ[2] * (-fx * iz2) + g[0] * fx * iz;
+        float dp1 = dJ[5] * (-fy * iz2) + g[1] * fy * iz;
+        float dp2 = dJ[0] * (-fx * iz2) + dJ[2] * (2.0f * fx * x * iz2 * iz) + dJ[4] * (-fy * iz2) +
+                    dJ[5] * (2.0f * fy * y * iz2 * iz) - g[0] * fx * x * iz2 - g[1] * fy * y * iz2;
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) dmean[kk] += R[kk] * dp0 + R[3 + kk] * dp1 + R[6 + kk] * dp2;
+        // Sigma = M M^T, M = Rq diag(s)
+        float dM[9];
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk)
+                dM[3 * rr + kk] = 2.0f * (dS[3 * rr] * M[kk] + dS[3 * rr + 1] * M[3 + kk] + dS[3 * rr + 2] * M[6 + kk]);
+        float G[9];
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+            float ds = 0.0f;
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr) {
+                ds += dM[3 * rr + kk] * d.Rq[3 * rr + kk];
+                G[3 * rr + kk] = dM[3 * rr + kk] * d.s[kk];
+            }
+            dls[kk] += ds * d.s[kk];
+        }
+        // rotation from the unit quaternion
+        float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        float iq = 1.0f / qn;
+        float w = q[0] * iq, qx = q[1] * iq, qy = q[2] * iq, qz = q[3] * iq;
+        float dqh[4];
+        dqh[0] = 2.0f * (-qz * G[1] + qy * G[2] + qz * G[3] - qx * G[5] - qy * G[6] + qx * G[7]);
+        dqh[1] = 2.0f * (qy * G[1] + qz * G[2] + qy * G[3] - 2.0f * qx * G[4] - w * G[5] + qz * G[6] + w * G[7] - 2.0f * qx * G[8]);
+        dqh[2] = 2.0f * (-2.0f * qy * G[0] + qx * G[1] + w * G[2] + qx * G[3] + qz * G[5] - w * G[6] + qz * G[7] - 2.0f * qy * G[8]);
+        dqh[3] = 2.0f * (-2.0f * qz * G[0] - w * G[1] + qx * G[2] + w * G[3] - 2.0f * qz * G[4] + qy * G[5] + qx * G[6] + qy * G[7]);
+        float dot = dqh[0] * w + dqh[1] * qx + dqh[2] * qy + dqh[3] * qz;
+        dq[0] += (dqh[0] - w * dot) * iq;
+        dq[1] += (dqh[1] - qx * dot) * iq;
+        dq[2] += (dqh[2] - qy * dot) * iq;
+        dq[3] += (dqh[3] - qz * dot) * iq;
+        // opacity
+        float o = 1.0f / (1.0f + expf(-lg));
+        dlog += g[5] * o * (1.0f - o);
+        // colour
+        float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
+        float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+        float ux = vx * inv, uy = vy * inv, uz = vz * inv;
+        float Y[16];
+        sh_basis(ux, uy, uz, Y);
+        float GY[16][3];
+        sh_basis_grad(ux, uy, uz, GY);
+        float gd[3] = {0, 0, 0};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float pre = 0.5f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) pre = fmaf(Y[j], k[3 * j + ch], pre);
+            if (!(pre > 0.0f)) continue;
+            float gc = g[6 + ch];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                dsh[3 * j + ch] += gc * Y[j];
+                float gk = gc * k[3 * j + ch];
+                gd[0] += gk * GY[j][0];
+                gd[1] += gk * GY[j][1];
+                gd[2] += gk * GY[j][2];
+            }
+        }
+        float gdd = gd[0] * ux + gd[1] * uy + gd[2] * uz;
+        dmean[0] += (gd[0] - ux * gdd) * inv;
+        dmean[1] += (gd[1] - uy * gdd) * inv;
+        dmean[2] += (gd[2] - uz * gdd) * inv;
+    }
+    const long long n = N;
+    float *pm = dparams, *pls = dparams + 3 * n, *pq = dparams + 6 * n, *plg = dparams + 10 * n,
+          *psh = dparams + 11 * n;
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) { pm[3 * i + kk] = dmean[kk]; pls[3 * i + kk] = dls[kk]; }
+    reinterpret_cast<float4 *>(pq)[i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+    plg[i] = dlog;
+    float4 *ps = reinterpret_cast<float4 *>(psh) + 12 * i;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) ps[j] = make_float4(dsh[4 * j], dsh[4 * j + 1], dsh[4 * j + 2], dsh[4 * j + 3]);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int make_geom_batch(const gs_camera *cams, int n_views, GeomBatch *out) {
+    if (!cams || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_ARG;
+    out->n = n_views;
+    for (int v = 0; v < n_views; ++v) {
+        const gs_camera &c = cams[v];
+        if (c.W <= 0 || c.H <= 0 || c.W > 32767 * GS_TILE || c.H > 32767 * GS_TILE) return GS_ERR_ARG;
+        ViewGeom &g = out->v[v];
+        g.W = c.W; g.H = c.H;
+        g.TX = (c.W + GS_TILE - 1) / GS_TILE;
+        g.TY = (c.H + GS_TILE - 1) / GS_TILE;
+        g.fx = c.fx; g.fy = c.fy; g.cx = c.cx; g.cy = c.cy;
+        for (int k = 0; k < 9; ++k) g.R[k] = c.R[k];
+        for (int k = 0; k < 3; ++k) { g.t[k] = c.t[k]; g.campos[k] = c.campos[k]; }
+        g.znear = c.znear;
+    }
+    return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+template <int SDT>
+static void launch_project(int rdt, const GeomBatch &vb, int N, const float *m, const float *ls,
+                           const float *q, const float *lg, const void *sh, void *splats,
+                           float *depth, short4 *rect, int *touched, int *radius, int *ew,
+                           cudaStream_t st) {
+    long long total = (long long)vb.n * N;
+    int grid = cdiv(total, 128);
+    if (rdt == GS_F32)
+        { k_project<SDT, GS_F32><<<grid, 128, 0, st>>>(vb, N, m, ls, q, lg, sh, splats, depth, rect, touched, radius, ew); count_launches(1); }
+    else if (rdt == GS_BF16)
+        { k_project<SDT, GS_BF16><<<grid, 128, 0, st>>>(vb, N, m, ls, q, lg, sh, splats, depth, rect, touched, radius, ew); count_launches(1); }
+    else
+        { k_project<SDT, GS_F16><<<grid, 128, 0, st>>>(vb, N, m, ls, q, lg, sh, splats, depth, rect, touched, radius, ew); count_launches(1); }
+}
+
+extern "C" int gs_project(const gs_camera *cams, int n_views, int N, const float *d_means,
+                          const float *d_log_scales, const float *d_quats,
+                          const float *d_opacity_logits, const void *d_sh, int sh_dtype,
+                          void *d_splats, int rgb_dtype, float *d_depth, int16_t *d_rect,
+                          int32_t *d_touched, int32_t *d_radius, int *d_err_word,
+                          gs_stream_t stream) {
+    GeomBatch vb;
+    if (make_geom_batch(cams, n_views, &vb) != GS_OK) return GS_ERR_ARG;
+    if (N < 0) return GS_ERR_ARG;
+    if (N == 0) return GS_OK;
+    if (!d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_sh || !d_splats ||
+        !d_depth || !d_rect || !d_touched)
+        return GS_ERR_ARG;
+    if (sh_dtype < GS_F32 || sh_dtype > GS_F16 || rgb_dtype < GS_F32 || rgb_dtype > GS_F16) return GS_ERR_ARG;
+    if (!aligned(d_quats, 16) || !aligned(d_sh, 16) || !aligned(d_splats, 16) || !aligned(d_rect, 8))
+        return GS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    short4 *rect = reinterpret_cast<short4 *>(d_rect);
+    if (sh_dtype == GS_F32)
+        launch_project<GS_F32>(rgb_dtype, vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_splats, d_depth, rect, d_touched, d_radius, d_err_word, st);
+    else if (sh_dtype == GS_BF16)
+        launch_project<GS_BF16>(rgb_dtype, vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_splats, d_depth, rect, d_touched, d_radius, d_err_word, st);
+    else
+        launch_project<GS_F16>(rgb_dtype, vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_splats, d_depth, rect, d_touched, d_radius, d_err_word, st);
+    return launch_status();
+}
+
+extern "C" int gs_project_bwd(const gs_camera *cams, int n_views, int N, const float *d_means,
+                              const float *d_log_scales, const float *d_quats,
+                              const float *d_opacity_logits, const void *d_sh, int sh_dtype,
+                              const int32_t *d_touched, const float *d_grad2d, float *d_dparams,
+                              gs_stream_t stream) {
+    GeomBatch vb;
+    if (make_geom_batch(cams, n_views, &vb) != GS_OK) return GS_ERR_ARG;
+    if (N < 0) return GS_ERR_ARG;
+    if (N == 0) return GS_OK;
+    if (!d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_sh || !d_touched ||
+        !d_grad2d || !d_dparams)
+        return GS_ERR_ARG;
+    // the grouped gradient layout keeps the quaternion and SH groups 16-byte
+    // aligned only when N is a multiple of 4
+    if (N % 4 != 0) return GS_ERR_ARG;
+    if (!aligned(d_quats, 16) || !aligned(d_sh, 16) || !aligned(d_grad2d, 16) || !aligned(d_dparams, 16))
+        return GS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int grid = cdiv(N, 128);
+    if (sh_dtype == GS_F32)
+        { k_project_bwd<GS_F32><<<grid, 128, 0, st>>>(vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams); count_launches(1); }
+    else if (sh_dtype == GS_BF16)
+        { k_project_bwd<GS_BF16><<<grid, 128, 0, st>>>(vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams); count_launches(1); }
+    else if (sh_dtype == GS_F16)
+        { k_project_bwd<GS_F16><<<grid, 128, 0, st>>>(vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams); count_launches(1); }
+    else
+        return GS_ERR_ARG;
+    return launch_status();
+}

@@ -1,0 +1,305 @@
+// sched.cu -- a8 the learned tile-cost scheduler (sm_103a).
+//
+// The paper balances rendering work by a density metric rho = active
+// Gaussians / pixels per region (Sec. IV-C2).  Here that balance is a work
+// order: a small MLP (8 tile features -> 32 ReLU -> 1, FP16 weights, FP32
+// accumulation) predicts the log of each tile's render time, and persistent
+// render CTAs take tiles longest-predicted first from an atomic queue.  The
+// network is trained on the per-tile times the renderer measures.  Only the
+// order changes, never the arithmetic of a tile, so images do not depend on
+// the schedule.
+#include "gs_common.cuh"
+
+namespace gs {
+
+constexpr int kMlpH = 32;
+constexpr int kMlpF = 8;
+constexpr int kMlpW = kMlpH * kMlpF + kMlpH + kMlpH + 1;   // 321
+
+// Eight features per tile, one warp per tile, over the first `cap` entries
+// of its list:
+//   f0 log1p(count)                 f1 mean opacity     f2 max opacity
+//   f3 mean coverage, cov = min(1, pi sqrt(det Sigma') / 256)
+//   f4 log1p(sum o cov)             f5 log1p(sum of the expected
+//   transmittance Th_j while Th_j >= 1e-4; Th_{j+1} = Th_j (1 - min(0.99, o_j cov_j)))
+//   f6 in-image pixel fraction      f7 log1p(W H) / 16
+template <int DT>
+__global__ void __launch_bounds__(256) k_tile_features(TileBatch tb, const uint2 *__restrict__ ranges,
+                                                       const uint32_t *__restrict__ vals,
+                                                       const void *__restrict__ splats, int cap,
+                                                       float *__restrict__ feats) {
+    const int tile = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int l = threadIdx.x & 31;
+    if (tile >= tb.total_tiles) return;
+    const uint2 rg = __ldg(ranges + tile);
+    const int cnt = (int)(rg.y - rg.x);
+    const int K = cnt < cap ? cnt : cap;
+    float so = 0.f, mo = 0.f, sc = 0.f, soc = 0.f, sth = 0.f, Th = 1.0f;
+    for (int j0 = 0; j0 < K; j0 += 32) {
+        const int j = j0 + l;
+        float o = 0.f, cov = 0.f, fac = 1.0f;
+        if (j < K) {
+            Splat s = load_splat<DT>(splats, __ldg(vals + rg.x + j));
+            o = exp2f(s.lo);
+            float A = -2.0f * kLn2 * s.Ap, B = -kLn2 * s.Bp, C = -2.0f * kLn2 * s.Cp;
+            float dc = A * C - B * B;
+            cov = dc > 0.f ? fminf(1.0f, 3.14159265358979f * rsqrtf(dc) / 256.0f) : 1.0f;
+            so += o;
+            mo = fmaxf(mo, o);
+            sc += cov;
+            soc += o * cov;
+            fac = 1.0f - fminf(0.99f, o * cov);
+        }
+        if (Th >= kTMin) {
+            // inclusive prefix product of the factors across the warp
+            float inc = fac;
+#pragma unroll
+            for (int s = 1; s < 32; s <<= 1) {
+                float t = __shfl_up_sync(0xffffffffu, inc, s);
+                if (l >= s) inc *= t;
+            }
+            float exc = __shfl_up_sync(0xffffffffu, inc, 1);
+            if (l == 0) exc = 1.0f;
+            float th = Th * exc;                  // Th in front of entry j
+            sth += (j < K && th >= kTMin) ? th : 0.0f;
+            Th *= __shfl_sync(0xffffffffu, inc, 31);
+        }
+    }
+    so = warp_sum(so); sc = warp_sum(sc); soc = warp_sum(soc); sth = warp_sum(sth);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mo = fmaxf(mo, __shfl_xor_sync(0xffffffffu, mo, o));
+    if (l == 0) {
+        const int v = view_of_tile(tb, tile);
+        const ViewTiles &vt = tb.v[v];
+        const int lt = tile - vt.tile_base, tx = lt % vt.TX, ty = lt / vt.TX;
+        const int inx = min(kTile, vt.W - tx * kTile), iny = min(kTile, vt.H - ty * kTile);
+        float *f = feats + 8ll * tile;
+        f[0] = log1pf((float)cnt);
+        f[1] = K > 0 ? so / K : 0.f;
+        f[2] = mo;
+        f[3] = K > 0 ? sc / K : 0.f;
+        f[4] = log1pf(soc);
+        f[5] = log1pf(sth);
+        f[6] = (float)(inx * iny) / (float)kTilePix;
+        f[7] = log1pf((float)vt.W * (float)vt.H) / 16.0f;
+    }
+}
+
+// y = W2 relu(W1 f + b1) + b2 with FP16 weights, FP32 accumulation.
+__global__ void __launch_bounds__(256) k_mlp_predict(const __half *__restrict__ w16,
+                                                     const float *__restrict__ feats, int n,
+                                                     float *__restrict__ y) {
+    __shared__ float s_w[kMlpW];
+    for (int k = threadIdx.x; k < kMlpW; k += blockDim.x) s_w[k] = __half2float(w16[k]);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float f[kMlpF];
+#pragma unroll
+    for (int k = 0; k < kMlpF; ++k) f[k] = __ldg(feats + 8ll * i + k);
+    const float *W1 = s_w, *b1 = s_w + 256, *W2 = s_w + 288;
+    float acc = s_w[320];
+#pragma unroll 8
+    for (int h = 0; h < kMlpH; ++h) {
+        float z = b1[h];
+#pragma unroll
+        for (int k = 0; k < kMlpF; ++k) z = fmaf(W1[8 * h + k], f[k], z);
+        acc = fmaf(W2[h], fmaxf(z, 0.f), acc);
+    }
+    y[i] = acc;
+}
+
+// Gradient of the mean squared error of the MLP (FP32 weights) against
+// log(tile ns) targets; one CTA reduces 256 rows, then one atomic per weight.
+__global__ void __launch_bounds__(256) k_mlp_grad(const float *__restrict__ w32,
+                                                  const float *__restrict__ feats,
+                                                  const unsigned long long *__restrict__ tile_ns,
+                                                  const float *__restrict__ target, int n, float inv_n,
+                                                  float *__restrict__ grad, float *__restrict__ loss) {
+    __shared__ float s_w[kMlpW];
+    __shared__ float s_f[256][kMlpF + 1];
+    __shared__ float s_dz[256][kMlpH + 1];
+    __shared__ float s_h[256][kMlpH + 1];
+    __shared__ float s_dy[256];
+    for (int k = threadIdx.x; k < kMlpW; k += blockDim.x) s_w[k] = w32[k];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = threadIdx.x;
+    const float *W1 = s_w, *b1 = s_w + 256, *W2 = s_w + 288;
+    float e2 = 0.f;
+    if (i < n) {
+        float f[kMlpF];
+#pragma unroll
+        for (int k = 0; k < kMlpF; ++k) { f[k] = __ldg(feats + 8ll * i + k); s_f[r][k] = f[k]; }
+        float y = s_w[320];
+        float z[kMlpH];
+#pragma unroll
+        for (int h = 0; h < kMlpH; ++h) {
+            float a = b1[h];
+#pragma unroll
+            for (int k = 0; k < kMlpF; ++k) a = fmaf(W1[8 * h + k], f[k], a);
+            z[h] = a;
+            float hh = fmaxf(a, 0.f);
+            s_h[r][h] = hh;
+            y = fmaf(W2[h], hh, y);
+        }
+        float t = target ? __ldg(target + i) : logf(fmaxf((float)__ldg(tile_ns + i), 1.0f));
+        float e = y - t;
+        e2 = e * e;
+        float dy = 2.0f * e * inv_n;
+        s_dy[r] = dy;
+#pragma unroll
+        for (int h = 0; h < kMlpH; ++h) s_dz[r][h] = z[h] > 0.f ? dy * W2[h] : 0.f;
+    } else {
+        s_dy[r] = 0.f;
+#pragma unroll
+        for (int k = 0; k < kMlpF; ++k) s_f[r][k] = 0.f;
+#pragma unroll
+        for (int h = 0; h < kMlpH; ++h) { s_dz[r][h] = 0.f; s_h[r][h] = 0.f; }
+    }
+    __syncthreads();
+    // thread t: gW1[t / 8][t % 8]
+    {
+        const int h = threadIdx.x >> 3, k = threadIdx.x & 7;
+        float acc = 0.f;
+        for (int rr = 0; rr < 256; ++rr) acc = fmaf(s_dz[rr][h], s_f[rr][k], acc);
+        atomicAdd(grad + threadIdx.x, acc);
+    }
+    if (threadIdx.x < kMlpH) {
+        const int h = threadIdx.x;
+        float gb = 0.f, gw = 0.f;
+        for (int rr = 0; rr < 256; ++rr) { gb += s_dz[rr][h]; gw = fmaf(s_dy[rr], s_h[rr][h], gw); }
+        atomicAdd(grad + 256 + h, gb);
+        atomicAdd(grad + 288 + h, gw);
+    }
+    e2 = warp_sum(e2);
+    float dyw = warp_sum(s_dy[r]);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(grad + 320, dyw);
+        atomicAdd(loss, e2 * inv_n);
+    }
+}
+
+__global__ void k_to_half(const float *__restrict__ w32, __half *__restrict__ w16, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w16[i] = __float2half_rn(w32[i]);
+}
+
+// Descending order of a float cost: radix keys that sort ascending.
+__global__ void k_cost_keys(const float *__restrict__ cost, int n, uint32_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t b = __float_as_uint(cost[i]);
+    uint32_t asc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);   // order-preserving map
+    keys[i] = ~asc;
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void k_range_cost(const uint2 *__restrict__ r, int n, float *__restrict__ cost) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { uint2 v = r[i]; cost[i] = (float)(v.y - v.x); }
+}
+
+__global__ void k_int_cost(const int *__restrict__ c, int n, float *__restrict__ cost) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cost[i] = (float)c[i];
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" int gs_tile_features(const gs_camera *cams, int n_views, const uint32_t *d_tile_ranges,
+                                const uint32_t *d_vals, const void *d_splats, int rgb_dtype, int cap,
+                                float *d_feats, gs_stream_t stream) {
+    TileBatch tb;
+    if (make_tile_batch(cams, n_views, &tb) != GS_OK) return GS_ERR_ARG;
+    if (!d_tile_ranges || !d_vals || !d_splats || !d_feats || cap < 1) return GS_ERR_ARG;
+    if (!aligned(d_splats, 16) || !aligned(d_tile_ranges, 8)) return GS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int grid = cdiv((long long)tb.total_tiles * 32, 256);
+    const uint2 *rg = reinterpret_cast<const uint2 *>(d_tile_ranges);
+    if (rgb_dtype == GS_F32)
+        { k_tile_features<GS_F32><<<grid, 256, 0, st>>>(tb, rg, d_vals, d_splats, cap, d_feats); count_launches(1); }
+    else if (rgb_dtype == GS_BF16)
+        { k_tile_features<GS_BF16><<<grid, 256, 0, st>>>(tb, rg, d_vals, d_splats, cap, d_feats); count_launches(1); }
+    else if (rgb_dtype == GS_F16)
+        { k_tile_features<GS_F16><<<grid, 256, 0, st>>>(tb, rg, d_vals, d_splats, cap, d_feats); count_launches(1); }
+    else
+        return GS_ERR_ARG;
+    return launch_status();
+}
+
+extern "C" int gs_mlp_predict(const void *d_w16, const float *d_feats, int n, float *d_pred,
+                              gs_stream_t stream) {
+    if (!d_w16 || !d_feats || !d_pred || n < 0) return GS_ERR_ARG;
+    if (n == 0) return GS_OK;
+    { k_mlp_predict<<<cdiv(n, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const __half *>(d_w16), d_feats, n, d_pred); count_launches(1); }
+    return launch_status();
+}
+
+extern "C" int gs_mlp_grad(const float *d_w32, const float *d_feats, const uint64_t *d_tile_ns,
+                           const float *d_target, int n, float *d_grad, float *d_loss,
+                           gs_stream_t stream) {
+    if (!d_w32 || !d_feats || (!d_tile_ns && !d_target) || !d_grad || !d_loss || n < 1) return GS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(d_grad, 0, sizeof(float) * kMlpW, st);
+    cudaMemsetAsync(d_loss, 0, sizeof(float), st);
+    { k_mlp_grad<<<cdiv(n, 256), 256, 0, st>>>(d_w32, d_feats,
+                                              reinterpret_cast<const unsigned long long *>(d_tile_ns),
+                                              d_target, n, 1.0f / (float)n, d_grad, d_loss); count_launches(1); }
+    return launch_status();
+}
+
+extern "C" int gs_mlp_train_step(float *d_w32, void *d_w16, float *d_m, float *d_v, int t, float lr,
+                                 const float *d_feats, const uint64_t *d_tile_ns,
+                                 const float *d_target, int n, float *d_grad, float *d_loss,
+                                 gs_stream_t stream) {
+    if (!d_w16) return GS_ERR_ARG;
+    int rc = gs_mlp_grad(d_w32, d_feats, d_tile_ns, d_target, n, d_grad, d_loss, stream);
+    if (rc != GS_OK) return rc;
+    rc = gs_adam_flat(kMlpW, d_w32, d_grad, d_m, d_v, lr, 0.9f, 0.999f, 1e-8f, t, stream);
+    if (rc != GS_OK) return rc;
+    { k_to_half<<<cdiv(kMlpW, 128), 128, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        d_w32, reinterpret_cast<__half *>(d_w16), kMlpW); count_launches(1); }
+    return launch_status();
+}
+
+extern "C" int gs_int_cost(const int32_t *d_counts, int n, float *d_cost, gs_stream_t stream) {
+    if (!d_counts || !d_cost || n < 0) return GS_ERR_ARG;
+    if (n == 0) return GS_OK;
+    { k_int_cost<<<cdiv(n, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(d_counts, n, d_cost); count_launches(1); }
+    return launch_status();
+}
+
+extern "C" int gs_range_cost(const uint32_t *d_tile_ranges, int T, float *d_cost, gs_stream_t stream) {
+    if (!d_tile_ranges || !d_cost || T < 0) return GS_ERR_ARG;
+    if (!aligned(d_tile_ranges, 8)) return GS_ERR_ARG;
+    if (T == 0) return GS_OK;
+    { k_range_cost<<<cdiv(T, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const uint2 *>(d_tile_ranges), T, d_cost); count_launches(1); }
+    return launch_status();
+}
+
+extern "C" int gs_sched_order_workspace(int n, size_t *bytes) {
+    if (!bytes || n < 0) return GS_ERR_ARG;
+    *bytes = radix_sort_workspace(n);
+    return GS_OK;
+}
+
+extern "C" int gs_sched_order(const float *d_cost, int n, int32_t *d_order, void *d_workspace,
+                              size_t workspace_bytes, gs_stream_t stream) {
+    if (!d_cost || !d_order || !d_workspace || n < 0) return GS_ERR_ARG;
+    if (!aligned(d_workspace, 256)) return GS_ERR_ARG;
+    if (workspace_bytes < radix_sort_workspace(n)) return GS_ERR_CAPACITY;
+    if (n == 0) return GS_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(d_workspace);
+    size_t al = ((size_t)n * 4 + 255) & ~(size_t)255;
+    uint32_t *k0 = (uint32_t *)ws, *v0 = (uint32_t *)(ws + al);
+    { k_cost_keys<<<cdiv(n, 256), 256, 0, st>>>(d_cost, n, k0, v0); count_launches(1); }
+    radix_sort_pairs(k0, v0, reinterpret_cast<uint32_t *>(d_order), n, 32, ws + 2 * al, st);
+    return launch_status();
+}

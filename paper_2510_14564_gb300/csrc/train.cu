@@ -1,0 +1,186 @@
+// train.cu -- a4 L1 loss and a7 Adam (sm_103a).  Both are streaming,
+// HBM-bound kernels: float4 loads and stores, grid-stride over the data.
+#include <atomic>
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+__global__ void __launch_bounds__(256) k_l1(long long n, const float *__restrict__ img,
+                                            const float *__restrict__ tgt, float inv_n,
+                                            float *__restrict__ loss, float *__restrict__ dimg) {
+    __shared__ float s_w[8];
+    float acc = 0.0f;
+    const long long n4 = n / 4;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        float4 a = __ldg(reinterpret_cast<const float4 *>(img) + i);
+        float4 b = __ldg(reinterpret_cast<const float4 *>(tgt) + i);
+        float4 d = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+        acc += fabsf(d.x) + fabsf(d.y) + fabsf(d.z) + fabsf(d.w);
+        auto sg = [inv_n](float x) { return x > 0.0f ? inv_n : (x < 0.0f ? -inv_n : 0.0f); };
+        reinterpret_cast<float4 *>(dimg)[i] = make_float4(sg(d.x), sg(d.y), sg(d.z), sg(d.w));
+    }
+    for (long long i = 4 * n4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float d = img[i] - tgt[i];
+        acc += fabsf(d);
+        dimg[i] = d > 0.0f ? inv_n : (d < 0.0f ? -inv_n : 0.0f);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int k = 0; k < 8; ++k) s += s_w[k];
+        atomicAdd(loss, s * inv_n);
+    }
+}
+
+struct AdamGroups {
+    long long b[5];     // group ends: 3N, 6N, 10N, 11N, 59N
+    long long sh0;      // start of the SH group (11N)
+    float lr[6];
+};
+
+__device__ __forceinline__ float group_lr(const AdamGroups &g, long long i) {
+    if (i < g.b[0]) return g.lr[0];
+    if (i < g.b[1]) return g.lr[1];
+    if (i < g.b[2]) return g.lr[2];
+    if (i < g.b[3]) return g.lr[3];
+    long long s = i - g.sh0;
+    return (s % 48) < 3 ? g.lr[4] : g.lr[5];
+}
+
+template <int SHD>
+__device__ __forceinline__ void adam_one(long long i, float &p, float g, float &m, float &v, float lr,
+                                         float b1, float b2, float inv_c1, float inv_c2, float eps,
+                                         void *shadow, long long sh0, long long total) {
+    m = b1 * m + (1.0f - b1) * g;
+    v = b2 * v + (1.0f - b2) * g * g;
+    p -= lr * (m * inv_c1) / (sqrtf(v * inv_c2) + eps);
+    if (SHD != 0 && i >= sh0 && i < total) {
+        long long s = i - sh0;
+        if (SHD == GS_BF16) reinterpret_cast<__nv_bfloat16 *>(shadow)[s] = __float2bfloat16_rn(p);
+        else reinterpret_cast<__half *>(shadow)[s] = __float2half_rn(p);
+    }
+}
+
+template <int SHD>
+__global__ void __launch_bounds__(256) k_adam(long long total, float *__restrict__ p,
+                                              const float *__restrict__ g, float *__restrict__ m,
+                                              float *__restrict__ v, AdamGroups grp, float b1, float b2,
+                                              float inv_c1, float inv_c2, float eps, void *shadow) {
+    const long long n4 = total / 4;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+        float4 pp = reinterpret_cast<float4 *>(p)[q];
+        float4 gg = __ldg(reinterpret_cast<const float4 *>(g) + q);
+        float4 mm = reinterpret_cast<float4 *>(m)[q];
+        float4 vv = reinterpret_cast<float4 *>(v)[q];
+        long long i = 4 * q;
+        adam_one<SHD>(i, pp.x, gg.x, mm.x, vv.x, group_lr(grp, i), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
+        adam_one<SHD>(i + 1, pp.y, gg.y, mm.y, vv.y, group_lr(grp, i + 1), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
+        adam_one<SHD>(i + 2, pp.z, gg.z, mm.z, vv.z, group_lr(grp, i + 2), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
+        adam_one<SHD>(i + 3, pp.w, gg.w, mm.w, vv.w, group_lr(grp, i + 3), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
+        reinterpret_cast<float4 *>(p)[q] = pp;
+        reinterpret_cast<float4 *>(m)[q] = mm;
+        reinterpret_cast<float4 *>(v)[q] = vv;
+    }
+    for (long long i = 4 * n4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        float pp = p[i], mm = m[i], vv = v[i];
+        adam_one<SHD>(i, pp, g[i], mm, vv, group_lr(grp, i), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
+        p[i] = pp; m[i] = mm; v[i] = vv;
+    }
+}
+
+inline int stream_grid(long long work, int threads) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long want = (work + threads - 1) / threads;
+    long long cap = (long long)sms * 8;    // 8 CTAs of 256 per SM fill it
+    if (want > cap) want = cap;
+    return want < 1 ? 1 : (int)want;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" int gs_l1_loss(long long n, const float *d_img, const float *d_tgt, float *d_loss,
+                          float *d_dimg, gs_stream_t stream) {
+    if (n < 0 || !d_img || !d_tgt || !d_loss || !d_dimg) return GS_ERR_ARG;
+    if (!aligned(d_img, 16) || !aligned(d_tgt, 16) || !aligned(d_dimg, 16)) return GS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(d_loss, 0, sizeof(float), st);
+    if (n == 0) return launch_status();
+    { k_l1<<<stream_grid(n / 4 + 1, 256), 256, 0, st>>>(n, d_img, d_tgt, (float)(1.0 / (double)n), d_loss, d_dimg); count_launches(1); }
+    return launch_status();
+}
+
+static int adam_launch(long long total, float *p, const float *g, float *m, float *v, AdamGroups grp,
+                       float b1, float b2, float eps, int t, void *shadow, int shd, cudaStream_t st) {
+    if (t < 1) return GS_ERR_ARG;
+    double c1 = 1.0 - pow((double)b1, t), c2 = 1.0 - pow((double)b2, t);
+    float ic1 = (float)(1.0 / c1), ic2 = (float)(1.0 / c2);
+    int grid = stream_grid(total / 4 + 1, 256);
+    if (!shadow)
+        { k_adam<0><<<grid, 256, 0, st>>>(total, p, g, m, v, grp, b1, b2, ic1, ic2, eps, nullptr); count_launches(1); }
+    else if (shd == GS_BF16)
+        { k_adam<GS_BF16><<<grid, 256, 0, st>>>(total, p, g, m, v, grp, b1, b2, ic1, ic2, eps, shadow); count_launches(1); }
+    else if (shd == GS_F16)
+        { k_adam<GS_F16><<<grid, 256, 0, st>>>(total, p, g, m, v, grp, b1, b2, ic1, ic2, eps, shadow); count_launches(1); }
+    else
+        return GS_ERR_ARG;
+    return launch_status();
+}
+
+extern "C" int gs_adam_step(int N, float *d_params, const float *d_grads, float *d_m, float *d_v,
+                            const float *lr, float b1, float b2, float eps, int t, void *d_sh_shadow,
+                            int shadow_dtype, gs_stream_t stream) {
+    if (N < 0 || !d_params || !d_grads || !d_m || !d_v || !lr) return GS_ERR_ARG;
+    if (!aligned(d_params, 16) || !aligned(d_grads, 16) || !aligned(d_m, 16) || !aligned(d_v, 16))
+        return GS_ERR_ARG;
+    if (N == 0) return GS_OK;
+    AdamGroups grp;
+    long long n = N;
+    grp.b[0] = 3 * n; grp.b[1] = 6 * n; grp.b[2] = 10 * n; grp.b[3] = 11 * n; grp.b[4] = 59 * n;
+    grp.sh0 = 11 * n;
+    for (int k = 0; k < 6; ++k) grp.lr[k] = lr[k];
+    return adam_launch(59 * n, d_params, d_grads, d_m, d_v, grp, b1, b2, eps, t, d_sh_shadow,
+                       shadow_dtype, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int gs_adam_flat(long long n, float *d_p, const float *d_g, float *d_m, float *d_v, float lr,
+                            float b1, float b2, float eps, int t, gs_stream_t stream) {
+    if (n < 0 || !d_p || !d_g || !d_m || !d_v) return GS_ERR_ARG;
+    if (!aligned(d_p, 16) || !aligned(d_g, 16) || !aligned(d_m, 16) || !aligned(d_v, 16)) return GS_ERR_ARG;
+    if (n == 0) return GS_OK;
+    AdamGroups grp;
+    for (int k = 0; k < 5; ++k) grp.b[k] = n;
+    grp.sh0 = n;
+    for (int k = 0; k < 6; ++k) grp.lr[k] = lr;
+    return adam_launch(n, d_p, d_g, d_m, d_v, grp, b1, b2, eps, t, nullptr, 0,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+namespace gs {
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace gs
+
+extern "C" long long gs_launch_count(void) { return gs::g_launches.load(std::memory_order_relaxed); }
+
+extern "C" int gs_version(void) { return GS_VERSION; }
+
+extern "C" const char *gs_strerror(int status) {
+    switch (status) {
+        case GS_OK: return "ok";
+        case GS_ERR_ARG: return "invalid argument (null, misaligned, bad size or dtype)";
+        case GS_ERR_CAPACITY: return "buffer too small";
+        case GS_ERR_CUDA: return "CUDA launch or copy failed";
+        case GS_ERR_TIMEOUT: return "persistent kernel exceeded its time budget";
+        case GS_ERR_NONFINITE: return "non-finite input";
+        default: return "unknown status";
+    }
+}

@@ -1,0 +1,333 @@
+"""The 3DGS training step on the CUDA library: buffers, schedule, autograd.
+
+`Frame` owns the device buffers of one batch of views for N Gaussians and runs
+the hot path through the C ABI:
+
+    project -> bin_sort -> [features -> MLP -> order] -> render_fwd -> L1
+            -> render_bwd -> project_bwd -> Adam
+
+`RasterizeGaussians` is the same forward/backward behind torch.autograd.
+Every arithmetic step runs in libgs103.so; torch only provides device memory
+and the stream.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from .scenes import PARAM_FLOATS
+
+# Per-group Adam learning rates: means, log-scales, quaternions, opacity
+# logits, SH DC, SH rest (the 3DGS defaults).
+DEFAULT_LR = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3, 1.25e-4)
+ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-15
+MLP_W = 321
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        raise L.GsError("a CUDA device is required (no CPU fallback)")
+    return torch.device("cuda")
+
+
+def param_views(flat: torch.Tensor, N: int) -> dict:
+    """Named views of a grouped 59 N buffer."""
+    o, out = 0, {}
+    for name, w in (("means", 3), ("log_scales", 3), ("quats", 4), ("opacity_logits", 1), ("sh", 48)):
+        out[name] = flat[o:o + w * N]
+        o += w * N
+    return out
+
+
+def to_device_params(scene, device=None) -> torch.Tensor:
+    """The scene's grouped parameter buffer on the device (59 N floats)."""
+    return torch.from_numpy(scene.flat()).to(device or _dev())
+
+
+@dataclass
+class Schedule:
+    """How render CTAs take tiles: 'raster' (one CTA per tile), 'count'
+    (persistent, most instances first) or 'learned' (persistent, longest
+    predicted time first, MLP trained on measured tile times)."""
+    mode: str = "raster"
+    feature_cap: int = 2048
+    mlp_lr: float = 3e-3
+    train_every: int = 1
+    seed: int = 0
+
+
+class Frame:
+    """Device buffers and calls for one batch of views of N Gaussians."""
+
+    def __init__(self, cams, N: int, rgb_dtype: int = L.GS_F32, sh_dtype: int = L.GS_F32,
+                 capacity: int | None = None, schedule: Schedule | None = None, device=None):
+        self.dev = device or _dev()
+        self.cams = list(cams)
+        self.V = len(self.cams)
+        self.N = int(N)
+        self.rgb_dtype = rgb_dtype
+        self.sh_dtype = sh_dtype
+        self.sched = schedule or Schedule()
+        d = self.dev
+        VN = self.V * self.N
+        self.T = sum(c.n_tiles for c in self.cams)
+        self.P = sum(c.W * c.H for c in self.cams)
+        nb = L.SPLAT_BYTES[rgb_dtype]
+        self.splats = torch.empty(VN * nb // 4, dtype=torch.float32, device=d)
+        self.depth = torch.empty(VN, dtype=torch.float32, device=d)
+        self.rect = torch.empty(VN * 4, dtype=torch.int16, device=d)
+        self.touched = torch.empty(VN, dtype=torch.int32, device=d)
+        self.radius = torch.empty(VN, dtype=torch.int32, device=d)
+        self.err = torch.zeros(1, dtype=torch.int32, device=d)
+        self.n_inst = torch.zeros(1, dtype=torch.int64, device=d)
+        self.ranges = torch.empty(self.T * 2, dtype=torch.int32, device=d)
+        self.img = torch.empty(3 * self.P, dtype=torch.float32, device=d)
+        self.T_final = torch.empty(self.P, dtype=torch.float32, device=d)
+        self.n_proc = torch.empty(self.P, dtype=torch.int32, device=d)
+        self.tile_nproc = torch.empty(self.T, dtype=torch.int32, device=d)
+        self.tile_ns = torch.zeros(self.T, dtype=torch.int64, device=d)
+        self.dimg = torch.empty(3 * self.P, dtype=torch.float32, device=d)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=d)
+        self.grad2d = torch.empty(VN * 12, dtype=torch.float32, device=d)
+        self.dparams = torch.empty(PARAM_FLOATS * self.N, dtype=torch.float32, device=d)
+        self.capacity = 0
+        self.vals = None
+        self.keys = None
+        self.ws = None
+        if capacity is not None:
+            self.reserve(capacity)
+        # scheduler state
+        self.queue = torch.zeros(1, dtype=torch.int32, device=d)
+        self.feats = torch.zeros(self.T * 8, dtype=torch.float32, device=d)
+        self.cost = torch.zeros(self.T, dtype=torch.float32, device=d)
+        self.order_f = torch.arange(self.T, dtype=torch.int32, device=d)
+        self.order_b = torch.arange(self.T, dtype=torch.int32, device=d)
+        self.order_ws = torch.empty(L.gs_sched_order_workspace(self.T) // 4 + 64,
+                                    dtype=torch.float32, device=d)
+        rng = np.random.Generator(np.random.PCG64(self.sched.seed))
+        w = np.zeros(MLP_W, np.float32)
+        w[:256] = rng.normal(0, math.sqrt(2.0 / 8), 256)
+        w[288:320] = rng.normal(0, math.sqrt(1.0 / 32), 32)
+        w[320] = 10.0                      # log(ns) of a typical tile
+        self.mlp_w32 = torch.from_numpy(w).to(d)
+        self.mlp_w16 = self.mlp_w32.to(torch.float16)
+        self.mlp_m = torch.zeros(MLP_W, dtype=torch.float32, device=d)
+        self.mlp_v = torch.zeros(MLP_W, dtype=torch.float32, device=d)
+        self.mlp_g = torch.zeros(MLP_W, dtype=torch.float32, device=d)
+        self.mlp_loss = torch.zeros(1, dtype=torch.float32, device=d)
+        self.mlp_t = 0
+        self.pred = torch.zeros(self.T, dtype=torch.float32, device=d)
+        self.use_learned = self.sched.mode == "learned"
+        self.step_count = 0
+
+    # -- buffers -----------------------------------------------------------
+    def reserve(self, capacity: int, with_keys: bool = False) -> None:
+        capacity = int(max(capacity, 1))
+        if capacity <= self.capacity and (not with_keys or self.keys is not None):
+            return
+        self.capacity = max(capacity, self.capacity)
+        self.vals = torch.empty(self.capacity, dtype=torch.int32, device=self.dev)
+        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=self.dev) if with_keys else None
+        nbytes = L.gs_bin_sort_workspace(self.cams, self.N, self.capacity)
+        self.ws = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device=self.dev)
+
+    # -- forward -----------------------------------------------------------
+    def project(self, params: dict) -> None:
+        L.gs_project(self.cams, self.N, params["means"], params["log_scales"], params["quats"],
+                     params["opacity_logits"], params["sh"], self.sh_dtype, self.splats,
+                     self.rgb_dtype, self.depth, self.rect, self.touched, self.radius, self.err)
+
+    def bin_sort(self, want_keys: bool = False) -> None:
+        if self.vals is None:
+            # first call: size the instance buffers from the exact count
+            self.reserve(1)
+            L.gs_bin_sort(self.cams, self.N, self.depth, self.rect, self.touched, 0, self.vals,
+                          self.ranges, None, self.n_inst, self.ws, self.err)
+            need = int(self.n_inst.item())
+            self.reserve(int(need * 1.25) + 1024, with_keys=want_keys)
+            self.err.zero_()
+        elif want_keys and self.keys is None:
+            self.reserve(self.capacity, with_keys=True)
+        L.gs_bin_sort(self.cams, self.N, self.depth, self.rect, self.touched, self.capacity, self.vals,
+                      self.ranges, self.keys if want_keys else None, self.n_inst, self.ws, self.err)
+
+    def _sched_fwd(self):
+        m = self.sched.mode
+        if m == "raster":
+            return None
+        if m == "count" or not self.use_learned:
+            L.gs_range_cost(self.ranges, self.T, self.cost)
+            L.gs_sched_order(self.cost, self.T, self.order_f, self.order_ws)
+        else:
+            L.gs_tile_features(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype,
+                               self.sched.feature_cap, self.feats)
+            L.gs_mlp_predict(self.mlp_w16, self.feats, self.T, self.pred)
+            L.gs_sched_order(self.pred, self.T, self.order_f, self.order_ws)
+        return {"mode": L.GS_SCHED_ORDER, "order": self.order_f, "queue": self.queue}
+
+    def _sched_bwd(self):
+        if self.sched.mode == "raster":
+            return None
+        L.gs_int_cost(self.tile_nproc, self.T, self.cost)
+        L.gs_sched_order(self.cost, self.T, self.order_b, self.order_ws)
+        return {"mode": L.GS_SCHED_ORDER, "order": self.order_b, "queue": self.queue}
+
+    def render(self, timing: bool = False, mark=None) -> None:
+        s = self._sched_fwd()
+        if mark:
+            mark("render_fwd")
+        L.gs_render_fwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, s, self.img,
+                        self.T_final, self.n_proc, self.tile_nproc, self.tile_ns if timing else None,
+                        self.err)
+
+    def forward(self, params: dict, timing: bool = False) -> torch.Tensor:
+        self.project(params)
+        self.bin_sort()
+        self.render(timing=timing)
+        return self.img
+
+    # -- backward ----------------------------------------------------------
+    def backward(self, params: dict, dimg: torch.Tensor, mark=None) -> torch.Tensor:
+        self.grad2d.zero_()
+        s = self._sched_bwd()
+        if mark:
+            mark("render_bwd")
+        L.gs_render_bwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, s, dimg,
+                        self.T_final, self.n_proc, self.tile_nproc, self.grad2d, self.err)
+        if mark:
+            mark("project_bwd")
+        L.gs_project_bwd(self.cams, self.N, params["means"], params["log_scales"], params["quats"],
+                         params["opacity_logits"], params["sh"], self.sh_dtype, self.touched,
+                         self.grad2d, self.dparams)
+        return self.dparams
+
+    def l1(self, target: torch.Tensor) -> torch.Tensor:
+        L.gs_l1_loss(3 * self.P, self.img, target, self.loss, self.dimg)
+        return self.loss
+
+    # -- scheduler training ------------------------------------------------
+    def train_scheduler(self) -> None:
+        """One MLP step on the tile times of the last timed forward."""
+        if self.sched.mode != "learned":
+            return
+        self.mlp_t += 1
+        if not self.use_learned:
+            L.gs_tile_features(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype,
+                               self.sched.feature_cap, self.feats)
+        L.gs_mlp_train_step(self.mlp_w32, self.mlp_w16, self.mlp_m, self.mlp_v, self.mlp_t,
+                            self.sched.mlp_lr, self.feats, self.tile_ns, None, self.T, self.mlp_g,
+                            self.mlp_loss)
+
+    def check_errors(self) -> int:
+        return int(self.err.item())
+
+    # -- views ---------------------------------------------------------------
+    def image(self, v: int = 0) -> torch.Tensor:
+        base = sum(c.W * c.H for c in self.cams[:v])
+        c = self.cams[v]
+        return self.img[3 * base:3 * (base + c.W * c.H)].view(3, c.H, c.W)
+
+    def pixel_map(self, buf: torch.Tensor, v: int = 0) -> torch.Tensor:
+        base = sum(c.W * c.H for c in self.cams[:v])
+        c = self.cams[v]
+        return buf[base:base + c.W * c.H].view(c.H, c.W)
+
+
+class Trainer:
+    """Full training step: forward, L1 against targets, backward, Adam."""
+
+    def __init__(self, cams, params_flat: torch.Tensor, N: int, targets: torch.Tensor,
+                 rgb_dtype: int = L.GS_F32, sh_storage: int = L.GS_F32,
+                 schedule: Schedule | None = None, lr=DEFAULT_LR):
+        self.N = N
+        self.p = params_flat
+        self.m = torch.zeros_like(params_flat)
+        self.v = torch.zeros_like(params_flat)
+        self.lr = lr
+        self.t = 0
+        self.sh_storage = sh_storage
+        self.views = param_views(self.p, N)
+        if sh_storage != L.GS_F32:
+            dt = torch.bfloat16 if sh_storage == L.GS_BF16 else torch.float16
+            self.sh_shadow = self.views["sh"].to(dt)
+        else:
+            self.sh_shadow = None
+        self.frame = Frame(cams, N, rgb_dtype=rgb_dtype, sh_dtype=sh_storage, schedule=schedule,
+                           device=params_flat.device)
+        self.targets = targets
+
+    def params_for_kernels(self) -> dict:
+        d = dict(self.views)
+        if self.sh_shadow is not None:
+            d["sh"] = self.sh_shadow
+        return d
+
+    def step(self, mark=None, targets: torch.Tensor | None = None) -> torch.Tensor:
+        """One training step.  `mark(name)`, if given, is called before each
+        stage (and with "end" after the last) so a caller can time stages."""
+        mk = mark or (lambda name: None)
+        f = self.frame
+        pk = self.params_for_kernels()
+        timing = f.sched.mode == "learned"
+        mk("project")
+        f.project(pk)
+        mk("bin_sort")
+        f.bin_sort()
+        mk("sched_fwd")
+        f.render(timing=timing, mark=mark)
+        mk("l1")
+        f.l1(self.targets if targets is None else targets)
+        mk("sched_bwd")
+        g = f.backward(pk, f.dimg, mark=mark)
+        mk("adam")
+        self.t += 1
+        L.gs_adam_step(self.N, self.p, g, self.m, self.v, self.lr, ADAM_B1, ADAM_B2, ADAM_EPS, self.t,
+                       self.sh_shadow, self.sh_storage)
+        if timing and (f.step_count % max(1, f.sched.train_every) == 0):
+            mk("mlp_train")
+            f.train_scheduler()
+        mk("end")
+        f.step_count += 1
+        return f.loss
+
+
+class RasterizeGaussians(torch.autograd.Function):
+    """image = render(means, log_scales, quats, opacity_logits, sh) for one
+    view; backward through the hand-written reverse-mode kernels."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, cam, rgb_dtype=L.GS_F32):
+        N = means.shape[0]
+        fr = Frame([cam], N, rgb_dtype=rgb_dtype, sh_dtype=_sh_dtype(sh), device=means.device)
+        params = {"means": means.contiguous(), "log_scales": log_scales.contiguous(),
+                  "quats": quats.contiguous(), "opacity_logits": opacity_logits.contiguous(),
+                  "sh": sh.contiguous()}
+        fr.forward(params)
+        ctx.frame = fr
+        ctx.params = params
+        ctx.sh_float = sh.dtype
+        return fr.image(0).clone()
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        fr = ctx.frame
+        g = fr.backward(ctx.params, grad_img.contiguous().view(-1))
+        N = fr.N
+        v = param_views(g, N)
+        return (v["means"].view(N, 3).clone(), v["log_scales"].view(N, 3).clone(),
+                v["quats"].view(N, 4).clone(), v["opacity_logits"].view(N).clone(),
+                v["sh"].view(N, 16, 3).to(ctx.sh_float), None, None)
+
+
+def _sh_dtype(sh: torch.Tensor) -> int:
+    if sh.dtype == torch.float32:
+        return L.GS_F32
+    if sh.dtype == torch.bfloat16:
+        return L.GS_BF16
+    if sh.dtype == torch.float16:
+        return L.GS_F16
+    raise L.GsError(f"unsupported SH dtype {sh.dtype}")
