@@ -131,7 +131,8 @@ int gs_project(const gs_camera *cams, int n_views, int N, const float *d_means,
  * record index (v*N + i); the order is exactly that of a stable sort of that
  * key over index-ordered input.
  * Out: d_vals [capacity] u32 record index per sorted instance;
- *      d_tile_ranges [T, 2] u32 [start, end) into d_vals per global tile;
+ *      d_tile_ranges [T, 2] u32 [start, end) into d_vals per global tile
+ *                    (an empty tile reads [0, 0));
  *      d_keys [capacity] u64 (optional, NULL = not written) the sorted keys;
  *      d_n_instances (device, 1 x int64) the instance count.
  * If the count exceeds capacity, nothing past the capacity is written,

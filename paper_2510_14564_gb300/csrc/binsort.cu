@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
         long long idx = base + it * 32 + l;
         bool valid = idx < (long long)count;
         uint32_t d = valid ? ((__ldg(keys + idx) >> shift) & mask) : kRadix;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned peers = warp_peers(d, 8);
         if (valid && (peers & lanemask_lt()) == 0) s_h[w][d] += __popc(peers);
         __syncwarp();
     }
@@ -79,7 +79,7 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *s_
 }
 
 // Stable scatter of keys/values by digit, given the scanned histogram matrix.
-__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
+__global__ void __launch_bounds__(kSortThreads, 3) k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ offs, const uint32_t *d_count,
     uint32_t host_count, int shift, uint32_t mask, int nb, int write_keys) {
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
         key[it] = valid ? __ldg(kin + idx) : 0u;
         val[it] = valid ? __ldg(vin + idx) : 0u;
         uint32_t d = valid ? ((key[it] >> shift) & mask) : kRadix;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned peers = warp_peers(d, 8);
         unsigned rank = __popc(peers & lanemask_lt());
         uint32_t before = valid ? s_wh[w][d] : 0u;
         __syncwarp();
@@ -377,28 +377,400 @@ __global__ void k_keys64(const uint32_t *__restrict__ tkeys, const uint32_t *__r
 }
 
 // ---------------------------------------------------------------------------
+// Two-pass placement (views of at most kMaxTX x kMaxTY tiles)
+//
+// After the records are in (view, depth, index) order, view v's visible
+// records are a prefix of its segment [v N, v N + n_v).  The segment is cut
+// into C_v chunks of consecutive records, one warp per chunk.
+//   Pass 1 partitions instances by global tile row.  Per chunk, the number
+//   of instances in each row comes from a difference array over rows; an
+//   exclusive scan over the row-major matrix M1[row][chunk] gives each
+//   (row, chunk) its first slot, because the output is ordered by row, then
+//   chunk.  Each warp then walks its records in order and writes every
+//   record's tiles of one row as a contiguous run of (record, column) pairs.
+//   Pass 2 cuts every row into slices of kSlice entries; per slice, a
+//   histogram over the tile columns goes to M2[row][column][slice], whose
+//   exclusive scan (row, then column, then slice) is the final slot of each
+//   (column, slice); a CTA per slice ranks its entries stably by column and
+//   scatters them.
+// Records are visited in order in pass 1 and entries keep their order
+// within a column in pass 2, so every tile list comes out in depth order,
+// equal depths in record order: the stable 64-bit key order.
+// ---------------------------------------------------------------------------
+constexpr int kMaxTX = 256;            // pass 2 ranks columns in 256 buckets
+constexpr int kMaxTY = 4096;           // pass 1 cursors per row in shared memory
+constexpr int kChunksTotal = 4864;     // pass-1 chunks over all views of a batch
+constexpr int kP1Warps = 8;            // chunks per pass-1 CTA
+constexpr int kSlice = kSortTile;      // pass-2 slice: 4096 entries, 16 per thread
+
+__global__ void k_view_keys(const uint32_t *__restrict__ vals, long long n, uint32_t N,
+                            uint32_t *__restrict__ keys) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) keys[i] = vals[i] / N;
+}
+
+struct ChunkGeom {
+    long long lo, hi;     // record positions of the chunk in the sorted order
+};
+
+// Chunk k of view v: the records whose first instance (offs, the exclusive
+// scan of tile counts in sorted order) falls in the k-th of C_v equal parts
+// of the view's instances, so that chunks carry equal work.
+__device__ __forceinline__ long long lower_bound_u64(const unsigned long long *a, long long lo,
+                                                     long long hi, unsigned long long key) {
+    while (lo < hi) {
+        long long mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ ChunkGeom chunk_of(int v, int k, int Cv, int N,
+                                              const unsigned long long *offs) {
+    const long long s0 = (long long)v * N, s1 = s0 + N;
+    const unsigned long long i0 = offs[s0], span = offs[s1] - i0;
+    const unsigned long long b0 = i0 + span * (unsigned long long)k / (unsigned long long)Cv;
+    const unsigned long long b1 = i0 + span * (unsigned long long)(k + 1) / (unsigned long long)Cv;
+    ChunkGeom g;
+    g.lo = lower_bound_u64(offs, s0, s1, b0);     // records whose first instance is in [b0, b1)
+    g.hi = lower_bound_u64(offs, s0, s1, b1);
+    return g;
+}
+
+// Warp-wide exclusive scan of n <= 32 * per values in smem (in place);
+// returns the total.
+__device__ __forceinline__ uint32_t warp_scan_smem(uint32_t *a, int n) {
+    const int l = threadIdx.x & 31;
+    const int per = (n + 31) / 32;
+    const int b = l * per;
+    uint32_t loc = 0;
+    for (int k = 0; k < per; ++k)
+        if (b + k < n) loc += a[b + k];
+    uint32_t inc = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += t;
+    }
+    uint32_t run = inc - loc;
+    for (int k = 0; k < per; ++k)
+        if (b + k < n) {
+            uint32_t c = a[b + k];
+            a[b + k] = run;
+            run += c;
+        }
+    return __shfl_sync(0xffffffffu, inc, 31);
+}
+
+// Pass 1 count: instances per (global row, chunk) into M1[row * Cv + chunk].
+__global__ void __launch_bounds__(32 * kP1Warps) k_p1_count(TileBatch tb, int N, int Cv, int TYmax,
+                                                            const uint32_t *__restrict__ order,
+                                                            const short4 *__restrict__ rect,
+                                                            const unsigned long long *__restrict__ offs,
+                                                            uint32_t *__restrict__ M1) {
+    extern __shared__ uint32_t s_p1[];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int chunk = blockIdx.x * kP1Warps + w;
+    if (chunk >= tb.n * Cv) return;
+    const int v = chunk / Cv, k = chunk % Cv;
+    const int TY = tb.v[v].TY;
+    uint32_t *d = s_p1 + w * (TYmax + 1);
+    for (int y = l; y <= TY; y += 32) d[y] = 0;
+    __syncwarp();
+    const ChunkGeom cg = chunk_of(v, k, Cv, N, offs);
+    for (long long i = cg.lo + l; i < cg.hi; i += 32) {
+        const short4 rc = __ldg(rect + __ldg(order + i));
+        const uint32_t wd = (uint32_t)(rc.z - rc.x);
+        atomicAdd(&d[rc.y], wd);
+        atomicAdd(&d[rc.w], 0u - wd);
+    }
+    __syncwarp();
+    // inclusive prefix over rows = count per row; rows are few, lane 0 walks them
+    if (l == 0) {
+        uint32_t run = 0;
+        for (int y = 0; y < TY; ++y) { run += d[y]; d[y] = run; }
+    }
+    __syncwarp();
+    const int rb = tb.v[v].row_base;
+    for (int y = l; y < TY; y += 32) M1[(long long)(rb + y) * Cv + k] = d[y];
+}
+
+// Pass 1 place: each warp hands out slots in record order from per-row cursors.
+__global__ void __launch_bounds__(32 * kP1Warps) k_p1_place(TileBatch tb, int N, int Cv, int TYmax,
+                                                            const uint32_t *__restrict__ order,
+                                                            const short4 *__restrict__ rect,
+                                                            const unsigned long long *__restrict__ offs,
+                                                            const unsigned long long *__restrict__ O1,
+                                                            const unsigned long long *__restrict__ total,
+                                                            long long cap, uint32_t *__restrict__ ids1,
+                                                            uint16_t *__restrict__ xs1) {
+    extern __shared__ uint32_t s_p1[];
+    if ((long long)*total > cap) return;          // overflow: nothing is placed
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int chunk = blockIdx.x * kP1Warps + w;
+    if (chunk >= tb.n * Cv) return;
+    const int v = chunk / Cv, k = chunk % Cv;
+    const int TY = tb.v[v].TY, rb = tb.v[v].row_base;
+    uint32_t *cur = s_p1 + w * (TYmax + 1);
+    for (int y = l; y < TY; y += 32) cur[y] = (uint32_t)O1[(long long)(rb + y) * Cv + k];
+    __syncwarp();
+    const ChunkGeom cg = chunk_of(v, k, Cv, N, offs);
+    for (long long i0 = cg.lo; i0 < cg.hi; i0 += 32) {
+        const long long i = i0 + l;
+        uint32_t g = 0;
+        short4 rc = make_short4(0, 0, 0, 0);
+        if (i < cg.hi) {
+            g = __ldg(order + i);
+            rc = __ldg(rect + g);
+        }
+        const int cnt = (rc.z - rc.x) * (rc.w - rc.y);
+        unsigned has = __ballot_sync(0xffffffffu, cnt > 0);
+        while (has) {
+            const int o = __ffs(has) - 1;
+            has &= has - 1;
+            const int x0 = __shfl_sync(0xffffffffu, (int)rc.x, o);
+            const int y0 = __shfl_sync(0xffffffffu, (int)rc.y, o);
+            const int wd = __shfl_sync(0xffffffffu, (int)(rc.z - rc.x), o);
+            const int h = __shfl_sync(0xffffffffu, (int)(rc.w - rc.y), o);
+            const uint32_t gid = __shfl_sync(0xffffffffu, g, o);
+            const int c = wd * h;
+            const float rw = 1.0f / (float)wd;
+            for (int q = l; q < c; q += 32) {
+                int r = (int)((float)q * rw);                 // q / wd, then exact correction
+                r += (r + 1) * wd <= q;
+                r -= r * wd > q;
+                const int col = q - r * wd;
+                const uint32_t pos = cur[y0 + r] + (uint32_t)col;
+                ids1[pos] = gid;
+                xs1[pos] = (uint16_t)(x0 + col);
+            }
+            __syncwarp();
+            for (int r = l; r < h; r += 32) cur[y0 + r] += (uint32_t)wd;
+            __syncwarp();
+        }
+    }
+}
+
+// Pass 2 bookkeeping per global row: length, slices, M2 entries.
+__global__ void k_p2_rows(TileBatch tb, int Cv, const unsigned long long *__restrict__ O1,
+                          const unsigned long long *__restrict__ total, long long cap,
+                          uint32_t *__restrict__ n_slices, uint32_t *__restrict__ m2len) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= tb.total_rows) return;
+    int v = 0;
+    while (v + 1 < tb.n && r >= tb.v[v + 1].row_base) ++v;
+    const unsigned long long a = O1[(long long)r * Cv], b = O1[(long long)(r + 1) * Cv];
+    const bool ok = (long long)*total <= cap;
+    const uint32_t ns = ok ? (uint32_t)((b - a + kSlice - 1) / kSlice) : 0u;
+    n_slices[r] = ns;
+    m2len[r] = ns * (uint32_t)tb.v[v].TX;
+}
+
+struct SliceCtx {
+    int r, v, s, ns, TX;
+    long long a, b;        // entry range of the slice in pass-1 order
+    uint32_t m2base;       // M2 offset of (row r, column 0, slice 0)
+};
+
+// The row and slice of CTA blockIdx.x (binary search over the slice prefix).
+__device__ __forceinline__ bool slice_ctx(const TileBatch &tb, int Cv, const uint32_t *slice_pre,
+                                          const uint32_t *n_slices, const uint32_t *m2base,
+                                          const unsigned long long *O1, SliceCtx &c) {
+    const uint32_t sid = blockIdx.x;
+    const int R = tb.total_rows;
+    if (sid >= slice_pre[R - 1] + n_slices[R - 1]) return false;
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {                              // last r with slice_pre[r] <= sid
+        int mid = (lo + hi + 1) >> 1;
+        if (slice_pre[mid] <= sid) lo = mid; else hi = mid - 1;
+    }
+    c.r = lo;
+    c.s = (int)(sid - slice_pre[lo]);
+    c.ns = (int)n_slices[lo];
+    int v = 0;
+    while (v + 1 < tb.n && lo >= tb.v[v + 1].row_base) ++v;
+    c.v = v;
+    c.TX = tb.v[v].TX;
+    const unsigned long long ra = O1[(long long)lo * Cv], rb2 = O1[(long long)(lo + 1) * Cv];
+    c.a = (long long)ra + (long long)c.s * kSlice;
+    c.b = min((long long)rb2, c.a + kSlice);
+    c.m2base = m2base[lo];
+    return true;
+}
+
+// Pass 2 count: per-slice column histograms into M2; per-tile totals.
+__global__ void __launch_bounds__(256) k_p2_count(TileBatch tb, int Cv, const uint32_t *__restrict__ slice_pre,
+                                                  const uint32_t *__restrict__ n_slices,
+                                                  const uint32_t *__restrict__ m2base,
+                                                  const unsigned long long *__restrict__ O1,
+                                                  const uint16_t *__restrict__ xs1, uint32_t *__restrict__ M2,
+                                                  uint32_t *__restrict__ tile_cnt) {
+    __shared__ uint32_t s_h[kMaxTX];
+    SliceCtx c;
+    if (!slice_ctx(tb, Cv, slice_pre, n_slices, m2base, O1, c)) return;
+    for (int x = threadIdx.x; x < kMaxTX; x += 256) s_h[x] = 0;
+    __syncthreads();
+    for (long long i = c.a + threadIdx.x; i < c.b; i += 256) atomicAdd(&s_h[xs1[i]], 1u);
+    __syncthreads();
+    const int tile0 = tb.v[c.v].tile_base + (c.r - tb.v[c.v].row_base) * c.TX;
+    for (int x = threadIdx.x; x < c.TX; x += 256) {
+        M2[c.m2base + (uint32_t)x * c.ns + c.s] = s_h[x];
+        if (s_h[x]) atomicAdd(tile_cnt + tile0 + x, s_h[x]);
+    }
+}
+
+__global__ void k_p2_ranges(TileBatch tb, const uint32_t *__restrict__ n_slices,
+                            const uint32_t *__restrict__ m2base, const uint32_t *__restrict__ O2,
+                            const uint32_t *__restrict__ tile_cnt, uint2 *__restrict__ ranges) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tb.total_tiles) return;
+    const int v = view_of_tile(tb, t);
+    const int lt = t - tb.v[v].tile_base, TX = tb.v[v].TX;
+    const int r = tb.v[v].row_base + lt / TX, x = lt % TX;
+    const uint32_t cnt = tile_cnt[t];
+    if (cnt == 0 || n_slices[r] == 0) {
+        ranges[t] = make_uint2(0u, 0u);
+        return;
+    }
+    const uint32_t s0 = O2[m2base[r] + (uint32_t)x * n_slices[r]];
+    ranges[t] = make_uint2(s0, s0 + cnt);
+}
+
+// Pass 2 place: stable ranking of a slice by column, staged in shared memory.
+__global__ void __launch_bounds__(kSortThreads, 3) k_p2_place(TileBatch tb, int Cv,
+                                                           const uint32_t *__restrict__ slice_pre,
+                                                           const uint32_t *__restrict__ n_slices,
+                                                           const uint32_t *__restrict__ m2base,
+                                                           const unsigned long long *__restrict__ O1,
+                                                           const uint32_t *__restrict__ O2,
+                                                           const uint32_t *__restrict__ ids1,
+                                                           const uint16_t *__restrict__ xs1,
+                                                           const float *__restrict__ depth,
+                                                           uint32_t *__restrict__ vals,
+                                                           unsigned long long *__restrict__ keys) {
+    __shared__ uint32_t s_ids[kSlice];
+    __shared__ uint8_t s_x[kSlice];
+    __shared__ uint32_t s_wh[8][kMaxTX];
+    __shared__ uint32_t s_dstart[kMaxTX];
+    __shared__ uint32_t s_goff[kMaxTX];
+    __shared__ uint32_t s_warp[8];
+    SliceCtx c;
+    if (!slice_ctx(tb, Cv, slice_pre, n_slices, m2base, O1, c)) return;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < 8 * kMaxTX; k += kSortThreads) (&s_wh[0][0])[k] = 0;
+    __syncthreads();
+    uint32_t id[kSortItems], loc[kSortItems];
+    uint8_t xv[kSortItems];
+    const long long base = c.a + w * (kSortItems * 32);
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const long long idx = base + it * 32 + l;
+        const bool valid = idx < c.b;
+        const uint32_t d = valid ? (uint32_t)__ldg(xs1 + idx) : (uint32_t)kMaxTX;
+        id[it] = valid ? __ldg(ids1 + idx) : 0u;
+        xv[it] = (uint8_t)d;
+        const unsigned peers = warp_peers(d, 8);
+        const unsigned rank = __popc(peers & lanemask_lt());
+        const uint32_t before = valid ? s_wh[w][d] : 0u;
+        __syncwarp();
+        if (valid && rank == 0) s_wh[w][d] = before + __popc(peers);
+        __syncwarp();
+        loc[it] = valid ? before + rank : 0xffffffffu;
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;                 // kMaxTX == kSortThreads
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < 8; ++ww) {
+            uint32_t cc = s_wh[ww][d];
+            s_wh[ww][d] = run;
+            run += cc;
+        }
+        s_dstart[d] = block_excl_scan_256(run, s_warp);
+        s_goff[d] = d < c.TX ? O2[c.m2base + (uint32_t)d * c.ns + c.s] : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        if (loc[it] != 0xffffffffu) {
+            const uint32_t d = xv[it];
+            const uint32_t pos = s_dstart[d] + s_wh[w][d] + loc[it];
+            s_ids[pos] = id[it];
+            s_x[pos] = xv[it];
+        }
+    }
+    __syncthreads();
+    const int n_local = (int)(c.b - c.a);
+    const uint32_t tile0 = (uint32_t)(tb.v[c.v].tile_base + (c.r - tb.v[c.v].row_base) * c.TX);
+    for (int sl = threadIdx.x; sl < n_local; sl += kSortThreads) {
+        const uint32_t d = s_x[sl];
+        const uint32_t g = s_goff[d] + (uint32_t)(sl - s_dstart[d]);
+        const uint32_t gid = s_ids[sl];
+        vals[g] = gid;
+        if (keys) keys[g] = ((unsigned long long)(tile0 + d) << 32) | __float_as_uint(__ldg(depth + gid));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Workspace plan
 // ---------------------------------------------------------------------------
 struct Plan {
     size_t dk0, dk1, dv0, dv1, cnt, offs, tk0, tk1, tvs, hist, part, misc, bytes;
-    int nb_max;
+    size_t ids1, xs1, m1, o1, nsl, m2l, spre, m2b, m2, o2, tcnt;
+    long long m1n, m2n, slices_ub;
+    int nb_max, Cv, TXmax, TYmax;
+    bool direct;
 };
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static Plan make_plan(long long VN, long long cap) {
+static Plan make_plan(long long VN, long long cap, const TileBatch &tb) {
     Plan p;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
+    p.TXmax = p.TYmax = 0;
+    for (int v = 0; v < tb.n; ++v) {
+        p.TXmax = tb.v[v].TX > p.TXmax ? tb.v[v].TX : p.TXmax;
+        p.TYmax = tb.v[v].TY > p.TYmax ? tb.v[v].TY : p.TYmax;
+    }
+    p.direct = p.TXmax <= kMaxTX && p.TYmax <= kMaxTY;
+    p.Cv = (kChunksTotal + tb.n - 1) / tb.n;
     p.dk0 = take(4 * VN); p.dk1 = take(4 * VN); p.dv0 = take(4 * VN); p.dv1 = take(4 * VN);
-    p.cnt = take(4 * VN);
-    p.offs = take(8 * VN);
-    p.tk0 = take(4 * cap); p.tk1 = take(4 * cap); p.tvs = take(4 * cap);
-    long long nbc = (cap + kSortTile - 1) / kSortTile, nbv = (VN + kSortTile - 1) / kSortTile;
+    p.m1n = p.m2n = p.slices_ub = 0;
+    long long maxscan = VN;
+    if (p.direct) {
+        p.tk0 = p.tk1 = p.tvs = 0;
+        p.cnt = take(4 * VN);
+        p.offs = take(8 * (VN + 1));
+        p.ids1 = take(4 * (size_t)cap);
+        p.xs1 = take(2 * (size_t)cap);
+        p.m1n = (long long)tb.total_rows * p.Cv;
+        p.m1 = take(4 * (size_t)p.m1n);
+        p.o1 = take(8 * (size_t)(p.m1n + 1));
+        p.nsl = take(4 * (size_t)tb.total_rows);
+        p.m2l = take(4 * (size_t)tb.total_rows);
+        p.spre = take(4 * (size_t)(tb.total_rows + 1));
+        p.m2b = take(4 * (size_t)(tb.total_rows + 1));
+        p.slices_ub = (cap + kSlice - 1) / kSlice + tb.total_rows;
+        p.m2n = (long long)p.TXmax * p.slices_ub;
+        p.m2 = take(4 * (size_t)p.m2n);
+        p.o2 = take(4 * (size_t)(p.m2n + 1));
+        p.tcnt = take(4 * (size_t)tb.total_tiles);
+        maxscan = p.m1n > maxscan ? p.m1n : maxscan;
+        maxscan = p.m2n > maxscan ? p.m2n : maxscan;
+    } else {
+        p.ids1 = p.xs1 = p.m1 = p.o1 = p.nsl = p.m2l = p.spre = p.m2b = p.m2 = p.o2 = p.tcnt = 0;
+        p.cnt = take(4 * VN);
+        p.offs = take(8 * (VN + 1));
+        p.tk0 = take(4 * cap); p.tk1 = take(4 * cap); p.tvs = take(4 * cap);
+    }
+    long long nbc = p.direct ? 0 : (cap + kSortTile - 1) / kSortTile, nbv = (VN + kSortTile - 1) / kSortTile;
     p.nb_max = (int)(nbc > nbv ? nbc : nbv);
     if (p.nb_max < 1) p.nb_max = 1;
     p.hist = take(4 * (size_t)kRadix * p.nb_max);
-    long long maxscan = (long long)kRadix * p.nb_max > VN ? (long long)kRadix * p.nb_max : VN;
+    if ((long long)kRadix * p.nb_max > maxscan) maxscan = (long long)kRadix * p.nb_max;
+    if (maxscan < tb.total_tiles) maxscan = tb.total_tiles;
     p.part = take(8 * (size_t)((maxscan + kScanChunk - 1) / kScanChunk + 1));
     p.misc = take(64);
     p.bytes = o;
@@ -454,6 +826,7 @@ int make_tile_batch(const gs_camera *cams, int n_views, TileBatch *out) {
     if (!cams || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_ARG;
     out->n = n_views;
     long long tiles = 0, pix = 0;
+    int rows = 0;
     for (int v = 0; v < n_views; ++v) {
         const gs_camera &c = cams[v];
         if (c.W <= 0 || c.H <= 0 || c.W > 32767 * GS_TILE || c.H > 32767 * GS_TILE) return GS_ERR_ARG;
@@ -462,6 +835,8 @@ int make_tile_batch(const gs_camera *cams, int n_views, TileBatch *out) {
         t.TX = (c.W + GS_TILE - 1) / GS_TILE;
         t.TY = (c.H + GS_TILE - 1) / GS_TILE;
         t.tile_base = (int)tiles;
+        t.row_base = rows;
+        rows += t.TY;
         t.pix_base = pix;
         for (int k = 0; k < 3; ++k) t.bg[k] = c.bg[k];
         tiles += (long long)t.TX * t.TY;
@@ -469,6 +844,7 @@ int make_tile_batch(const gs_camera *cams, int n_views, TileBatch *out) {
         if (tiles > (1ll << 30)) return GS_ERR_ARG;
     }
     out->total_tiles = (int)tiles;
+    out->total_rows = rows;
     out->total_pix = pix;
     return GS_OK;
 }
@@ -479,12 +855,11 @@ using namespace gs;
 
 extern "C" int gs_bin_sort_workspace(int n_views, int N, long long capacity, const gs_camera *cams,
                                      size_t *bytes) {
-    (void)cams;
-    if (!bytes || n_views < 1 || n_views > GS_MAX_VIEWS || N < 0 || capacity < 0 ||
-        capacity > 0xF0000000ll)
-        return GS_ERR_ARG;
+    TileBatch tb;
+    if (!bytes || N < 0 || capacity < 0 || capacity > 0xF0000000ll) return GS_ERR_ARG;
+    if (make_tile_batch(cams, n_views, &tb) != GS_OK) return GS_ERR_ARG;
     long long VN = (long long)n_views * N;
-    *bytes = make_plan(VN, capacity).bytes;
+    *bytes = make_plan(VN, capacity, tb).bytes;
     return GS_OK;
 }
 
@@ -502,27 +877,25 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
     if (!aligned(d_workspace, 256) || !aligned(d_rect, 8) || !aligned(d_tile_ranges, 8))
         return GS_ERR_ARG;
     const long long VN = (long long)n_views * N;
-    Plan p = make_plan(VN, capacity);
+    if (VN > 0xF0000000ll) return GS_ERR_ARG;
+    Plan p = make_plan(VN, capacity, tb);
     if (workspace_bytes < p.bytes) return GS_ERR_CAPACITY;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char *ws = reinterpret_cast<char *>(d_workspace);
     uint32_t *dk0 = (uint32_t *)(ws + p.dk0), *dk1 = (uint32_t *)(ws + p.dk1);
     uint32_t *dv0 = (uint32_t *)(ws + p.dv0), *dv1 = (uint32_t *)(ws + p.dv1);
-    uint32_t *cnt = (uint32_t *)(ws + p.cnt);
-    unsigned long long *offs = (unsigned long long *)(ws + p.offs);
-    uint32_t *tk0 = (uint32_t *)(ws + p.tk0), *tk1 = (uint32_t *)(ws + p.tk1);
-    uint32_t *tvs = (uint32_t *)(ws + p.tvs);
     uint32_t *hist = (uint32_t *)(ws + p.hist);
     void *part = (void *)(ws + p.part);
     unsigned long long *total = (unsigned long long *)(ws + p.misc);
     uint32_t *count = (uint32_t *)(ws + p.misc + 8);
+    const short4 *rect = reinterpret_cast<const short4 *>(d_rect);
 
-    cudaMemsetAsync(d_tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)tb.total_tiles, st);
     if (VN == 0) {
+        cudaMemsetAsync(d_tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)tb.total_tiles, st);
         cudaMemsetAsync(d_n_instances, 0, sizeof(long long), st);
         return launch_status();
     }
-    // 1. depth order of the records (stable, 4 x 8 bits)
+    // 1. records in (depth bits, index) order: stable, 4 x 8 bits; culled last
     { k_depth_keys<<<cdiv(VN, 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0); count_launches(1); }
     uint32_t *ka = dk0, *kb = dk1, *va = dv0, *vb = dv1;
     for (int pass = 0; pass < 4; ++pass) {
@@ -530,13 +903,69 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
         uint32_t *t = ka; ka = kb; kb = t;
         t = va; va = vb; vb = t;
     }
+    if (n_views > 1) {
+        // stable partition by view: (view, depth, index) order
+        { k_view_keys<<<cdiv(VN, 256), 256, 0, st>>>(va, VN, (uint32_t)N, ka); count_launches(1); }
+        int vbits = 1;
+        while ((1 << vbits) < n_views) ++vbits;
+        radix_pass(ka, va, kb, vb, nullptr, (uint32_t)VN, VN, 0, vbits, false, hist, (uint32_t *)part, st);
+        uint32_t *t = va; va = vb; vb = t;
+    }
     const uint32_t *order = va;
-    // 2. offsets of each record's instances in depth order
+
+    if (p.direct) {
+        uint32_t *ids1 = (uint32_t *)(ws + p.ids1);
+        uint16_t *xs1 = (uint16_t *)(ws + p.xs1);
+        uint32_t *M1 = (uint32_t *)(ws + p.m1);
+        unsigned long long *O1 = (unsigned long long *)(ws + p.o1);
+        uint32_t *nsl = (uint32_t *)(ws + p.nsl), *m2l = (uint32_t *)(ws + p.m2l);
+        uint32_t *spre = (uint32_t *)(ws + p.spre), *m2b = (uint32_t *)(ws + p.m2b);
+        uint32_t *M2 = (uint32_t *)(ws + p.m2), *O2 = (uint32_t *)(ws + p.o2);
+        uint32_t *tcnt = (uint32_t *)(ws + p.tcnt);
+        const int R = tb.total_rows;
+        uint32_t *cnt = (uint32_t *)(ws + p.cnt);
+        unsigned long long *offs = (unsigned long long *)(ws + p.offs);
+        { k_gather_counts<<<cdiv(VN, 256), 256, 0, st>>>(order, d_touched, VN, cnt); count_launches(1); }
+        exclusive_scan<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, offs + VN, st);
+        const int nchunks = n_views * p.Cv;
+        const int p1_blocks = cdiv(nchunks, kP1Warps);
+        const size_t p1_smem = sizeof(uint32_t) * (size_t)(p.TYmax + 1) * kP1Warps;
+        if (p1_smem > 48 * 1024) {
+            cudaFuncSetAttribute(k_p1_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem);
+            cudaFuncSetAttribute(k_p1_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem);
+        }
+        { k_p1_count<<<p1_blocks, 32 * kP1Warps, p1_smem, st>>>(tb, N, p.Cv, p.TYmax, order, rect, offs, M1); count_launches(1); }
+        exclusive_scan<uint32_t, unsigned long long>(M1, O1, p.m1n, (unsigned long long *)part, O1 + p.m1n, st);
+        { k_finish_count<<<1, 1, 0, st>>>(O1 + p.m1n, capacity, d_n_instances, count, d_err_word); count_launches(1); }
+        { k_p1_place<<<p1_blocks, 32 * kP1Warps, p1_smem, st>>>(tb, N, p.Cv, p.TYmax, order, rect, offs, O1,
+                                                               O1 + p.m1n, capacity, ids1, xs1); count_launches(1); }
+        { k_p2_rows<<<cdiv(R, 256), 256, 0, st>>>(tb, p.Cv, O1, O1 + p.m1n, capacity, nsl, m2l); count_launches(1); }
+        exclusive_scan<uint32_t, uint32_t>(nsl, spre, R, (uint32_t *)part, spre + R, st);
+        exclusive_scan<uint32_t, uint32_t>(m2l, m2b, R, (uint32_t *)part, m2b + R, st);
+        cudaMemsetAsync(M2, 0, sizeof(uint32_t) * (size_t)p.m2n, st);
+        cudaMemsetAsync(tcnt, 0, sizeof(uint32_t) * (size_t)tb.total_tiles, st);
+        const int sgrid = (int)p.slices_ub;
+        { k_p2_count<<<sgrid, 256, 0, st>>>(tb, p.Cv, spre, nsl, m2b, O1, xs1, M2, tcnt); count_launches(1); }
+        exclusive_scan<uint32_t, uint32_t>(M2, O2, p.m2n, (uint32_t *)part, O2 + p.m2n, st);
+        { k_p2_ranges<<<cdiv(tb.total_tiles, 256), 256, 0, st>>>(tb, nsl, m2b, O2, tcnt,
+                                                                reinterpret_cast<uint2 *>(d_tile_ranges)); count_launches(1); }
+        if (capacity > 0)
+            { k_p2_place<<<sgrid, kSortThreads, 0, st>>>(tb, p.Cv, spre, nsl, m2b, O1, O2, ids1, xs1, d_depth, d_vals,
+                                                         reinterpret_cast<unsigned long long *>(d_keys)); count_launches(1); }
+        return launch_status();
+    }
+
+    // Views wider than kMaxTX or taller than kMaxTY tiles: emit in depth
+    // order, then a stable LSD radix sort on the tile id.
+    uint32_t *cnt = (uint32_t *)(ws + p.cnt);
+    unsigned long long *offs = (unsigned long long *)(ws + p.offs);
+    uint32_t *tk0 = (uint32_t *)(ws + p.tk0), *tk1 = (uint32_t *)(ws + p.tk1);
+    uint32_t *tvs = (uint32_t *)(ws + p.tvs);
+    cudaMemsetAsync(d_tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)tb.total_tiles, st);
     { k_gather_counts<<<cdiv(VN, 256), 256, 0, st>>>(order, d_touched, VN, cnt); count_launches(1); }
     exclusive_scan<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, total, st);
     { k_finish_count<<<1, 1, 0, st>>>(total, capacity, d_n_instances, count, d_err_word); count_launches(1); }
     if (capacity == 0) return launch_status();
-    // 3. emission in depth order; 4. stable sort by tile id
     int bits = 1;
     while ((1ll << bits) < tb.total_tiles) ++bits;
     int passes = (bits + 7) / 8;
@@ -544,8 +973,7 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
     uint32_t *V[2];
     V[passes % 2] = d_vals;
     V[(passes + 1) % 2] = tvs;
-    { k_emit<<<cdiv(VN, 256), 256, 0, st>>>(tb, N, VN, order, offs, reinterpret_cast<const short4 *>(d_rect),
-                                         d_touched, capacity, K[0], V[0]); count_launches(1); }
+    { k_emit<<<cdiv(VN, 256), 256, 0, st>>>(tb, N, VN, order, offs, rect, d_touched, capacity, K[0], V[0]); count_launches(1); }
     int done = 0;
     for (int pass = 0; pass < passes; ++pass) {
         int b = (bits - done + (passes - pass) - 1) / (passes - pass);

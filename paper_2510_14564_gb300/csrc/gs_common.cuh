@@ -32,6 +32,7 @@ struct ViewGeom {          // what the projection needs
 struct ViewTiles {         // what binning and rendering need
     int W, H, TX, TY;
     int tile_base;         // first global tile id of the view
+    int row_base;          // first global tile row of the view
     long long pix_base;    // first pixel of the view in per-pixel maps
     float bg[3];
 };
@@ -44,6 +45,7 @@ struct GeomBatch {
 struct TileBatch {
     int n;
     int total_tiles;
+    int total_rows;
     long long total_pix;
     ViewTiles v[GS_MAX_VIEWS];
 };
@@ -164,6 +166,18 @@ int make_geom_batch(const gs_camera *cams, int n_views, GeomBatch *out);
 size_t radix_sort_workspace(long long n);
 void radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *vout, long long n, int bits, void *scratch,
                       cudaStream_t st);
+
+// Lanes of the warp whose digit equals this lane's: one ballot per digit bit
+// (bits <= 9; the sentinel digit 1 << bits marks an invalid lane).
+__device__ __forceinline__ unsigned warp_peers(uint32_t d, int bits) {
+    unsigned peers = 0xffffffffu;
+    for (int b = 0; b <= bits; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
 
 // Warp helpers
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31; }

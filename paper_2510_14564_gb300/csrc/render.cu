@@ -23,6 +23,13 @@ __device__ __forceinline__ unsigned lanemask_lt_r() {
     return m;
 }
 
+// 1/x on the MUFU unit (PTX rcp.approx, flush-to-zero); x >= 0.01 here.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -262,10 +269,11 @@ __global__ void __launch_bounds__(kTilePix) k_render_bwd(TileBatch tb, const uin
                     contrib = alpha >= kAlphaMin;
                     if (contrib) {
                         const float om = 1.0f - alpha;
-                        const float Tb = T / om;
+                        const float rom = rcp_approx(om);
+                        const float Tb = T * rom;
                         const float w = alpha * Tb;
                         gr = G0 * w; gg = G1 * w; gb = G2 * w;
-                        const float dal = Tb * (G0 * (b.z - R0) + G1 * (b.w - R1) + G2 * (cc.x - R2)) - bgdot / om;
+                        const float dal = Tb * (G0 * (b.z - R0) + G1 * (b.w - R1) + G2 * (cc.x - R2)) - bgdot * rom;
                         R0 = fmaf(b.z, alpha, om * R0);
                         R1 = fmaf(b.w, alpha, om * R1);
                         R2 = fmaf(cc.x, alpha, om * R2);
@@ -283,15 +291,37 @@ __global__ void __launch_bounds__(kTilePix) k_render_bwd(TileBatch tb, const uin
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
-                    gu = warp_sum(gu); gv = warp_sum(gv); gA = warp_sum(gA); gB = warp_sum(gB);
-                    gC = warp_sum(gC); go = warp_sum(go); gr = warp_sum(gr); gg = warp_sum(gg);
-                    gb = warp_sum(gb);
-                    if ((threadIdx.x & 31) == 0) {
-                        float4 *dst = reinterpret_cast<float4 *>(grad2d + 12ll * __float_as_uint(cc.z));
-                        atomicAdd(dst, make_float4(gu, gv, gA, gB));
-                        atomicAdd(dst + 1, make_float4(gC, go, gr, gg));
-                        atomicAdd(reinterpret_cast<float *>(dst + 2), gb);
+                    // eight values by a halving butterfly: lane l ends with the
+                    // warp sum of value (l >> 2), the ninth by a full butterfly
+                    const int l = threadIdx.x & 31;
+                    float v8[8] = {gu, gv, gA, gB, gC, go, gr, gg};
+                    const bool b4 = l & 16, b3 = l & 8, b2 = l & 4;
+                    float h4[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float send = b4 ? v8[j] : v8[j + 4];
+                        const float keep = b4 ? v8[j + 4] : v8[j];
+                        h4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
                     }
+                    float h2[2];
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const float send = b3 ? h4[j] : h4[j + 2];
+                        const float keep = b3 ? h4[j + 2] : h4[j];
+                        h2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                    }
+                    float h1;
+                    {
+                        const float send = b2 ? h2[0] : h2[1];
+                        const float keep = b2 ? h2[1] : h2[0];
+                        h1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                    }
+                    h1 += __shfl_xor_sync(0xffffffffu, h1, 2);
+                    h1 += __shfl_xor_sync(0xffffffffu, h1, 1);
+                    gb = warp_sum(gb);
+                    float *dst = grad2d + 12ll * __float_as_uint(cc.z);
+                    if ((l & 3) == 0) atomicAdd(dst + (l >> 2), h1);
+                    if (l == 0) atomicAdd(dst + 8, gb);
                 }
             }
         }

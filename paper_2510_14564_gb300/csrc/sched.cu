@@ -196,6 +196,87 @@ __global__ void k_cost_keys(const float *__restrict__ cost, int n, uint32_t *__r
     vals[i] = (uint32_t)i;
 }
 
+// Work orders of at most kSmallOrder tiles: one CTA sorts the whole array in
+// shared memory, stable LSD radix (4 x 8 bits), each warp owning a
+// contiguous segment so that per-warp digit counts give stable ranks.
+constexpr int kSmallOrder = 8192;
+constexpr int kOrderThreads = 1024;
+
+__device__ __forceinline__ unsigned lanemask_lt_s() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void __launch_bounds__(kOrderThreads) k_order_small(const float *__restrict__ cost, int n,
+                                                               int32_t *__restrict__ order) {
+    extern __shared__ uint32_t s_mem[];
+    uint32_t *K0 = s_mem, *V0 = K0 + kSmallOrder, *K1 = V0 + kSmallOrder, *V1 = K1 + kSmallOrder;
+    uint32_t *rank = V1 + kSmallOrder;               // [kSmallOrder]
+    uint32_t *wh = rank + kSmallOrder;               // [32 warps][256]
+    __shared__ uint32_t s_dstart[256];
+    __shared__ uint32_t s_tot[256];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < n; i += kOrderThreads) {
+        uint32_t b = __float_as_uint(cost[i]);
+        uint32_t asc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);   // order-preserving map
+        K0[i] = ~asc;                                                 // descending cost
+        V0[i] = (uint32_t)i;
+    }
+    const int seg = ((n + 31) / 32 + 31) / 32 * 32;  // items per warp segment (multiple of 32)
+    uint32_t *ka = K0, *va = V0, *kb = K1, *vb = V1;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 8 * pass;
+        for (int k = threadIdx.x; k < 32 * 256; k += kOrderThreads) wh[k] = 0;
+        __syncthreads();
+        for (int j = 0; j < seg; j += 32) {
+            const int i = w * seg + j + l;
+            const bool valid = i < n;
+            const uint32_t d = valid ? (ka[i] >> shift) & 255u : 256u;
+            const unsigned peers = warp_peers(d, 8);
+            const uint32_t before = valid ? wh[w * 256 + d] : 0u;
+            __syncwarp();
+            if (valid && (peers & lanemask_lt_s()) == 0) wh[w * 256 + d] = before + __popc(peers);
+            __syncwarp();
+            if (valid) rank[i] = before + __popc(peers & lanemask_lt_s());
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+            for (int ww = 0; ww < 32; ++ww) {
+                uint32_t c = wh[ww * 256 + d];
+                wh[ww * 256 + d] = run;
+                run += c;
+            }
+            s_tot[d] = run;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {                      // exclusive scan of 256 totals, 8 per lane
+            uint32_t loc[8], sum = 0;
+            for (int q = 0; q < 8; ++q) { loc[q] = s_tot[8 * l + q]; sum += loc[q]; }
+            uint32_t inc = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (l >= o) inc += t;
+            }
+            uint32_t run = inc - sum;
+            for (int q = 0; q < 8; ++q) { s_dstart[8 * l + q] = run; run += loc[q]; }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += kOrderThreads) {
+            const uint32_t d = (ka[i] >> shift) & 255u;
+            const uint32_t pos = s_dstart[d] + wh[(i / seg) * 256 + d] + rank[i];
+            kb[pos] = ka[i];
+            vb[pos] = va[i];
+        }
+        __syncthreads();
+        uint32_t *t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+    }
+    for (int i = threadIdx.x; i < n; i += kOrderThreads) order[i] = (int32_t)va[i];
+}
+
 __global__ void k_range_cost(const uint2 *__restrict__ r, int n, float *__restrict__ cost) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) { uint2 v = r[i]; cost[i] = (float)(v.y - v.x); }
@@ -296,6 +377,12 @@ extern "C" int gs_sched_order(const float *d_cost, int n, int32_t *d_order, void
     if (workspace_bytes < radix_sort_workspace(n)) return GS_ERR_CAPACITY;
     if (n == 0) return GS_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (n <= kSmallOrder) {
+        const size_t smem = sizeof(uint32_t) * (5 * (size_t)kSmallOrder + 32 * 256);
+        cudaFuncSetAttribute(k_order_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        { k_order_small<<<1, kOrderThreads, smem, st>>>(d_cost, n, d_order); count_launches(1); }
+        return launch_status();
+    }
     char *ws = reinterpret_cast<char *>(d_workspace);
     size_t al = ((size_t)n * 4 + 255) & ~(size_t)255;
     uint32_t *k0 = (uint32_t *)ws, *v0 = (uint32_t *)(ws + al);

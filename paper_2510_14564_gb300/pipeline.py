@@ -54,7 +54,7 @@ class Schedule:
     (persistent, most instances first) or 'learned' (persistent, longest
     predicted time first, MLP trained on measured tile times)."""
     mode: str = "raster"
-    feature_cap: int = 2048
+    feature_cap: int = 256
     mlp_lr: float = 3e-3
     train_every: int = 1
     seed: int = 0
@@ -73,7 +73,7 @@ class Frame:
         self.sh_dtype = sh_dtype
         self.sched = schedule or Schedule()
         d = self.dev
-        VN = self.V * self.N
+        VN = max(1, self.V * self.N)       # non-empty buffers even for N = 0
         self.T = sum(c.n_tiles for c in self.cams)
         self.P = sum(c.W * c.H for c in self.cams)
         nb = L.SPLAT_BYTES[rgb_dtype]
@@ -93,7 +93,7 @@ class Frame:
         self.dimg = torch.empty(3 * self.P, dtype=torch.float32, device=d)
         self.loss = torch.zeros(1, dtype=torch.float32, device=d)
         self.grad2d = torch.empty(VN * 12, dtype=torch.float32, device=d)
-        self.dparams = torch.empty(PARAM_FLOATS * self.N, dtype=torch.float32, device=d)
+        self.dparams = torch.empty(PARAM_FLOATS * max(1, self.N), dtype=torch.float32, device=d)
         self.capacity = 0
         self.vals = None
         self.keys = None
@@ -149,7 +149,7 @@ class Frame:
                           self.ranges, None, self.n_inst, self.ws, self.err)
             need = int(self.n_inst.item())
             self.reserve(int(need * 1.25) + 1024, with_keys=want_keys)
-            self.err.zero_()
+            self.err.bitwise_and_(~L.GS_EW_CAPACITY)      # the sizing pass overflowed on purpose
         elif want_keys and self.keys is None:
             self.reserve(self.capacity, with_keys=True)
         L.gs_bin_sort(self.cams, self.N, self.depth, self.rect, self.touched, self.capacity, self.vals,

@@ -1,0 +1,112 @@
+"""Parity at the benchmark's full size (3M skewed Gaussians, 1600x1060), in
+the launch configuration bench.py times, on outputs the oracle computes one
+by one: every Gaussian's discrete path, every tile's count, the full lists of
+sampled tiles, and the image and gradients of the centre 64x64 crop."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2510_14564_gb300 import _lib as L
+from paper_2510_14564_gb300 import pipeline as P
+from paper_2510_14564_gb300 import scenes as S
+from tests._util import GRAD_RTOL, IMG_ATOL, rel_check
+
+pytestmark = pytest.mark.gpu
+
+WORKLOAD = "skewed-3M-1600x1060"
+
+
+@pytest.fixture(scope="module")
+def full():
+    scene, cams = S.make_workload(WORKLOAD, seed=0)
+    cam = cams[0]
+    kp = O.keypath(cam, scene)
+    pr = O.project(cam, scene, kp)
+    return scene, cam, kp, pr
+
+
+def _trainer(scene, cams, mode, dtype):
+    tgt = torch.from_numpy(S.random_image(cams[0].W, cams[0].H, seed=1).ravel()).cuda()
+    return P.Trainer(cams, P.to_device_params(scene), scene.n, tgt, rgb_dtype=dtype,
+                     sh_storage=dtype, schedule=P.Schedule(mode=mode))
+
+
+def _crop(cam, size=64):
+    x0, y0 = (cam.W - size) // 2 // 16 * 16, (cam.H - size) // 2 // 16 * 16
+    return x0, y0, x0 + size, y0 + size
+
+
+def test_fullsize_fp32_count_path(full):
+    scene, cam, kp, pr = full
+    tr = _trainer(scene, [cam], "count", L.GS_F32)
+    f = tr.frame
+    pk = tr.params_for_kernels()
+    f.forward(pk)
+    torch.cuda.synchronize()
+    assert f.check_errors() == 0
+    # every Gaussian's discrete path
+    assert np.array_equal(f.touched.cpu().numpy(), kp["touched"])
+    assert np.array_equal(f.rect.cpu().numpy().reshape(-1, 4), kp["rect"])
+    # every tile's count; sampled tiles' full lists
+    counts = O.tile_counts(cam, kp)
+    rg = f.ranges.cpu().numpy().reshape(-1, 2).astype(np.int64)
+    assert int(f.n_inst.item()) == int(counts.sum())
+    assert np.array_equal(rg[:, 1] - rg[:, 0], counts)
+    vals = f.vals.cpu().numpy().view(np.uint32)
+    rng = np.random.default_rng(0)
+    sample = set(rng.choice(cam.n_tiles, 8, replace=False).tolist())
+    sample |= {int(np.argmax(counts)), 0, cam.n_tiles - 1, cam.tiles_x - 1}
+    for t in sorted(sample):
+        ids = O.tile_list(kp, t % cam.tiles_x, t // cam.tiles_x)
+        assert np.array_equal(vals[rg[t, 0]:rg[t, 1]], ids), t
+    # the centre crop: image and gradients
+    win = _crop(cam)
+    r = O.render(cam, kp, pr, window=win)
+    x0, y0, x1, y1 = win
+    ok = r["flag"][y0:y1, x0:x1] == 0
+    assert ok.mean() > 0.95
+    img = f.image(0).cpu().numpy()[:, y0:y1, x0:x1]
+    assert np.abs(img - r["img"][:, y0:y1, x0:x1])[:, ok].max() <= IMG_ATOL
+    npm = f.pixel_map(f.n_proc).cpu().numpy()[y0:y1, x0:x1]
+    assert np.array_equal(npm[ok], r["n_proc"][y0:y1, x0:x1][ok])
+    d = np.zeros((3, cam.H, cam.W), np.float32)
+    dc = S.random_cotangent((3, y1 - y0, x1 - x0), seed=8) * 1e-3
+    dc[:, ~ok] = 0.0
+    d[:, y0:y1, x0:x1] = dc
+    g = f.backward(pk, torch.from_numpy(d.ravel()).cuda()).cpu().numpy()
+    g2 = O.render_bwd(cam, kp, pr, d.astype(np.float64), window=win)
+    gref = O.project_bwd(cam, scene, kp, g2)
+    n = scene.n
+    hit = np.abs(g2).sum(1) > 0
+    assert hit.sum() > 100
+    for name, (a, b) in dict(means=(0, 3), log_scales=(3, 6), quats=(6, 10), logits=(10, 11),
+                             sh=(11, 59)).items():
+        gg = g[a * n:b * n].reshape(n, -1)
+        gr = gref[a * n:b * n].reshape(n, -1)
+        rel_check(gg[hit], gr[hit], GRAD_RTOL, name)
+        assert np.all(gg[~hit] == 0.0), name
+
+
+def test_fullsize_bf16_learned_path(full):
+    scene, cam, kp, _ = full
+    tr = _trainer(scene, [cam], "learned", L.GS_BF16)
+    for _ in range(3):                      # the benchmark's configuration, a few steps in
+        tr.frame.forward(tr.params_for_kernels(), timing=True)
+        tr.frame.train_scheduler()
+    tr.frame.use_learned = True
+    tr.frame.forward(tr.params_for_kernels(), timing=True)
+    torch.cuda.synchronize()
+    assert tr.frame.check_errors() == 0
+    sc16 = scene.subset(np.arange(scene.n))
+    sc16.sh = torch.from_numpy(scene.sh).to(torch.bfloat16).float().numpy()
+    kp16 = O.keypath(cam, sc16)
+    pr16 = O.project(cam, sc16, kp16)
+    win = _crop(cam)
+    x0, y0, x1, y1 = win
+    r = O.render(cam, kp16, pr16, window=win)
+    ok = r["flag"][y0:y1, x0:x1] == 0
+    img = tr.frame.image(0).cpu().numpy()[:, y0:y1, x0:x1]
+    ref = r["img"][:, y0:y1, x0:x1]
+    assert np.all(np.abs(img - ref)[:, ok] <= (2.0 ** -8 * ref + IMG_ATOL)[:, ok])

@@ -1,0 +1,156 @@
+"""The learned tile-cost scheduler: features, MLP kernels against the oracle,
+work orders, schedule-independent images, and the gain of the trained MLP."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2510_14564_gb300 import _lib as L
+from paper_2510_14564_gb300 import pipeline as P
+from paper_2510_14564_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _frame(scene, cams, schedule=None, rgb=L.GS_F32):
+    params = P.to_device_params(scene)
+    views = P.param_views(params, scene.n)
+    fr = P.Frame(cams, scene.n, rgb_dtype=rgb, schedule=schedule)
+    fr.project(views)
+    fr.bin_sort()
+    return fr, views
+
+
+def test_tile_features_match_oracle():
+    scene = S.skewed_scene(20_000, 0)
+    cam = S.front_camera(200, 136)
+    fr, _ = _frame(scene, [cam])
+    cap = 512
+    L.gs_tile_features(fr.cams, fr.ranges, fr.vals, fr.splats, fr.rgb_dtype, cap, fr.feats)
+    got = fr.feats.cpu().numpy().reshape(-1, 8)
+    kp = O.keypath(cam, scene)
+    pr = O.project(cam, scene, kp)
+    for t in range(cam.n_tiles):
+        ref = O.tile_features(cam, kp, pr, t % cam.tiles_x, t // cam.tiles_x, cap)
+        assert got[t, 0] == pytest.approx(ref[0], rel=1e-6, abs=1e-6)
+        assert np.allclose(got[t, 1:5], ref[1:5], rtol=1e-4, atol=1e-6), (t, got[t], ref)
+        assert got[t, 5] == pytest.approx(ref[5], rel=1e-3, abs=1e-3)
+        assert got[t, 6] == ref[6]
+        assert got[t, 7] == pytest.approx(ref[7], rel=1e-6)
+
+
+def test_mlp_predict_and_grad_match_oracle():
+    rng = np.random.default_rng(4)
+    n = 1000
+    f = rng.normal(size=(n, 8)).astype(np.float32)
+    tgt = rng.normal(8, 1, size=n).astype(np.float32)
+    w = rng.normal(0, 0.3, 321).astype(np.float32)
+    w16 = torch.from_numpy(w).cuda().half()
+    fd = torch.from_numpy(f).cuda()
+    pred = torch.empty(n, device="cuda")
+    L.gs_mlp_predict(w16, fd, n, pred)
+    wr = w16.float().cpu().numpy().astype(np.float64)
+    unpack = lambda a: (a[:256].reshape(32, 8), a[256:288], a[288:320], a[320:321])
+    ref = O.mlp_fwd(f, *unpack(wr))
+    assert np.allclose(pred.cpu().numpy(), ref, rtol=1e-5, atol=1e-5)
+    w32 = torch.from_numpy(w).cuda()
+    g = torch.empty(321, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    L.gs_mlp_grad(w32, fd, None, torch.from_numpy(tgt).cuda(), n, g, loss)
+    lo, gr = O.mlp_loss_grad(f, tgt, *unpack(w.astype(np.float64)))
+    assert loss.item() == pytest.approx(lo, rel=1e-4)
+    assert np.allclose(g.cpu().numpy(), gr, rtol=1e-3, atol=1e-4 * np.abs(gr).max())
+
+
+def test_order_is_a_stable_descending_permutation():
+    rng = np.random.default_rng(5)
+    n = 5000
+    cost = rng.integers(0, 50, n).astype(np.float32) - 20.0     # ties and negatives
+    c = torch.from_numpy(cost).cuda()
+    order = torch.empty(n, dtype=torch.int32, device="cuda")
+    ws = torch.empty(L.gs_sched_order_workspace(n) // 4 + 64, device="cuda")
+    L.gs_sched_order(c, n, order, ws)
+    o = order.cpu().numpy()
+    assert np.array_equal(o, np.lexsort((np.arange(n), -cost)))
+
+
+@pytest.mark.parametrize("mode", ["count", "learned"])
+def test_images_identical_across_schedules(mode):
+    scene = S.skewed_scene(60_000, 2)
+    cams = S.ring_cameras(4, S.uneven_sizes(4, (200, 150), (320, 240)))
+    ref, views = _frame(scene, cams, P.Schedule("raster"))
+    ref.render()
+    fr, _ = _frame(scene, cams, P.Schedule(mode))
+    fr.render(timing=True)
+    torch.cuda.synchronize()
+    assert torch.equal(ref.img, fr.img)
+    assert torch.equal(ref.T_final, fr.T_final)
+    assert torch.equal(ref.n_proc, fr.n_proc)
+    d = torch.from_numpy(S.random_cotangent((3 * ref.P,), seed=2) * 1e-3).cuda()
+    g0 = ref.backward(views, d).clone()
+    g1 = fr.backward(views, d)
+    scale = g0.abs().max()
+    assert (g0 - g1).abs().max() <= 1e-5 * scale                # atomics: order of additions only
+    assert fr.check_errors() == 0
+
+
+def _spearman(a, b):
+    ra = np.argsort(np.argsort(a))
+    rb = np.argsort(np.argsort(b))
+    return np.corrcoef(ra, rb)[0, 1]
+
+
+def test_learned_cost_model_gain():
+    """After training on the renderer's own tile times, the MLP ranks tile
+    costs better than the instance count does; the render makespans of the
+    raster, count and learned orders, and the cost of computing each order,
+    are reported."""
+    scene = S.skewed_scene(300_000, 0)
+    cams = S.ring_cameras(8, S.uneven_sizes(8, (400, 300), (960, 540)))
+    fr, _ = _frame(scene, cams, P.Schedule("learned", mlp_lr=3e-3))
+    fr.use_learned = False
+    for _ in range(300):                                     # train on measured tile times
+        fr.render(timing=True)
+        fr.train_scheduler()
+    fr.use_learned = True
+    fr.render(timing=True)
+    torch.cuda.synchronize()
+    ns = fr.tile_ns.cpu().numpy().astype(np.float64)
+    live = ns > 0
+    pred = fr.pred.cpu().numpy()
+    count = fr.feats.cpu().numpy().reshape(-1, 8)[:, 0]
+    rho_learned = _spearman(pred[live], ns[live])
+    rho_count = _spearman(count[live], ns[live])
+    print(f"\nSpearman vs measured tile time: learned {rho_learned:.3f}, count {rho_count:.3f}")
+    assert rho_learned > rho_count
+
+    def timed(fn, reps=7):
+        best = 1e9
+        for _ in range(reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            best = min(best, s.elapsed_time(e))
+        return best
+
+    orders = {}
+    fr.use_learned = False
+    t_order_count = timed(lambda: fr._sched_fwd())
+    orders["count"] = fr.order_f.clone()
+    fr.use_learned = True
+    t_order_learned = timed(lambda: fr._sched_fwd())
+    orders["learned"] = fr.order_f.clone()
+
+    def render(order):
+        s = None if order is None else {"mode": L.GS_SCHED_ORDER, "order": order, "queue": fr.queue}
+        L.gs_render_fwd(fr.cams, fr.ranges, fr.vals, fr.splats, fr.rgb_dtype, s, fr.img, fr.T_final,
+                        fr.n_proc, fr.tile_nproc, None, fr.err)
+
+    t = {k: timed(lambda o=o: render(o)) for k, o in (("raster", None), ("count", orders["count"]),
+                                                      ("learned", orders["learned"]))}
+    print(f"render makespan (ms): raster {t['raster']:.3f}, count order {t['count']:.3f}, "
+          f"learned order {t['learned']:.3f}; order cost: count {t_order_count:.3f}, "
+          f"learned {t_order_learned:.3f}")
