@@ -146,6 +146,28 @@ int gs_bin_sort(const gs_camera *cams, int n_views, int N, const float *d_depth,
                 long long *d_n_instances, void *d_workspace, size_t workspace_bytes,
                 int *d_err_word, gs_stream_t stream);
 
+/* gs_bin_sort without a workspace argument: no counterpart in the paper.
+ * For callers that cannot allocate device memory themselves (a runtime that
+ * owns all device memory through its own pool, a steady-state loop that must
+ * not call cudaMalloc/cudaFree because they can synchronise the device, an
+ * embedding handed only its inputs and outputs).  The call allocates nothing:
+ * its scratch is a file-scope device array of GS_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading this library holds until the process exits.  The caller
+ * still passes every input and output, with the meaning gs_bin_sort gives
+ * them.  A problem whose gs_bin_sort_workspace exceeds that size is rejected
+ * with GS_ERR_CAPACITY before any work is queued.  The first call on a device
+ * looks up the array's device address on the current device (once per
+ * device); make that first call before any stream capture.  All calls share
+ * the one array, which keeps the previous call's contents (the call clears
+ * what it needs zeroed), so calls that overlap on the GPU (other streams,
+ * other host threads) race on it and must be serialised by the caller. */
+#define GS_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define GS_NOALLOC_MAX_DEVICES 64
+int gs_bin_sort_noalloc(const gs_camera *cams, int n_views, int N, const float *d_depth,
+                        const int16_t *d_rect, const int32_t *d_touched, long long capacity,
+                        uint32_t *d_vals, uint32_t *d_tile_ranges, uint64_t *d_keys,
+                        long long *d_n_instances, int *d_err_word, gs_stream_t stream);
+
 /* Work schedule for the render kernels (a8).  mode GS_SCHED_RASTER: one CTA
  * per tile in tile order.  GS_SCHED_ORDER: persistent CTAs take tiles from
  * d_order (a permutation of the T global tiles) through an atomic queue

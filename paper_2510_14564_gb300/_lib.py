@@ -24,7 +24,7 @@ GS_MAX_VIEWS = 64
 SPLAT_BYTES = {GS_F32: 48, GS_BF16: 32, GS_F16: 32}
 
 # Every symbol include/gs103.h declares.
-EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort",
+EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_bin_sort_noalloc",
            "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_project_bwd", "gs_adam_step",
            "gs_adam_flat", "gs_tile_features", "gs_mlp_predict", "gs_mlp_grad",
            "gs_mlp_train_step", "gs_int_cost", "gs_range_cost", "gs_sched_order_workspace", "gs_sched_order"]
@@ -73,6 +73,7 @@ def lib():
                                  VP, VP, VP]
         L.gs_bin_sort_workspace.argtypes = [I32, I32, I64, P(GsCamera), P(SZ)]
         L.gs_bin_sort.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, I64, VP, VP, VP, VP, VP, SZ, VP, VP]
+        L.gs_bin_sort_noalloc.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, I64, VP, VP, VP, VP, VP, VP]
         L.gs_render_fwd.argtypes = [P(GsCamera), I32, VP, VP, VP, I32, P(GsSchedule), VP, VP, VP, VP,
                                     VP, VP, VP]
         L.gs_l1_loss.argtypes = [I64, VP, VP, VP, VP, VP]
@@ -175,6 +176,15 @@ def gs_bin_sort(cams, N, depth, rect, touched, capacity, vals, tile_ranges, keys
                             int(capacity), ptr(vals), ptr(tile_ranges), ptr(keys), ptr(n_instances),
                             ptr(workspace), workspace.numel() * workspace.element_size(),
                             ptr(err_word), stream_ptr(stream)), "gs_bin_sort")
+
+
+def gs_bin_sort_noalloc(cams, N, depth, rect, touched, capacity, vals, tile_ranges, keys, n_instances,
+                        err_word, stream=None):
+    ca = camera_array(cams)
+    check(lib().gs_bin_sort_noalloc(ca, len(cams), int(N), ptr(depth), ptr(rect), ptr(touched),
+                                    int(capacity), ptr(vals), ptr(tile_ranges), ptr(keys),
+                                    ptr(n_instances), ptr(err_word), stream_ptr(stream)),
+          "gs_bin_sort_noalloc")
 
 
 def _sched(sched):

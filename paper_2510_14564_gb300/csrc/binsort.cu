@@ -12,6 +12,8 @@
 // Stability carries the depth order (and the index order of equal depths)
 // through step 4, so the result equals the 64-bit sort.  Tile ranges come
 // from the boundaries of the sorted tile ids.
+#include <mutex>
+
 #include "gs_common.cuh"
 
 namespace gs {
@@ -987,4 +989,50 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
         { k_keys64<<<cdiv(capacity, 256), 256, 0, st>>>(tkeys, d_vals, d_depth, count,
                                                      reinterpret_cast<unsigned long long *>(d_keys)); count_launches(1); }
     return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// gs_bin_sort_noalloc: gs_bin_sort with its scratch in a fixed device array
+// ---------------------------------------------------------------------------
+// Some callers cannot allocate device memory: a runtime that owns every
+// device allocation through its own pool and forbids others, an engine that
+// must not call cudaMalloc/cudaFree in its steady-state loop (both can
+// synchronise the device), or an embedding that is handed only its input and
+// output buffers.  For them the scratch of the binning sort lives in this
+// file-scope array, reserved on every GPU that loads the library until the
+// process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GS_NOALLOC_SCRATCH_BYTES];
+
+// Device addresses of g_noalloc_scratch, one per device ordinal.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// with cudaGetSymbolAddress on the device that is current.
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[GS_NOALLOC_MAX_DEVICES];
+
+static int noalloc_scratch(void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= GS_NOALLOC_MAX_DEVICES) return GS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GS_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return GS_OK;
+}
+
+extern "C" int gs_bin_sort_noalloc(const gs_camera *cams, int n_views, int N, const float *d_depth,
+                                   const int16_t *d_rect, const int32_t *d_touched, long long capacity,
+                                   uint32_t *d_vals, uint32_t *d_tile_ranges, uint64_t *d_keys,
+                                   long long *d_n_instances, int *d_err_word, gs_stream_t stream) {
+    size_t need = 0;
+    int rc = gs_bin_sort_workspace(n_views, N, capacity, cams, &need);
+    if (rc != GS_OK) return rc;
+    if (need > (size_t)GS_NOALLOC_SCRATCH_BYTES) return GS_ERR_CAPACITY;   // beyond the fixed scratch
+    void *scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc != GS_OK) return rc;
+    return gs_bin_sort(cams, n_views, N, d_depth, d_rect, d_touched, capacity, d_vals, d_tile_ranges,
+                       d_keys, d_n_instances, scratch, (size_t)GS_NOALLOC_SCRATCH_BYTES, d_err_word, stream);
 }
