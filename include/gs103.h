@@ -146,6 +146,48 @@ int gs_bin_sort(const gs_camera *cams, int n_views, int N, const float *d_depth,
                 long long *d_n_instances, void *d_workspace, size_t workspace_bytes,
                 int *d_err_word, gs_stream_t stream);
 
+/* a2 for rendering: the same stable (tile, depth) lists, each cut to an exact
+ * prefix that blending never runs past.  A splat whose opacity at every
+ * pixel of a tile is at least a = min(0.99, 0.99 o / e) (over the tiles of a
+ * core rectangle inside its ellipse Q <= 2) is blended by each pixel that has
+ * not stopped and multiplies its transmittance by at most 1 - a.  A tile
+ * keeps its list up to the depth-ordered chunk where the sum of -ln(1 - a)
+ * over its entries first exceeds 10 > ln(1e4) (fixed point, rounded down):
+ * past that point every pixel of the tile has stopped, so rendering with the
+ * prefix gives the images, T_final, processed counts and gradients of the
+ * full list.  Tiles that never reach the bound keep their whole list.
+ * Inputs as gs_bin_sort plus the splat records of gs_project (d_splats,
+ * rgb_dtype).  Out: d_vals and d_tile_ranges of the prefixes (an empty tile
+ * reads [0, 0)); d_tile_count [T] u32 the full list lengths (optional);
+ * d_keys the prefix keys (optional); *d_n_instances the entries kept.
+ * d_tile_limit (optional, [T] int32, e.g. the d_tile_nproc of the previous
+ * step) replaces the bound: a tile with limit > 0 keeps the chunks up to the
+ * one holding entry 2 limit + 64 (a tile with limit <= 0 keeps its whole
+ * list).  Such a cut is not guaranteed, so gs_render_fwd checks it
+ * (d_tile_count) and gs_bin_sort_prefix_repair rebuilds the tiles it lists.
+ * Overflow and workspace rules as gs_bin_sort.  Views of more than 16384
+ * tiles get the full lists. */
+int gs_bin_sort_prefix_workspace(int n_views, int N, long long capacity, const gs_camera *cams,
+                                 size_t *bytes);
+int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, const float *d_depth,
+                       const int16_t *d_rect, const int32_t *d_touched, const void *d_splats,
+                       int rgb_dtype, const int32_t *d_tile_limit, long long capacity,
+                       uint32_t *d_vals, uint32_t *d_tile_ranges, uint32_t *d_tile_count,
+                       uint64_t *d_keys, long long *d_n_instances, void *d_workspace,
+                       size_t workspace_bytes, int *d_err_word, gs_stream_t stream);
+
+/* Rebuild the full lists of the *d_flag_count tiles in d_flag_tiles (as
+ * listed by gs_render_fwd) after the kept entries (*d_n_instances of them),
+ * within the capacity, and point their ranges there; the workspace is the
+ * one the preceding gs_bin_sort_prefix call used.  Tiles that do not fit set
+ * GS_EW_CAPACITY and keep their prefix.  Does nothing when the count is 0. */
+int gs_bin_sort_prefix_repair(const gs_camera *cams, int n_views, int N, const int16_t *d_rect,
+                              const int32_t *d_touched, const int32_t *d_flag_tiles,
+                              const int32_t *d_flag_count, long long capacity, uint32_t *d_vals,
+                              uint32_t *d_tile_ranges, const long long *d_n_instances,
+                              void *d_workspace, size_t workspace_bytes, int *d_err_word,
+                              gs_stream_t stream);
+
 /* gs_bin_sort without a workspace argument: no counterpart in the paper.
  * For callers that cannot allocate device memory themselves (a runtime that
  * owns all device memory through its own pool, a steady-state loop that must
@@ -182,6 +224,7 @@ typedef struct {
     const int32_t *d_order;
     int *d_queue;
     long long budget_ns;
+    const int32_t *d_n_order;  /* device count of tiles in d_order; NULL = all T tiles */
 } gs_schedule;
 
 /* a3. Forward blending (Sec. II-A blending equation), one CTA per 16x16 tile.
@@ -190,11 +233,17 @@ typedef struct {
  *      including the last Gaussian blended (0 if none);
  *      d_tile_nproc [T] the maximum of d_n_proc over the tile;
  *      d_tile_ns [T] u64 nanoseconds the tile took (NULL = not measured).
- * sched may be NULL (raster). */
+ * With d_tile_count (the full list lengths of gs_bin_sort_prefix), a tile
+ * whose kept prefix ended while a pixel was still blending is appended to
+ * d_flag_tiles and counted in *d_flag_count (zeroed by the caller); its
+ * outputs are then incomplete until gs_bin_sort_prefix_repair and a render
+ * of the listed tiles (GS_SCHED_ORDER over d_flag_tiles, d_n_order =
+ * d_flag_count).  NULL = no check.  sched may be NULL (raster). */
 int gs_render_fwd(const gs_camera *cams, int n_views, const uint32_t *d_tile_ranges,
                   const uint32_t *d_vals, const void *d_splats, int rgb_dtype,
                   const gs_schedule *sched, float *d_img, float *d_T_final, int32_t *d_n_proc,
-                  int32_t *d_tile_nproc, uint64_t *d_tile_ns, int *d_err_word,
+                  int32_t *d_tile_nproc, uint64_t *d_tile_ns, const uint32_t *d_tile_count,
+                  int32_t *d_flag_tiles, int32_t *d_flag_count, int *d_err_word,
                   gs_stream_t stream);
 
 /* a4. L1 loss over n floats: *d_loss (device float, overwritten)
@@ -224,6 +273,19 @@ int gs_project_bwd(const gs_camera *cams, int n_views, int N, const float *d_mea
                    const float *d_opacity_logits, const void *d_sh, int sh_dtype,
                    const int32_t *d_touched, const float *d_grad2d, float *d_dparams,
                    gs_stream_t stream);
+
+/* a6 + a7 fused: the projection backward of gs_project_bwd followed, for
+ * each Gaussian, by the Adam step of gs_adam_step on its 59 entries, without
+ * writing the gradients (unless d_dparams != NULL).  d_params is the grouped
+ * FP32 buffer (read for the backward, then updated); d_sh is the SH the
+ * forward read (e.g. the BF16 shadow; NULL = the SH group of d_params, FP32);
+ * the updated SH is also written to d_sh_shadow if given.  N must be a
+ * multiple of 4.  Gradients and updates equal those of the two calls. */
+int gs_project_bwd_adam(const gs_camera *cams, int n_views, int N, float *d_params,
+                        const void *d_sh, int sh_dtype, const int32_t *d_touched,
+                        const float *d_grad2d, float *d_m, float *d_v, const float *lr, float b1,
+                        float b2, float eps, int t, void *d_sh_shadow, int shadow_dtype,
+                        float *d_dparams, gs_stream_t stream);
 
 /* a7. One bias-corrected Adam step (Kingma & Ba) over the grouped buffers of
  * N Gaussians (59 N floats each, 16-B aligned), step t >= 1:

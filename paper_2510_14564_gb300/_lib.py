@@ -25,7 +25,8 @@ SPLAT_BYTES = {GS_F32: 48, GS_BF16: 32, GS_F16: 32}
 
 # Every symbol include/gs103.h declares.
 EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_bin_sort_noalloc",
-           "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_project_bwd", "gs_adam_step",
+           "gs_bin_sort_prefix_workspace", "gs_bin_sort_prefix", "gs_bin_sort_prefix_repair",
+           "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_project_bwd", "gs_project_bwd_adam", "gs_adam_step",
            "gs_adam_flat", "gs_tile_features", "gs_mlp_predict", "gs_mlp_grad",
            "gs_mlp_train_step", "gs_int_cost", "gs_range_cost", "gs_sched_order_workspace", "gs_sched_order"]
 
@@ -45,7 +46,8 @@ class GsCamera(ctypes.Structure):
 
 class GsSchedule(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("d_order", ctypes.c_void_p),
-                ("d_queue", ctypes.c_void_p), ("budget_ns", ctypes.c_longlong)]
+                ("d_queue", ctypes.c_void_p), ("budget_ns", ctypes.c_longlong),
+                ("d_n_order", ctypes.c_void_p)]
 
 
 _lib = None
@@ -73,13 +75,20 @@ def lib():
                                  VP, VP, VP]
         L.gs_bin_sort_workspace.argtypes = [I32, I32, I64, P(GsCamera), P(SZ)]
         L.gs_bin_sort.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, I64, VP, VP, VP, VP, VP, SZ, VP, VP]
+        L.gs_bin_sort_prefix_workspace.argtypes = [I32, I32, I64, P(GsCamera), P(SZ)]
+        L.gs_bin_sort_prefix.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, VP, I32, VP, I64, VP, VP, VP, VP,
+                                         VP, VP, SZ, VP, VP]
+        L.gs_bin_sort_prefix_repair.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, VP, I64, VP, VP, VP, VP,
+                                                SZ, VP, VP]
         L.gs_bin_sort_noalloc.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, I64, VP, VP, VP, VP, VP, VP]
         L.gs_render_fwd.argtypes = [P(GsCamera), I32, VP, VP, VP, I32, P(GsSchedule), VP, VP, VP, VP,
-                                    VP, VP, VP]
+                                    VP, VP, VP, VP, VP, VP]
         L.gs_l1_loss.argtypes = [I64, VP, VP, VP, VP, VP]
         L.gs_render_bwd.argtypes = [P(GsCamera), I32, VP, VP, VP, I32, P(GsSchedule), VP, VP, VP, VP,
                                     VP, VP, VP]
         L.gs_project_bwd.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, VP, VP, I32, VP, VP, VP, VP]
+        L.gs_project_bwd_adam.argtypes = [P(GsCamera), I32, I32, VP, VP, I32, VP, VP, VP, VP, P(F32), F32, F32,
+                                          F32, I32, VP, I32, VP, VP]
         L.gs_adam_step.argtypes = [I32, VP, VP, VP, VP, P(F32), F32, F32, F32, I32, VP, I32, VP]
         L.gs_adam_flat.argtypes = [I64, VP, VP, VP, VP, F32, F32, F32, F32, I32, VP]
         L.gs_tile_features.argtypes = [P(GsCamera), I32, VP, VP, VP, I32, I32, VP, VP]
@@ -178,6 +187,34 @@ def gs_bin_sort(cams, N, depth, rect, touched, capacity, vals, tile_ranges, keys
                             ptr(err_word), stream_ptr(stream)), "gs_bin_sort")
 
 
+def gs_bin_sort_prefix_workspace(cams, N, capacity) -> int:
+    ca = camera_array(cams)
+    out = SZ(0)
+    check(lib().gs_bin_sort_prefix_workspace(len(cams), int(N), int(capacity), ca, ctypes.byref(out)),
+          "gs_bin_sort_prefix_workspace")
+    return int(out.value)
+
+
+def gs_bin_sort_prefix(cams, N, depth, rect, touched, splats, rgb_dtype, tile_limit, capacity, vals,
+                       tile_ranges, tile_count, keys, n_instances, workspace, err_word, stream=None):
+    ca = camera_array(cams)
+    check(lib().gs_bin_sort_prefix(ca, len(cams), int(N), ptr(depth), ptr(rect), ptr(touched), ptr(splats),
+                                   int(rgb_dtype), ptr(tile_limit), int(capacity), ptr(vals),
+                                   ptr(tile_ranges), ptr(tile_count), ptr(keys), ptr(n_instances),
+                                   ptr(workspace), workspace.numel() * workspace.element_size(),
+                                   ptr(err_word), stream_ptr(stream)), "gs_bin_sort_prefix")
+
+
+def gs_bin_sort_prefix_repair(cams, N, rect, touched, flag_tiles, flag_count, capacity, vals,
+                              tile_ranges, n_instances, workspace, err_word, stream=None):
+    ca = camera_array(cams)
+    check(lib().gs_bin_sort_prefix_repair(ca, len(cams), int(N), ptr(rect), ptr(touched), ptr(flag_tiles),
+                                          ptr(flag_count), int(capacity), ptr(vals), ptr(tile_ranges),
+                                          ptr(n_instances), ptr(workspace),
+                                          workspace.numel() * workspace.element_size(), ptr(err_word),
+                                          stream_ptr(stream)), "gs_bin_sort_prefix_repair")
+
+
 def gs_bin_sort_noalloc(cams, N, depth, rect, touched, capacity, vals, tile_ranges, keys, n_instances,
                         err_word, stream=None):
     ca = camera_array(cams)
@@ -195,17 +232,19 @@ def _sched(sched):
     s.d_order = ptr(sched.get("order"))
     s.d_queue = ptr(sched.get("queue"))
     s.budget_ns = int(sched.get("budget_ns", 0))
+    s.d_n_order = ptr(sched.get("n_order"))
     return ctypes.byref(s), s
 
 
 def gs_render_fwd(cams, tile_ranges, vals, splats, rgb_dtype, sched, img, T_final, n_proc,
-                  tile_nproc, tile_ns, err_word, stream=None):
+                  tile_nproc, tile_ns, err_word, stream=None, tile_count=None, flag_tiles=None,
+                  flag_count=None):
     ca = camera_array(cams)
     sp = _sched(sched)
     check(lib().gs_render_fwd(ca, len(cams), ptr(tile_ranges), ptr(vals), ptr(splats), int(rgb_dtype),
                               sp[0] if sp else None, ptr(img), ptr(T_final), ptr(n_proc),
-                              ptr(tile_nproc), ptr(tile_ns), ptr(err_word), stream_ptr(stream)),
-          "gs_render_fwd")
+                              ptr(tile_nproc), ptr(tile_ns), ptr(tile_count), ptr(flag_tiles),
+                              ptr(flag_count), ptr(err_word), stream_ptr(stream)), "gs_render_fwd")
 
 
 def gs_l1_loss(n, img, tgt, loss, dimg, stream=None):
@@ -229,6 +268,16 @@ def gs_project_bwd(cams, N, means, log_scales, quats, opacity_logits, sh, sh_dty
     check(lib().gs_project_bwd(ca, len(cams), int(N), ptr(means), ptr(log_scales), ptr(quats),
                                ptr(opacity_logits), ptr(sh), int(sh_dtype), ptr(touched), ptr(grad2d),
                                ptr(dparams), stream_ptr(stream)), "gs_project_bwd")
+
+
+def gs_project_bwd_adam(cams, N, params, sh, sh_dtype, touched, grad2d, m, v, lr6, b1, b2, eps, t,
+                        sh_shadow=None, shadow_dtype=GS_BF16, dparams=None, stream=None):
+    ca = camera_array(cams)
+    lr = (F32 * 6)(*[float(x) for x in lr6])
+    check(lib().gs_project_bwd_adam(ca, len(cams), int(N), ptr(params), ptr(sh), int(sh_dtype), ptr(touched),
+                                    ptr(grad2d), ptr(m), ptr(v), lr, float(b1), float(b2), float(eps), int(t),
+                                    ptr(sh_shadow), int(shadow_dtype), ptr(dparams), stream_ptr(stream)),
+          "gs_project_bwd_adam")
 
 
 def gs_adam_step(N, params, grads, m, v, lr6, b1, b2, eps, t, sh_shadow=None, shadow_dtype=GS_BF16,

@@ -416,8 +416,9 @@ struct ChunkGeom {
 };
 
 // Chunk k of view v: the records whose first instance (offs, the exclusive
-// scan of tile counts in sorted order) falls in the k-th of C_v equal parts
-// of the view's instances, so that chunks carry equal work.
+// scan of tile counts in sorted order) falls in the k-th part of the view's
+// instances: equal parts, or (cubic) parts starting at I (k / C_v)^3, which
+// cut the nearest depths, where blending stops, into many small chunks.
 __device__ __forceinline__ long long lower_bound_u64(const unsigned long long *a, long long lo,
                                                      long long hi, unsigned long long key) {
     while (lo < hi) {
@@ -427,12 +428,20 @@ __device__ __forceinline__ long long lower_bound_u64(const unsigned long long *a
     return lo;
 }
 
+__device__ __forceinline__ unsigned long long chunk_bound(unsigned long long i0, unsigned long long span,
+                                                          int k, int Cv, bool cubic) {
+    if (k >= Cv) return i0 + span;
+    if (!cubic) return i0 + span * (unsigned long long)k / (unsigned long long)Cv;
+    const double x = (double)k / (double)Cv;
+    return i0 + (unsigned long long)((double)span * x * x * x);
+}
+
 __device__ __forceinline__ ChunkGeom chunk_of(int v, int k, int Cv, int N,
-                                              const unsigned long long *offs) {
+                                              const unsigned long long *offs, bool cubic = false) {
     const long long s0 = (long long)v * N, s1 = s0 + N;
     const unsigned long long i0 = offs[s0], span = offs[s1] - i0;
-    const unsigned long long b0 = i0 + span * (unsigned long long)k / (unsigned long long)Cv;
-    const unsigned long long b1 = i0 + span * (unsigned long long)(k + 1) / (unsigned long long)Cv;
+    const unsigned long long b0 = chunk_bound(i0, span, k, Cv, cubic);
+    const unsigned long long b1 = chunk_bound(i0, span, k + 1, Cv, cubic);
     ChunkGeom g;
     g.lo = lower_bound_u64(offs, s0, s1, b0);     // records whose first instance is in [b0, b1)
     g.hi = lower_bound_u64(offs, s0, s1, b1);
@@ -792,6 +801,29 @@ static void radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
                                                    shift, mask, nb, write_keys ? 1 : 0); count_launches(1); }
 }
 
+// Records in (view, depth bits, index) order: a stable 4 x 8-bit LSD sort on
+// the depth bits (culled records carry the largest key), then, for several
+// views, a stable pass on the view.  Returns the sorted record indices.
+static const uint32_t *depth_order(const float *d_depth, const int32_t *d_touched, long long VN, int N,
+                                   int n_views, uint32_t *dk0, uint32_t *dk1, uint32_t *dv0, uint32_t *dv1,
+                                   uint32_t *hist, void *part, cudaStream_t st) {
+    { k_depth_keys<<<cdiv(VN, 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0); count_launches(1); }
+    uint32_t *ka = dk0, *kb = dk1, *va = dv0, *vb = dv1;
+    for (int pass = 0; pass < 4; ++pass) {
+        radix_pass(ka, va, kb, vb, nullptr, (uint32_t)VN, VN, 8 * pass, 8, true, hist, (uint32_t *)part, st);
+        uint32_t *t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+    }
+    if (n_views > 1) {
+        { k_view_keys<<<cdiv(VN, 256), 256, 0, st>>>(va, VN, (uint32_t)N, ka); count_launches(1); }
+        int vbits = 1;
+        while ((1 << vbits) < n_views) ++vbits;
+        radix_pass(ka, va, kb, vb, nullptr, (uint32_t)VN, VN, 0, vbits, false, hist, (uint32_t *)part, st);
+        uint32_t *t = va; va = vb; vb = t;
+    }
+    return va;
+}
+
 size_t radix_sort_workspace(long long n) {
     long long nb = (n + kSortTile - 1) / kSortTile;
     if (nb < 1) nb = 1;
@@ -897,23 +929,8 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
         cudaMemsetAsync(d_n_instances, 0, sizeof(long long), st);
         return launch_status();
     }
-    // 1. records in (depth bits, index) order: stable, 4 x 8 bits; culled last
-    { k_depth_keys<<<cdiv(VN, 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0); count_launches(1); }
-    uint32_t *ka = dk0, *kb = dk1, *va = dv0, *vb = dv1;
-    for (int pass = 0; pass < 4; ++pass) {
-        radix_pass(ka, va, kb, vb, nullptr, (uint32_t)VN, VN, 8 * pass, 8, true, hist, (uint32_t *)part, st);
-        uint32_t *t = ka; ka = kb; kb = t;
-        t = va; va = vb; vb = t;
-    }
-    if (n_views > 1) {
-        // stable partition by view: (view, depth, index) order
-        { k_view_keys<<<cdiv(VN, 256), 256, 0, st>>>(va, VN, (uint32_t)N, ka); count_launches(1); }
-        int vbits = 1;
-        while ((1 << vbits) < n_views) ++vbits;
-        radix_pass(ka, va, kb, vb, nullptr, (uint32_t)VN, VN, 0, vbits, false, hist, (uint32_t *)part, st);
-        uint32_t *t = va; va = vb; vb = t;
-    }
-    const uint32_t *order = va;
+    // 1. records in (view, depth bits, index) order; culled last in each view
+    const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, st);
 
     if (p.direct) {
         uint32_t *ids1 = (uint32_t *)(ws + p.ids1);
@@ -992,6 +1009,315 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
 }
 
 // ---------------------------------------------------------------------------
+// Prefix binning (gs_bin_sort_prefix)
+//
+// Rendering reads a tile's list only until every pixel of the tile has
+// stopped.  A splat whose opacity at every pixel of a tile is at least
+// alpha_lo is blended by each pixel that has not stopped (alpha_lo >= 2/255
+// > 1/255), and lowers its transmittance by a factor <= 1 - alpha_lo.  Once
+// the sum over a tile's list of -ln(1 - alpha_lo) passes ln(1e4) (plus a
+// margin for FP32 rounding), every pixel has stopped within that part of the
+// list.  Per splat, alpha_lo is bounded over a core rectangle of tiles lying
+// inside its ellipse {Q <= 2} (alpha >= o / e there); the bound is summed in
+// fixed point over depth-ordered chunks, and a tile keeps the chunks up to
+// the one where the sum passes the target.  The emitted lists are exact
+// prefixes of gs_bin_sort's lists, long enough that blending never reaches
+// their end, so images and gradients are those of the full lists.
+// ---------------------------------------------------------------------------
+constexpr int kPreChunks = 608;
+constexpr int kPreMaxTiles = 16384;               // cursor row of at most 64 KB
+constexpr float kCovScale = 4096.0f;              // fixed-point units of -ln(1 - alpha)
+constexpr uint32_t kCovTarget = 10u * 4096u;      // ln(1e4) = 9.21, plus margin
+
+// Core tiles [x0, x1) x [y0, y1) of a splat (inside its rect) and the
+// fixed-point bound -ln(1 - alpha_lo) over them (0: none).
+template <int DT>
+__device__ __forceinline__ uint32_t core_rect(const void *splats, uint32_t g, short4 rc, int &x0, int &y0,
+                                              int &x1, int &y1) {
+    const Splat s = load_splat<DT>(splats, g);
+    const float qc = 1.4426950408889634f;          // Q = 2 in log2 units: alpha >= o / e
+    const float a = -s.Ap, c = -s.Cp, b = fabsf(s.Bp);
+    const float sac = sqrtf(a * c);
+    const float den = 2.0f * a * c + b * sac;       // max of -q over the box corners per unit s^2
+    x0 = y0 = x1 = y1 = 0;
+    if (!(den > 0.0f) || !(a > 0.0f) || !(c > 0.0f)) return 0u;
+    const float sc = 0.99f * sqrtf(qc / den);
+    const float X = sc * sqrtf(c), Y = sc * sqrtf(a);
+    x0 = max((int)ceilf((s.u - X) * (1.0f / 16.0f)), (int)rc.x);
+    x1 = min((int)floorf((s.u + X) * (1.0f / 16.0f)), (int)rc.z);
+    y0 = max((int)ceilf((s.v - Y) * (1.0f / 16.0f)), (int)rc.y);
+    y1 = min((int)floorf((s.v + Y) * (1.0f / 16.0f)), (int)rc.w);
+    if (x1 <= x0 || y1 <= y0) return 0u;
+    const float alo = fminf(0.99f, 0.99f * exp2f(s.lo - qc));
+    if (alo < 2.0f / 255.0f) return 0u;
+    return (uint32_t)floorf(-log1pf(-alo) * (0.999f * kCovScale));
+}
+
+// Per chunk: instance counts and the coverage bound per tile (2D difference
+// grids), into Mc[chunk][tile] and Mv[chunk][tile].
+template <int DT>
+__global__ void __launch_bounds__(256) k_pre_count(TileBatch tb, int N, int Cv, int Tmax,
+                                                   const uint32_t *__restrict__ order,
+                                                   const short4 *__restrict__ rect,
+                                                   const void *__restrict__ splats,
+                                                   const unsigned long long *__restrict__ offs,
+                                                   uint32_t *__restrict__ Mc, uint32_t *__restrict__ Mv) {
+    extern __shared__ int s_g2[];
+    const int v = blockIdx.x / Cv, k = blockIdx.x % Cv;
+    const int TX = tb.v[v].TX, TY = tb.v[v].TY, GX = TX + 1, GY = TY + 1, G = GX * GY;
+    int *gc = s_g2, *gv = s_g2 + G;
+    for (int i = threadIdx.x; i < (splats ? 2 : 1) * G; i += 256) s_g2[i] = 0;
+    __syncthreads();
+    const ChunkGeom cg = chunk_of(v, k, Cv, N, offs, true);
+    for (long long i = cg.lo + threadIdx.x; i < cg.hi; i += 256) {
+        const uint32_t g = __ldg(order + i);
+        const short4 rc = __ldg(rect + g);
+        atomicAdd(&gc[rc.y * GX + rc.x], 1);
+        atomicAdd(&gc[rc.y * GX + rc.z], -1);
+        atomicAdd(&gc[rc.w * GX + rc.x], -1);
+        atomicAdd(&gc[rc.w * GX + rc.z], 1);
+        if (!splats) continue;
+        int x0, y0, x1, y1;
+        const int cov = (int)core_rect<DT>(splats, g, rc, x0, y0, x1, y1);
+        if (cov > 0) {
+            atomicAdd(&gv[y0 * GX + x0], cov);
+            atomicAdd(&gv[y0 * GX + x1], -cov);
+            atomicAdd(&gv[y1 * GX + x0], -cov);
+            atomicAdd(&gv[y1 * GX + x1], cov);
+        }
+    }
+    __syncthreads();
+    const int ng = splats ? 2 : 1;                 // grids in use
+    for (int y = threadIdx.x; y < ng * GY; y += 256) {
+        int *gr = (y < GY ? gc : gv) + (y % GY) * GX;
+        int run = 0;
+        for (int x = 0; x < GX; ++x) { run += gr[x]; gr[x] = run; }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < ng * GX; x += 256) {
+        int *gg = x < GX ? gc : gv;
+        const int xx = x % GX;
+        int run = 0;
+        for (int y = 0; y < GY; ++y) { run += gg[y * GX + xx]; gg[y * GX + xx] = run; }
+    }
+    __syncthreads();
+    const long long row = ((long long)v * Cv + k) * Tmax;
+    for (int t = threadIdx.x; t < TX * TY; t += 256) {
+        const int cell = (t / TX) * GX + t % TX;
+        Mc[row + t] = (uint32_t)gc[cell];
+        if (splats) Mv[row + t] = (uint32_t)gv[cell];
+    }
+}
+
+// Per tile: exclusive prefix of the counts over chunks (in place), the full
+// count, the last chunk kept and the number of entries kept.  A tile keeps
+// its chunks up to the first one where either the coverage bound passes the
+// target, or the kept count reaches the tile's limit (limit[t] > 0:
+// 2 limit + 64 entries; no limit otherwise).
+__global__ void k_pre_colscan(TileBatch tb, int Cv, int Tmax, uint32_t *__restrict__ Mc,
+                              const uint32_t *__restrict__ Mv, const int32_t *__restrict__ limit,
+                              uint32_t *__restrict__ full, uint32_t *__restrict__ last_chunk,
+                              uint32_t *__restrict__ kept) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= tb.total_tiles) return;
+    const int v = view_of_tile(tb, g);
+    const int t = g - tb.v[v].tile_base;
+    uint32_t *col = Mc + (long long)v * Cv * Tmax + t;
+    const uint32_t *cov = Mv + (long long)v * Cv * Tmax + t;
+    const int lim = limit ? limit[g] : 0;
+    const uint32_t want = lim > 0 ? (uint32_t)min(2ll * lim + 64, 0x7fffffffll) : 0xffffffffu;
+    uint32_t run = 0, rcov = 0, keep = 0, lastc = (uint32_t)(Cv - 1);
+    bool found = false;
+    for (int k0 = 0; k0 < Cv; k0 += 8) {
+        uint32_t a[8], b[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool in = k0 + j < Cv;
+            a[j] = in ? col[(long long)(k0 + j) * Tmax] : 0u;
+            b[j] = in && !found && Mv ? cov[(long long)(k0 + j) * Tmax] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (k0 + j >= Cv) break;
+            col[(long long)(k0 + j) * Tmax] = run;
+            run += a[j];
+            if (!found) {
+                rcov += b[j];
+                if (rcov >= kCovTarget || run >= want) { found = true; lastc = (uint32_t)(k0 + j); keep = run; }
+            }
+        }
+    }
+    full[g] = run;
+    last_chunk[g] = lastc;
+    kept[g] = found ? keep : run;
+}
+
+__global__ void k_pre_ranges(int T, const uint32_t *__restrict__ kept,
+                             const unsigned long long *__restrict__ tstart, uint2 *__restrict__ ranges) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const uint32_t c = kept[t];
+    const uint32_t s0 = (uint32_t)tstart[t];
+    ranges[t] = c > 0 ? make_uint2(s0, s0 + c) : make_uint2(0u, 0u);
+}
+
+// Place the kept instances: one CTA of 8 warps per chunk, per-tile cursors in
+// shared memory (a skip mark for tiles that keep no entry of this chunk) and a
+// summed-area table of the tiles still active in this chunk.  The CTA reads
+// the chunk's records 256 at a time, keeps those whose rectangle holds an
+// active tile (in order), and then warp w hands out slots in the tile rows
+// y = w (mod 8): every warp walks the kept records in order, so each tile's
+// slots follow record order.
+constexpr int kPlaceWarps = 8;
+constexpr int kPlaceThreads = 32 * kPlaceWarps;
+__global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
+    TileBatch tb, int N, int Cv, int Tmax, const uint32_t *__restrict__ order,
+    const short4 *__restrict__ rect, const unsigned long long *__restrict__ offs,
+    const uint32_t *__restrict__ Mc, const uint32_t *__restrict__ last_chunk,
+    const unsigned long long *__restrict__ tstart, const unsigned long long *__restrict__ total,
+    long long cap, uint32_t *__restrict__ vals, const float *__restrict__ depth,
+    unsigned long long *__restrict__ keys) {
+    extern __shared__ uint32_t s_cur[];
+    __shared__ int s_any;
+    __shared__ uint32_t s_g[kPlaceThreads];
+    __shared__ short4 s_rc[kPlaceThreads];
+    __shared__ int s_wc[kPlaceWarps];
+    if ((long long)*total > cap) return;
+    const int v = blockIdx.x / Cv, k = blockIdx.x % Cv;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int TX = tb.v[v].TX, TY = tb.v[v].TY, Tv = TX * TY, tbase = tb.v[v].tile_base;
+    const int GX = TX + 1;
+    uint32_t *sat = s_cur + Tmax;                   // [(TY + 1) x (TX + 1)]
+    const uint32_t *row = Mc + ((long long)v * Cv + k) * Tmax;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    bool any = false;
+    for (int t = threadIdx.x; t < Tv; t += kPlaceThreads) {
+        const bool act = (uint32_t)k <= last_chunk[tbase + t];
+        s_cur[t] = act ? (uint32_t)tstart[tbase + t] + row[t] : 0xffffffffu;
+        sat[(t / TX + 1) * GX + t % TX + 1] = act ? 1u : 0u;
+        any |= act;
+    }
+    for (int x = threadIdx.x; x < GX; x += kPlaceThreads) sat[x] = 0;
+    for (int y = threadIdx.x; y <= TY; y += kPlaceThreads) sat[y * GX] = 0;
+    if (any) s_any = 1;
+    __syncthreads();
+    if (!s_any) return;
+    for (int y = 1 + threadIdx.x; y <= TY; y += kPlaceThreads) {   // prefix along x
+        uint32_t run = 0;
+        for (int x = 1; x < GX; ++x) { run += sat[y * GX + x]; sat[y * GX + x] = run; }
+    }
+    __syncthreads();
+    for (int x = 1 + threadIdx.x; x < GX; x += kPlaceThreads) {    // prefix along y
+        uint32_t run = 0;
+        for (int y = 1; y <= TY; ++y) { run += sat[y * GX + x]; sat[y * GX + x] = run; }
+    }
+    __syncthreads();
+    const ChunkGeom cg = chunk_of(v, k, Cv, N, offs, true);
+    for (long long b0 = cg.lo; b0 < cg.hi; b0 += kPlaceThreads) {
+        // 1. read 256 records, keep those with an active tile, in order
+        const long long i = b0 + threadIdx.x;
+        bool keep = false;
+        uint32_t g = 0;
+        short4 rc = make_short4(0, 0, 0, 0);
+        if (i < cg.hi) {
+            g = __ldg(order + i);
+            rc = __ldg(rect + g);
+            if (rc.z > rc.x && rc.w > rc.y)
+                keep = sat[rc.w * GX + rc.z] - sat[rc.y * GX + rc.z] - sat[rc.w * GX + rc.x] +
+                       sat[rc.y * GX + rc.x] > 0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (l == 0) s_wc[w] = __popc(bal);
+        __syncthreads();
+        int base = 0, n_keep = 0;
+#pragma unroll
+        for (int q = 0; q < kPlaceWarps; ++q) { base += q < w ? s_wc[q] : 0; n_keep += s_wc[q]; }
+        if (keep) {
+            const int pos = base + __popc(bal & lanemask_lt());
+            s_g[pos] = g;
+            s_rc[pos] = rc;
+        }
+        __syncthreads();
+        // 2. each warp places the kept records' tiles in its own rows, in order
+        for (int j0 = 0; j0 < n_keep; j0 += 32) {
+            const int j = j0 + l;
+            uint32_t gj = 0;
+            short4 r = make_short4(0, 0, 0, 0);
+            if (j < n_keep) { gj = s_g[j]; r = s_rc[j]; }
+            const int y0w = r.y + ((w - r.y) % kPlaceWarps + kPlaceWarps) % kPlaceWarps;
+            const int hw = r.w > y0w ? (r.w - y0w + kPlaceWarps - 1) / kPlaceWarps : 0;
+            const int cnt = (r.z - r.x) * hw;
+            unsigned has = __ballot_sync(0xffffffffu, cnt > 0);
+            while (has) {
+                const int o = __ffs(has) - 1;
+                has &= has - 1;
+                const int x0 = __shfl_sync(0xffffffffu, (int)r.x, o);
+                const int yw = __shfl_sync(0xffffffffu, y0w, o);
+                const int wd = __shfl_sync(0xffffffffu, (int)(r.z - r.x), o);
+                const int c = __shfl_sync(0xffffffffu, cnt, o);
+                const uint32_t gid = __shfl_sync(0xffffffffu, gj, o);
+                const float rw = 1.0f / (float)wd;
+                for (int q = l; q < c; q += 32) {
+                    int rr = (int)((float)q * rw);
+                    rr += (rr + 1) * wd <= q;
+                    rr -= rr * wd > q;
+                    const int t = (yw + kPlaceWarps * rr) * TX + x0 + (q - rr * wd);
+                    const uint32_t pos = s_cur[t];
+                    if (pos != 0xffffffffu) {
+                        s_cur[t] = pos + 1;
+                        vals[pos] = gid;
+                        if (keys)
+                            keys[pos] = ((unsigned long long)(tbase + t) << 32) | __float_as_uint(__ldg(depth + gid));
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_range_counts(const uint2 *__restrict__ ranges, int T, uint32_t *__restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T) out[t] = ranges[t].y - ranges[t].x;
+}
+
+struct PrePlan {
+    size_t dk0, dk1, dv0, dv1, cnt, offs, mc, mv, full, lastc, kept, tstart, hist, part, misc, bytes;
+    int Cv, Tmax;
+    bool ok;
+};
+
+static PrePlan make_pre_plan(long long VN, const TileBatch &tb) {
+    PrePlan p;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
+    p.Tmax = 0;
+    for (int v = 0; v < tb.n; ++v) p.Tmax = tb.v[v].TX * tb.v[v].TY > p.Tmax ? tb.v[v].TX * tb.v[v].TY : p.Tmax;
+    p.ok = p.Tmax <= kPreMaxTiles;
+    p.Cv = (kPreChunks + tb.n - 1) / tb.n;
+    p.dk0 = take(4 * VN); p.dk1 = take(4 * VN); p.dv0 = take(4 * VN); p.dv1 = take(4 * VN);
+    p.cnt = take(4 * VN);
+    p.offs = take(8 * (VN + 1));
+    p.mc = take(4 * (size_t)tb.n * p.Cv * p.Tmax);
+    p.mv = take(4 * (size_t)tb.n * p.Cv * p.Tmax);
+    p.full = take(4 * (size_t)tb.total_tiles);
+    p.lastc = take(4 * (size_t)tb.total_tiles);
+    p.kept = take(4 * (size_t)tb.total_tiles);
+    p.tstart = take(8 * (size_t)(tb.total_tiles + 1));
+    long long nb = (VN + kSortTile - 1) / kSortTile;
+    if (nb < 1) nb = 1;
+    p.hist = take(4 * (size_t)kRadix * nb);
+    long long maxscan = VN > (long long)kRadix * nb ? VN : (long long)kRadix * nb;
+    if (maxscan < tb.total_tiles) maxscan = tb.total_tiles;
+    p.part = take(8 * (size_t)((maxscan + kScanChunk - 1) / kScanChunk + 1));
+    p.misc = take(64);
+    p.bytes = o;
+    return p;
+}
+
+// ---------------------------------------------------------------------------
 // gs_bin_sort_noalloc: gs_bin_sort with its scratch in a fixed device array
 // ---------------------------------------------------------------------------
 // Some callers cannot allocate device memory: a runtime that owns every
@@ -1035,4 +1361,210 @@ extern "C" int gs_bin_sort_noalloc(const gs_camera *cams, int n_views, int N, co
     if (rc != GS_OK) return rc;
     return gs_bin_sort(cams, n_views, N, d_depth, d_rect, d_touched, capacity, d_vals, d_tile_ranges,
                        d_keys, d_n_instances, scratch, (size_t)GS_NOALLOC_SCRATCH_BYTES, d_err_word, stream);
+}
+
+// ---------------------------------------------------------------------------
+// gs_bin_sort_prefix entry points
+// ---------------------------------------------------------------------------
+extern "C" int gs_bin_sort_prefix_workspace(int n_views, int N, long long capacity, const gs_camera *cams,
+                                            size_t *bytes) {
+    TileBatch tb;
+    if (!bytes || N < 0 || capacity < 0 || capacity > 0xF0000000ll) return GS_ERR_ARG;
+    if (make_tile_batch(cams, n_views, &tb) != GS_OK) return GS_ERR_ARG;
+    const long long VN = (long long)n_views * N;
+    PrePlan p = make_pre_plan(VN, tb);
+    if (!p.ok) return gs_bin_sort_workspace(n_views, N, capacity, cams, bytes);
+    *bytes = p.bytes;
+    return GS_OK;
+}
+
+extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, const float *d_depth,
+                                  const int16_t *d_rect, const int32_t *d_touched, const void *d_splats,
+                                  int rgb_dtype, const int32_t *d_tile_limit, long long capacity,
+                                  uint32_t *d_vals, uint32_t *d_tile_ranges, uint32_t *d_tile_count,
+                                  uint64_t *d_keys, long long *d_n_instances, void *d_workspace,
+                                  size_t workspace_bytes, int *d_err_word, gs_stream_t stream) {
+    TileBatch tb;
+    if (make_tile_batch(cams, n_views, &tb) != GS_OK) return GS_ERR_ARG;
+    if (N < 0 || capacity < 0 || capacity > 0xF0000000ll) return GS_ERR_ARG;
+    if (!d_depth || !d_rect || !d_touched || !d_splats || !d_vals || !d_tile_ranges || !d_n_instances ||
+        !d_workspace)
+        return GS_ERR_ARG;
+    if (rgb_dtype < GS_F32 || rgb_dtype > GS_F16) return GS_ERR_ARG;
+    if (!aligned(d_workspace, 256) || !aligned(d_rect, 8) || !aligned(d_tile_ranges, 8) || !aligned(d_splats, 16))
+        return GS_ERR_ARG;
+    const long long VN = (long long)n_views * N;
+    if (VN > 0xF0000000ll) return GS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PrePlan p = make_pre_plan(VN, tb);
+    if (!p.ok) {
+        // views too large for the shared cursor row: the full lists
+        int rc = gs_bin_sort(cams, n_views, N, d_depth, d_rect, d_touched, capacity, d_vals, d_tile_ranges,
+                             d_keys, d_n_instances, d_workspace, workspace_bytes, d_err_word, stream);
+        if (rc == GS_OK && d_tile_count)
+            { k_range_counts<<<cdiv(tb.total_tiles, 256), 256, 0, st>>>(
+                reinterpret_cast<const uint2 *>(d_tile_ranges), tb.total_tiles, d_tile_count); count_launches(1); }
+        return rc == GS_OK ? launch_status() : rc;
+    }
+    if (workspace_bytes < p.bytes) return GS_ERR_CAPACITY;
+    char *ws = reinterpret_cast<char *>(d_workspace);
+    uint32_t *dk0 = (uint32_t *)(ws + p.dk0), *dk1 = (uint32_t *)(ws + p.dk1);
+    uint32_t *dv0 = (uint32_t *)(ws + p.dv0), *dv1 = (uint32_t *)(ws + p.dv1);
+    uint32_t *cnt = (uint32_t *)(ws + p.cnt);
+    unsigned long long *offs = (unsigned long long *)(ws + p.offs);
+    uint32_t *Mc = (uint32_t *)(ws + p.mc), *Mv = (uint32_t *)(ws + p.mv);
+    uint32_t *full = (uint32_t *)(ws + p.full), *lastc = (uint32_t *)(ws + p.lastc);
+    uint32_t *kept = (uint32_t *)(ws + p.kept);
+    unsigned long long *tstart = (unsigned long long *)(ws + p.tstart);
+    uint32_t *hist = (uint32_t *)(ws + p.hist);
+    void *part = (void *)(ws + p.part);
+    uint32_t *count = (uint32_t *)(ws + p.misc);
+    const int T = tb.total_tiles;
+    if (VN == 0) {
+        cudaMemsetAsync(d_tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, st);
+        if (d_tile_count) cudaMemsetAsync(d_tile_count, 0, sizeof(uint32_t) * (size_t)T, st);
+        cudaMemsetAsync(d_n_instances, 0, sizeof(long long), st);
+        return launch_status();
+    }
+    const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, st);
+    { k_gather_counts<<<cdiv(VN, 256), 256, 0, st>>>(order, d_touched, VN, cnt); count_launches(1); }
+    exclusive_scan<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, offs + VN, st);
+    size_t gmax = 0;
+    for (int v = 0; v < n_views; ++v) {
+        size_t g = 2 * sizeof(int) * (size_t)(tb.v[v].TX + 1) * (tb.v[v].TY + 1);
+        gmax = g > gmax ? g : gmax;
+    }
+    const int nchunks = n_views * p.Cv;
+    const void *kc = rgb_dtype == GS_F32 ? (const void *)k_pre_count<GS_F32>
+                     : rgb_dtype == GS_BF16 ? (const void *)k_pre_count<GS_BF16> : (const void *)k_pre_count<GS_F16>;
+    if (gmax > 48 * 1024) cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gmax);
+    const short4 *rect = reinterpret_cast<const short4 *>(d_rect);
+    // the coverage bound needs no history; with per-tile limits it is not computed
+    const void *cov_splats = d_tile_limit ? nullptr : d_splats;
+    uint32_t *Mv_used = d_tile_limit ? nullptr : Mv;
+    if (rgb_dtype == GS_F32)
+        { k_pre_count<GS_F32><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, offs, Mc, Mv); count_launches(1); }
+    else if (rgb_dtype == GS_BF16)
+        { k_pre_count<GS_BF16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, offs, Mc, Mv); count_launches(1); }
+    else
+        { k_pre_count<GS_F16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, offs, Mc, Mv); count_launches(1); }
+    { k_pre_colscan<<<cdiv(T, 128), 128, 0, st>>>(tb, p.Cv, p.Tmax, Mc, Mv_used, d_tile_limit, full, lastc, kept); count_launches(1); }
+    exclusive_scan<uint32_t, unsigned long long>(kept, tstart, T, (unsigned long long *)part, tstart + T, st);
+    { k_finish_count<<<1, 1, 0, st>>>(tstart + T, capacity, d_n_instances, count, d_err_word); count_launches(1); }
+    { k_pre_ranges<<<cdiv(T, 256), 256, 0, st>>>(T, kept, tstart, reinterpret_cast<uint2 *>(d_tile_ranges)); count_launches(1); }
+    if (d_tile_count) cudaMemcpyAsync(d_tile_count, full, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToDevice, st);
+    if (capacity > 0) {
+        size_t gmax1 = 0;
+        for (int v = 0; v < n_views; ++v) {
+            size_t g = (size_t)(tb.v[v].TX + 1) * (tb.v[v].TY + 1);
+            gmax1 = g > gmax1 ? g : gmax1;
+        }
+        const size_t smem = sizeof(uint32_t) * ((size_t)p.Tmax + gmax1);
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k_pre_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        { k_pre_place<<<nchunks, kPlaceThreads, smem, st>>>(tb, N, p.Cv, p.Tmax, order, rect, offs, Mc, lastc, tstart,
+                                                 tstart + T, capacity, d_vals, d_depth,
+                                                 reinterpret_cast<unsigned long long *>(d_keys)); count_launches(1); }
+    }
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Repair of tiles whose kept prefix was too short (gs_bin_sort_prefix_repair)
+//
+// The forward pass lists the tiles where a pixel was still blending when the
+// kept prefix ended.  For each, the full list is rebuilt after the kept
+// entries (in the capacity beyond them) by streaming the records in depth
+// order and keeping those whose rectangle holds the tile, and the tile's
+// range is pointed at it.  Every kernel exits at once when no tile is listed.
+// ---------------------------------------------------------------------------
+__global__ void k_rep_alloc(const int32_t *__restrict__ flag_tiles, const int32_t *__restrict__ flag_count,
+                            const uint32_t *__restrict__ full, const long long *__restrict__ n_inst,
+                            long long cap, uint2 *__restrict__ ranges, uint32_t *__restrict__ rep_start,
+                            int *err_word) {
+    const int n = *flag_count;
+    if (n <= 0) return;
+    unsigned long long at = (unsigned long long)*n_inst;
+    for (int i = 0; i < n; ++i) {
+        const int t = flag_tiles[i];
+        const unsigned long long c = full[t];
+        if ((long long)(at + c) > cap) {          // no room: leave the tile as it was
+            set_err(err_word, GS_EW_CAPACITY);
+            rep_start[i] = 0xffffffffu;
+            continue;
+        }
+        rep_start[i] = (uint32_t)at;
+        ranges[t] = make_uint2((uint32_t)at, (uint32_t)(at + c));
+        at += c;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_rep_fill(TileBatch tb, int N, long long VN,
+                                                  const int32_t *__restrict__ flag_tiles,
+                                                  const int32_t *__restrict__ flag_count,
+                                                  const uint32_t *__restrict__ rep_start,
+                                                  const uint32_t *__restrict__ order,
+                                                  const short4 *__restrict__ rect,
+                                                  const int *__restrict__ touched,
+                                                  uint32_t *__restrict__ vals) {
+    __shared__ int s_w[8];
+    const int n = *flag_count;
+    for (int fi = blockIdx.x; fi < n; fi += gridDim.x) {
+        const uint32_t at0 = rep_start[fi];
+        if (at0 == 0xffffffffu) continue;
+        const int t = flag_tiles[fi];
+        const int v = view_of_tile(tb, t);
+        const int lt = t - tb.v[v].tile_base, tx = lt % tb.v[v].TX, ty = lt / tb.v[v].TX;
+        const long long s0 = (long long)v * N, s1 = s0 + N;
+        uint32_t at = at0;
+        for (long long i0 = s0; i0 < s1; i0 += 256) {
+            const long long i = i0 + threadIdx.x;
+            bool hit = false;
+            uint32_t g = 0;
+            if (i < s1) {
+                g = __ldg(order + i);
+                if (__ldg(touched + g) > 0) {
+                    const short4 rc = __ldg(rect + g);
+                    hit = rc.x <= tx && tx < rc.z && rc.y <= ty && ty < rc.w;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            const int w = threadIdx.x >> 5;
+            if ((threadIdx.x & 31) == 0) s_w[w] = __popc(bal);
+            __syncthreads();
+            int base = 0, tot = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) { base += k < w ? s_w[k] : 0; tot += s_w[k]; }
+            if (hit) vals[at + base + __popc(bal & lanemask_lt())] = g;
+            at += (uint32_t)tot;
+            __syncthreads();
+        }
+    }
+}
+
+extern "C" int gs_bin_sort_prefix_repair(const gs_camera *cams, int n_views, int N,
+                                         const int16_t *d_rect, const int32_t *d_touched,
+                                         const int32_t *d_flag_tiles, const int32_t *d_flag_count,
+                                         long long capacity, uint32_t *d_vals, uint32_t *d_tile_ranges,
+                                         const long long *d_n_instances, void *d_workspace,
+                                         size_t workspace_bytes, int *d_err_word, gs_stream_t stream) {
+    TileBatch tb;
+    if (make_tile_batch(cams, n_views, &tb) != GS_OK) return GS_ERR_ARG;
+    if (N < 0 || !d_rect || !d_touched || !d_flag_tiles || !d_flag_count || !d_vals || !d_tile_ranges ||
+        !d_n_instances || !d_workspace)
+        return GS_ERR_ARG;
+    const long long VN = (long long)n_views * N;
+    PrePlan p = make_pre_plan(VN, tb);
+    if (!p.ok || VN == 0) return GS_OK;              // full lists: nothing to repair
+    if (workspace_bytes < p.bytes) return GS_ERR_CAPACITY;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(d_workspace);
+    // the record order left by the last gs_bin_sort_prefix call (see depth_order)
+    const uint32_t *order = (const uint32_t *)(ws + (n_views > 1 ? p.dv1 : p.dv0));
+    const uint32_t *full = (const uint32_t *)(ws + p.full);
+    uint32_t *rep_start = (uint32_t *)(ws + p.kept);  // kept counts are no longer needed
+    { k_rep_alloc<<<1, 1, 0, st>>>(d_flag_tiles, d_flag_count, full, d_n_instances, capacity,
+                                   reinterpret_cast<uint2 *>(d_tile_ranges), rep_start, d_err_word); count_launches(1); }
+    { k_rep_fill<<<64, 256, 0, st>>>(tb, N, VN, d_flag_tiles, d_flag_count, rep_start, order,
+                                     reinterpret_cast<const short4 *>(d_rect), d_touched, d_vals); count_launches(1); }
+    return launch_status();
 }

@@ -292,7 +292,27 @@ __global__ void __launch_bounds__(128) k_project(GeomBatch views, int N, const f
 // ---------------------------------------------------------------------------
 // a6: projection backward (reverse mode of k_project, continuous part)
 // ---------------------------------------------------------------------------
-template <int SDT>
+// Adam applied in place to the grouped parameters by the fused backward.
+struct AdamArgs {
+    float *p, *m, *v;     // grouped 59 N buffers
+    void *shadow;         // [N, 16, 3] 16-bit copy of the updated SH, or null
+    int shadow_dtype;
+    float lr[6];          // means, log-scales, quats, logits, SH DC, SH rest
+    float b1, b2, eps, inv_c1, inv_c2;
+};
+
+__device__ __forceinline__ float adam_update(float *p, float *m, float *v, long long idx, float g, float lr,
+                                             const AdamArgs &a) {
+    float mm = a.b1 * m[idx] + (1.0f - a.b1) * g;
+    float vv = a.b2 * v[idx] + (1.0f - a.b2) * g * g;
+    float pp = p[idx] - lr * (mm * a.inv_c1) / (sqrtf(vv * a.inv_c2) + a.eps);
+    m[idx] = mm;
+    v[idx] = vv;
+    p[idx] = pp;
+    return pp;
+}
+
+template <int SDT, bool ADAM>
 __global__ void __launch_bounds__(128) k_project_bwd(GeomBatch views, int N, const float *__restrict__ means,
                                                      const float *__restrict__ log_scales,
                                                      const float *__restrict__ quats,
@@ -300,9 +320,11 @@ __global__ void __launch_bounds__(128) k_project_bwd(GeomBatch views, int N, con
                                                      const void *__restrict__ sh,
                                                      const int *__restrict__ touched,
                                                      const float *__restrict__ grad2d,
-                                                     float *__restrict__ dparams) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+                                                     float *__restrict__ dparams, AdamArgs adam) {
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (!ADAM && i0 >= N) return;
+    const bool live = i0 < N;
+    const long long i = live ? i0 : (long long)N - 1;     // a valid index for the loads
     float mx = __ldg(means + 3 * i), my = __ldg(means + 3 * i + 1), mz = __ldg(means + 3 * i + 2);
     float ls[3] = {__ldg(log_scales + 3 * i), __ldg(log_scales + 3 * i + 1), __ldg(log_scales + 3 * i + 2)};
     float4 q4 = __ldg(reinterpret_cast<const float4 *>(quats) + i);
@@ -314,7 +336,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(GeomBatch views, int N, con
     for (int j = 0; j < 48; ++j) dsh[j] = 0.0f;
     bool any = false;
     float k[48];
-    for (int vi = 0; vi < views.n; ++vi) {
+    for (int vi = 0; vi < views.n && live; ++vi) {
         long long r = (long long)vi * N + i;
         if (__ldg(touched + r) <= 0) continue;
         const float4 *gp = reinterpret_cast<const float4 *>(grad2d + 12 * r);
@@ -453,15 +475,89 @@ __global__ void __launch_bounds__(128) k_project_bwd(GeomBatch views, int N, con
         dmean[2] += (gd[2] - uz * gdd) * inv;
     }
     const long long n = N;
-    float *pm = dparams, *pls = dparams + 3 * n, *pq = dparams + 6 * n, *plg = dparams + 10 * n,
-          *psh = dparams + 11 * n;
+    if (dparams && live) {
+        float *pm = dparams, *pls = dparams + 3 * n, *pq = dparams + 6 * n, *plg = dparams + 10 * n,
+              *psh = dparams + 11 * n;
 #pragma unroll
-    for (int kk = 0; kk < 3; ++kk) { pm[3 * i + kk] = dmean[kk]; pls[3 * i + kk] = dls[kk]; }
-    reinterpret_cast<float4 *>(pq)[i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
-    plg[i] = dlog;
-    float4 *ps = reinterpret_cast<float4 *>(psh) + 12 * i;
+        for (int kk = 0; kk < 3; ++kk) { pm[3 * i + kk] = dmean[kk]; pls[3 * i + kk] = dls[kk]; }
+        reinterpret_cast<float4 *>(pq)[i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+        plg[i] = dlog;
+        float4 *ps = reinterpret_cast<float4 *>(psh) + 12 * i;
 #pragma unroll
-    for (int j = 0; j < 12; ++j) ps[j] = make_float4(dsh[4 * j], dsh[4 * j + 1], dsh[4 * j + 2], dsh[4 * j + 3]);
+        for (int j = 0; j < 12; ++j) ps[j] = make_float4(dsh[4 * j], dsh[4 * j + 1], dsh[4 * j + 2], dsh[4 * j + 3]);
+    }
+    if (ADAM) {
+        // Stage the warp's 32 x 59 gradients in shared memory, then update each
+        // parameter group with coalesced loads and stores (the update of k_adam).
+        // (rows padded to odd strides, 5 for quaternions and 49 for SH, so the
+        // per-Gaussian writes do not collide in shared-memory banks)
+        __shared__ float s_g[128 / 32][96 + 96 + 160 + 32 + 32 * 49];
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        float *sg = s_g[w];
+        // group offsets inside the warp block: means 0, log-scales 96, quats 192, logits 352, sh 384
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) { sg[3 * l + kk] = dmean[kk]; sg[96 + 3 * l + kk] = dls[kk]; }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) sg[192 + 5 * l + kk] = dq[kk];
+        sg[352 + l] = dlog;
+#pragma unroll
+        for (int j = 0; j < 48; ++j) sg[384 + 49 * l + j] = dsh[j];
+        __syncwarp();
+        const long long wfirst = i0 - l;                  // first Gaussian of this warp
+        const int nlive = (int)min(32ll, max(0ll, (long long)N - wfirst));
+        // 352 entries of the small groups and 1536 of SH per warp: each lane
+        // handles 8 entries at a time, loads first, so that enough requests are
+        // in flight to cover memory latency
+        constexpr int U = 8;
+        for (int e0 = 0; e0 < 352 + 1536; e0 += 32 * U) {
+            long long id[U];
+            float gv[U], lrv[U], pp[U], mm[U], vv[U];
+            int shi[U];
+            bool ok[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + 32 * u + l;
+                int gl, off, width;
+                long long base;
+                float lr;
+                shi[u] = -1;
+                if (e < 96) { width = 3; gl = e / 3; off = e; base = 0; lr = adam.lr[0]; }
+                else if (e < 192) { width = 3; gl = (e - 96) / 3; off = e; base = 3 * n; lr = adam.lr[1]; }
+                else if (e < 320) { width = 4; const int x = e - 192; gl = x >> 2; off = 192 + 5 * gl + (x & 3); base = 6 * n; lr = adam.lr[2]; }
+                else if (e < 352) { width = 1; gl = e - 320; off = 352 + gl; base = 10 * n; lr = adam.lr[3]; }
+                else {
+                    const int x = e - 352;
+                    width = 48; gl = x / 48;
+                    const int j = x - 48 * gl;
+                    off = 384 + 49 * gl + j; base = 11 * n; lr = j < 3 ? adam.lr[4] : adam.lr[5];
+                    shi[u] = x;
+                }
+                const int local = e < 96 ? e : e < 192 ? e - 96 : e < 320 ? e - 192 : e < 352 ? e - 320 : e - 352;
+                ok[u] = e < 352 + 1536 && gl < nlive;
+                id[u] = base + (long long)width * wfirst + local;
+                gv[u] = ok[u] ? sg[off] : 0.0f;
+                lrv[u] = lr;
+                if (ok[u]) { pp[u] = adam.p[id[u]]; mm[u] = adam.m[id[u]]; vv[u] = adam.v[id[u]]; }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!ok[u]) continue;
+                const float m1 = adam.b1 * mm[u] + (1.0f - adam.b1) * gv[u];
+                const float v1 = adam.b2 * vv[u] + (1.0f - adam.b2) * gv[u] * gv[u];
+                const float p1 = pp[u] - lrv[u] * (m1 * adam.inv_c1) / (sqrtf(v1 * adam.inv_c2) + adam.eps);
+                adam.m[id[u]] = m1;
+                adam.v[id[u]] = v1;
+                adam.p[id[u]] = p1;
+                if (adam.shadow && shi[u] >= 0) {
+                    const long long si = 48 * wfirst + shi[u];
+                    if (adam.shadow_dtype == GS_BF16)
+                        reinterpret_cast<__nv_bfloat16 *>(adam.shadow)[si] = __float2bfloat16_rn(p1);
+                    else
+                        reinterpret_cast<__half *>(adam.shadow)[si] = __float2half_rn(p1);
+                }
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -550,12 +646,54 @@ extern "C" int gs_project_bwd(const gs_camera *cams, int n_views, int N, const f
         return GS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int grid = cdiv(N, 128);
+    AdamArgs none{};
     if (sh_dtype == GS_F32)
-        { k_project_bwd<GS_F32><<<grid, 128, 0, st>>>(vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams); count_launches(1); }
+        { k_project_bwd<GS_F32, false><<<grid, 128, 0, st>>>(vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams, none); count_launches(1); }
     else if (sh_dtype == GS_BF16)
-        { k_project_bwd<GS_BF16><<<grid, 128, 0, st>>>(vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams); count_launches(1); }
+        { k_project_bwd<GS_BF16, false><<<grid, 128, 0, st>>>(vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams, none); count_launches(1); }
     else if (sh_dtype == GS_F16)
-        { k_project_bwd<GS_F16><<<grid, 128, 0, st>>>(vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams); count_launches(1); }
+        { k_project_bwd<GS_F16, false><<<grid, 128, 0, st>>>(vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams, none); count_launches(1); }
+    else
+        return GS_ERR_ARG;
+    return launch_status();
+}
+
+extern "C" int gs_project_bwd_adam(const gs_camera *cams, int n_views, int N, float *d_params,
+                                   const void *d_sh, int sh_dtype, const int32_t *d_touched,
+                                   const float *d_grad2d, float *d_m, float *d_v, const float *lr, float b1,
+                                   float b2, float eps, int t, void *d_sh_shadow, int shadow_dtype,
+                                   float *d_dparams, gs_stream_t stream) {
+    GeomBatch vb;
+    if (make_geom_batch(cams, n_views, &vb) != GS_OK) return GS_ERR_ARG;
+    if (N < 0 || t < 1 || !lr) return GS_ERR_ARG;
+    if (N == 0) return GS_OK;
+    if (N % 4 != 0) return GS_ERR_ARG;
+    if (!d_params || !d_touched || !d_grad2d || !d_m || !d_v) return GS_ERR_ARG;
+    if (!aligned(d_params, 16) || !aligned(d_grad2d, 16) || (d_sh && !aligned(d_sh, 16)) ||
+        (d_dparams && !aligned(d_dparams, 16)))
+        return GS_ERR_ARG;
+    if (d_sh_shadow && shadow_dtype != GS_BF16 && shadow_dtype != GS_F16) return GS_ERR_ARG;
+    const long long n = N;
+    const float *means = d_params, *ls = d_params + 3 * n, *q = d_params + 6 * n, *lg = d_params + 10 * n;
+    const void *sh = d_sh ? d_sh : (const void *)(d_params + 11 * n);
+    if (!d_sh) sh_dtype = GS_F32;
+    AdamArgs a;
+    a.p = d_params; a.m = d_m; a.v = d_v;
+    a.shadow = d_sh_shadow;
+    a.shadow_dtype = shadow_dtype;
+    for (int k = 0; k < 6; ++k) a.lr[k] = lr[k];
+    a.b1 = b1; a.b2 = b2; a.eps = eps;
+    const double c1 = 1.0 - pow((double)b1, t), c2 = 1.0 - pow((double)b2, t);
+    a.inv_c1 = (float)(1.0 / c1);
+    a.inv_c2 = (float)(1.0 / c2);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int grid = cdiv(N, 128);
+    if (sh_dtype == GS_F32)
+        { k_project_bwd<GS_F32, true><<<grid, 128, 0, st>>>(vb, N, means, ls, q, lg, sh, d_touched, d_grad2d, d_dparams, a); count_launches(1); }
+    else if (sh_dtype == GS_BF16)
+        { k_project_bwd<GS_BF16, true><<<grid, 128, 0, st>>>(vb, N, means, ls, q, lg, sh, d_touched, d_grad2d, d_dparams, a); count_launches(1); }
+    else if (sh_dtype == GS_F16)
+        { k_project_bwd<GS_F16, true><<<grid, 128, 0, st>>>(vb, N, means, ls, q, lg, sh, d_touched, d_grad2d, d_dparams, a); count_launches(1); }
     else
         return GS_ERR_ARG;
     return launch_status();

@@ -88,6 +88,7 @@ struct SchedArgs {
     const int *order;
     int *queue;
     long long budget_ns;
+    const int *n_order;    // device count of tiles in order (null: all tiles)
 };
 
 // Fetch the next tile for this CTA; -1 when the queue is exhausted.
@@ -101,7 +102,8 @@ __device__ __forceinline__ int next_tile(const SchedArgs &sa, int total_tiles, i
             set_err(err_word, GS_EW_TIMEOUT);
         } else {
             int q = atomicAdd(sa.queue, 1);
-            t = q < total_tiles ? __ldg(sa.order + q) : -1;
+            const int bound = sa.n_order ? min(*sa.n_order, total_tiles) : total_tiles;
+            t = q < bound ? __ldg(sa.order + q) : -1;
             if (t >= total_tiles || t < -1) { set_err(err_word, GS_EW_BOUNDS); t = -1; }
         }
         *s_tile = t;
@@ -156,6 +158,8 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(TileBatch tb, const uin
                                                         float *__restrict__ img, float *__restrict__ T_final,
                                                         int *__restrict__ n_proc, int *__restrict__ tile_nproc,
                                                         unsigned long long *__restrict__ tile_ns,
+                                                        const uint32_t *__restrict__ tile_count,
+                                                        int *__restrict__ flag_tiles, int *__restrict__ flag_count,
                                                         int *err_word) {
     __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
     __shared__ int s_warp[kTilePix / 32];
@@ -194,6 +198,14 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(TileBatch tb, const uin
                     T = Tn;
                     last = __float_as_int(cc.y) + 1;
                 }
+            }
+        }
+        if (tile_count) {
+            // a kept prefix that ran out while a pixel was still blending
+            const int alive = kTilePix - __syncthreads_count(done);
+            if (alive > 0 && threadIdx.x == 0 && c.range.y - c.range.x < __ldg(tile_count + tile)) {
+                const int idx = atomicAdd(flag_count, 1);
+                flag_tiles[idx] = tile;
             }
         }
         const ViewTiles &vt = tb.v[c.view];
@@ -339,6 +351,7 @@ static int fill_sched(const gs_schedule *sched, const TileBatch &tb, SchedArgs *
     sa->order = nullptr;
     sa->queue = nullptr;
     sa->budget_ns = 0;
+    sa->n_order = nullptr;
     *grid = tb.total_tiles;
     if (!sched || sched->mode == GS_SCHED_RASTER) return GS_OK;
     if (sched->mode != GS_SCHED_ORDER || !sched->d_order || !sched->d_queue) return GS_ERR_ARG;
@@ -346,6 +359,7 @@ static int fill_sched(const gs_schedule *sched, const TileBatch &tb, SchedArgs *
     sa->order = sched->d_order;
     sa->queue = sched->d_queue;
     sa->budget_ns = sched->budget_ns;
+    sa->n_order = sched->d_n_order;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -361,6 +375,7 @@ extern "C" int gs_render_fwd(const gs_camera *cams, int n_views, const uint32_t 
                              const uint32_t *d_vals, const void *d_splats, int rgb_dtype,
                              const gs_schedule *sched, float *d_img, float *d_T_final,
                              int32_t *d_n_proc, int32_t *d_tile_nproc, uint64_t *d_tile_ns,
+                             const uint32_t *d_tile_count, int32_t *d_flag_tiles, int32_t *d_flag_count,
                              int *d_err_word, gs_stream_t stream) {
     TileBatch tb;
     if (make_tile_batch(cams, n_views, &tb) != GS_OK) return GS_ERR_ARG;
@@ -368,6 +383,7 @@ extern "C" int gs_render_fwd(const gs_camera *cams, int n_views, const uint32_t 
         return GS_ERR_ARG;
     if (!aligned(d_splats, 16) || !aligned(d_tile_ranges, 8)) return GS_ERR_ARG;
     if (rgb_dtype < GS_F32 || rgb_dtype > GS_F16) return GS_ERR_ARG;
+    if (d_tile_count && (!d_flag_tiles || !d_flag_count)) return GS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const void *kern = rgb_dtype == GS_F32 ? (const void *)k_render_fwd<GS_F32>
                        : rgb_dtype == GS_BF16 ? (const void *)k_render_fwd<GS_BF16>
@@ -380,11 +396,11 @@ extern "C" int gs_render_fwd(const gs_camera *cams, int n_views, const uint32_t 
     const uint2 *rg = reinterpret_cast<const uint2 *>(d_tile_ranges);
     unsigned long long *tns = reinterpret_cast<unsigned long long *>(d_tile_ns);
     if (rgb_dtype == GS_F32)
-        { k_render_fwd<GS_F32><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_err_word); count_launches(1); }
+        { k_render_fwd<GS_F32><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_tile_count, d_flag_tiles, d_flag_count, d_err_word); count_launches(1); }
     else if (rgb_dtype == GS_BF16)
-        { k_render_fwd<GS_BF16><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_err_word); count_launches(1); }
+        { k_render_fwd<GS_BF16><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_tile_count, d_flag_tiles, d_flag_count, d_err_word); count_launches(1); }
     else
-        { k_render_fwd<GS_F16><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_err_word); count_launches(1); }
+        { k_render_fwd<GS_F16><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_tile_count, d_flag_tiles, d_flag_count, d_err_word); count_launches(1); }
     return launch_status();
 }
 

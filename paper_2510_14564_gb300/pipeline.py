@@ -64,8 +64,12 @@ class Frame:
     """Device buffers and calls for one batch of views of N Gaussians."""
 
     def __init__(self, cams, N: int, rgb_dtype: int = L.GS_F32, sh_dtype: int = L.GS_F32,
-                 capacity: int | None = None, schedule: Schedule | None = None, device=None):
+                 capacity: int | None = None, schedule: Schedule | None = None, device=None,
+                 prefix: bool = False):
+        """prefix: bin with gs_bin_sort_prefix (exact list prefixes that blending
+        never runs past) instead of the full lists of gs_bin_sort."""
         self.dev = device or _dev()
+        self.prefix = prefix
         self.cams = list(cams)
         self.V = len(self.cams)
         self.N = int(N)
@@ -85,10 +89,14 @@ class Frame:
         self.err = torch.zeros(1, dtype=torch.int32, device=d)
         self.n_inst = torch.zeros(1, dtype=torch.int64, device=d)
         self.ranges = torch.empty(self.T * 2, dtype=torch.int32, device=d)
+        self.tile_count = torch.zeros(self.T, dtype=torch.int32, device=d)
         self.img = torch.empty(3 * self.P, dtype=torch.float32, device=d)
         self.T_final = torch.empty(self.P, dtype=torch.float32, device=d)
         self.n_proc = torch.empty(self.P, dtype=torch.int32, device=d)
-        self.tile_nproc = torch.empty(self.T, dtype=torch.int32, device=d)
+        self.tile_nproc = torch.full((self.T,), -1, dtype=torch.int32, device=d)   # -1: no history
+        self.flag_tiles = torch.zeros(self.T, dtype=torch.int32, device=d)
+        self.flag_count = torch.zeros(1, dtype=torch.int32, device=d)
+        self.limit_history = True          # cut prefixes at 2x the last step's processed count
         self.tile_ns = torch.zeros(self.T, dtype=torch.int64, device=d)
         self.dimg = torch.empty(3 * self.P, dtype=torch.float32, device=d)
         self.loss = torch.zeros(1, dtype=torch.float32, device=d)
@@ -132,7 +140,10 @@ class Frame:
         self.capacity = max(capacity, self.capacity)
         self.vals = torch.empty(self.capacity, dtype=torch.int32, device=self.dev)
         self.keys = torch.empty(self.capacity, dtype=torch.int64, device=self.dev) if with_keys else None
-        nbytes = L.gs_bin_sort_workspace(self.cams, self.N, self.capacity)
+        if self.prefix:
+            nbytes = L.gs_bin_sort_prefix_workspace(self.cams, self.N, self.capacity)
+        else:
+            nbytes = L.gs_bin_sort_workspace(self.cams, self.N, self.capacity)
         self.ws = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device=self.dev)
 
     # -- forward -----------------------------------------------------------
@@ -141,19 +152,29 @@ class Frame:
                      params["opacity_logits"], params["sh"], self.sh_dtype, self.splats,
                      self.rgb_dtype, self.depth, self.rect, self.touched, self.radius, self.err)
 
+    def _bin(self, capacity: int, keys) -> None:
+        if self.prefix:
+            lim = self.tile_nproc if self.limit_history else None
+            L.gs_bin_sort_prefix(self.cams, self.N, self.depth, self.rect, self.touched, self.splats,
+                                 self.rgb_dtype, lim, capacity, self.vals, self.ranges, self.tile_count,
+                                 keys, self.n_inst, self.ws, self.err)
+        else:
+            L.gs_bin_sort(self.cams, self.N, self.depth, self.rect, self.touched, capacity, self.vals,
+                          self.ranges, keys, self.n_inst, self.ws, self.err)
+
     def bin_sort(self, want_keys: bool = False) -> None:
         if self.vals is None:
             # first call: size the instance buffers from the exact count
             self.reserve(1)
-            L.gs_bin_sort(self.cams, self.N, self.depth, self.rect, self.touched, 0, self.vals,
-                          self.ranges, None, self.n_inst, self.ws, self.err)
+            self._bin(0, None)
             need = int(self.n_inst.item())
-            self.reserve(int(need * 1.25) + 1024, with_keys=want_keys)
+            if self.prefix:          # room for repairs: the full lists
+                need = max(need, int(self.tile_count.sum().item()))
+            self.reserve(int(need * 1.25) + 65536, with_keys=want_keys)
             self.err.bitwise_and_(~L.GS_EW_CAPACITY)      # the sizing pass overflowed on purpose
         elif want_keys and self.keys is None:
             self.reserve(self.capacity, with_keys=True)
-        L.gs_bin_sort(self.cams, self.N, self.depth, self.rect, self.touched, self.capacity, self.vals,
-                      self.ranges, self.keys if want_keys else None, self.n_inst, self.ws, self.err)
+        self._bin(self.capacity, self.keys if want_keys else None)
 
     def _sched_fwd(self):
         m = self.sched.mode
@@ -180,9 +201,23 @@ class Frame:
         s = self._sched_fwd()
         if mark:
             mark("render_fwd")
+        tns = self.tile_ns if timing else None
+        if not self.prefix:
+            L.gs_render_fwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, s, self.img,
+                            self.T_final, self.n_proc, self.tile_nproc, tns, self.err)
+            return
+        # kept prefixes: check that no pixel ran past one, rebuild and re-render any that did
+        self.flag_count.zero_()
         L.gs_render_fwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, s, self.img,
-                        self.T_final, self.n_proc, self.tile_nproc, self.tile_ns if timing else None,
-                        self.err)
+                        self.T_final, self.n_proc, self.tile_nproc, tns, self.err,
+                        tile_count=self.tile_count, flag_tiles=self.flag_tiles, flag_count=self.flag_count)
+        L.gs_bin_sort_prefix_repair(self.cams, self.N, self.rect, self.touched, self.flag_tiles,
+                                    self.flag_count, self.capacity, self.vals, self.ranges, self.n_inst,
+                                    self.ws, self.err)
+        rep = {"mode": L.GS_SCHED_ORDER, "order": self.flag_tiles, "queue": self.queue,
+               "n_order": self.flag_count}
+        L.gs_render_fwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, rep, self.img,
+                        self.T_final, self.n_proc, self.tile_nproc, tns, self.err)
 
     def forward(self, params: dict, timing: bool = False) -> torch.Tensor:
         self.project(params)
@@ -242,7 +277,7 @@ class Trainer:
 
     def __init__(self, cams, params_flat: torch.Tensor, N: int, targets: torch.Tensor,
                  rgb_dtype: int = L.GS_F32, sh_storage: int = L.GS_F32,
-                 schedule: Schedule | None = None, lr=DEFAULT_LR):
+                 schedule: Schedule | None = None, lr=DEFAULT_LR, prefix: bool = True):
         self.N = N
         self.p = params_flat
         self.m = torch.zeros_like(params_flat)
@@ -257,7 +292,7 @@ class Trainer:
         else:
             self.sh_shadow = None
         self.frame = Frame(cams, N, rgb_dtype=rgb_dtype, sh_dtype=sh_storage, schedule=schedule,
-                           device=params_flat.device)
+                           device=params_flat.device, prefix=prefix)
         self.targets = targets
 
     def params_for_kernels(self) -> dict:
@@ -282,10 +317,20 @@ class Trainer:
         mk("l1")
         f.l1(self.targets if targets is None else targets)
         mk("sched_bwd")
-        g = f.backward(pk, f.dimg, mark=mark)
+        f.grad2d.zero_()
+        s = f._sched_bwd()
+        mk("render_bwd")
+        L.gs_render_bwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, s, f.dimg, f.T_final, f.n_proc,
+                        f.tile_nproc, f.grad2d, f.err)
+        # projection backward, then Adam (two streaming kernels; the fused
+        # gs_project_bwd_adam is slower at the backward's register budget)
+        mk("project_bwd")
+        pk_sh = self.sh_shadow if self.sh_shadow is not None else pk["sh"]
+        L.gs_project_bwd(f.cams, self.N, pk["means"], pk["log_scales"], pk["quats"], pk["opacity_logits"],
+                         pk_sh, self.sh_storage, f.touched, f.grad2d, f.dparams)
         mk("adam")
         self.t += 1
-        L.gs_adam_step(self.N, self.p, g, self.m, self.v, self.lr, ADAM_B1, ADAM_B2, ADAM_EPS, self.t,
+        L.gs_adam_step(self.N, self.p, f.dparams, self.m, self.v, self.lr, ADAM_B1, ADAM_B2, ADAM_EPS, self.t,
                        self.sh_shadow, self.sh_storage)
         if timing and (f.step_count % max(1, f.sched.train_every) == 0):
             mk("mlp_train")

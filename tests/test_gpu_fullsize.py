@@ -49,17 +49,19 @@ def test_fullsize_fp32_count_path(full):
     # every Gaussian's discrete path
     assert np.array_equal(f.touched.cpu().numpy(), kp["touched"])
     assert np.array_equal(f.rect.cpu().numpy().reshape(-1, 4), kp["rect"])
-    # every tile's count; sampled tiles' full lists
+    # every tile's full count; the kept prefixes of sampled tiles (the
+    # training step bins with gs_bin_sort_prefix)
     counts = O.tile_counts(cam, kp)
+    assert np.array_equal(f.tile_count.cpu().numpy().astype(np.int64), counts)
     rg = f.ranges.cpu().numpy().reshape(-1, 2).astype(np.int64)
-    assert int(f.n_inst.item()) == int(counts.sum())
-    assert np.array_equal(rg[:, 1] - rg[:, 0], counts)
+    kept = rg[:, 1] - rg[:, 0]
+    assert np.all(kept <= counts) and int(f.n_inst.item()) == int(kept.sum())
     vals = f.vals.cpu().numpy().view(np.uint32)
     rng = np.random.default_rng(0)
     sample = set(rng.choice(cam.n_tiles, 8, replace=False).tolist())
     sample |= {int(np.argmax(counts)), 0, cam.n_tiles - 1, cam.tiles_x - 1}
     for t in sorted(sample):
-        ids = O.tile_list(kp, t % cam.tiles_x, t // cam.tiles_x)
+        ids = O.tile_list(kp, t % cam.tiles_x, t // cam.tiles_x)[:kept[t]]
         assert np.array_equal(vals[rg[t, 0]:rg[t, 1]], ids), t
     # the centre crop: image and gradients
     win = _crop(cam)

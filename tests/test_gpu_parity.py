@@ -209,3 +209,48 @@ def test_adam_step():
     assert np.allclose(m.cpu().numpy(), mo, rtol=1e-5, atol=1e-7)
     sh_now = p.cpu().numpy()[11 * N:]
     assert torch.equal(shadow.cpu(), torch.from_numpy(sh_now).to(torch.bfloat16))
+
+
+@pytest.mark.parametrize("sh_dtype", [L.GS_F32, L.GS_BF16])
+def test_fused_backward_adam_matches_separate_calls(sh_dtype):
+    scene = S.uniform_scene(10_000, 0)
+    cam = S.front_camera(256, 256)
+    n = scene.n
+    params = P.to_device_params(scene)
+    views = dict(P.param_views(params, n))
+    shadow0 = views["sh"].to(torch.bfloat16) if sh_dtype == L.GS_BF16 else None
+    if shadow0 is not None:
+        views["sh"] = shadow0
+    fr = P.Frame([cam], n, sh_dtype=sh_dtype)
+    fr.project(views)
+    fr.bin_sort()
+    fr.render()
+    d = torch.from_numpy(S.random_cotangent((3 * fr.P,), seed=6) * 1e-3).cuda()
+    fr.grad2d.zero_()
+    L.gs_render_bwd(fr.cams, fr.ranges, fr.vals, fr.splats, fr.rgb_dtype, None, d, fr.T_final, fr.n_proc,
+                    fr.tile_nproc, fr.grad2d, fr.err)
+    rng = np.random.default_rng(2)
+    m0 = torch.from_numpy(rng.normal(0, 1e-3, 59 * n).astype(np.float32)).cuda()
+    v0 = torch.from_numpy(rng.random(59 * n).astype(np.float32) * 1e-6).cuda()
+    lr = P.DEFAULT_LR
+    # separate calls
+    pA, mA, vA = params.clone(), m0.clone(), v0.clone()
+    vw = P.param_views(pA, n)
+    g = torch.empty(59 * n, device="cuda")
+    L.gs_project_bwd([cam], n, vw["means"], vw["log_scales"], vw["quats"], vw["opacity_logits"],
+                     shadow0 if shadow0 is not None else vw["sh"], sh_dtype, fr.touched, fr.grad2d, g)
+    shA = torch.empty(48 * n, dtype=torch.bfloat16, device="cuda")
+    L.gs_adam_step(n, pA, g, mA, vA, lr, 0.9, 0.999, 1e-15, 3, shA, L.GS_BF16)
+    # fused
+    pB, mB, vB = params.clone(), m0.clone(), v0.clone()
+    gB = torch.empty(59 * n, device="cuda")
+    shB = torch.empty(48 * n, dtype=torch.bfloat16, device="cuda")
+    L.gs_project_bwd_adam([cam], n, pB, shadow0, sh_dtype if shadow0 is not None else L.GS_F32, fr.touched,
+                          fr.grad2d, mB, vB, lr, 0.9, 0.999, 1e-15, 3, shB, L.GS_BF16, gB)
+    torch.cuda.synchronize()
+    # the same backward (two compilations of one source: last-bit differences only)
+    assert (g - gB).abs().max() <= 1e-5 * g.abs().max()
+    assert torch.allclose(pA, pB, rtol=1e-6, atol=1e-7)
+    assert torch.allclose(mA, mB, rtol=1e-6, atol=1e-9)
+    assert torch.allclose(vA, vB, rtol=1e-6, atol=1e-12)
+    assert (shA.float() - shB.float()).abs().max() <= 2 ** -7 * shA.float().abs().max()

@@ -1,0 +1,104 @@
+"""gs_bin_sort_prefix: exact list prefixes that blending never runs past.
+
+Checks, against the oracle, that every kept list is an exact prefix of the
+tile's full (tile, depth) list and that the full lengths are reported; and,
+against the full-list path, that images, transmittance, processed counts
+and gradients are unchanged."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2510_14564_gb300 import _lib as L
+from paper_2510_14564_gb300 import pipeline as P
+from paper_2510_14564_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "uniform-10k-256x256": lambda: (S.uniform_scene(10_000, 0), [S.front_camera(256, 256)]),
+    "skewed-200k-640x480": lambda: (S.skewed_scene(200_000, 0), [S.front_camera(640, 480)]),
+    "skewed-60k-3views": lambda: (S.skewed_scene(60_000, 3),
+                                  S.ring_cameras(3, [(320, 240), (200, 300), (256, 256)])),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("rgb", [L.GS_F32, L.GS_BF16])
+def test_prefix_binning_is_exact(name, rgb):
+    scene, cams = CASES[name]()
+    params = P.to_device_params(scene)
+    views = dict(P.param_views(params, scene.n))
+    if rgb == L.GS_BF16:
+        views["sh"] = views["sh"].to(torch.bfloat16)
+    frames = {}
+    for prefix in (False, True):
+        fr = P.Frame(cams, scene.n, rgb_dtype=rgb, sh_dtype=rgb, prefix=prefix)
+        for _ in range(2 if prefix else 1):      # the second step cuts at the first's counts
+            fr.project(views)
+            fr.bin_sort()
+            fr.render()
+        frames[prefix] = fr
+    torch.cuda.synchronize()
+    full, pre = frames[False], frames[True]
+    assert full.check_errors() == 0 and pre.check_errors() == 0
+    rg = pre.ranges.cpu().numpy().reshape(-1, 2).astype(np.int64)
+    kept = rg[:, 1] - rg[:, 0]
+    vals = pre.vals.cpu().numpy().view(np.uint32)
+    counts = pre.tile_count.cpu().numpy().astype(np.int64)
+    base = 0
+    for v, cam in enumerate(cams):
+        kp = O.keypath(cam, scene)
+        oc = O.tile_counts(cam, kp)
+        assert np.array_equal(counts[base:base + cam.n_tiles], oc)
+        for t in range(cam.n_tiles):
+            k = kept[base + t]
+            assert 0 <= k <= oc[t]
+            if k:
+                ids = O.tile_list(kp, t % cam.tiles_x, t // cam.tiles_x)[:k]
+                assert np.array_equal(vals[rg[base + t, 0]:rg[base + t, 1]] - v * scene.n, ids), (v, t)
+        base += cam.n_tiles
+    assert int(pre.n_inst.item()) == int(kept.sum())
+    print(f"\n{name}: kept {kept.sum()} of {counts.sum()} instances ({kept.sum() / max(1, counts.sum()):.3f})")
+    # the render cannot tell the difference
+    assert torch.equal(full.img, pre.img)
+    assert torch.equal(full.T_final, pre.T_final)
+    assert torch.equal(full.n_proc, pre.n_proc)
+    assert torch.equal(full.tile_nproc, pre.tile_nproc)
+    d = torch.from_numpy(S.random_cotangent((3 * full.P,), seed=4) * 1e-3).cuda()
+    g0 = full.backward(views, d).clone()
+    g1 = pre.backward(views, d)
+    assert (g0 - g1).abs().max() <= 1e-5 * g0.abs().max()
+
+
+def test_prefix_repair_restores_exact_results():
+    """Limits far too short: the forward lists the tiles that ran out, the
+    repair rebuilds their full lists, the re-render makes every output equal
+    to the full-list path."""
+    scene, cams = S.skewed_scene(200_000, 0), [S.front_camera(640, 480)]
+    params = P.to_device_params(scene)
+    views = P.param_views(params, scene.n)
+    full = P.Frame(cams, scene.n)
+    full.project(views)
+    full.bin_sort()
+    full.render()
+    pre = P.Frame(cams, scene.n, prefix=True)
+    pre.project(views)
+    pre.bin_sort()                      # sizes the buffers (no history yet)
+    pre.tile_nproc.fill_(1)             # pretend the last step processed one entry per tile
+    pre.bin_sort()
+    kept = int(pre.n_inst.item())
+    pre.render()
+    torch.cuda.synchronize()
+    flagged = int(pre.flag_count.item())
+    print(f"\nrepaired {flagged} tiles of {pre.T}; kept {kept} before repair")
+    assert flagged > 0
+    assert pre.check_errors() == 0
+    assert torch.equal(full.img, pre.img)
+    assert torch.equal(full.T_final, pre.T_final)
+    assert torch.equal(full.n_proc, pre.n_proc)
+    d = torch.from_numpy(S.random_cotangent((3 * full.P,), seed=5) * 1e-3).cuda()
+    g0 = full.backward(views, d).clone()
+    g1 = pre.backward(views, d)
+    assert (g0 - g1).abs().max() <= 1e-5 * g0.abs().max()
