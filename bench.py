@@ -196,6 +196,8 @@ def run_ours(args):
         plain.step()
     plain_ms, _ = timed(plain, args.steps)
     plain_ips = args.steps / (plain_ms / 1e3)
+    plain_stages = {}
+    timed(plain, args.steps, stage_times=plain_stages)
     assert plain.frame.check_errors() == 0, "kernel error word set (plain path)"
     del plain
     torch.cuda.empty_cache()
@@ -217,6 +219,7 @@ def run_ours(args):
     assert tr.frame.check_errors() == 0, "kernel error word set (learned path)"
 
     f = tr.frame
+    sched_diag = schedule_diagnostics(f, L, torch)
     I = int(f.n_inst.item())
     I_proc = int(f.tile_nproc.sum().item())
     Pix = cam.W * cam.H
@@ -243,8 +246,10 @@ def run_ours(args):
                    "instances": I, "processed_instances": I_proc,
                    "l2": "inputs larger than L2 (0.4-0.7 GB of parameters, 1.5+ GB of instances)",
                    "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "mlp_calibration_steps": args.calib},
+                   "mlp_calibration_steps": args.calib,
+                   "schedules": sched_diag},
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "stage_ms_plain_fp32": {k: round(statistics.mean(v), 4) for k, v in plain_stages.items()},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                      "traffic": None, "peak_source": peak_kind,
@@ -260,6 +265,59 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def schedule_diagnostics(f, L, torch, reps=5) -> dict:
+    """Render makespans (best of `reps`, ms) of the forward and backward
+    passes under the raster, count and learned tile orders (orders computed
+    beforehand), the cost of computing each order, and per-tile time spread."""
+    def best(fn):
+        out = 1e9
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            out = min(out, a.elapsed_time(b))
+        return round(out, 4)
+
+    keep = f.use_learned
+    f.use_learned = False
+    t_count = best(lambda: f._sched_fwd())
+    o_count = f.order_f.clone()
+    f.use_learned = True
+    t_learned = best(lambda: f._sched_fwd())
+    o_learned = f.order_f.clone()
+    f.use_learned = keep
+    L.gs_int_cost(f.tile_nproc, f.T, f.cost)
+    L.gs_sched_order(f.cost, f.T, f.order_b, f.order_ws)
+    o_bwd = f.order_b.clone()
+
+    def sch(o):
+        return None if o is None else {"mode": L.GS_SCHED_ORDER, "order": o, "queue": f.queue}
+
+    def fwd(o):
+        L.gs_render_fwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, sch(o), f.img, f.T_final, f.n_proc,
+                        f.tile_nproc, None, f.err)
+
+    def bwd(o):
+        L.gs_render_bwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, sch(o), f.dimg, f.T_final, f.n_proc,
+                        f.tile_nproc, f.grad2d, f.err)
+
+    out = {"fwd_ms": {"raster": best(lambda: fwd(None)), "count": best(lambda: fwd(o_count)),
+                      "learned": best(lambda: fwd(o_learned))},
+           "bwd_ms": {"raster": best(lambda: bwd(None)), "by_processed": best(lambda: bwd(o_bwd)),
+                      "learned": best(lambda: bwd(o_learned))},
+           "order_cost_ms": {"count": t_count, "learned": t_learned}}
+    fwd(o_learned)
+    L.gs_render_fwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, sch(o_learned), f.img, f.T_final,
+                    f.n_proc, f.tile_nproc, f.tile_ns, f.err)
+    torch.cuda.synchronize()
+    ns = f.tile_ns.double()
+    out["tile_us"] = {"mean": round(float(ns.mean()) / 1e3, 3), "max": round(float(ns.max()) / 1e3, 3),
+                      "p99": round(float(ns.quantile(0.99)) / 1e3, 3)}
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -314,10 +314,12 @@ int gs_adam_flat(long long n, float *d_p, const float *d_g, float *d_m, float *d
  *   f4 log1p(sum o cov),
  *   f5 log1p(sum of Th_j over entries with Th_j >= 1e-4), where Th_0 = 1 and
  *      Th_{j+1} = Th_j (1 - min(0.99, o_j cov_j)) (expected transmittance),
- *   f6 fraction of the tile's pixels inside the image, f7 log1p(W H) / 16. */
+ *   f6 fraction of the tile's pixels inside the image, f7 log1p(W H) / 16.
+ * With d_w16 (FP16 MLP weights, as gs_mlp_predict) and d_pred, the
+ * prediction of each tile is also written (both NULL: features only). */
 int gs_tile_features(const gs_camera *cams, int n_views, const uint32_t *d_tile_ranges,
                      const uint32_t *d_vals, const void *d_splats, int rgb_dtype, int cap,
-                     float *d_feats, gs_stream_t stream);
+                     float *d_feats, const void *d_w16, float *d_pred, gs_stream_t stream);
 
 /* MLP 8 -> 32 (ReLU) -> 1.  Weights are 321 values in the order W1 [32, 8]
  * (row-major), b1 [32], W2 [32], b2 [1].  gs_mlp_predict reads FP16 weights

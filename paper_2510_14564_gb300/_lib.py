@@ -91,7 +91,7 @@ def lib():
                                           F32, I32, VP, I32, VP, VP]
         L.gs_adam_step.argtypes = [I32, VP, VP, VP, VP, P(F32), F32, F32, F32, I32, VP, I32, VP]
         L.gs_adam_flat.argtypes = [I64, VP, VP, VP, VP, F32, F32, F32, F32, I32, VP]
-        L.gs_tile_features.argtypes = [P(GsCamera), I32, VP, VP, VP, I32, I32, VP, VP]
+        L.gs_tile_features.argtypes = [P(GsCamera), I32, VP, VP, VP, I32, I32, VP, VP, VP, VP]
         L.gs_mlp_predict.argtypes = [VP, VP, I32, VP, VP]
         L.gs_mlp_grad.argtypes = [VP, VP, VP, VP, I32, VP, VP, VP]
         L.gs_mlp_train_step.argtypes = [VP, VP, VP, VP, I32, F32, VP, VP, VP, I32, VP, VP, VP]
@@ -293,11 +293,12 @@ def gs_adam_flat(n, p, g, m, v, lr, b1, b2, eps, t, stream=None):
                              float(eps), int(t), stream_ptr(stream)), "gs_adam_flat")
 
 
-def gs_tile_features(cams, tile_ranges, vals, splats, rgb_dtype, cap, feats, stream=None):
+def gs_tile_features(cams, tile_ranges, vals, splats, rgb_dtype, cap, feats, w16=None, pred=None,
+                     stream=None):
     ca = camera_array(cams)
     check(lib().gs_tile_features(ca, len(cams), ptr(tile_ranges), ptr(vals), ptr(splats),
-                                 int(rgb_dtype), int(cap), ptr(feats), stream_ptr(stream)),
-          "gs_tile_features")
+                                 int(rgb_dtype), int(cap), ptr(feats), ptr(w16), ptr(pred),
+                                 stream_ptr(stream)), "gs_tile_features")
 
 
 def gs_mlp_predict(w16, feats, n, pred, stream=None):

@@ -23,11 +23,32 @@ constexpr int kMlpW = kMlpH * kMlpF + kMlpH + kMlpH + 1;   // 321
 //   f4 log1p(sum o cov)             f5 log1p(sum of the expected
 //   transmittance Th_j while Th_j >= 1e-4; Th_{j+1} = Th_j (1 - min(0.99, o_j cov_j)))
 //   f6 in-image pixel fraction      f7 log1p(W H) / 16
+// The MLP of k_mlp_predict on one feature row (weights already in smem).
+__device__ __forceinline__ float mlp_eval(const float *s_w, const float f[8]) {
+    const float *W1 = s_w, *b1 = s_w + 256, *W2 = s_w + 288;
+    float acc = s_w[320];
+#pragma unroll 8
+    for (int h = 0; h < kMlpH; ++h) {
+        float z = b1[h];
+#pragma unroll
+        for (int k = 0; k < kMlpF; ++k) z = fmaf(W1[8 * h + k], f[k], z);
+        acc = fmaf(W2[h], fmaxf(z, 0.f), acc);
+    }
+    return acc;
+}
+
 template <int DT>
 __global__ void __launch_bounds__(256) k_tile_features(TileBatch tb, const uint2 *__restrict__ ranges,
                                                        const uint32_t *__restrict__ vals,
                                                        const void *__restrict__ splats, int cap,
-                                                       float *__restrict__ feats) {
+                                                       float *__restrict__ feats,
+                                                       const __half *__restrict__ w16,
+                                                       float *__restrict__ pred) {
+    __shared__ float s_w[kMlpW];
+    if (w16) {
+        for (int k = threadIdx.x; k < kMlpW; k += blockDim.x) s_w[k] = __half2float(w16[k]);
+        __syncthreads();
+    }
     const int tile = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     const int l = threadIdx.x & 31;
     if (tile >= tb.total_tiles) return;
@@ -82,6 +103,10 @@ __global__ void __launch_bounds__(256) k_tile_features(TileBatch tb, const uint2
         f[5] = log1pf(sth);
         f[6] = (float)(inx * iny) / (float)kTilePix;
         f[7] = log1pf((float)vt.W * (float)vt.H) / 16.0f;
+        if (w16) {
+            const float fr[8] = {f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7]};
+            pred[tile] = mlp_eval(s_w, fr);
+        }
     }
 }
 
@@ -293,20 +318,22 @@ using namespace gs;
 
 extern "C" int gs_tile_features(const gs_camera *cams, int n_views, const uint32_t *d_tile_ranges,
                                 const uint32_t *d_vals, const void *d_splats, int rgb_dtype, int cap,
-                                float *d_feats, gs_stream_t stream) {
+                                float *d_feats, const void *d_w16, float *d_pred, gs_stream_t stream) {
     TileBatch tb;
     if (make_tile_batch(cams, n_views, &tb) != GS_OK) return GS_ERR_ARG;
     if (!d_tile_ranges || !d_vals || !d_splats || !d_feats || cap < 1) return GS_ERR_ARG;
+    if ((d_w16 == nullptr) != (d_pred == nullptr)) return GS_ERR_ARG;
+    const __half *w16 = reinterpret_cast<const __half *>(d_w16);
     if (!aligned(d_splats, 16) || !aligned(d_tile_ranges, 8)) return GS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int grid = cdiv((long long)tb.total_tiles * 32, 256);
     const uint2 *rg = reinterpret_cast<const uint2 *>(d_tile_ranges);
     if (rgb_dtype == GS_F32)
-        { k_tile_features<GS_F32><<<grid, 256, 0, st>>>(tb, rg, d_vals, d_splats, cap, d_feats); count_launches(1); }
+        { k_tile_features<GS_F32><<<grid, 256, 0, st>>>(tb, rg, d_vals, d_splats, cap, d_feats, w16, d_pred); count_launches(1); }
     else if (rgb_dtype == GS_BF16)
-        { k_tile_features<GS_BF16><<<grid, 256, 0, st>>>(tb, rg, d_vals, d_splats, cap, d_feats); count_launches(1); }
+        { k_tile_features<GS_BF16><<<grid, 256, 0, st>>>(tb, rg, d_vals, d_splats, cap, d_feats, w16, d_pred); count_launches(1); }
     else if (rgb_dtype == GS_F16)
-        { k_tile_features<GS_F16><<<grid, 256, 0, st>>>(tb, rg, d_vals, d_splats, cap, d_feats); count_launches(1); }
+        { k_tile_features<GS_F16><<<grid, 256, 0, st>>>(tb, rg, d_vals, d_splats, cap, d_feats, w16, d_pred); count_launches(1); }
     else
         return GS_ERR_ARG;
     return launch_status();

@@ -47,17 +47,22 @@ __device__ __forceinline__ float group_lr(const AdamGroups &g, long long i) {
     if (i < g.b[1]) return g.lr[1];
     if (i < g.b[2]) return g.lr[2];
     if (i < g.b[3]) return g.lr[3];
-    long long s = i - g.sh0;
-    return (s % 48) < 3 ? g.lr[4] : g.lr[5];
+    const unsigned long long s = (unsigned long long)(i - g.sh0);
+    return (s % 48ull) < 3 ? g.lr[4] : g.lr[5];
+}
+
+__device__ __forceinline__ void adam_core(float &p, float g, float &m, float &v, float lr, float b1, float b2,
+                                          float inv_c1, float inv_c2, float eps) {
+    m = b1 * m + (1.0f - b1) * g;
+    v = b2 * v + (1.0f - b2) * g * g;
+    p -= lr * (m * inv_c1) / (sqrtf(v * inv_c2) + eps);
 }
 
 template <int SHD>
 __device__ __forceinline__ void adam_one(long long i, float &p, float g, float &m, float &v, float lr,
                                          float b1, float b2, float inv_c1, float inv_c2, float eps,
                                          void *shadow, long long sh0, long long total) {
-    m = b1 * m + (1.0f - b1) * g;
-    v = b2 * v + (1.0f - b2) * g * g;
-    p -= lr * (m * inv_c1) / (sqrtf(v * inv_c2) + eps);
+    adam_core(p, g, m, v, lr, b1, b2, inv_c1, inv_c2, eps);
     if (SHD != 0 && i >= sh0 && i < total) {
         long long s = i - sh0;
         if (SHD == GS_BF16) reinterpret_cast<__nv_bfloat16 *>(shadow)[s] = __float2bfloat16_rn(p);
@@ -78,10 +83,23 @@ __global__ void __launch_bounds__(256) k_adam(long long total, float *__restrict
         float4 mm = reinterpret_cast<float4 *>(m)[q];
         float4 vv = reinterpret_cast<float4 *>(v)[q];
         long long i = 4 * q;
-        adam_one<SHD>(i, pp.x, gg.x, mm.x, vv.x, group_lr(grp, i), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
-        adam_one<SHD>(i + 1, pp.y, gg.y, mm.y, vv.y, group_lr(grp, i + 1), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
-        adam_one<SHD>(i + 2, pp.z, gg.z, mm.z, vv.z, group_lr(grp, i + 2), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
-        adam_one<SHD>(i + 3, pp.w, gg.w, mm.w, vv.w, group_lr(grp, i + 3), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
+        if (SHD != 0 && (grp.sh0 & 3) == 0 && i >= grp.sh0) {
+            // a float4 inside the SH group: one 8-byte store of the 16-bit shadow
+            const long long s4 = i - grp.sh0;
+            const float lr0 = group_lr(grp, i), lr1 = group_lr(grp, i + 1), lr2 = group_lr(grp, i + 2),
+                        lr3 = group_lr(grp, i + 3);
+            adam_core(pp.x, gg.x, mm.x, vv.x, lr0, b1, b2, inv_c1, inv_c2, eps);
+            adam_core(pp.y, gg.y, mm.y, vv.y, lr1, b1, b2, inv_c1, inv_c2, eps);
+            adam_core(pp.z, gg.z, mm.z, vv.z, lr2, b1, b2, inv_c1, inv_c2, eps);
+            adam_core(pp.w, gg.w, mm.w, vv.w, lr3, b1, b2, inv_c1, inv_c2, eps);
+            uint2 packed = make_uint2(pack2(pp.x, pp.y, SHD), pack2(pp.z, pp.w, SHD));
+            *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(shadow) + 2 * s4) = packed;
+        } else {
+            adam_one<SHD>(i, pp.x, gg.x, mm.x, vv.x, group_lr(grp, i), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
+            adam_one<SHD>(i + 1, pp.y, gg.y, mm.y, vv.y, group_lr(grp, i + 1), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
+            adam_one<SHD>(i + 2, pp.z, gg.z, mm.z, vv.z, group_lr(grp, i + 2), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
+            adam_one<SHD>(i + 3, pp.w, gg.w, mm.w, vv.w, group_lr(grp, i + 3), b1, b2, inv_c1, inv_c2, eps, shadow, grp.sh0, total);
+        }
         reinterpret_cast<float4 *>(p)[q] = pp;
         reinterpret_cast<float4 *>(m)[q] = mm;
         reinterpret_cast<float4 *>(v)[q] = vv;
@@ -141,6 +159,7 @@ extern "C" int gs_adam_step(int N, float *d_params, const float *d_grads, float 
     if (N < 0 || !d_params || !d_grads || !d_m || !d_v || !lr) return GS_ERR_ARG;
     if (!aligned(d_params, 16) || !aligned(d_grads, 16) || !aligned(d_m, 16) || !aligned(d_v, 16))
         return GS_ERR_ARG;
+    if (d_sh_shadow && !aligned(d_sh_shadow, 8)) return GS_ERR_ARG;
     if (N == 0) return GS_OK;
     AdamGroups grp;
     long long n = N;

@@ -54,9 +54,10 @@ class Schedule:
     (persistent, most instances first) or 'learned' (persistent, longest
     predicted time first, MLP trained on measured tile times)."""
     mode: str = "raster"
-    feature_cap: int = 256
+    feature_cap: int = 128
     mlp_lr: float = 3e-3
-    train_every: int = 1
+    train_every: int = 4
+    bwd_order: str = "forward"
     seed: int = 0
 
 
@@ -185,14 +186,17 @@ class Frame:
             L.gs_sched_order(self.cost, self.T, self.order_f, self.order_ws)
         else:
             L.gs_tile_features(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype,
-                               self.sched.feature_cap, self.feats)
-            L.gs_mlp_predict(self.mlp_w16, self.feats, self.T, self.pred)
+                               self.sched.feature_cap, self.feats, self.mlp_w16, self.pred)
             L.gs_sched_order(self.pred, self.T, self.order_f, self.order_ws)
         return {"mode": L.GS_SCHED_ORDER, "order": self.order_f, "queue": self.queue}
 
     def _sched_bwd(self):
+        """The backward reuses the forward's order ('forward'), or orders
+        tiles by the entries the forward processed ('processed')."""
         if self.sched.mode == "raster":
             return None
+        if self.sched.bwd_order == "forward":
+            return {"mode": L.GS_SCHED_ORDER, "order": self.order_f, "queue": self.queue}
         L.gs_int_cost(self.tile_nproc, self.T, self.cost)
         L.gs_sched_order(self.cost, self.T, self.order_b, self.order_ws)
         return {"mode": L.GS_SCHED_ORDER, "order": self.order_b, "queue": self.queue}
@@ -252,7 +256,7 @@ class Frame:
         self.mlp_t += 1
         if not self.use_learned:
             L.gs_tile_features(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype,
-                               self.sched.feature_cap, self.feats)
+                               self.sched.feature_cap, self.feats, self.mlp_w16, self.pred)
         L.gs_mlp_train_step(self.mlp_w32, self.mlp_w16, self.mlp_m, self.mlp_v, self.mlp_t,
                             self.sched.mlp_lr, self.feats, self.tile_ns, None, self.T, self.mlp_g,
                             self.mlp_loss)

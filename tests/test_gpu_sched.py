@@ -40,6 +40,23 @@ def test_tile_features_match_oracle():
         assert got[t, 7] == pytest.approx(ref[7], rel=1e-6)
 
 
+def test_features_with_fused_prediction():
+    scene = S.skewed_scene(20_000, 0)
+    cam = S.front_camera(200, 136)
+    fr, _ = _frame(scene, [cam])
+    rng = np.random.default_rng(9)
+    w16 = torch.from_numpy(rng.normal(0, 0.3, 321).astype(np.float32)).cuda().half()
+    feats2 = torch.empty_like(fr.feats)
+    pred = torch.empty(fr.T, device="cuda")
+    L.gs_tile_features(fr.cams, fr.ranges, fr.vals, fr.splats, fr.rgb_dtype, 256, fr.feats)
+    L.gs_tile_features(fr.cams, fr.ranges, fr.vals, fr.splats, fr.rgb_dtype, 256, feats2, w16, pred)
+    ref = torch.empty(fr.T, device="cuda")
+    L.gs_mlp_predict(w16, fr.feats, fr.T, ref)
+    torch.cuda.synchronize()
+    assert torch.equal(fr.feats, feats2)
+    assert torch.allclose(pred, ref, rtol=1e-6, atol=1e-6)
+
+
 def test_mlp_predict_and_grad_match_oracle():
     rng = np.random.default_rng(4)
     n = 1000
