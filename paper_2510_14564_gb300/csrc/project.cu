@@ -9,6 +9,8 @@
 // path: computed with IEEE-rounded intrinsics in a fixed order (no FMA
 // contraction), so that an independent IEEE implementation written to the
 // same order reproduces tile keys and counts bit for bit.
+#include <type_traits>
+
 #include "gs_common.cuh"
 
 namespace gs {
@@ -94,6 +96,87 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float G
     G[13][0] = SH_C3C * (5.0f * zz - 1.0f); G[13][2] = SH_C3C * 10.0f * x * z;
     G[14][0] = SH_C3E * 2.0f * x * z; G[14][1] = -SH_C3E * 2.0f * y * z; G[14][2] = SH_C3E * (xx - yy);
     G[15][0] = SH_C3A * 3.0f * (xx - yy); G[15][1] = -SH_C3A * 6.0f * x * y;
+}
+
+// Term J of the basis above and its gradient, computed on its own.
+template <int J>
+__device__ __forceinline__ void sh_term(float x, float y, float z, float &Y, float &gx, float &gy, float &gz) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gx = gy = gz = 0.0f;
+    if constexpr (J == 0) { Y = SH_C0; }
+    else if constexpr (J == 1) { Y = SH_C1 * y; gy = SH_C1; }
+    else if constexpr (J == 2) { Y = SH_C1 * z; gz = SH_C1; }
+    else if constexpr (J == 3) { Y = SH_C1 * x; gx = SH_C1; }
+    else if constexpr (J == 4) { Y = SH_C2A * x * y; gx = SH_C2A * y; gy = SH_C2A * x; }
+    else if constexpr (J == 5) { Y = SH_C2A * y * z; gy = SH_C2A * z; gz = SH_C2A * y; }
+    else if constexpr (J == 6) { Y = SH_C2B * (3.0f * zz - 1.0f); gz = SH_C2B * 6.0f * z; }
+    else if constexpr (J == 7) { Y = SH_C2A * x * z; gx = SH_C2A * z; gz = SH_C2A * x; }
+    else if constexpr (J == 8) { Y = SH_C2C * (xx - yy); gx = SH_C2C * 2.0f * x; gy = -SH_C2C * 2.0f * y; }
+    else if constexpr (J == 9) { Y = SH_C3A * y * (3.0f * xx - yy); gx = SH_C3A * 6.0f * x * y; gy = SH_C3A * 3.0f * (xx - yy); }
+    else if constexpr (J == 10) { Y = SH_C3B * x * y * z; gx = SH_C3B * y * z; gy = SH_C3B * x * z; gz = SH_C3B * x * y; }
+    else if constexpr (J == 11) { Y = SH_C3C * y * (5.0f * zz - 1.0f); gy = SH_C3C * (5.0f * zz - 1.0f); gz = SH_C3C * 10.0f * y * z; }
+    else if constexpr (J == 12) { Y = SH_C3D * z * (5.0f * zz - 3.0f); gz = SH_C3D * (15.0f * zz - 3.0f); }
+    else if constexpr (J == 13) { Y = SH_C3C * x * (5.0f * zz - 1.0f); gx = SH_C3C * (5.0f * zz - 1.0f); gz = SH_C3C * 10.0f * x * z; }
+    else if constexpr (J == 14) { Y = SH_C3E * (xx - yy) * z; gx = SH_C3E * 2.0f * x * z; gy = -SH_C3E * 2.0f * y * z; gz = SH_C3E * (xx - yy); }
+    else { Y = SH_C3A * x * (xx - 3.0f * yy); gx = SH_C3A * 3.0f * (xx - yy); gy = -SH_C3A * 6.0f * x * y; }
+}
+
+// Coefficient J (three channels) of Gaussian i.
+template <int SDT>
+__device__ __forceinline__ void load_sh_coef(const void *sh, long long i, int J, float &k0, float &k1, float &k2) {
+    if (SDT == GS_F32) {
+        const float *p = reinterpret_cast<const float *>(sh) + 48 * i + 3 * J;
+        k0 = __ldg(p); k1 = __ldg(p + 1); k2 = __ldg(p + 2);
+    } else {
+        const unsigned short *p = reinterpret_cast<const unsigned short *>(sh) + 48 * i + 3 * J;
+        const unsigned short a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+        if (SDT == GS_BF16) {
+            k0 = __uint_as_float((uint32_t)a << 16); k1 = __uint_as_float((uint32_t)b << 16);
+            k2 = __uint_as_float((uint32_t)c << 16);
+        } else {
+            k0 = __half2float(__ushort_as_half(a)); k1 = __half2float(__ushort_as_half(b));
+            k2 = __half2float(__ushort_as_half(c));
+        }
+    }
+}
+
+// Per channel: the pre-clamp colour and sum_j k_j grad Y_j (before the
+// upstream gradient), streaming the 16 coefficients.
+template <int SDT, int J>
+__device__ __forceinline__ void sh_stream(const void *sh, long long i, float ux, float uy, float uz,
+                                          float pre[3], float acc[3][3]) {
+    if constexpr (J < 16) {
+        float Y, gx, gy, gz, k0, k1, k2;
+        sh_term<J>(ux, uy, uz, Y, gx, gy, gz);
+        load_sh_coef<SDT>(sh, i, J, k0, k1, k2);
+        pre[0] = fmaf(Y, k0, pre[0]); pre[1] = fmaf(Y, k1, pre[1]); pre[2] = fmaf(Y, k2, pre[2]);
+        acc[0][0] = fmaf(k0, gx, acc[0][0]); acc[0][1] = fmaf(k0, gy, acc[0][1]); acc[0][2] = fmaf(k0, gz, acc[0][2]);
+        acc[1][0] = fmaf(k1, gx, acc[1][0]); acc[1][1] = fmaf(k1, gy, acc[1][1]); acc[1][2] = fmaf(k1, gz, acc[1][2]);
+        acc[2][0] = fmaf(k2, gx, acc[2][0]); acc[2][1] = fmaf(k2, gy, acc[2][1]); acc[2][2] = fmaf(k2, gz, acc[2][2]);
+        sh_stream<SDT, J + 1>(sh, i, ux, uy, uz, pre, acc);
+    }
+}
+
+// The SH gradient of one Gaussian, [16][3] as 12 float4: value (j, ch) is
+// w[ch] Y_j(u) (w = upstream colour gradient, zero on clamped channels).
+template <int Q>
+__device__ __forceinline__ void write_dsh(float4 *ps, float ux, float uy, float uz, const float w[3]) {
+    if constexpr (Q < 12) {
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = 0.0f;
+        auto term = [&](auto jc, int e, int ch) {
+            float Y, a, b, c;
+            sh_term<decltype(jc)::value>(ux, uy, uz, Y, a, b, c);
+            v[e] = w[ch] * Y;
+        };
+        term(std::integral_constant<int, (4 * Q + 0) / 3>{}, 0, (4 * Q + 0) % 3);
+        term(std::integral_constant<int, (4 * Q + 1) / 3>{}, 1, (4 * Q + 1) % 3);
+        term(std::integral_constant<int, (4 * Q + 2) / 3>{}, 2, (4 * Q + 2) % 3);
+        term(std::integral_constant<int, (4 * Q + 3) / 3>{}, 3, (4 * Q + 3) % 3);
+        ps[Q] = make_float4(v[0], v[1], v[2], v[3]);
+        write_dsh<Q + 1>(ps, ux, uy, uz, w);
+    }
 }
 
 // SH coefficients of one Gaussian as FP32 [16][3].
@@ -292,6 +375,114 @@ __global__ void __launch_bounds__(128) k_project(GeomBatch views, int N, const f
 // ---------------------------------------------------------------------------
 // a6: projection backward (reverse mode of k_project, continuous part)
 // ---------------------------------------------------------------------------
+// Reverse mode of the projection for one view, geometric part: chains the
+// 2D gradient g (u, v, A, B, C, opacity) to the mean, log-scales,
+// quaternion and opacity logit (accumulated into dmean, dls, dq, dlog).
+__device__ __forceinline__ void geom_bwd(const ViewGeom &cam, float mx, float my, float mz, const float ls[3],
+                                         const float q[4], float lg, const float g[9], float dmean[3],
+                                         float dls[3], float dq[4], float &dlog) {
+    const float *R = cam.R;
+    const float fx = cam.fx, fy = cam.fy;
+    // forward quantities (same values as k_project)
+    Discrete d;
+    discrete_path(cam, mx, my, mz, ls, q, d);
+    const float x = d.x, y = d.y, z = d.z;
+    float M[9], Sg[9];
+#pragma unroll
+    for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) M[3 * rr + kk] = d.Rq[3 * rr + kk] * d.s[kk];
+#pragma unroll
+    for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc)
+            Sg[3 * rr + cc] = M[3 * rr] * M[3 * cc] + M[3 * rr + 1] * M[3 * cc + 1] + M[3 * rr + 2] * M[3 * cc + 2];
+    float iz = 1.0f / z, iz2 = iz * iz;
+    float J[6] = {fx * iz, 0.0f, -fx * x * iz2, 0.0f, fy * iz, -fy * y * iz2};
+    float T[6];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk)
+            T[3 * rr + kk] = J[3 * rr] * R[kk] + J[3 * rr + 1] * R[3 + kk] + J[3 * rr + 2] * R[6 + kk];
+    const float a = d.ca, b = d.cb, c = d.cc;
+    float D = a * c - b * b, iD = 1.0f / D, iD2 = iD * iD;
+    // conic (A, B, C) = (c, -b, a) / D
+    float gA = g[2], gB = g[3], gC = g[4];
+    float ga_ = gA * (-c * c * iD2) + gB * (b * c * iD2) + gC * (iD - a * c * iD2);
+    float gb_ = gA * (2.0f * b * c * iD2) + gB * (-iD - 2.0f * b * b * iD2) + gC * (2.0f * a * b * iD2);
+    float gc_ = gA * (iD - a * c * iD2) + gB * (a * b * iD2) + gC * (-a * a * iD2);
+    float G2[4] = {ga_, 0.5f * gb_, 0.5f * gb_, gc_};
+    float TS[6];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk)
+            TS[3 * rr + kk] = T[3 * rr] * Sg[kk] + T[3 * rr + 1] * Sg[3 + kk] + T[3 * rr + 2] * Sg[6 + kk];
+    float dT[6];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk)
+            dT[3 * rr + kk] = 2.0f * (G2[2 * rr] * TS[kk] + G2[2 * rr + 1] * TS[3 + kk]);
+    float dS[9];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+            float t0 = G2[0] * T[kk] + G2[1] * T[3 + kk];
+            float t1 = G2[2] * T[kk] + G2[3] * T[3 + kk];
+            dS[3 * j + kk] = T[j] * t0 + T[3 + j] * t1;
+        }
+    float dJ[6];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            dJ[3 * rr + j] = dT[3 * rr] * R[3 * j] + dT[3 * rr + 1] * R[3 * j + 1] + dT[3 * rr + 2] * R[3 * j + 2];
+    float dp0 = dJ[2] * (-fx * iz2) + g[0] * fx * iz;
+    float dp1 = dJ[5] * (-fy * iz2) + g[1] * fy * iz;
+    float dp2 = dJ[0] * (-fx * iz2) + dJ[2] * (2.0f * fx * x * iz2 * iz) + dJ[4] * (-fy * iz2) +
+                dJ[5] * (2.0f * fy * y * iz2 * iz) - g[0] * fx * x * iz2 - g[1] * fy * y * iz2;
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) dmean[kk] += R[kk] * dp0 + R[3 + kk] * dp1 + R[6 + kk] * dp2;
+    // Sigma = M M^T, M = Rq diag(s)
+    float dM[9];
+#pragma unroll
+    for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk)
+            dM[3 * rr + kk] = 2.0f * (dS[3 * rr] * M[kk] + dS[3 * rr + 1] * M[3 + kk] + dS[3 * rr + 2] * M[6 + kk]);
+    float G[9];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        float ds = 0.0f;
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr) {
+            ds += dM[3 * rr + kk] * d.Rq[3 * rr + kk];
+            G[3 * rr + kk] = dM[3 * rr + kk] * d.s[kk];
+        }
+        dls[kk] += ds * d.s[kk];
+    }
+    // rotation from the unit quaternion
+    float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    float iq = 1.0f / qn;
+    float w = q[0] * iq, qx = q[1] * iq, qy = q[2] * iq, qz = q[3] * iq;
+    float dqh[4];
+    dqh[0] = 2.0f * (-qz * G[1] + qy * G[2] + qz * G[3] - qx * G[5] - qy * G[6] + qx * G[7]);
+    dqh[1] = 2.0f * (qy * G[1] + qz * G[2] + qy * G[3] - 2.0f * qx * G[4] - w * G[5] + qz * G[6] + w * G[7] - 2.0f * qx * G[8]);
+    dqh[2] = 2.0f * (-2.0f * qy * G[0] + qx * G[1] + w * G[2] + qx * G[3] + qz * G[5] - w * G[6] + qz * G[7] - 2.0f * qy * G[8]);
+    dqh[3] = 2.0f * (-2.0f * qz * G[0] - w * G[1] + qx * G[2] + w * G[3] - 2.0f * qz * G[4] + qy * G[5] + qx * G[6] + qy * G[7]);
+    float dot = dqh[0] * w + dqh[1] * qx + dqh[2] * qy + dqh[3] * qz;
+    dq[0] += (dqh[0] - w * dot) * iq;
+    dq[1] += (dqh[1] - qx * dot) * iq;
+    dq[2] += (dqh[2] - qy * dot) * iq;
+    dq[3] += (dqh[3] - qz * dot) * iq;
+    // opacity
+    float o = 1.0f / (1.0f + expf(-lg));
+    dlog += g[5] * o * (1.0f - o);
+}
+
 // Adam applied in place to the grouped parameters by the fused backward.
 struct AdamArgs {
     float *p, *m, *v;     // grouped 59 N buffers
@@ -344,106 +535,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(GeomBatch views, int N, con
         float g[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
         if (!any) { load_sh<SDT>(sh, i, k); any = true; }
         const ViewGeom &cam = views.v[vi];
-        const float *R = cam.R;
-        const float fx = cam.fx, fy = cam.fy;
-        // forward quantities (same values as k_project)
-        Discrete d;
-        discrete_path(cam, mx, my, mz, ls, q, d);
-        const float x = d.x, y = d.y, z = d.z;
-        float M[9], Sg[9];
-#pragma unroll
-        for (int rr = 0; rr < 3; ++rr)
-#pragma unroll
-            for (int kk = 0; kk < 3; ++kk) M[3 * rr + kk] = d.Rq[3 * rr + kk] * d.s[kk];
-#pragma unroll
-        for (int rr = 0; rr < 3; ++rr)
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc)
-                Sg[3 * rr + cc] = M[3 * rr] * M[3 * cc] + M[3 * rr + 1] * M[3 * cc + 1] + M[3 * rr + 2] * M[3 * cc + 2];
-        float iz = 1.0f / z, iz2 = iz * iz;
-        float J[6] = {fx * iz, 0.0f, -fx * x * iz2, 0.0f, fy * iz, -fy * y * iz2};
-        float T[6];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-            for (int kk = 0; kk < 3; ++kk)
-                T[3 * rr + kk] = J[3 * rr] * R[kk] + J[3 * rr + 1] * R[3 + kk] + J[3 * rr + 2] * R[6 + kk];
-        const float a = d.ca, b = d.cb, c = d.cc;
-        float D = a * c - b * b, iD = 1.0f / D, iD2 = iD * iD;
-        // conic (A, B, C) = (c, -b, a) / D
-        float gA = g[2], gB = g[3], gC = g[4];
-        float ga_ = gA * (-c * c * iD2) + gB * (b * c * iD2) + gC * (iD - a * c * iD2);
-        float gb_ = gA * (2.0f * b * c * iD2) + gB * (-iD - 2.0f * b * b * iD2) + gC * (2.0f * a * b * iD2);
-        float gc_ = gA * (iD - a * c * iD2) + gB * (a * b * iD2) + gC * (-a * a * iD2);
-        float G2[4] = {ga_, 0.5f * gb_, 0.5f * gb_, gc_};
-        float TS[6];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-            for (int kk = 0; kk < 3; ++kk)
-                TS[3 * rr + kk] = T[3 * rr] * Sg[kk] + T[3 * rr + 1] * Sg[3 + kk] + T[3 * rr + 2] * Sg[6 + kk];
-        float dT[6];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-            for (int kk = 0; kk < 3; ++kk)
-                dT[3 * rr + kk] = 2.0f * (G2[2 * rr] * TS[kk] + G2[2 * rr + 1] * TS[3 + kk]);
-        float dS[9];
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int kk = 0; kk < 3; ++kk) {
-                float t0 = G2[0] * T[kk] + G2[1] * T[3 + kk];
-                float t1 = G2[2] * T[kk] + G2[3] * T[3 + kk];
-                dS[3 * j + kk] = T[j] * t0 + T[3 + j] * t1;
-            }
-        float dJ[6];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                dJ[3 * rr + j] = dT[3 * rr] * R[3 * j] + dT[3 * rr + 1] * R[3 * j + 1] + dT[3 * rr + 2] * R[3 * j + 2];
-        float dp0 = dJ[2] * (-fx * iz2) + g[0] * fx * iz;
-        float dp1 = dJ[5] * (-fy * iz2) + g[1] * fy * iz;
-        float dp2 = dJ[0] * (-fx * iz2) + dJ[2] * (2.0f * fx * x * iz2 * iz) + dJ[4] * (-fy * iz2) +
-                    dJ[5] * (2.0f * fy * y * iz2 * iz) - g[0] * fx * x * iz2 - g[1] * fy * y * iz2;
-#pragma unroll
-        for (int kk = 0; kk < 3; ++kk) dmean[kk] += R[kk] * dp0 + R[3 + kk] * dp1 + R[6 + kk] * dp2;
-        // Sigma = M M^T, M = Rq diag(s)
-        float dM[9];
-#pragma unroll
-        for (int rr = 0; rr < 3; ++rr)
-#pragma unroll
-            for (int kk = 0; kk < 3; ++kk)
-                dM[3 * rr + kk] = 2.0f * (dS[3 * rr] * M[kk] + dS[3 * rr + 1] * M[3 + kk] + dS[3 * rr + 2] * M[6 + kk]);
-        float G[9];
-#pragma unroll
-        for (int kk = 0; kk < 3; ++kk) {
-            float ds = 0.0f;
-#pragma unroll
-            for (int rr = 0; rr < 3; ++rr) {
-                ds += dM[3 * rr + kk] * d.Rq[3 * rr + kk];
-                G[3 * rr + kk] = dM[3 * rr + kk] * d.s[kk];
-            }
-            dls[kk] += ds * d.s[kk];
-        }
-        // rotation from the unit quaternion
-        float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-        float iq = 1.0f / qn;
-        float w = q[0] * iq, qx = q[1] * iq, qy = q[2] * iq, qz = q[3] * iq;
-        float dqh[4];
-        dqh[0] = 2.0f * (-qz * G[1] + qy * G[2] + qz * G[3] - qx * G[5] - qy * G[6] + qx * G[7]);
-        dqh[1] = 2.0f * (qy * G[1] + qz * G[2] + qy * G[3] - 2.0f * qx * G[4] - w * G[5] + qz * G[6] + w * G[7] - 2.0f * qx * G[8]);
-        dqh[2] = 2.0f * (-2.0f * qy * G[0] + qx * G[1] + w * G[2] + qx * G[3] + qz * G[5] - w * G[6] + qz * G[7] - 2.0f * qy * G[8]);
-        dqh[3] = 2.0f * (-2.0f * qz * G[0] - w * G[1] + qx * G[2] + w * G[3] - 2.0f * qz * G[4] + qy * G[5] + qx * G[6] + qy * G[7]);
-        float dot = dqh[0] * w + dqh[1] * qx + dqh[2] * qy + dqh[3] * qz;
-        dq[0] += (dqh[0] - w * dot) * iq;
-        dq[1] += (dqh[1] - qx * dot) * iq;
-        dq[2] += (dqh[2] - qy * dot) * iq;
-        dq[3] += (dqh[3] - qz * dot) * iq;
-        // opacity
-        float o = 1.0f / (1.0f + expf(-lg));
-        dlog += g[5] * o * (1.0f - o);
+        geom_bwd(cam, mx, my, mz, ls, q, lg, g, dmean, dls, dq, dlog);
         // colour
         float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
         float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
@@ -560,6 +652,63 @@ __global__ void __launch_bounds__(128) k_project_bwd(GeomBatch views, int N, con
     }
 }
 
+// One view: the same backward with the SH part streamed term by term (no
+// per-thread arrays of 48 coefficients or gradients), so more warps fit.
+template <int SDT>
+__global__ void __launch_bounds__(128) k_project_bwd1(ViewGeom cam, int N, const float *__restrict__ means,
+                                                      const float *__restrict__ log_scales,
+                                                      const float *__restrict__ quats,
+                                                      const float *__restrict__ logits,
+                                                      const void *__restrict__ sh,
+                                                      const int *__restrict__ touched,
+                                                      const float *__restrict__ grad2d,
+                                                      float *__restrict__ dparams) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const long long n = N;
+    float *pm = dparams, *pls = dparams + 3 * n, *pq = dparams + 6 * n, *plg = dparams + 10 * n;
+    float4 *ps = reinterpret_cast<float4 *>(dparams + 11 * n) + 12 * i;
+    if (__ldg(touched + i) <= 0) {
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) { pm[3 * i + kk] = 0.0f; pls[3 * i + kk] = 0.0f; }
+        reinterpret_cast<float4 *>(pq)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        plg[i] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 12; ++j) ps[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const float mx = __ldg(means + 3 * i), my = __ldg(means + 3 * i + 1), mz = __ldg(means + 3 * i + 2);
+    const float ls[3] = {__ldg(log_scales + 3 * i), __ldg(log_scales + 3 * i + 1), __ldg(log_scales + 3 * i + 2)};
+    const float4 q4 = __ldg(reinterpret_cast<const float4 *>(quats) + i);
+    const float q[4] = {q4.x, q4.y, q4.z, q4.w};
+    const float lg = __ldg(logits + i);
+    const float4 *gp = reinterpret_cast<const float4 *>(grad2d + 12 * i);
+    const float4 ga = __ldg(gp), gb = __ldg(gp + 1), gc = __ldg(gp + 2);
+    const float g[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
+    float dmean[3] = {0, 0, 0}, dls[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dlog = 0.0f;
+    geom_bwd(cam, mx, my, mz, ls, q, lg, g, dmean, dls, dq, dlog);
+    // colour: max(0, 0.5 + sum_j Y_j(u) k_j), u = (mu - campos) / |mu - campos|
+    const float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
+    const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+    const float ux = vx * inv, uy = vy * inv, uz = vz * inv;
+    float pre[3] = {0.5f, 0.5f, 0.5f};
+    float acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    sh_stream<SDT, 0>(sh, i, ux, uy, uz, pre, acc);
+    const float w[3] = {pre[0] > 0.0f ? g[6] : 0.0f, pre[1] > 0.0f ? g[7] : 0.0f, pre[2] > 0.0f ? g[8] : 0.0f};
+    float gd[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gd[a] = w[0] * acc[0][a] + w[1] * acc[1][a] + w[2] * acc[2][a];
+    const float gdd = gd[0] * ux + gd[1] * uy + gd[2] * uz;
+    dmean[0] += (gd[0] - ux * gdd) * inv;
+    dmean[1] += (gd[1] - uy * gdd) * inv;
+    dmean[2] += (gd[2] - uz * gdd) * inv;
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) { pm[3 * i + kk] = dmean[kk]; pls[3 * i + kk] = dls[kk]; }
+    reinterpret_cast<float4 *>(pq)[i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+    plg[i] = dlog;
+    write_dsh<0>(ps, ux, uy, uz, w);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -647,6 +796,17 @@ extern "C" int gs_project_bwd(const gs_camera *cams, int n_views, int N, const f
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int grid = cdiv(N, 128);
     AdamArgs none{};
+    if (n_views == 1) {
+        if (sh_dtype == GS_F32)
+            { k_project_bwd1<GS_F32><<<grid, 128, 0, st>>>(vb.v[0], N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams); count_launches(1); }
+        else if (sh_dtype == GS_BF16)
+            { k_project_bwd1<GS_BF16><<<grid, 128, 0, st>>>(vb.v[0], N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams); count_launches(1); }
+        else if (sh_dtype == GS_F16)
+            { k_project_bwd1<GS_F16><<<grid, 128, 0, st>>>(vb.v[0], N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams); count_launches(1); }
+        else
+            return GS_ERR_ARG;
+        return launch_status();
+    }
     if (sh_dtype == GS_F32)
         { k_project_bwd<GS_F32, false><<<grid, 128, 0, st>>>(vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_touched, d_grad2d, d_dparams, none); count_launches(1); }
     else if (sh_dtype == GS_BF16)
