@@ -117,6 +117,12 @@ def algorithmic_bytes(N, P, I, I_proc, half: bool) -> dict:
         "render_bwd": I_proc * rec + P * 20 + N * 36,
         "project_bwd": N * (sh_read + 36 + 32 + 236),
         "adam": N * (1652 + (96 if half else 0)),
+        # fused, one view, two launches.  Geometry: 11 params, touched, the 2D
+        # gradient, the SH the forward read, m and v of the 11; writes p, m, v
+        # of the 11 and the 24-byte SH-gradient factors.  SH: the factors, p, m
+        # and v of the 48 SH entries read and written (+ the 16-bit shadow).
+        "project_bwd_adam": N * ((44 + 4 + 48 + (96 if half else 192) + 88 + 132 + 24)
+                                 + (24 + 576 + 576 + (96 if half else 0))),
     }
 
 
@@ -153,7 +159,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    def timed(tr, steps, stage_times=None, e2e=False):
+    def timed(tr, steps, stage_times=None, e2e=False, profile=False):
         st = torch.cuda.current_stream()
         marks = []
 
@@ -168,6 +174,8 @@ def run_ours(args):
         l0 = L.gs_launch_count()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        if profile:                     # a profiler started with --profile-from-start off sees only this
+            torch.cuda.profiler.start()
         t0.record(st)
         for _ in range(steps):
             if e2e:
@@ -177,6 +185,8 @@ def run_ours(args):
                 loss_host.copy_(tr.frame.loss, non_blocking=True)
         t1.record(st)
         torch.cuda.synchronize()
+        if profile:
+            torch.cuda.profiler.stop()
         launches = L.gs_launch_count() - l0
         barrier()
         ms = t0.elapsed_time(t1)
@@ -211,7 +221,7 @@ def run_ours(args):
         tr.step()
     stages = {}
     with Clocks(local) as clk:
-        ms, launches = timed(tr, args.steps, stage_times=stages)
+        ms, launches = timed(tr, args.steps, stage_times=stages, profile=True)
     clocks = clk.summary()
     ips = args.steps / (ms / 1e3)
     e2e_ms, _ = timed(tr, args.steps, e2e=True)
@@ -230,7 +240,7 @@ def run_ours(args):
     peaks, peak_kind = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = ab[dom] / (stage_ms[dom] / 1e3) / 1e9
-    step_bytes = sum(ab.values())
+    step_bytes = sum(v for k, v in ab.items() if k in stage_ms)
     whole = step_bytes / (ms / args.steps / 1e3) / 1e9
 
     out = {

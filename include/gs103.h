@@ -280,10 +280,16 @@ int gs_project_bwd(const gs_camera *cams, int n_views, int N, const float *d_mea
  * FP32 buffer (read for the backward, then updated); d_sh is the SH the
  * forward read (e.g. the BF16 shadow; NULL = the SH group of d_params, FP32);
  * the updated SH is also written to d_sh_shadow if given.  N must be a
- * multiple of 4.  Gradients and updates equal those of the two calls. */
+ * multiple of 4.  d_sh and d_sh_shadow may be the same buffer (the shadow
+ * refreshed in place): each Gaussian's coefficients are read before its
+ * update is written.  Gradients and updates equal those of the two calls (up
+ * to the last bit of the SH basis, evaluated by two code paths).  With one
+ * view d_grad2d is consumed: it serves as scratch (each record's entries 0..5
+ * hold the factors of its SH gradient) and its contents on return are
+ * unspecified; with several views it is only read. */
 int gs_project_bwd_adam(const gs_camera *cams, int n_views, int N, float *d_params,
                         const void *d_sh, int sh_dtype, const int32_t *d_touched,
-                        const float *d_grad2d, float *d_m, float *d_v, const float *lr, float b1,
+                        float *d_grad2d, float *d_m, float *d_v, const float *lr, float b1,
                         float b2, float eps, int t, void *d_sh_shadow, int shadow_dtype,
                         float *d_dparams, gs_stream_t stream);
 

@@ -179,6 +179,16 @@ __device__ __forceinline__ unsigned warp_peers(uint32_t d, int bits) {
     return peers;
 }
 
+// One Adam step (Kingma & Ba, Algorithm 1) on one entry, bias corrections
+// passed as 1/(1 - b1^t) and 1/(1 - b2^t); shared by every Adam kernel so the
+// fused and separate paths apply the same arithmetic.
+__device__ __forceinline__ void adam_core(float &p, float g, float &m, float &v, float lr, float b1, float b2,
+                                          float inv_c1, float inv_c2, float eps) {
+    m = b1 * m + (1.0f - b1) * g;
+    v = b2 * v + (1.0f - b2) * g * g;
+    p -= lr * (m * inv_c1) / (sqrtf(v * inv_c2) + eps);
+}
+
 // Warp helpers
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31; }
 

@@ -121,39 +121,76 @@ __device__ __forceinline__ void sh_term(float x, float y, float z, float &Y, flo
     else { Y = SH_C3A * x * (xx - 3.0f * yy); gx = SH_C3A * 3.0f * (xx - yy); gy = -SH_C3A * 6.0f * x * y; }
 }
 
-// Coefficient J (three channels) of Gaussian i.
-template <int SDT>
-__device__ __forceinline__ void load_sh_coef(const void *sh, long long i, int J, float &k0, float &k1, float &k2) {
-    if (SDT == GS_F32) {
-        const float *p = reinterpret_cast<const float *>(sh) + 48 * i + 3 * J;
-        k0 = __ldg(p); k1 = __ldg(p + 1); k2 = __ldg(p + 2);
+// Coefficient e (0..11 within a 48-byte block) of a block held as 12 words:
+// FP32 entries are whole words, 16-bit entries half-words (low half first).
+template <int SDT, int E>
+__device__ __forceinline__ float block_coef(const uint32_t (&w)[12]) {
+    if constexpr (SDT == GS_F32) {
+        return __uint_as_float(w[E]);
     } else {
-        const unsigned short *p = reinterpret_cast<const unsigned short *>(sh) + 48 * i + 3 * J;
-        const unsigned short a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
-        if (SDT == GS_BF16) {
-            k0 = __uint_as_float((uint32_t)a << 16); k1 = __uint_as_float((uint32_t)b << 16);
-            k2 = __uint_as_float((uint32_t)c << 16);
-        } else {
-            k0 = __half2float(__ushort_as_half(a)); k1 = __half2float(__ushort_as_half(b));
-            k2 = __half2float(__ushort_as_half(c));
-        }
+        const uint32_t h = (E & 1) ? (w[E >> 1] >> 16) : (w[E >> 1] & 0xffffu);
+        if constexpr (SDT == GS_BF16) return __uint_as_float(h << 16);
+        else return __half2float(__ushort_as_half((unsigned short)h));
     }
 }
 
-// Per channel: the pre-clamp colour and sum_j k_j grad Y_j (before the
-// upstream gradient), streaming the 16 coefficients.
-template <int SDT, int J>
-__device__ __forceinline__ void sh_stream(const void *sh, long long i, float ux, float uy, float uz,
-                                          float pre[3], float acc[3][3]) {
-    if constexpr (J < 16) {
-        float Y, gx, gy, gz, k0, k1, k2;
+// Terms T0 .. T0+TPB-1 of block B: pre-clamp colour and sum_j k_j grad Y_j.
+template <int SDT, int J, int JEND>
+__device__ __forceinline__ void sh_block_terms(const uint32_t (&w)[12], float ux, float uy, float uz,
+                                               float pre[3], float acc[3][3]) {
+    if constexpr (J < JEND) {
+        constexpr int TPB = SDT == GS_F32 ? 4 : 8;
+        constexpr int e = 3 * (J % TPB);
+        float Y, gx, gy, gz;
         sh_term<J>(ux, uy, uz, Y, gx, gy, gz);
-        load_sh_coef<SDT>(sh, i, J, k0, k1, k2);
+        const float k0 = block_coef<SDT, e>(w), k1 = block_coef<SDT, e + 1>(w), k2 = block_coef<SDT, e + 2>(w);
         pre[0] = fmaf(Y, k0, pre[0]); pre[1] = fmaf(Y, k1, pre[1]); pre[2] = fmaf(Y, k2, pre[2]);
         acc[0][0] = fmaf(k0, gx, acc[0][0]); acc[0][1] = fmaf(k0, gy, acc[0][1]); acc[0][2] = fmaf(k0, gz, acc[0][2]);
         acc[1][0] = fmaf(k1, gx, acc[1][0]); acc[1][1] = fmaf(k1, gy, acc[1][1]); acc[1][2] = fmaf(k1, gz, acc[1][2]);
         acc[2][0] = fmaf(k2, gx, acc[2][0]); acc[2][1] = fmaf(k2, gy, acc[2][1]); acc[2][2] = fmaf(k2, gz, acc[2][2]);
-        sh_stream<SDT, J + 1>(sh, i, ux, uy, uz, pre, acc);
+        sh_block_terms<SDT, J + 1, JEND>(w, ux, uy, uz, pre, acc);
+    }
+}
+
+// Per channel: the pre-clamp colour and sum_j k_j grad Y_j (before the
+// upstream gradient), streaming the 16 coefficients of Gaussian i in 48-byte
+// blocks (three 16-byte loads each: 4 terms in FP32, 8 in 16-bit storage).
+template <int SDT, int B = 0>
+__device__ __forceinline__ void sh_stream(const void *sh, long long i, float ux, float uy, float uz,
+                                          float pre[3], float acc[3][3]) {
+    constexpr int TPB = SDT == GS_F32 ? 4 : 8;
+    if constexpr (B * TPB < 16) {
+        const size_t gbytes = SDT == GS_F32 ? 192 : 96;
+        const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(sh) + gbytes * i + 48 * B);
+        const uint4 r0 = __ldg(src), r1 = __ldg(src + 1), r2 = __ldg(src + 2);
+        const uint32_t w[12] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
+        sh_block_terms<SDT, B * TPB, B * TPB + TPB>(w, ux, uy, uz, pre, acc);
+        sh_stream<SDT, B + 1>(sh, i, ux, uy, uz, pre, acc);
+    }
+}
+
+// The same, from the Gaussian's coefficients already loaded as NB blocks of
+// 12 words (so that a kernel can issue every load of a Gaussian up front).
+template <int SDT, int NB>
+__device__ __forceinline__ void load_sh_words(const void *sh, long long i, uint32_t (&w)[NB][12]) {
+    const size_t gbytes = SDT == GS_F32 ? 192 : 96;
+    const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(sh) + gbytes * i);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const uint4 r0 = __ldg(src + 3 * b), r1 = __ldg(src + 3 * b + 1), r2 = __ldg(src + 3 * b + 2);
+        w[b][0] = r0.x; w[b][1] = r0.y; w[b][2] = r0.z; w[b][3] = r0.w;
+        w[b][4] = r1.x; w[b][5] = r1.y; w[b][6] = r1.z; w[b][7] = r1.w;
+        w[b][8] = r2.x; w[b][9] = r2.y; w[b][10] = r2.z; w[b][11] = r2.w;
+    }
+}
+
+template <int SDT, int NB, int B = 0>
+__device__ __forceinline__ void sh_eval_words(const uint32_t (&w)[NB][12], float ux, float uy, float uz,
+                                              float pre[3], float acc[3][3]) {
+    constexpr int TPB = SDT == GS_F32 ? 4 : 8;
+    if constexpr (B < NB) {
+        sh_block_terms<SDT, B * TPB, B * TPB + TPB>(w[B], ux, uy, uz, pre, acc);
+        sh_eval_words<SDT, NB, B + 1>(w, ux, uy, uz, pre, acc);
     }
 }
 
@@ -693,7 +730,7 @@ __global__ void __launch_bounds__(128) k_project_bwd1(ViewGeom cam, int N, const
     const float ux = vx * inv, uy = vy * inv, uz = vz * inv;
     float pre[3] = {0.5f, 0.5f, 0.5f};
     float acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    sh_stream<SDT, 0>(sh, i, ux, uy, uz, pre, acc);
+    sh_stream<SDT>(sh, i, ux, uy, uz, pre, acc);
     const float w[3] = {pre[0] > 0.0f ? g[6] : 0.0f, pre[1] > 0.0f ? g[7] : 0.0f, pre[2] > 0.0f ? g[8] : 0.0f};
     float gd[3];
 #pragma unroll
@@ -707,6 +744,165 @@ __global__ void __launch_bounds__(128) k_project_bwd1(ViewGeom cam, int N, const
     reinterpret_cast<float4 *>(pq)[i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
     plg[i] = dlog;
     write_dsh<0>(ps, ux, uy, uz, w);
+}
+
+// One view, fused with Adam, in two launches.  Part 1, one lane per
+// Gaussian: the backward, the Adam step of the 11 geometric entries, and the
+// SH gradient left as its two factors -- w_ch (the upstream colour gradient,
+// zero on clamped channels) and the view direction u -- written over the
+// Gaussian's consumed 2D-gradient record (entries 0..5).
+template <int SDT>
+__global__ void __launch_bounds__(128, 4) k_bwd_adam_geom(ViewGeom cam, int N, const void *__restrict__ sh,
+                                                       const int *__restrict__ touched,
+                                                       float *__restrict__ grad2d, float *__restrict__ dparams,
+                                                       AdamArgs a) {
+    constexpr int NB = SDT == GS_F32 ? 4 : 2;                      // 48-byte blocks of SH coefficients
+    const long long n = N;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float *__restrict__ p = a.p;
+    float *__restrict__ m = a.m;
+    float *__restrict__ v = a.v;
+    // every load of this Gaussian first (one round trip to memory)
+    const int hit = __ldg(touched + i);
+    float4 *rec = reinterpret_cast<float4 *>(grad2d + 12 * i);
+    const float4 ga = rec[0], gb = rec[1], gc = rec[2];
+    uint32_t shw[NB][12];
+    load_sh_words<SDT, NB>(sh, i, shw);
+    const float mx = p[3 * i], my = p[3 * i + 1], mz = p[3 * i + 2];
+    const float ls[3] = {p[3 * n + 3 * i], p[3 * n + 3 * i + 1], p[3 * n + 3 * i + 2]};
+    const float4 q4 = reinterpret_cast<const float4 *>(p + 6 * n)[i];
+    const float lg = p[10 * n + i];
+    float mv_m[11], mv_v[11];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { mv_m[k] = m[3 * i + k]; mv_v[k] = v[3 * i + k]; }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { mv_m[3 + k] = m[3 * n + 3 * i + k]; mv_v[3 + k] = v[3 * n + 3 * i + k]; }
+    {
+        const float4 mq = reinterpret_cast<const float4 *>(m + 6 * n)[i];
+        const float4 vq = reinterpret_cast<const float4 *>(v + 6 * n)[i];
+        mv_m[6] = mq.x; mv_m[7] = mq.y; mv_m[8] = mq.z; mv_m[9] = mq.w;
+        mv_v[6] = vq.x; mv_v[7] = vq.y; mv_v[8] = vq.z; mv_v[9] = vq.w;
+    }
+    mv_m[10] = m[10 * n + i];
+    mv_v[10] = v[10 * n + i];
+
+    const float q[4] = {q4.x, q4.y, q4.z, q4.w};
+    float dmean[3] = {0, 0, 0}, dls[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dlog = 0.0f;
+    float w[3] = {0.0f, 0.0f, 0.0f};
+    float ux = 0.0f, uy = 0.0f, uz = 1.0f;
+    if (hit > 0) {
+        const float g[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
+        geom_bwd(cam, mx, my, mz, ls, q, lg, g, dmean, dls, dq, dlog);
+        const float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
+        const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+        ux = vx * inv; uy = vy * inv; uz = vz * inv;
+        float pre[3] = {0.5f, 0.5f, 0.5f};
+        float acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        sh_eval_words<SDT, NB>(shw, ux, uy, uz, pre, acc);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) w[ch] = pre[ch] > 0.0f ? g[6 + ch] : 0.0f;
+        float gd[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) gd[ax] = w[0] * acc[0][ax] + w[1] * acc[1][ax] + w[2] * acc[2][ax];
+        const float gdd = gd[0] * ux + gd[1] * uy + gd[2] * uz;
+        dmean[0] += (gd[0] - ux * gdd) * inv;
+        dmean[1] += (gd[1] - uy * gdd) * inv;
+        dmean[2] += (gd[2] - uz * gdd) * inv;
+    }
+    rec[0] = make_float4(w[0], w[1], w[2], ux);
+    *reinterpret_cast<float2 *>(grad2d + 12 * i + 4) = make_float2(uy, uz);
+    if (dparams) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { dparams[3 * i + k] = dmean[k]; dparams[3 * n + 3 * i + k] = dls[k]; }
+        reinterpret_cast<float4 *>(dparams + 6 * n)[i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+        dparams[10 * n + i] = dlog;
+    }
+    float pv[11] = {mx, my, mz, ls[0], ls[1], ls[2], q4.x, q4.y, q4.z, q4.w, lg};
+    const float gv[11] = {dmean[0], dmean[1], dmean[2], dls[0], dls[1], dls[2], dq[0], dq[1], dq[2], dq[3], dlog};
+#pragma unroll
+    for (int k = 0; k < 11; ++k) {
+        const float lr = k < 3 ? a.lr[0] : k < 6 ? a.lr[1] : k < 10 ? a.lr[2] : a.lr[3];
+        adam_core(pv[k], gv[k], mv_m[k], mv_v[k], lr, a.b1, a.b2, a.inv_c1, a.inv_c2, a.eps);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[3 * i + k] = pv[k]; m[3 * i + k] = mv_m[k]; v[3 * i + k] = mv_v[k];
+        p[3 * n + 3 * i + k] = pv[3 + k]; m[3 * n + 3 * i + k] = mv_m[3 + k]; v[3 * n + 3 * i + k] = mv_v[3 + k];
+    }
+    reinterpret_cast<float4 *>(p + 6 * n)[i] = make_float4(pv[6], pv[7], pv[8], pv[9]);
+    reinterpret_cast<float4 *>(m + 6 * n)[i] = make_float4(mv_m[6], mv_m[7], mv_m[8], mv_m[9]);
+    reinterpret_cast<float4 *>(v + 6 * n)[i] = make_float4(mv_v[6], mv_v[7], mv_v[8], mv_v[9]);
+    p[10 * n + i] = pv[10]; m[10 * n + i] = mv_m[10]; v[10 * n + i] = mv_v[10];
+}
+
+// Part 2: each warp updates the SH block of its 32 Gaussians (1536
+// contiguous floats in each of p, m and v) with coalesced float4 accesses,
+// rebuilding each SH gradient w_ch Y_j(u) from the factors part 1 left,
+// with the 16 basis values and w of each Gaussian staged in shared memory.
+template <int SHD>
+__global__ void __launch_bounds__(256, 4) k_bwd_adam_sh(int N, const float *__restrict__ grad2d,
+                                                     float *__restrict__ dparams, AdamArgs a) {
+    __shared__ float s_y[8][32 * 17];        // per warp: 16 basis values per Gaussian (stride 17)
+    __shared__ float s_w[8][32 * 3];
+    const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const long long n = N;
+    const long long wfirst = (long long)blockIdx.x * blockDim.x + 32 * wp;
+    const long long left = n - wfirst;
+    if (left <= 0) return;
+    {
+        float w0 = 0.0f, w1 = 0.0f, w2 = 0.0f, ux = 0.0f, uy = 0.0f, uz = 1.0f;
+        if (l < left) {
+            const float *r = grad2d + 12 * (wfirst + l);
+            const float4 a4 = __ldg(reinterpret_cast<const float4 *>(r));
+            const float2 b2 = __ldg(reinterpret_cast<const float2 *>(r + 4));
+            w0 = a4.x; w1 = a4.y; w2 = a4.z; ux = a4.w; uy = b2.x; uz = b2.y;
+        }
+        float Y[16];
+        sh_basis(ux, uy, uz, Y);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) s_y[wp][17 * l + j] = Y[j];
+        s_w[wp][3 * l] = w0; s_w[wp][3 * l + 1] = w1; s_w[wp][3 * l + 2] = w2;
+    }
+    __syncwarp();
+    const int total4 = 12 * (int)(left < 32 ? left : 32);
+    const long long base4 = (11 * n + 48 * wfirst) >> 2;          // N % 4 == 0: float4-aligned
+    float4 *P4 = reinterpret_cast<float4 *>(a.p) + base4;
+    float4 *M4 = reinterpret_cast<float4 *>(a.m) + base4;
+    float4 *V4 = reinterpret_cast<float4 *>(a.v) + base4;
+    float4 *G4 = dparams ? reinterpret_cast<float4 *>(dparams) + base4 : nullptr;
+    uint2 *S2 = SHD ? reinterpret_cast<uint2 *>(a.shadow) + 12 * wfirst : nullptr;
+    const float *sy = s_y[wp], *sw = s_w[wp];
+    constexpr int U = 2;                  // float4 per lane per array in flight
+    for (int q0 = 0; q0 < total4; q0 += 32 * U) {
+        float4 pp[U], mm[U], vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int qq = q0 + 32 * u + l;
+            if (qq < total4) { pp[u] = P4[qq]; mm[u] = M4[qq]; vv[u] = V4[qq]; }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int qq = q0 + 32 * u + l;
+            if (qq >= total4) continue;
+            const int gl = qq / 12;
+            const int r = 4 * (qq - 12 * gl);                     // first of the 4 entries (j, ch) = divmod(e, 3)
+            float gr[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = r + k, j = e / 3, ch = e - 3 * j;
+                gr[k] = sw[3 * gl + ch] * sy[17 * gl + j];
+            }
+            const float lr0 = r == 0 ? a.lr[4] : a.lr[5];         // entries 0..2 are the DC band
+            adam_core(pp[u].x, gr[0], mm[u].x, vv[u].x, lr0, a.b1, a.b2, a.inv_c1, a.inv_c2, a.eps);
+            adam_core(pp[u].y, gr[1], mm[u].y, vv[u].y, lr0, a.b1, a.b2, a.inv_c1, a.inv_c2, a.eps);
+            adam_core(pp[u].z, gr[2], mm[u].z, vv[u].z, lr0, a.b1, a.b2, a.inv_c1, a.inv_c2, a.eps);
+            adam_core(pp[u].w, gr[3], mm[u].w, vv[u].w, a.lr[5], a.b1, a.b2, a.inv_c1, a.inv_c2, a.eps);
+            P4[qq] = pp[u]; M4[qq] = mm[u]; V4[qq] = vv[u];
+            if (G4) G4[qq] = make_float4(gr[0], gr[1], gr[2], gr[3]);
+            if (SHD) S2[qq] = make_uint2(pack2(pp[u].x, pp[u].y, SHD), pack2(pp[u].z, pp[u].w, SHD));
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -820,7 +1016,7 @@ extern "C" int gs_project_bwd(const gs_camera *cams, int n_views, int N, const f
 
 extern "C" int gs_project_bwd_adam(const gs_camera *cams, int n_views, int N, float *d_params,
                                    const void *d_sh, int sh_dtype, const int32_t *d_touched,
-                                   const float *d_grad2d, float *d_m, float *d_v, const float *lr, float b1,
+                                   float *d_grad2d, float *d_m, float *d_v, const float *lr, float b1,
                                    float b2, float eps, int t, void *d_sh_shadow, int shadow_dtype,
                                    float *d_dparams, gs_stream_t stream) {
     GeomBatch vb;
@@ -833,6 +1029,7 @@ extern "C" int gs_project_bwd_adam(const gs_camera *cams, int n_views, int N, fl
         (d_dparams && !aligned(d_dparams, 16)))
         return GS_ERR_ARG;
     if (d_sh_shadow && shadow_dtype != GS_BF16 && shadow_dtype != GS_F16) return GS_ERR_ARG;
+    if (d_sh_shadow && !aligned(d_sh_shadow, 8)) return GS_ERR_ARG;
     const long long n = N;
     const float *means = d_params, *ls = d_params + 3 * n, *q = d_params + 6 * n, *lg = d_params + 10 * n;
     const void *sh = d_sh ? d_sh : (const void *)(d_params + 11 * n);
@@ -848,6 +1045,27 @@ extern "C" int gs_project_bwd_adam(const gs_camera *cams, int n_views, int N, fl
     a.inv_c2 = (float)(1.0 / c2);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int grid = cdiv(N, 128);
+    if (n_views == 1) {
+        // part 1 writes the SH gradient factors over the consumed 2D gradients
+        float *scratch = d_grad2d;
+        if (sh_dtype == GS_F32)
+            { k_bwd_adam_geom<GS_F32><<<grid, 128, 0, st>>>(vb.v[0], N, sh, d_touched, scratch, d_dparams, a); count_launches(1); }
+        else if (sh_dtype == GS_BF16)
+            { k_bwd_adam_geom<GS_BF16><<<grid, 128, 0, st>>>(vb.v[0], N, sh, d_touched, scratch, d_dparams, a); count_launches(1); }
+        else if (sh_dtype == GS_F16)
+            { k_bwd_adam_geom<GS_F16><<<grid, 128, 0, st>>>(vb.v[0], N, sh, d_touched, scratch, d_dparams, a); count_launches(1); }
+        else
+            return GS_ERR_ARG;
+        const int grid2 = cdiv(N, 256);
+        const int shd = d_sh_shadow ? shadow_dtype : 0;
+        if (shd == 0)
+            { k_bwd_adam_sh<0><<<grid2, 256, 0, st>>>(N, d_grad2d, d_dparams, a); count_launches(1); }
+        else if (shd == GS_BF16)
+            { k_bwd_adam_sh<GS_BF16><<<grid2, 256, 0, st>>>(N, d_grad2d, d_dparams, a); count_launches(1); }
+        else
+            { k_bwd_adam_sh<GS_F16><<<grid2, 256, 0, st>>>(N, d_grad2d, d_dparams, a); count_launches(1); }
+        return launch_status();
+    }
     if (sh_dtype == GS_F32)
         { k_project_bwd<GS_F32, true><<<grid, 128, 0, st>>>(vb, N, means, ls, q, lg, sh, d_touched, d_grad2d, d_dparams, a); count_launches(1); }
     else if (sh_dtype == GS_BF16)

@@ -51,13 +51,6 @@ __device__ __forceinline__ float group_lr(const AdamGroups &g, long long i) {
     return (s % 48ull) < 3 ? g.lr[4] : g.lr[5];
 }
 
-__device__ __forceinline__ void adam_core(float &p, float g, float &m, float &v, float lr, float b1, float b2,
-                                          float inv_c1, float inv_c2, float eps) {
-    m = b1 * m + (1.0f - b1) * g;
-    v = b2 * v + (1.0f - b2) * g * g;
-    p -= lr * (m * inv_c1) / (sqrtf(v * inv_c2) + eps);
-}
-
 template <int SHD>
 __device__ __forceinline__ void adam_one(long long i, float &p, float g, float &m, float &v, float lr,
                                          float b1, float b2, float inv_c1, float inv_c2, float eps,

@@ -326,16 +326,23 @@ class Trainer:
         mk("render_bwd")
         L.gs_render_bwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, s, f.dimg, f.T_final, f.n_proc,
                         f.tile_nproc, f.grad2d, f.err)
-        # projection backward, then Adam (two streaming kernels; the fused
-        # gs_project_bwd_adam is slower at the backward's register budget)
-        mk("project_bwd")
         pk_sh = self.sh_shadow if self.sh_shadow is not None else pk["sh"]
-        L.gs_project_bwd(f.cams, self.N, pk["means"], pk["log_scales"], pk["quats"], pk["opacity_logits"],
-                         pk_sh, self.sh_storage, f.touched, f.grad2d, f.dparams)
-        mk("adam")
         self.t += 1
-        L.gs_adam_step(self.N, self.p, f.dparams, self.m, self.v, self.lr, ADAM_B1, ADAM_B2, ADAM_EPS, self.t,
-                       self.sh_shadow, self.sh_storage)
+        if len(f.cams) == 1:
+            # one view: the projection backward and Adam in one streaming pass
+            # (the per-Gaussian gradients never go to memory)
+            mk("project_bwd_adam")
+            L.gs_project_bwd_adam(f.cams, self.N, self.p, self.sh_shadow, self.sh_storage, f.touched, f.grad2d,
+                                  self.m, self.v, self.lr, ADAM_B1, ADAM_B2, ADAM_EPS, self.t,
+                                  self.sh_shadow, self.sh_storage)
+        else:
+            # several views: gradients summed over views, then Adam
+            mk("project_bwd")
+            L.gs_project_bwd(f.cams, self.N, pk["means"], pk["log_scales"], pk["quats"], pk["opacity_logits"],
+                             pk_sh, self.sh_storage, f.touched, f.grad2d, f.dparams)
+            mk("adam")
+            L.gs_adam_step(self.N, self.p, f.dparams, self.m, self.v, self.lr, ADAM_B1, ADAM_B2, ADAM_EPS,
+                           self.t, self.sh_shadow, self.sh_storage)
         if timing and (f.step_count % max(1, f.sched.train_every) == 0):
             mk("mlp_train")
             f.train_scheduler()
