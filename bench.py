@@ -35,6 +35,38 @@ METRIC = "fwd+bwd splat iters/s @3M Gaussians 1600x1060, learned vs plain schedu
 WORKLOAD = "skewed-3M-1600x1060"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 
+# DRAM bytes (read + write) per Gaussian of the dominant call, from one ncu
+# capture of the full-size workload (profiles/project_bwd_adam_skewed-3M-1600x1060.md).
+# Valid only while the kernel sources hash as they did when captured.
+MEASURED_TRAFFIC = {
+    "project_bwd_adam": {
+        "bytes_per_gaussian": (0.8400720 + 0.4822640 + 1.8720535 + 1.9520630) * 1e9 / 3e6,
+        "sources": {
+            "paper_2510_14564_gb300/csrc/project.cu":
+                "5ae04c54b1467bafd4f19124cf10b8f4e50dc820838fa29302985fe8b87c787d",
+            "paper_2510_14564_gb300/csrc/gs_common.cuh":
+                "7b566d05e89e1f2b0e3eff97194528e114567584a1a832cbd05301dc8fdefb80",
+        },
+    },
+}
+
+
+def measured_traffic(stage: str, N: int):
+    """Captured DRAM traffic of `stage` scaled to N Gaussians, or None if
+    there is no capture or a kernel source changed since it was taken."""
+    import hashlib
+    rec = MEASURED_TRAFFIC.get(stage)
+    if rec is None:
+        return None
+    for rel, digest in rec["sources"].items():
+        try:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return int(rec["bytes_per_gaussian"] * N)
+
 
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -65,7 +97,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
         time.sleep(0.3)
@@ -262,7 +294,8 @@ def run_ours(args):
         "stage_ms_plain_fp32": {k: round(statistics.mean(v), 4) for k, v in plain_stages.items()},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                     "traffic": None, "peak_source": peak_kind,
+                     "traffic": measured_traffic(dom, N), "algorithmic_bytes": int(ab[dom]),
+                     "peak_source": peak_kind,
                      "whole_step_hbm_frac": round(whole / hbm, 4)},
         "e2e": {"value": round(e2e_ips * world, 3), "unit": "iters/s",
                 "h2d_bytes_per_step": int(tgt.numel() * 4), "d2h_bytes_per_step": 4},
@@ -270,7 +303,7 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(scene, cam, samples=1)
+        out["cpu_baseline"] = cpu_baseline(scene, cam)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -333,38 +366,82 @@ def schedule_diagnostics(f, L, torch, reps=5) -> dict:
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(scene, cam, crop=64):
-    """One bounded oracle iteration: every per-Gaussian stage over all N
-    Gaussians, every per-pixel stage over the centre crop x crop window.
-    Returns (seconds, extrapolated seconds for the whole view)."""
-    from oracle import oracle as O
-    x0, y0 = (cam.W - crop) // 2 // 16 * 16, (cam.H - crop) // 2 // 16 * 16
-    win = (x0, y0, x0 + crop, y0 + crop)
-    t0 = time.perf_counter()
-    kp = O.keypath(cam, scene)
-    pr = O.project(cam, scene, kp)
-    tg = time.perf_counter()
-    r = O.render(cam, kp, pr, window=win)
-    _, dimg = O.l1(r["img"], np.zeros_like(r["img"]))
-    g2 = O.render_bwd(cam, kp, pr, dimg, window=win)
-    tp = time.perf_counter()
-    O.project_bwd(cam, scene, kp, g2)
-    t1 = time.perf_counter()
-    per_gauss = (tg - t0) + (t1 - tp)
-    per_pix = tp - tg
-    full = per_gauss + per_pix * (cam.n_tiles / ((crop // 16) ** 2))
-    return t1 - t0, full
-
-
-def cpu_baseline(scene, cam, samples=1) -> dict:
+def cpu_baseline(scene, cam) -> dict:
+    """The oracle on the host cores, one bounded step of about 20 s."""
     from oracle import oracle as O
     O.build()
-    cores = O.get_threads()
-    fulls = [oracle_sample(scene, cam)[1] for _ in range(samples)]
-    full = statistics.median(fulls)
-    return {"value": round(1.0 / full, 6), "unit": "iters/s", "cores": cores, "kind": "oracle",
-            "sample": "per-Gaussian stages on all Gaussians + per-pixel stages on the centre 64x64 "
-                      "crop, extrapolated to the full view by tile count"}
+    step = OracleStep(scene, cam, steps_total=1, budget_s=20.0)
+    full = step()
+    return {"value": round(1.0 / full, 6), "unit": "iters/s", "cores": O.get_threads(), "kind": "oracle",
+            "sample": step.describe()}
+
+
+class OracleStep:
+    """One bounded step of the oracle on the benchmark workload, sized so
+    that `steps_total` steps take about `budget_s` seconds: the per-Gaussian
+    stages (key path, projection, projection backward) on a seeded subset of
+    the Gaussians, the per-pixel stages (render, L1, backward render) on
+    seeded random segments of tile rows; each part's time is extrapolated to
+    the whole view (by the Gaussian count and by the tile count; the segments
+    are a uniform sample, and each call's fixed cost, which a whole-view run
+    pays once, is charged to every segment)."""
+
+    def __init__(self, scene, cam, steps_total: int, budget_s: float = 120.0):
+        from oracle import oracle as O
+        self.O, self.scene, self.cam = O, scene, cam
+        t0 = time.perf_counter()
+        self.kp = O.keypath(cam, scene)                       # full key path and projection, untimed:
+        self.pr = O.project(cam, scene, self.kp)              # the tile renders need every Gaussian
+        rng = np.random.default_rng(7)
+        per_step = max(0.05, budget_s / max(1, steps_total))
+        probe = scene.subset(np.sort(rng.choice(scene.n, min(scene.n, 50_000), replace=False)))
+        tg = self._gauss_part(probe)
+        self.n_sub = int(min(scene.n, max(10_000, 0.5 * per_step * probe.n / tg)))
+        # row segments: whole rows when a row fits half the step, else quarter rows
+        tx = cam.tiles_x
+        probe_seg = [(cam.tiles_y // 2, 0, tx)]
+        t_row = self._pixel_part(probe_seg)
+        self.seg = tx if t_row <= 0.5 * per_step else max(1, tx // 4)
+        per_seg = t_row * self.seg / tx
+        nseg = int(np.clip(0.5 * per_step / per_seg, 1, 64))
+        segs = [(ty, x0, min(tx, x0 + self.seg)) for ty in range(cam.tiles_y) for x0 in range(0, tx, self.seg)]
+        pick = rng.choice(len(segs), min(nseg, len(segs)), replace=False)
+        self.segs = [segs[k] for k in pick]
+        self.seg_tiles = sum(b - a for _, a, b in self.segs)
+        self.sub = scene.subset(np.sort(rng.choice(scene.n, self.n_sub, replace=False)))
+        self.setup_s = time.perf_counter() - t0
+
+    def _gauss_part(self, sc):
+        O, cam = self.O, self.cam
+        t0 = time.perf_counter()
+        kp = O.keypath(cam, sc)
+        O.project(cam, sc, kp)
+        O.project_bwd(cam, sc, kp, np.full((sc.n, 9), 1e-3))
+        return time.perf_counter() - t0
+
+    def _pixel_part(self, segs):
+        O, cam = self.O, self.cam
+        t0 = time.perf_counter()
+        for ty, a, b in segs:
+            x0, y0, x1, y1 = 16 * a, 16 * ty, min(16 * b, cam.W), min(16 * ty + 16, cam.H)
+            r = O.render(cam, self.kp, self.pr, window=(x0, y0, x1, y1))
+            crop = np.ascontiguousarray(r["img"][:, y0:y1, x0:x1])
+            _, dc = O.l1(crop, np.zeros_like(crop))
+            dimg = np.zeros_like(r["img"])
+            dimg[:, y0:y1, x0:x1] = dc
+            O.render_bwd(cam, self.kp, self.pr, dimg, window=(x0, y0, x1, y1))
+        return time.perf_counter() - t0
+
+    def __call__(self) -> float:
+        """Seconds of one whole-view oracle iteration (extrapolated)."""
+        tg = self._gauss_part(self.sub) * (self.scene.n / self.n_sub)
+        tp = self._pixel_part(self.segs) * (self.cam.n_tiles / self.seg_tiles)
+        return tg + tp
+
+    def describe(self) -> str:
+        return (f"per-Gaussian stages on a seeded subset of {self.n_sub} of {self.scene.n} Gaussians; "
+                f"per-pixel stages on {len(self.segs)} seeded random tile-row segments ({self.seg_tiles} of "
+                f"{self.cam.n_tiles} tiles); each extrapolated to the whole view by Gaussian and tile count")
 
 
 def run_reference(args):
@@ -377,12 +454,13 @@ def run_reference(args):
     O.build()
     scene, cams = S.make_workload(args.workload, seed=0)
     cam = cams[0]
+    step = OracleStep(scene, cam, args.steps + args.warmup)
     for _ in range(args.warmup):
-        oracle_sample(scene, cam)
+        step()
     fulls = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        fulls.append(oracle_sample(scene, cam)[1])
+        fulls.append(step())
     wall = time.perf_counter() - t0
     full = statistics.mean(fulls)
     v = 1.0 / full
@@ -392,8 +470,7 @@ def run_reference(args):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "sample_wall_s": round(wall, 2)},
            "cpu_baseline": {"kind": "oracle", "cores": O.get_threads(), "value": round(v, 6),
-                            "sample": "per-Gaussian stages on all Gaussians + per-pixel stages on "
-                                      "the centre 64x64 crop, extrapolated by tile count"},
+                            "sample": step.describe()},
            "e2e": {"value": round(v, 6), "unit": "iters/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -402,7 +479,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
