@@ -258,11 +258,25 @@ def run_ours(args):
     ips = args.steps / (ms / 1e3)
     e2e_ms, _ = timed(tr, args.steps, e2e=True)
     e2e_ips = args.steps / (e2e_ms / 1e3)
+    # the fwd+bwd iteration alone (projection .. projection backward + L1, no Adam)
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        tr.iteration()
+    barrier()
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(st)
+    for _ in range(args.steps):
+        tr.iteration()
+    a1.record(st)
+    torch.cuda.synchronize()
+    it_ips = args.steps / (a0.elapsed_time(a1) / 1e3)
     assert tr.frame.check_errors() == 0, "kernel error word set (learned path)"
 
     f = tr.frame
     sched_diag = schedule_diagnostics(f, L, torch)
     I = int(f.n_inst.item())
+    I_full = int(f.tile_count.sum().item())
     I_proc = int(f.tile_nproc.sum().item())
     Pix = cam.W * cam.H
     ab = algorithmic_bytes(N, Pix, I, I_proc, True)
@@ -285,7 +299,8 @@ def run_ours(args):
                    "storage": "bf16 SH + bf16 colour, fp32 blending and gradients",
                    "plain_fp32_count_iters_per_s": round(plain_ips * world, 3),
                    "learned_vs_plain": round(ips / plain_ips, 4),
-                   "instances": I, "processed_instances": I_proc,
+                   "fwd_bwd_iters_per_s_no_adam": round(it_ips * world, 3),
+                   "instances_full_lists": I_full, "instances_kept": I, "processed_instances": I_proc,
                    "l2": "inputs larger than L2 (0.4-0.7 GB of parameters, 1.5+ GB of instances)",
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "mlp_calibration_steps": args.calib,

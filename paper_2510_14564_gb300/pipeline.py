@@ -305,6 +305,16 @@ class Trainer:
             d["sh"] = self.sh_shadow
         return d
 
+    def iteration(self, targets: torch.Tensor | None = None) -> torch.Tensor:
+        """Forward, L1 and backward to the 59 parameter gradients (in
+        frame.dparams), without the Adam step: one fwd+bwd iteration."""
+        f = self.frame
+        pk = self.params_for_kernels()
+        f.forward(pk, timing=f.sched.mode == "learned")
+        f.l1(self.targets if targets is None else targets)
+        f.backward(pk, f.dimg)
+        return f.loss
+
     def step(self, mark=None, targets: torch.Tensor | None = None) -> torch.Tensor:
         """One training step.  `mark(name)`, if given, is called before each
         stage (and with "end" after the last) so a caller can time stages."""
