@@ -151,6 +151,146 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_downsweep(
 }
 
 // ---------------------------------------------------------------------------
+// Onesweep LSD radix sort of 32-bit keys with 32-bit values (Adinets and
+// Garland, "Onesweep: a faster least significant digit radix sort for GPUs",
+// 2022): one pass over the keys builds the global histograms of all four
+// 8-bit digits; then each digit pass is one kernel in which a tile of 4096
+// keys ranks itself, publishes its digit counts, obtains the counts of all
+// earlier tiles by decoupled look-back, and scatters.  Tiles take their index
+// from an atomic counter in the order they start, so a tile only ever waits
+// on tiles that are already running; every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kLbAgg = 1u << 30;            // status word: tile's own count is ready
+constexpr uint32_t kLbPre = 2u << 30;            // status word: inclusive prefix is ready
+constexpr uint32_t kLbVal = (1u << 30) - 1u;
+constexpr int kLbSpinLimit = 1 << 20;
+
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Global histograms of the four 8-bit digits of n keys: ghist[4][256] (zeroed
+// by the caller).
+__global__ void __launch_bounds__(256) k_onesweep_hist(const uint32_t *__restrict__ keys, uint32_t n,
+                                                       uint32_t *__restrict__ ghist) {
+    __shared__ uint32_t s_h[4 * kRadix];
+    for (int k = threadIdx.x; k < 4 * kRadix; k += 256) s_h[k] = 0;
+    __syncthreads();
+    for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < n; i += gridDim.x * 256u) {
+        const uint32_t k = __ldg(keys + i);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) atomicAdd(&s_h[d * kRadix + ((k >> (8 * d)) & 255u)], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 4 * kRadix; k += 256)
+        if (s_h[k]) atomicAdd(ghist + k, s_h[k]);
+}
+
+// One digit pass.  status [nb][256] and *tile_counter are zeroed by the
+// caller; ghist is this digit's global histogram.
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, uint32_t n, int shift, const uint32_t *__restrict__ ghist,
+    uint32_t *status, uint32_t *tile_counter, int *err_word) {
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t s_wh[8][kRadix];
+    __shared__ uint32_t s_dstart[kRadix];
+    __shared__ uint32_t s_goff[kRadix];
+    __shared__ uint32_t s_warp[8], s_warp2[8];
+    __shared__ uint32_t s_bid;
+    if (threadIdx.x == 0) s_bid = atomicAdd(tile_counter, 1u);
+    for (int k = threadIdx.x; k < 8 * kRadix; k += kSortThreads) (&s_wh[0][0])[k] = 0;
+    __syncthreads();
+    const uint32_t bid = s_bid;
+    const long long bbase = (long long)bid * kSortTile;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
+    const long long base = bbase + w * (kSortItems * 32);
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const long long idx = base + it * 32 + l;
+        const bool valid = idx < (long long)n;
+        key[it] = valid ? __ldg(kin + idx) : 0u;
+        val[it] = valid ? __ldg(vin + idx) : 0u;
+        const uint32_t d = valid ? ((key[it] >> shift) & 255u) : kRadix;
+        const unsigned peers = warp_peers(d, 8);
+        const unsigned rank = __popc(peers & lanemask_lt());
+        const uint32_t before = valid ? s_wh[w][d] : 0u;
+        __syncwarp();
+        if (valid && rank == 0) s_wh[w][d] = before + __popc(peers);
+        __syncwarp();
+        loc[it] = valid ? before + rank : 0xffffffffu;
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        uint32_t c = 0;
+#pragma unroll
+        for (int ww = 0; ww < 8; ++ww) {
+            const uint32_t x = s_wh[ww][d];
+            s_wh[ww][d] = c;
+            c += x;
+        }
+        // publish this tile's count of digit d, then look back for the counts
+        // of all earlier tiles
+        uint32_t *my = status + (size_t)bid * kRadix + d;
+        st_relaxed(my, (bid == 0 ? kLbPre : kLbAgg) | c);
+        s_dstart[d] = block_excl_scan_256(c, s_warp);
+        const uint32_t gbase = block_excl_scan_256(__ldg(ghist + d), s_warp2);
+        uint32_t excl = 0;
+        if (bid > 0) {
+            long long j = (long long)bid - 1;
+            int spins = 0;
+            while (j >= 0) {
+                const uint32_t v = ld_relaxed(status + (size_t)j * kRadix + d);
+                const uint32_t f = v & ~kLbVal;
+                if (f == 0u) {
+                    if (++spins > kLbSpinLimit) { set_err(err_word, GS_EW_TIMEOUT); break; }
+                    continue;
+                }
+                excl += v & kLbVal;
+                if (f == kLbPre) break;
+                --j;
+            }
+            st_relaxed(my, kLbPre | (excl + c));
+        }
+        s_goff[d] = gbase + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        if (loc[it] != 0xffffffffu) {
+            const uint32_t d = (key[it] >> shift) & 255u;
+            const uint32_t pos = s_dstart[d] + s_wh[w][d] + loc[it];
+            s_keys[pos] = key[it];
+            s_vals[pos] = val[it];
+        }
+    }
+    __syncthreads();
+    const int n_local = (int)min((long long)kSortTile, (long long)n - bbase);
+    for (int q = threadIdx.x; q < n_local; q += kSortThreads) {
+        const uint32_t k = s_keys[q];
+        const uint32_t d = (k >> shift) & 255u;
+        const uint32_t g = s_goff[d] + (uint32_t)(q - s_dstart[d]);
+        kout[g] = k;
+        vout[g] = s_vals[q];
+    }
+}
+
+// Scratch of the onesweep depth sort of n keys (status words of four passes,
+// four digit histograms, four tile counters).
+static size_t onesweep_scratch_bytes(long long n) {
+    const long long nb = (n + kSortTile - 1) / kSortTile;
+    return 4 * (size_t)(4 * kRadix * nb + 4 * kRadix + 4);
+}
+
+// ---------------------------------------------------------------------------
 // Exclusive scan (device-wide, three kernels)
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 256;
@@ -779,7 +919,10 @@ static Plan make_plan(long long VN, long long cap, const TileBatch &tb) {
     long long nbc = p.direct ? 0 : (cap + kSortTile - 1) / kSortTile, nbv = (VN + kSortTile - 1) / kSortTile;
     p.nb_max = (int)(nbc > nbv ? nbc : nbv);
     if (p.nb_max < 1) p.nb_max = 1;
-    p.hist = take(4 * (size_t)kRadix * p.nb_max);
+    {
+        const size_t hb = 4 * (size_t)kRadix * p.nb_max, ob = onesweep_scratch_bytes(VN);
+        p.hist = take(hb > ob ? hb : ob);
+    }
     if ((long long)kRadix * p.nb_max > maxscan) maxscan = (long long)kRadix * p.nb_max;
     if (maxscan < tb.total_tiles) maxscan = tb.total_tiles;
     p.part = take(8 * (size_t)((maxscan + kScanChunk - 1) / kScanChunk + 1));
@@ -806,13 +949,32 @@ static void radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
 // views, a stable pass on the view.  Returns the sorted record indices.
 static const uint32_t *depth_order(const float *d_depth, const int32_t *d_touched, long long VN, int N,
                                    int n_views, uint32_t *dk0, uint32_t *dk1, uint32_t *dv0, uint32_t *dv1,
-                                   uint32_t *hist, void *part, cudaStream_t st) {
+                                   uint32_t *hist, void *part, int *err_word, cudaStream_t st) {
     { k_depth_keys<<<cdiv(VN, 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0); count_launches(1); }
     uint32_t *ka = dk0, *kb = dk1, *va = dv0, *vb = dv1;
-    for (int pass = 0; pass < 4; ++pass) {
-        radix_pass(ka, va, kb, vb, nullptr, (uint32_t)VN, VN, 8 * pass, 8, true, hist, (uint32_t *)part, st);
-        uint32_t *t = ka; ka = kb; kb = t;
-        t = va; va = vb; vb = t;
+    if (VN < (long long)kLbVal) {
+        // onesweep: status words of the four passes, the four histograms and
+        // the four tile counters, zeroed together
+        const long long nb = (VN + kSortTile - 1) / kSortTile;
+        uint32_t *status = hist, *ghist = hist + 4 * kRadix * nb, *counters = ghist + 4 * kRadix;
+        cudaMemsetAsync(hist, 0, onesweep_scratch_bytes(VN), st);
+        if (VN > 0) {
+            const int hb = (int)(VN / 4096 + 1 < 1024 ? VN / 4096 + 1 : 1024);
+            { k_onesweep_hist<<<hb, 256, 0, st>>>(ka, (uint32_t)VN, ghist); count_launches(1); }
+            for (int pass = 0; pass < 4; ++pass) {
+                { k_onesweep_pass<<<(int)nb, kSortThreads, 0, st>>>(ka, va, kb, vb, (uint32_t)VN, 8 * pass, ghist + kRadix * pass,
+                                                                   status + (size_t)kRadix * nb * pass, counters + pass, err_word);
+                  count_launches(1); }
+                uint32_t *t = ka; ka = kb; kb = t;
+                t = va; va = vb; vb = t;
+            }
+        }
+    } else {
+        for (int pass = 0; pass < 4; ++pass) {
+            radix_pass(ka, va, kb, vb, nullptr, (uint32_t)VN, VN, 8 * pass, 8, true, hist, (uint32_t *)part, st);
+            uint32_t *t = ka; ka = kb; kb = t;
+            t = va; va = vb; vb = t;
+        }
     }
     if (n_views > 1) {
         { k_view_keys<<<cdiv(VN, 256), 256, 0, st>>>(va, VN, (uint32_t)N, ka); count_launches(1); }
@@ -930,7 +1092,7 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
         return launch_status();
     }
     // 1. records in (view, depth bits, index) order; culled last in each view
-    const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, st);
+    const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, d_err_word, st);
 
     if (p.direct) {
         uint32_t *ids1 = (uint32_t *)(ws + p.ids1);
@@ -1113,43 +1275,101 @@ __global__ void __launch_bounds__(256) k_pre_count(TileBatch tb, int N, int Cv, 
 // count, the last chunk kept and the number of entries kept.  A tile keeps
 // its chunks up to the first one where either the coverage bound passes the
 // target, or the kept count reaches the tile's limit (limit[t] > 0:
-// 2 limit + 64 entries; no limit otherwise).
-__global__ void k_pre_colscan(TileBatch tb, int Cv, int Tmax, uint32_t *__restrict__ Mc,
-                              const uint32_t *__restrict__ Mv, const int32_t *__restrict__ limit,
-                              uint32_t *__restrict__ full, uint32_t *__restrict__ last_chunk,
-                              uint32_t *__restrict__ kept) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= tb.total_tiles) return;
-    const int v = view_of_tile(tb, g);
-    const int t = g - tb.v[v].tile_base;
+// 2 limit + 64 entries; no limit otherwise); both running sums only grow, so
+// that chunk is the first where the inclusive sums meet the rule.  One CTA
+// per 32 tiles of a view (lane = tile: coalesced rows), its 8 warps taking 8
+// contiguous chunk ranges: each warp sums its range, the CTA adds up the
+// warps before it, and each warp writes its range's prefixes and finds the
+// first chunk of its range that meets the rule; the first warp that found
+// one decides.
+constexpr int kColWarps = 8;
+__global__ void __launch_bounds__(32 * kColWarps) k_pre_colscan(TileBatch tb, int Cv, int Tmax,
+                                                               uint32_t *__restrict__ Mc,
+                                                               const uint32_t *__restrict__ Mv,
+                                                               const int32_t *__restrict__ limit,
+                                                               uint32_t *__restrict__ full,
+                                                               uint32_t *__restrict__ last_chunk,
+                                                               uint32_t *__restrict__ kept) {
+    __shared__ uint32_t s_c[kColWarps][32];
+    __shared__ unsigned long long s_v[kColWarps][32];
+    __shared__ uint32_t s_fk[kColWarps][32], s_keep[kColWarps][32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    int b = blockIdx.x, v = 0;
+    for (; v < tb.n; ++v) {                        // blocks of 32 tiles, view by view
+        const int nb = (tb.v[v].TX * tb.v[v].TY + 31) / 32;
+        if (b < nb) break;
+        b -= nb;
+    }
+    if (v >= tb.n) return;                         // uniform over the CTA
+    const int Tv = tb.v[v].TX * tb.v[v].TY;
+    const int t = 32 * b + l;
+    const bool live = t < Tv;
     uint32_t *col = Mc + (long long)v * Cv * Tmax + t;
-    const uint32_t *cov = Mv + (long long)v * Cv * Tmax + t;
-    const int lim = limit ? limit[g] : 0;
-    const uint32_t want = lim > 0 ? (uint32_t)min(2ll * lim + 64, 0x7fffffffll) : 0xffffffffu;
-    uint32_t run = 0, rcov = 0, keep = 0, lastc = (uint32_t)(Cv - 1);
-    bool found = false;
-    for (int k0 = 0; k0 < Cv; k0 += 8) {
-        uint32_t a[8], b[8];
+    const uint32_t *cov = Mv ? Mv + (long long)v * Cv * Tmax + t : nullptr;
+    const int per = (Cv + kColWarps - 1) / kColWarps;
+    const int k0 = min(Cv, w * per), k1 = min(Cv, k0 + per);
+    // 1. sums of this warp's range
+    uint32_t sc = 0;
+    unsigned long long sv = 0;
+    if (live) {
+        for (int k = k0; k < k1; k += 8) {
+            uint32_t a[8], c[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const bool in = k0 + j < Cv;
-            a[j] = in ? col[(long long)(k0 + j) * Tmax] : 0u;
-            b[j] = in && !found && Mv ? cov[(long long)(k0 + j) * Tmax] : 0u;
+            for (int j = 0; j < 8; ++j) {
+                const bool in = k + j < k1;
+                a[j] = in ? col[(long long)(k + j) * Tmax] : 0u;
+                c[j] = in && cov ? __ldg(cov + (long long)(k + j) * Tmax) : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) { sc += a[j]; sv += c[j]; }
         }
+    }
+    s_c[w][l] = sc;
+    s_v[w][l] = sv;
+    __syncthreads();
+    uint32_t run = 0, total = 0;
+    unsigned long long rcov = 0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (k0 + j >= Cv) break;
-            col[(long long)(k0 + j) * Tmax] = run;
-            run += a[j];
-            if (!found) {
-                rcov += b[j];
-                if (rcov >= kCovTarget || run >= want) { found = true; lastc = (uint32_t)(k0 + j); keep = run; }
+    for (int q = 0; q < kColWarps; ++q) {
+        if (q < w) { run += s_c[q][l]; rcov += s_v[q][l]; }
+        total += s_c[q][l];
+    }
+    const int g = tb.v[v].tile_base + t;
+    const int lim = live && limit ? limit[g] : 0;
+    const uint32_t want = lim > 0 ? (uint32_t)min(2ll * lim + 64, 0x7fffffffll) : 0xffffffffu;
+    // 2. exclusive prefixes of this range; the first chunk meeting the rule
+    uint32_t fk = 0xffffffffu, fkeep = 0;
+    if (live) {
+        for (int k = k0; k < k1; k += 8) {
+            uint32_t a[8], c[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const bool in = k + j < k1;
+                a[j] = in ? col[(long long)(k + j) * Tmax] : 0u;
+                c[j] = in && cov && fk == 0xffffffffu ? __ldg(cov + (long long)(k + j) * Tmax) : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (k + j >= k1) break;
+                col[(long long)(k + j) * Tmax] = run;
+                run += a[j];
+                rcov += c[j];
+                if (fk == 0xffffffffu && (rcov >= kCovTarget || run >= want)) { fk = (uint32_t)(k + j); fkeep = run; }
             }
         }
     }
-    full[g] = run;
-    last_chunk[g] = lastc;
-    kept[g] = found ? keep : run;
+    s_fk[w][l] = fk;
+    s_keep[w][l] = fkeep;
+    __syncthreads();
+    if (w == 0 && live) {
+        uint32_t lastc = (uint32_t)(Cv - 1), keep = total;
+#pragma unroll
+        for (int q = kColWarps - 1; q >= 0; --q)
+            if (s_fk[q][l] != 0xffffffffu) { lastc = s_fk[q][l]; keep = s_keep[q][l]; }
+        full[g] = total;
+        last_chunk[g] = lastc;
+        kept[g] = keep;
+    }
 }
 
 __global__ void k_pre_ranges(int T, const uint32_t *__restrict__ kept,
@@ -1308,7 +1528,10 @@ static PrePlan make_pre_plan(long long VN, const TileBatch &tb) {
     p.tstart = take(8 * (size_t)(tb.total_tiles + 1));
     long long nb = (VN + kSortTile - 1) / kSortTile;
     if (nb < 1) nb = 1;
-    p.hist = take(4 * (size_t)kRadix * nb);
+    {
+        const size_t hb = 4 * (size_t)kRadix * nb, ob = onesweep_scratch_bytes(VN);
+        p.hist = take(hb > ob ? hb : ob);
+    }
     long long maxscan = VN > (long long)kRadix * nb ? VN : (long long)kRadix * nb;
     if (maxscan < tb.total_tiles) maxscan = tb.total_tiles;
     p.part = take(8 * (size_t)((maxscan + kScanChunk - 1) / kScanChunk + 1));
@@ -1426,7 +1649,7 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
         cudaMemsetAsync(d_n_instances, 0, sizeof(long long), st);
         return launch_status();
     }
-    const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, st);
+    const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, d_err_word, st);
     { k_gather_counts<<<cdiv(VN, 256), 256, 0, st>>>(order, d_touched, VN, cnt); count_launches(1); }
     exclusive_scan<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, offs + VN, st);
     size_t gmax = 0;
@@ -1448,7 +1671,12 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
         { k_pre_count<GS_BF16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, offs, Mc, Mv); count_launches(1); }
     else
         { k_pre_count<GS_F16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, offs, Mc, Mv); count_launches(1); }
-    { k_pre_colscan<<<cdiv(T, 128), 128, 0, st>>>(tb, p.Cv, p.Tmax, Mc, Mv_used, d_tile_limit, full, lastc, kept); count_launches(1); }
+    {
+        int nblk = 0;
+        for (int v = 0; v < n_views; ++v) nblk += cdiv(tb.v[v].TX * tb.v[v].TY, 32);
+        k_pre_colscan<<<nblk, 32 * kColWarps, 0, st>>>(tb, p.Cv, p.Tmax, Mc, Mv_used, d_tile_limit, full, lastc, kept);
+        count_launches(1);
+    }
     exclusive_scan<uint32_t, unsigned long long>(kept, tstart, T, (unsigned long long *)part, tstart + T, st);
     { k_finish_count<<<1, 1, 0, st>>>(tstart + T, capacity, d_n_instances, count, d_err_word); count_launches(1); }
     { k_pre_ranges<<<cdiv(T, 256), 256, 0, st>>>(T, kept, tstart, reinterpret_cast<uint2 *>(d_tile_ranges)); count_launches(1); }
