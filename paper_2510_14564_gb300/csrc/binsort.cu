@@ -1381,14 +1381,14 @@ __global__ void k_pre_ranges(int T, const uint32_t *__restrict__ kept,
     ranges[t] = c > 0 ? make_uint2(s0, s0 + c) : make_uint2(0u, 0u);
 }
 
-// Place the kept instances: one CTA of 8 warps per chunk, per-tile cursors in
+// Place the kept instances: one CTA of 16 warps per chunk, per-tile cursors in
 // shared memory (a skip mark for tiles that keep no entry of this chunk) and a
 // summed-area table of the tiles still active in this chunk.  The CTA reads
-// the chunk's records 256 at a time, keeps those whose rectangle holds an
+// the chunk's records 512 at a time, keeps those whose rectangle holds an
 // active tile (in order), and then warp w hands out slots in the tile rows
-// y = w (mod 8): every warp walks the kept records in order, so each tile's
+// y = w (mod 16): every warp walks the kept records in order, so each tile's
 // slots follow record order.
-constexpr int kPlaceWarps = 8;
+constexpr int kPlaceWarps = 16;
 constexpr int kPlaceThreads = 32 * kPlaceWarps;
 __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     TileBatch tb, int N, int Cv, int Tmax, const uint32_t *__restrict__ order,

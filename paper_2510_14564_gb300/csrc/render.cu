@@ -1,11 +1,13 @@
 // render.cu -- a3 forward blending and a5 its reverse mode (sm_103a).
 //
 // Sec. II-A: C = sum_i c_i alpha_i prod_{j<i} (1 - alpha_j) over the depth-
-// sorted Gaussians of a pixel, one 16x16 pixel block per CTA (Sec. IV-C1),
-// one pixel per thread.  Per batch of 256 list entries every thread stages
-// one splat record into shared memory (the per-tile batch loading of
-// Sec. V-C, with each record's geometry and colour contiguous), then every
-// pixel walks the batch.
+// sorted Gaussians of a pixel, one 16x16 pixel block per CTA (Sec. IV-C1).
+// The forward pass takes one pixel per thread (256 threads); the reverse
+// pass two vertically adjacent pixels per thread (128 threads, each warp a
+// 16x4 block), which halves its warp reductions and atomics per pixel.  Per
+// batch of 256 list entries the threads stage the splat records into shared
+// memory (the per-tile batch loading of Sec. V-C, with each record's geometry
+// and colour contiguous), then every pixel walks the batch.
 //
 // Staging also drops entries that cannot reach alpha >= 1/255 anywhere in
 // the tile (a conservative bound of the Gaussian over the tile square, with
@@ -60,23 +62,30 @@ __device__ __forceinline__ float tile_bound(float u, float v, float Ap, float Bp
 // log2(1/255) minus a margin that covers FP32 rounding of the bound.
 constexpr float kCullLog2 = -7.99435343685886f - 0.02f;
 
+constexpr int kBatch = kTilePix;               // list entries staged per batch
+constexpr int kFwdPPT = 1;                     // pixels per thread, forward
+constexpr int kBwdPPT = 2;                     // pixels per thread, reverse
+
+template <int PPT>
 struct TileCtx {
-    int tile, view, px, py;
-    bool inside;
+    int tile, view, px, py;                    // this thread's pixels: (px, py + p), p < PPT
+    bool in[PPT];
     uint2 range;
     float x0, y0;
 };
 
-__device__ __forceinline__ TileCtx tile_ctx(const TileBatch &tb, const uint2 *ranges, int tile) {
-    TileCtx c;
+template <int PPT>
+__device__ __forceinline__ TileCtx<PPT> tile_ctx(const TileBatch &tb, const uint2 *ranges, int tile) {
+    TileCtx<PPT> c;
     c.tile = tile;
     c.view = view_of_tile(tb, tile);
     const ViewTiles &vt = tb.v[c.view];
     int lt = tile - vt.tile_base;
     int tx = lt % vt.TX, ty = lt / vt.TX;
     c.px = tx * kTile + (threadIdx.x & (kTile - 1));
-    c.py = ty * kTile + (threadIdx.x / kTile);
-    c.inside = c.px < vt.W && c.py < vt.H;
+    c.py = ty * kTile + PPT * (threadIdx.x / kTile);
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) c.in[p] = c.px < vt.W && c.py + p < vt.H;
     c.range = __ldg(ranges + tile);
     c.x0 = (float)(tx * kTile);
     c.y0 = (float)(ty * kTile);
@@ -115,54 +124,73 @@ __device__ __forceinline__ int next_tile(const SchedArgs &sa, int total_tiles, i
 }
 
 // Stage list entries [j0, j1) of the tile into shared memory, dropping those
-// the tile bound rules out.  Order of the kept entries is preserved.  Each
-// thread handles entry j0 + threadIdx.x.  Returns the kept count.
-template <int DT>
-__device__ __forceinline__ int stage_batch(const uint32_t *vals, const void *splats, const TileCtx &c,
+// the tile bound rules out.  Order of the kept entries is preserved.  With NT
+// = 256 / PPT threads, thread i handles entries j0 + r NT + i, r < PPT.
+// Returns the kept count.
+template <int DT, int PPT>
+__device__ __forceinline__ int stage_batch(const uint32_t *vals, const void *splats, const TileCtx<PPT> &c,
                                            int j0, int j1, float4 *s_a, float4 *s_b, float4 *s_c,
-                                           int *s_warp) {
-    const int j = j0 + threadIdx.x;
-    bool keep = false;
-    Splat s;
-    uint32_t id = 0;
-    if (j < j1) {
-        id = __ldg(vals + j);
-        s = load_splat<DT>(splats, id);
-        keep = tile_bound(s.u, s.v, s.Ap, s.Bp, s.Cp, s.lo, c.x0, c.y0) >= kCullLog2;
-    }
-    unsigned bal = __ballot_sync(0xffffffffu, keep);
+                                           int *s_warp /*[PPT * NW]*/) {
+    constexpr int NT = kTilePix / PPT, NW = NT / 32;
     const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) s_warp[w] = __popc(bal);
-    __syncthreads();
-    int base = 0, total = 0;
+    bool keep[PPT];
+    unsigned bal[PPT];
+    Splat s[PPT];
+    uint32_t id[PPT];
 #pragma unroll
-    for (int k = 0; k < kTilePix / 32; ++k) {
-        int cnt = s_warp[k];
-        base += (k < w) ? cnt : 0;
-        total += cnt;
+    for (int r = 0; r < PPT; ++r) {
+        const int j = j0 + r * NT + threadIdx.x;
+        keep[r] = false;
+        id[r] = 0;
+        if (j < j1) {
+            id[r] = __ldg(vals + j);
+            s[r] = load_splat<DT>(splats, id[r]);
+            keep[r] = tile_bound(s[r].u, s[r].v, s[r].Ap, s[r].Bp, s[r].Cp, s[r].lo, c.x0, c.y0) >= kCullLog2;
+        }
+        bal[r] = __ballot_sync(0xffffffffu, keep[r]);
+        if ((threadIdx.x & 31) == 0) s_warp[r * NW + w] = __popc(bal[r]);
     }
-    if (keep) {
-        int pos = base + __popc(bal & lanemask_lt_r());
-        s_a[pos] = make_float4(s.u, s.v, s.Ap, s.Bp);
-        s_b[pos] = make_float4(s.Cp, s.lo, s.r, s.g);
-        s_c[pos] = make_float4(s.b, __int_as_float(j - (int)c.range.x), __uint_as_float(id), ex2(-s.lo));
+    __syncthreads();
+    int base[PPT], total = 0;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        int pre = 0, tot = 0;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            const int cnt = s_warp[r * NW + q];
+            tot += cnt;
+            pre += (q < w) ? cnt : 0;
+        }
+        base[r] = total + pre;
+        total += tot;
+    }
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        if (keep[r]) {
+            const int pos = base[r] + __popc(bal[r] & lanemask_lt_r());
+            const int j = j0 + r * NT + threadIdx.x;
+            s_a[pos] = make_float4(s[r].u, s[r].v, s[r].Ap, s[r].Bp);
+            s_b[pos] = make_float4(s[r].Cp, s[r].lo, s[r].r, s[r].g);
+            s_c[pos] = make_float4(s[r].b, __int_as_float(j - (int)c.range.x), __uint_as_float(id[r]), ex2(-s[r].lo));
+        }
     }
     __syncthreads();
     return total;
 }
 
-template <int DT>
-__global__ void __launch_bounds__(kTilePix) k_render_fwd(TileBatch tb, const uint2 *__restrict__ ranges,
-                                                        const uint32_t *__restrict__ vals,
-                                                        const void *__restrict__ splats, SchedArgs sa,
-                                                        float *__restrict__ img, float *__restrict__ T_final,
-                                                        int *__restrict__ n_proc, int *__restrict__ tile_nproc,
-                                                        unsigned long long *__restrict__ tile_ns,
-                                                        const uint32_t *__restrict__ tile_count,
-                                                        int *__restrict__ flag_tiles, int *__restrict__ flag_count,
-                                                        int *err_word) {
-    __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
-    __shared__ int s_warp[kTilePix / 32];
+template <int DT, int PPT>
+__global__ void __launch_bounds__(kTilePix / PPT) k_render_fwd(TileBatch tb, const uint2 *__restrict__ ranges,
+                                                              const uint32_t *__restrict__ vals,
+                                                              const void *__restrict__ splats, SchedArgs sa,
+                                                              float *__restrict__ img, float *__restrict__ T_final,
+                                                              int *__restrict__ n_proc, int *__restrict__ tile_nproc,
+                                                              unsigned long long *__restrict__ tile_ns,
+                                                              const uint32_t *__restrict__ tile_count,
+                                                              int *__restrict__ flag_tiles,
+                                                              int *__restrict__ flag_count, int *err_word) {
+    constexpr int NT = kTilePix / PPT;
+    __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch];
+    __shared__ int s_warp[PPT * NT / 32];
     __shared__ int s_tile;
     __shared__ int s_max;
     const unsigned long long t_start = globaltimer();
@@ -171,55 +199,96 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(TileBatch tb, const uin
         if (tile < 0) break;
         const unsigned long long t0 = tile_ns ? globaltimer() : 0ull;
         if (threadIdx.x == 0) s_max = 0;
-        const TileCtx c = tile_ctx(tb, ranges, tile);
-        const float pcx = (float)c.px + 0.5f, pcy = (float)c.py + 0.5f;
-        float T = 1.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
-        int last = 0;
-        bool done = !c.inside;
-        for (int j0 = (int)c.range.x; j0 < (int)c.range.y; j0 += kTilePix) {
-            if (__syncthreads_count(done) == kTilePix) break;
-            const int j1 = min(j0 + kTilePix, (int)c.range.y);
-            const int n = stage_batch<DT>(vals, splats, c, j0, j1, s_a, s_b, s_c, s_warp);
-            if (!done) {
+        const TileCtx<PPT> c = tile_ctx<PPT>(tb, ranges, tile);
+        const float pcx = (float)c.px + 0.5f;
+        float pcy[PPT], T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
+        int last[PPT];
+        bool done[PPT];
+        bool all_done = true;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            pcy[p] = (float)(c.py + p) + 0.5f;
+            T[p] = 1.0f; Cr[p] = Cg[p] = Cb[p] = 0.0f;
+            last[p] = 0;
+            done[p] = !c.in[p];
+            all_done = all_done && done[p];
+        }
+        for (int j0 = (int)c.range.x; j0 < (int)c.range.y; j0 += kBatch) {
+            if (__syncthreads_count(all_done) == NT) break;
+            const int j1 = min(j0 + kBatch, (int)c.range.y);
+            const int n = stage_batch<DT, PPT>(vals, splats, c, j0, j1, s_a, s_b, s_c, s_warp);
+            if (all_done) continue;
+            if constexpr (PPT == 1) {
+                // one pixel: leave the batch as soon as it stops
                 for (int k = 0; k < n; ++k) {
                     const float4 a = s_a[k];
                     const float4 b = s_b[k];
                     float q;
-                    const float araw = pair_alpha_raw(a.z, a.w, b.x, b.y, pcx - a.x, pcy - a.y, &q);
+                    const float araw = pair_alpha_raw(a.z, a.w, b.x, b.y, pcx - a.x, pcy[0] - a.y, &q);
                     const float alpha = fminf(kAlphaMax, araw);
                     if (alpha < kAlphaMin) continue;
-                    const float Tn = T * (1.0f - alpha);
-                    if (Tn < kTMin) { done = true; break; }
+                    const float Tn = T[0] * (1.0f - alpha);
+                    if (Tn < kTMin) { done[0] = true; all_done = true; break; }
                     const float4 cc = s_c[k];
-                    const float w = alpha * T;
-                    Cr = fmaf(b.z, w, Cr);
-                    Cg = fmaf(b.w, w, Cg);
-                    Cb = fmaf(cc.x, w, Cb);
-                    T = Tn;
-                    last = __float_as_int(cc.y) + 1;
+                    const float w = alpha * T[0];
+                    Cr[0] = fmaf(b.z, w, Cr[0]);
+                    Cg[0] = fmaf(b.w, w, Cg[0]);
+                    Cb[0] = fmaf(cc.x, w, Cb[0]);
+                    T[0] = Tn;
+                    last[0] = __float_as_int(cc.y) + 1;
                 }
+                continue;
+            }
+            for (int k = 0; k < n; ++k) {
+                const float4 a = s_a[k];
+                const float4 b = s_b[k];
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    if (done[p]) continue;
+                    float q;
+                    const float araw = pair_alpha_raw(a.z, a.w, b.x, b.y, pcx - a.x, pcy[p] - a.y, &q);
+                    const float alpha = fminf(kAlphaMax, araw);
+                    if (alpha < kAlphaMin) continue;
+                    const float Tn = T[p] * (1.0f - alpha);
+                    if (Tn < kTMin) { done[p] = true; continue; }
+                    const float4 cc = s_c[k];
+                    const float w = alpha * T[p];
+                    Cr[p] = fmaf(b.z, w, Cr[p]);
+                    Cg[p] = fmaf(b.w, w, Cg[p]);
+                    Cb[p] = fmaf(cc.x, w, Cb[p]);
+                    T[p] = Tn;
+                    last[p] = __float_as_int(cc.y) + 1;
+                }
+                all_done = true;
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) all_done = all_done && done[p];
+                if (all_done) break;
             }
         }
         if (tile_count) {
             // a kept prefix that ran out while a pixel was still blending
-            const int alive = kTilePix - __syncthreads_count(done);
+            const int alive = NT - __syncthreads_count(all_done);
             if (alive > 0 && threadIdx.x == 0 && c.range.y - c.range.x < __ldg(tile_count + tile)) {
                 const int idx = atomicAdd(flag_count, 1);
                 flag_tiles[idx] = tile;
             }
         }
         const ViewTiles &vt = tb.v[c.view];
-        if (c.inside) {
-            const long long HW = (long long)vt.W * vt.H;
-            const long long p = (long long)c.py * vt.W + c.px;
-            float *im = img + 3 * vt.pix_base;
-            im[p] = fmaf(T, vt.bg[0], Cr);
-            im[HW + p] = fmaf(T, vt.bg[1], Cg);
-            im[2 * HW + p] = fmaf(T, vt.bg[2], Cb);
-            T_final[vt.pix_base + p] = T;
-            n_proc[vt.pix_base + p] = last;
+        const long long HW = (long long)vt.W * vt.H;
+        float *im = img + 3 * vt.pix_base;
+        int lmax = 0;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            lmax = max(lmax, last[p]);
+            if (!c.in[p]) continue;
+            const long long q = (long long)(c.py + p) * vt.W + c.px;
+            im[q] = fmaf(T[p], vt.bg[0], Cr[p]);
+            im[HW + q] = fmaf(T[p], vt.bg[1], Cg[p]);
+            im[2 * HW + q] = fmaf(T[p], vt.bg[2], Cb[p]);
+            T_final[vt.pix_base + q] = T[p];
+            n_proc[vt.pix_base + q] = last[p];
         }
-        int wmax = __reduce_max_sync(0xffffffffu, last);
+        int wmax = __reduce_max_sync(0xffffffffu, lmax);
         __syncthreads();
         if ((threadIdx.x & 31) == 0) atomicMax(&s_max, wmax);
         __syncthreads();
@@ -230,76 +299,84 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(TileBatch tb, const uin
     }
 }
 
-template <int DT>
-__global__ void __launch_bounds__(kTilePix) k_render_bwd(TileBatch tb, const uint2 *__restrict__ ranges,
-                                                        const uint32_t *__restrict__ vals,
-                                                        const void *__restrict__ splats, SchedArgs sa,
-                                                        const float *__restrict__ dimg,
-                                                        const float *__restrict__ T_final,
-                                                        const int *__restrict__ n_proc,
-                                                        const int *__restrict__ tile_nproc,
-                                                        float *__restrict__ grad2d, int *err_word) {
-    __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
-    __shared__ int s_warp[kTilePix / 32];
+template <int DT, int PPT>
+__global__ void __launch_bounds__(kTilePix / PPT, 12 / PPT) k_render_bwd(
+    TileBatch tb, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+    const void *__restrict__ splats, SchedArgs sa, const float *__restrict__ dimg,
+    const float *__restrict__ T_final, const int *__restrict__ n_proc, const int *__restrict__ tile_nproc,
+    float *__restrict__ grad2d, int *err_word) {
+    constexpr int NT = kTilePix / PPT;
+    __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch];
+    __shared__ int s_warp[PPT * NT / 32];
     __shared__ int s_tile;
     const unsigned long long t_start = globaltimer();
     for (int iter = 0;; ++iter) {
         const int tile = next_tile(sa, tb.total_tiles, &s_tile, t_start, err_word, iter);
         if (tile < 0) break;
-        const TileCtx c = tile_ctx(tb, ranges, tile);
+        const TileCtx<PPT> c = tile_ctx<PPT>(tb, ranges, tile);
         const ViewTiles &vt = tb.v[c.view];
-        const float pcx = (float)c.px + 0.5f, pcy = (float)c.py + 0.5f;
-        float Tf = 1.0f, G0 = 0.0f, G1 = 0.0f, G2 = 0.0f;
-        int last = 0;
-        if (c.inside) {
-            const long long HW = (long long)vt.W * vt.H;
-            const long long p = (long long)c.py * vt.W + c.px;
-            const float *di = dimg + 3 * vt.pix_base;
-            G0 = __ldg(di + p); G1 = __ldg(di + HW + p); G2 = __ldg(di + 2 * HW + p);
-            Tf = __ldg(T_final + vt.pix_base + p);
-            last = __ldg(n_proc + vt.pix_base + p);
+        const float pcx = (float)c.px + 0.5f;
+        float pcy[PPT], T[PPT], G0[PPT], G1[PPT], G2[PPT], bgdot[PPT], R0[PPT], R1[PPT], R2[PPT];
+        int last[PPT];
+        const long long HW = (long long)vt.W * vt.H;
+        const float *di = dimg + 3 * vt.pix_base;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            pcy[p] = (float)(c.py + p) + 0.5f;
+            float Tf = 1.0f;
+            G0[p] = G1[p] = G2[p] = 0.0f;
+            last[p] = 0;
+            if (c.in[p]) {
+                const long long q = (long long)(c.py + p) * vt.W + c.px;
+                G0[p] = __ldg(di + q); G1[p] = __ldg(di + HW + q); G2[p] = __ldg(di + 2 * HW + q);
+                Tf = __ldg(T_final + vt.pix_base + q);
+                last[p] = __ldg(n_proc + vt.pix_base + q);
+            }
+            bgdot[p] = Tf * (vt.bg[0] * G0[p] + vt.bg[1] * G1[p] + vt.bg[2] * G2[p]);
+            T[p] = Tf;
+            R0[p] = R1[p] = R2[p] = 0.0f;
         }
-        const float bgdot = Tf * (vt.bg[0] * G0 + vt.bg[1] * G1 + vt.bg[2] * G2);
-        float T = Tf, R0 = 0.0f, R1 = 0.0f, R2 = 0.0f;
         const int jend = (int)c.range.x + __ldg(tile_nproc + tile);
-        for (int j1 = jend; j1 > (int)c.range.x; j1 -= kTilePix) {
-            const int j0 = max((int)c.range.x, j1 - kTilePix);
+        for (int j1 = jend; j1 > (int)c.range.x; j1 -= kBatch) {
+            const int j0 = max((int)c.range.x, j1 - kBatch);
             __syncthreads();
-            const int n = stage_batch<DT>(vals, splats, c, j0, j1, s_a, s_b, s_c, s_warp);
+            const int n = stage_batch<DT, PPT>(vals, splats, c, j0, j1, s_a, s_b, s_c, s_warp);
             for (int k = n - 1; k >= 0; --k) {
                 const float4 a = s_a[k];
                 const float4 b = s_b[k];
                 const float4 cc = s_c[k];
                 const int e = __float_as_int(cc.y);
-                float dx = pcx - a.x, dy = pcy - a.y;
                 float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
-                bool contrib = e < last;
-                if (contrib) {
+                bool contrib = false;
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    if (e >= last[p]) continue;
+                    const float dx = pcx - a.x, dy = pcy[p] - a.y;
                     float q;
                     const float araw = pair_alpha_raw(a.z, a.w, b.x, b.y, dx, dy, &q);
                     const float alpha = fminf(kAlphaMax, araw);
-                    contrib = alpha >= kAlphaMin;
-                    if (contrib) {
-                        const float om = 1.0f - alpha;
-                        const float rom = rcp_approx(om);
-                        const float Tb = T * rom;
-                        const float w = alpha * Tb;
-                        gr = G0 * w; gg = G1 * w; gb = G2 * w;
-                        const float dal = Tb * (G0 * (b.z - R0) + G1 * (b.w - R1) + G2 * (cc.x - R2)) - bgdot * rom;
-                        R0 = fmaf(b.z, alpha, om * R0);
-                        R1 = fmaf(b.w, alpha, om * R1);
-                        R2 = fmaf(cc.x, alpha, om * R2);
-                        T = Tb;
-                        if (araw <= kAlphaMax) {
-                            const float dpow = dal * alpha;
-                            go = dpow * cc.w;                       // dal * G, G = alpha / o
-                            gA = -0.5f * dpow * dx * dx;
-                            gB = -dpow * dx * dy;
-                            gC = -0.5f * dpow * dy * dy;
-                            // A dx + B dy = -ln2 (2 Ap dx + Bp dy); B dx + C dy = -ln2 (Bp dx + 2 Cp dy)
-                            gu = -kLn2 * dpow * (2.0f * a.z * dx + a.w * dy);
-                            gv = -kLn2 * dpow * (a.w * dx + 2.0f * b.x * dy);
-                        }
+                    if (alpha < kAlphaMin) continue;
+                    contrib = true;
+                    const float om = 1.0f - alpha;
+                    const float rom = rcp_approx(om);
+                    const float Tb = T[p] * rom;
+                    const float w = alpha * Tb;
+                    gr = fmaf(G0[p], w, gr); gg = fmaf(G1[p], w, gg); gb = fmaf(G2[p], w, gb);
+                    const float dal = Tb * (G0[p] * (b.z - R0[p]) + G1[p] * (b.w - R1[p]) + G2[p] * (cc.x - R2[p])) -
+                                      bgdot[p] * rom;
+                    R0[p] = fmaf(b.z, alpha, om * R0[p]);
+                    R1[p] = fmaf(b.w, alpha, om * R1[p]);
+                    R2[p] = fmaf(cc.x, alpha, om * R2[p]);
+                    T[p] = Tb;
+                    if (araw <= kAlphaMax) {
+                        const float dpow = dal * alpha;
+                        go = fmaf(dpow, cc.w, go);                     // dal * G, G = alpha / o
+                        gA = fmaf(-0.5f * dpow, dx * dx, gA);
+                        gB = fmaf(-dpow, dx * dy, gB);
+                        gC = fmaf(-0.5f * dpow, dy * dy, gC);
+                        // A dx + B dy = -ln2 (2 Ap dx + Bp dy); B dx + C dy = -ln2 (Bp dx + 2 Cp dy)
+                        gu = fmaf(-kLn2 * dpow, 2.0f * a.z * dx + a.w * dy, gu);
+                        gv = fmaf(-kLn2 * dpow, a.w * dx + 2.0f * b.x * dy, gv);
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
@@ -346,7 +423,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_bwd(TileBatch tb, const uin
 using namespace gs;
 
 static int fill_sched(const gs_schedule *sched, const TileBatch &tb, SchedArgs *sa, int *grid,
-                      cudaStream_t st, const void *kernel, int smem) {
+                      cudaStream_t st, const void *kernel, int threads, int smem) {
     sa->mode = GS_SCHED_RASTER;
     sa->order = nullptr;
     sa->queue = nullptr;
@@ -363,7 +440,7 @@ static int fill_sched(const gs_schedule *sched, const TileBatch &tb, SchedArgs *
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kTilePix, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
     if (per < 1) per = 1;
     *grid = sms * per;
     if (*grid > tb.total_tiles) *grid = tb.total_tiles;
@@ -385,22 +462,22 @@ extern "C" int gs_render_fwd(const gs_camera *cams, int n_views, const uint32_t 
     if (rgb_dtype < GS_F32 || rgb_dtype > GS_F16) return GS_ERR_ARG;
     if (d_tile_count && (!d_flag_tiles || !d_flag_count)) return GS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const void *kern = rgb_dtype == GS_F32 ? (const void *)k_render_fwd<GS_F32>
-                       : rgb_dtype == GS_BF16 ? (const void *)k_render_fwd<GS_BF16>
-                                              : (const void *)k_render_fwd<GS_F16>;
+    const void *kern = rgb_dtype == GS_F32 ? (const void *)k_render_fwd<GS_F32, kFwdPPT>
+                       : rgb_dtype == GS_BF16 ? (const void *)k_render_fwd<GS_BF16, kFwdPPT>
+                                              : (const void *)k_render_fwd<GS_F16, kFwdPPT>;
     SchedArgs sa;
     int grid;
-    int rc = fill_sched(sched, tb, &sa, &grid, st, kern, 0);
+    int rc = fill_sched(sched, tb, &sa, &grid, st, kern, kTilePix / kFwdPPT, 0);
     if (rc != GS_OK) return rc;
     if (grid < 1) return GS_OK;
     const uint2 *rg = reinterpret_cast<const uint2 *>(d_tile_ranges);
     unsigned long long *tns = reinterpret_cast<unsigned long long *>(d_tile_ns);
     if (rgb_dtype == GS_F32)
-        { k_render_fwd<GS_F32><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_tile_count, d_flag_tiles, d_flag_count, d_err_word); count_launches(1); }
+        { k_render_fwd<GS_F32, kFwdPPT><<<grid, kTilePix / kFwdPPT, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_tile_count, d_flag_tiles, d_flag_count, d_err_word); count_launches(1); }
     else if (rgb_dtype == GS_BF16)
-        { k_render_fwd<GS_BF16><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_tile_count, d_flag_tiles, d_flag_count, d_err_word); count_launches(1); }
+        { k_render_fwd<GS_BF16, kFwdPPT><<<grid, kTilePix / kFwdPPT, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_tile_count, d_flag_tiles, d_flag_count, d_err_word); count_launches(1); }
     else
-        { k_render_fwd<GS_F16><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_tile_count, d_flag_tiles, d_flag_count, d_err_word); count_launches(1); }
+        { k_render_fwd<GS_F16, kFwdPPT><<<grid, kTilePix / kFwdPPT, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_img, d_T_final, d_n_proc, d_tile_nproc, tns, d_tile_count, d_flag_tiles, d_flag_count, d_err_word); count_launches(1); }
     return launch_status();
 }
 
@@ -417,20 +494,20 @@ extern "C" int gs_render_bwd(const gs_camera *cams, int n_views, const uint32_t 
     if (!aligned(d_splats, 16) || !aligned(d_grad2d, 16) || !aligned(d_tile_ranges, 8)) return GS_ERR_ARG;
     if (rgb_dtype < GS_F32 || rgb_dtype > GS_F16) return GS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const void *kern = rgb_dtype == GS_F32 ? (const void *)k_render_bwd<GS_F32>
-                       : rgb_dtype == GS_BF16 ? (const void *)k_render_bwd<GS_BF16>
-                                              : (const void *)k_render_bwd<GS_F16>;
+    const void *kern = rgb_dtype == GS_F32 ? (const void *)k_render_bwd<GS_F32, kBwdPPT>
+                       : rgb_dtype == GS_BF16 ? (const void *)k_render_bwd<GS_BF16, kBwdPPT>
+                                              : (const void *)k_render_bwd<GS_F16, kBwdPPT>;
     SchedArgs sa;
     int grid;
-    int rc = fill_sched(sched, tb, &sa, &grid, st, kern, 0);
+    int rc = fill_sched(sched, tb, &sa, &grid, st, kern, kTilePix / kBwdPPT, 0);
     if (rc != GS_OK) return rc;
     if (grid < 1) return GS_OK;
     const uint2 *rg = reinterpret_cast<const uint2 *>(d_tile_ranges);
     if (rgb_dtype == GS_F32)
-        { k_render_bwd<GS_F32><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_dimg, d_T_final, d_n_proc, d_tile_nproc, d_grad2d, d_err_word); count_launches(1); }
+        { k_render_bwd<GS_F32, kBwdPPT><<<grid, kTilePix / kBwdPPT, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_dimg, d_T_final, d_n_proc, d_tile_nproc, d_grad2d, d_err_word); count_launches(1); }
     else if (rgb_dtype == GS_BF16)
-        { k_render_bwd<GS_BF16><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_dimg, d_T_final, d_n_proc, d_tile_nproc, d_grad2d, d_err_word); count_launches(1); }
+        { k_render_bwd<GS_BF16, kBwdPPT><<<grid, kTilePix / kBwdPPT, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_dimg, d_T_final, d_n_proc, d_tile_nproc, d_grad2d, d_err_word); count_launches(1); }
     else
-        { k_render_bwd<GS_F16><<<grid, kTilePix, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_dimg, d_T_final, d_n_proc, d_tile_nproc, d_grad2d, d_err_word); count_launches(1); }
+        { k_render_bwd<GS_F16, kBwdPPT><<<grid, kTilePix / kBwdPPT, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_dimg, d_T_final, d_n_proc, d_tile_nproc, d_grad2d, d_err_word); count_launches(1); }
     return launch_status();
 }
