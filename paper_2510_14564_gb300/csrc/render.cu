@@ -3,8 +3,8 @@
 // Sec. II-A: C = sum_i c_i alpha_i prod_{j<i} (1 - alpha_j) over the depth-
 // sorted Gaussians of a pixel, one 16x16 pixel block per CTA (Sec. IV-C1).
 // The forward pass takes one pixel per thread (256 threads); the reverse
-// pass two vertically adjacent pixels per thread (128 threads, each warp a
-// 16x4 block), which halves its warp reductions and atomics per pixel.  Per
+// pass four vertically adjacent pixels per thread (64 threads, each warp a
+// 16x8 block), which divides its warp reductions and atomics per pixel by 4.  Per
 // batch of 256 list entries the threads stage the splat records into shared
 // memory (the per-tile batch loading of Sec. V-C, with each record's geometry
 // and colour contiguous), then every pixel walks the batch.
@@ -64,7 +64,7 @@ constexpr float kCullLog2 = -7.99435343685886f - 0.02f;
 
 constexpr int kBatch = kTilePix;               // list entries staged per batch
 constexpr int kFwdPPT = 1;                     // pixels per thread, forward
-constexpr int kBwdPPT = 2;                     // pixels per thread, reverse
+constexpr int kBwdPPT = 4;                     // pixels per thread, reverse
 
 template <int PPT>
 struct TileCtx {
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_render_fwd(TileBatch tb, con
 }
 
 template <int DT, int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT, 12 / PPT) k_render_bwd(
+__global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 8) k_render_bwd(
     TileBatch tb, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
     const void *__restrict__ splats, SchedArgs sa, const float *__restrict__ dimg,
     const float *__restrict__ T_final, const int *__restrict__ n_proc, const int *__restrict__ tile_nproc,
