@@ -1231,21 +1231,30 @@ __global__ void __launch_bounds__(256) k_pre_count(TileBatch tb, int N, int Cv, 
     for (int i = threadIdx.x; i < (splats ? 2 : 1) * G; i += 256) s_g2[i] = 0;
     __syncthreads();
     const ChunkGeom cg = chunk_of(v, k, Cv, N, offs, true);
-    for (long long i = cg.lo + threadIdx.x; i < cg.hi; i += 256) {
-        const uint32_t g = __ldg(order + i);
-        const short4 rc = __ldg(rect + g);
-        atomicAdd(&gc[rc.y * GX + rc.x], 1);
-        atomicAdd(&gc[rc.y * GX + rc.z], -1);
-        atomicAdd(&gc[rc.w * GX + rc.x], -1);
-        atomicAdd(&gc[rc.w * GX + rc.z], 1);
-        if (!splats) continue;
-        int x0, y0, x1, y1;
-        const int cov = (int)core_rect<DT>(splats, g, rc, x0, y0, x1, y1);
-        if (cov > 0) {
-            atomicAdd(&gv[y0 * GX + x0], cov);
-            atomicAdd(&gv[y0 * GX + x1], -cov);
-            atomicAdd(&gv[y1 * GX + x0], -cov);
-            atomicAdd(&gv[y1 * GX + x1], cov);
+    constexpr int R = 4;                           // records per thread per step, loads issued together
+    for (long long i0 = cg.lo + threadIdx.x; i0 < cg.hi; i0 += R * 256) {
+        uint32_t g[R];
+        short4 rc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) g[r] = i0 + r * 256 < cg.hi ? __ldg(order + i0 + r * 256) : 0xffffffffu;
+#pragma unroll
+        for (int r = 0; r < R; ++r) rc[r] = g[r] != 0xffffffffu ? __ldg(rect + g[r]) : make_short4(0, 0, 0, 0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (g[r] == 0xffffffffu) continue;
+            atomicAdd(&gc[rc[r].y * GX + rc[r].x], 1);
+            atomicAdd(&gc[rc[r].y * GX + rc[r].z], -1);
+            atomicAdd(&gc[rc[r].w * GX + rc[r].x], -1);
+            atomicAdd(&gc[rc[r].w * GX + rc[r].z], 1);
+            if (!splats) continue;
+            int x0, y0, x1, y1;
+            const int cov = (int)core_rect<DT>(splats, g[r], rc[r], x0, y0, x1, y1);
+            if (cov > 0) {
+                atomicAdd(&gv[y0 * GX + x0], cov);
+                atomicAdd(&gv[y0 * GX + x1], -cov);
+                atomicAdd(&gv[y1 * GX + x0], -cov);
+                atomicAdd(&gv[y1 * GX + x1], cov);
+            }
         }
     }
     __syncthreads();
@@ -1384,12 +1393,14 @@ __global__ void k_pre_ranges(int T, const uint32_t *__restrict__ kept,
 // Place the kept instances: one CTA of 16 warps per chunk, per-tile cursors in
 // shared memory (a skip mark for tiles that keep no entry of this chunk) and a
 // summed-area table of the tiles still active in this chunk.  The CTA reads
-// the chunk's records 512 at a time, keeps those whose rectangle holds an
+// the chunk's records 2048 at a time, keeps those whose rectangle holds an
 // active tile (in order), and then warp w hands out slots in the tile rows
 // y = w (mod 16): every warp walks the kept records in order, so each tile's
 // slots follow record order.
 constexpr int kPlaceWarps = 16;
 constexpr int kPlaceThreads = 32 * kPlaceWarps;
+constexpr int kPlaceRounds = 4;                        // records staged per thread per batch
+constexpr int kPlaceBatch = kPlaceRounds * kPlaceThreads;
 __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     TileBatch tb, int N, int Cv, int Tmax, const uint32_t *__restrict__ order,
     const short4 *__restrict__ rect, const unsigned long long *__restrict__ offs,
@@ -1399,9 +1410,9 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     unsigned long long *__restrict__ keys) {
     extern __shared__ uint32_t s_cur[];
     __shared__ int s_any;
-    __shared__ uint32_t s_g[kPlaceThreads];
-    __shared__ short4 s_rc[kPlaceThreads];
-    __shared__ int s_wc[kPlaceWarps];
+    __shared__ uint32_t s_g[kPlaceBatch];
+    __shared__ short4 s_rc[kPlaceBatch];
+    __shared__ int s_wc[kPlaceRounds * kPlaceWarps];
     if ((long long)*total > cap) return;
     const int v = blockIdx.x / Cv, k = blockIdx.x % Cv;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -1434,29 +1445,49 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     }
     __syncthreads();
     const ChunkGeom cg = chunk_of(v, k, Cv, N, offs, true);
-    for (long long b0 = cg.lo; b0 < cg.hi; b0 += kPlaceThreads) {
-        // 1. read 256 records, keep those with an active tile, in order
-        const long long i = b0 + threadIdx.x;
-        bool keep = false;
-        uint32_t g = 0;
-        short4 rc = make_short4(0, 0, 0, 0);
-        if (i < cg.hi) {
-            g = __ldg(order + i);
-            rc = __ldg(rect + g);
-            if (rc.z > rc.x && rc.w > rc.y)
-                keep = sat[rc.w * GX + rc.z] - sat[rc.y * GX + rc.z] - sat[rc.w * GX + rc.x] +
-                       sat[rc.y * GX + rc.x] > 0;
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (l == 0) s_wc[w] = __popc(bal);
-        __syncthreads();
-        int base = 0, n_keep = 0;
+    for (long long b0 = cg.lo; b0 < cg.hi; b0 += kPlaceBatch) {
+        // 1. read kPlaceBatch records (record b0 + r kPlaceThreads + thread in
+        //    round r), keep those with an active tile, in order
+        bool keep[kPlaceRounds];
+        uint32_t g[kPlaceRounds];
+        short4 rc[kPlaceRounds];
+        unsigned bal[kPlaceRounds];
 #pragma unroll
-        for (int q = 0; q < kPlaceWarps; ++q) { base += q < w ? s_wc[q] : 0; n_keep += s_wc[q]; }
-        if (keep) {
-            const int pos = base + __popc(bal & lanemask_lt());
-            s_g[pos] = g;
-            s_rc[pos] = rc;
+        for (int r = 0; r < kPlaceRounds; ++r) {
+            const long long i = b0 + r * kPlaceThreads + threadIdx.x;
+            keep[r] = false;
+            g[r] = 0;
+            rc[r] = make_short4(0, 0, 0, 0);
+            if (i < cg.hi) {
+                g[r] = __ldg(order + i);
+                rc[r] = __ldg(rect + g[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kPlaceRounds; ++r) {
+            const short4 q = rc[r];
+            if (q.z > q.x && q.w > q.y)
+                keep[r] = sat[q.w * GX + q.z] - sat[q.y * GX + q.z] - sat[q.w * GX + q.x] + sat[q.y * GX + q.x] > 0;
+            bal[r] = __ballot_sync(0xffffffffu, keep[r]);
+            if (l == 0) s_wc[r * kPlaceWarps + w] = __popc(bal[r]);
+        }
+        __syncthreads();
+        int n_keep = 0;
+#pragma unroll
+        for (int r = 0; r < kPlaceRounds; ++r) {
+            int pre = 0, tot = 0;
+#pragma unroll
+            for (int q = 0; q < kPlaceWarps; ++q) {
+                const int c = s_wc[r * kPlaceWarps + q];
+                tot += c;
+                pre += q < w ? c : 0;
+            }
+            if (keep[r]) {
+                const int pos = n_keep + pre + __popc(bal[r] & lanemask_lt());
+                s_g[pos] = g[r];
+                s_rc[pos] = rc[r];
+            }
+            n_keep += tot;
         }
         __syncthreads();
         // 2. each warp places the kept records' tiles in its own rows, in order
