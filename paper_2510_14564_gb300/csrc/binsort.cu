@@ -1215,6 +1215,63 @@ __device__ __forceinline__ uint32_t core_rect(const void *splats, uint32_t g, sh
     return (uint32_t)floorf(-log1pf(-alo) * (0.999f * kCovScale));
 }
 
+// Record bounds of every chunk of every view: bounds[v (Cv + 1) + k] = first
+// record of chunk k of view v, chunk k starting at instance fraction f(k/Cv)
+// of the view.  Placement work is in the part of the lists that is kept; with
+// per-tile limits (the previous step's processed counts) the kept share s of
+// instances is estimated as sum(2 limit + 64) / instances (an overestimate
+// where lists are cut), and the first half of the chunks splits the first s
+// of the instances evenly, the second half the rest with quadratic growth
+// (starting small, so an underestimate costs little).  Without limits the chunks grow cubically
+// (fine at the front of the depth order, where lists are cut).  One CTA.
+constexpr int kBoundThreads = 1024;
+__global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(int n_views, int Cv, int N, int T,
+                                                                const unsigned long long *__restrict__ offs,
+                                                                const int32_t *__restrict__ limit,
+                                                                long long *__restrict__ bounds) {
+    __shared__ double s_part[kBoundThreads / 32];
+    __shared__ double s_share;
+    double est = 0.0;
+    if (limit)
+        for (int t = threadIdx.x; t < T; t += kBoundThreads) {
+            const int lm = __ldg(limit + t);
+            if (lm > 0) est += 2.0 * lm + 64.0;
+        }
+    est = warp_sum(est);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = est;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int q = 0; q < kBoundThreads / 32; ++q) sum += s_part[q];
+        const double total = (double)offs[(long long)n_views * N];
+        s_share = (limit && total > 0.0) ? fmin(0.5, fmax(0.01, sum / total)) : -1.0;
+    }
+    __syncthreads();
+    const double share = s_share;
+    const int half = Cv / 2;
+    for (int j = threadIdx.x; j < n_views * (Cv + 1); j += kBoundThreads) {
+        const int v = j / (Cv + 1), k = j % (Cv + 1);
+        const long long s0 = (long long)v * N, s1 = s0 + N;
+        const unsigned long long i0 = offs[s0], span = offs[s1] - i0;
+        unsigned long long b;
+        if (k >= Cv) {
+            b = i0 + span;
+        } else if (share < 0.0 || half < 1) {
+            b = chunk_bound(i0, span, k, Cv, true);
+        } else {
+            double f;
+            if (k <= half) {
+                f = share * (double)k / (double)half;
+            } else {
+                const double y = (double)(k - half) / (double)(Cv - half);
+                f = share + (1.0 - share) * y * y;
+            }
+            b = i0 + (unsigned long long)((double)span * f);
+        }
+        bounds[j] = lower_bound_u64(offs, s0, s1, b);
+    }
+}
+
 // Per chunk: instance counts and the coverage bound per tile (2D difference
 // grids), into Mc[chunk][tile] and Mv[chunk][tile].
 template <int DT>
@@ -1222,7 +1279,7 @@ __global__ void __launch_bounds__(256) k_pre_count(TileBatch tb, int N, int Cv, 
                                                    const uint32_t *__restrict__ order,
                                                    const short4 *__restrict__ rect,
                                                    const void *__restrict__ splats,
-                                                   const unsigned long long *__restrict__ offs,
+                                                   const long long *__restrict__ bounds,
                                                    uint32_t *__restrict__ Mc, uint32_t *__restrict__ Mv) {
     extern __shared__ int s_g2[];
     const int v = blockIdx.x / Cv, k = blockIdx.x % Cv;
@@ -1230,7 +1287,9 @@ __global__ void __launch_bounds__(256) k_pre_count(TileBatch tb, int N, int Cv, 
     int *gc = s_g2, *gv = s_g2 + G;
     for (int i = threadIdx.x; i < (splats ? 2 : 1) * G; i += 256) s_g2[i] = 0;
     __syncthreads();
-    const ChunkGeom cg = chunk_of(v, k, Cv, N, offs, true);
+    ChunkGeom cg;
+    cg.lo = __ldg(bounds + v * (Cv + 1) + k);
+    cg.hi = __ldg(bounds + v * (Cv + 1) + k + 1);
     constexpr int R = 4;                           // records per thread per step, loads issued together
     for (long long i0 = cg.lo + threadIdx.x; i0 < cg.hi; i0 += R * 256) {
         uint32_t g[R];
@@ -1403,7 +1462,7 @@ constexpr int kPlaceRounds = 4;                        // records staged per thr
 constexpr int kPlaceBatch = kPlaceRounds * kPlaceThreads;
 __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     TileBatch tb, int N, int Cv, int Tmax, const uint32_t *__restrict__ order,
-    const short4 *__restrict__ rect, const unsigned long long *__restrict__ offs,
+    const short4 *__restrict__ rect, const long long *__restrict__ bounds,
     const uint32_t *__restrict__ Mc, const uint32_t *__restrict__ last_chunk,
     const unsigned long long *__restrict__ tstart, const unsigned long long *__restrict__ total,
     long long cap, uint32_t *__restrict__ vals, const float *__restrict__ depth,
@@ -1423,11 +1482,25 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
     bool any = false;
-    for (int t = threadIdx.x; t < Tv; t += kPlaceThreads) {
-        const bool act = (uint32_t)k <= last_chunk[tbase + t];
-        s_cur[t] = act ? (uint32_t)tstart[tbase + t] + row[t] : 0xffffffffu;
-        sat[(t / TX + 1) * GX + t % TX + 1] = act ? 1u : 0u;
-        any |= act;
+    for (int t0 = threadIdx.x; t0 < Tv; t0 += 4 * kPlaceThreads) {
+        uint32_t lc[4], rw[4];
+        unsigned long long ts[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {                // loads first: one round trip per four tiles
+            const int t = t0 + r * kPlaceThreads;
+            lc[r] = t < Tv ? __ldg(last_chunk + tbase + t) : 0u;
+            ts[r] = t < Tv ? __ldg(tstart + tbase + t) : 0ull;
+            rw[r] = t < Tv ? __ldg(row + t) : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int t = t0 + r * kPlaceThreads;
+            if (t >= Tv) continue;
+            const bool act = (uint32_t)k <= lc[r];
+            s_cur[t] = act ? (uint32_t)ts[r] + rw[r] : 0xffffffffu;
+            sat[(t / TX + 1) * GX + t % TX + 1] = act ? 1u : 0u;
+            any |= act;
+        }
     }
     for (int x = threadIdx.x; x < GX; x += kPlaceThreads) sat[x] = 0;
     for (int y = threadIdx.x; y <= TY; y += kPlaceThreads) sat[y * GX] = 0;
@@ -1444,7 +1517,9 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
         for (int y = 1; y <= TY; ++y) { run += sat[y * GX + x]; sat[y * GX + x] = run; }
     }
     __syncthreads();
-    const ChunkGeom cg = chunk_of(v, k, Cv, N, offs, true);
+    ChunkGeom cg;
+    cg.lo = __ldg(bounds + v * (Cv + 1) + k);
+    cg.hi = __ldg(bounds + v * (Cv + 1) + k + 1);
     for (long long b0 = cg.lo; b0 < cg.hi; b0 += kPlaceBatch) {
         // 1. read kPlaceBatch records (record b0 + r kPlaceThreads + thread in
         //    round r), keep those with an active tile, in order
@@ -1535,7 +1610,7 @@ __global__ void k_range_counts(const uint2 *__restrict__ ranges, int T, uint32_t
 }
 
 struct PrePlan {
-    size_t dk0, dk1, dv0, dv1, cnt, offs, mc, mv, full, lastc, kept, tstart, hist, part, misc, bytes;
+    size_t dk0, dk1, dv0, dv1, cnt, offs, mc, mv, full, lastc, kept, tstart, bnd, hist, part, misc, bytes;
     int Cv, Tmax;
     bool ok;
 };
@@ -1557,6 +1632,7 @@ static PrePlan make_pre_plan(long long VN, const TileBatch &tb) {
     p.lastc = take(4 * (size_t)tb.total_tiles);
     p.kept = take(4 * (size_t)tb.total_tiles);
     p.tstart = take(8 * (size_t)(tb.total_tiles + 1));
+    p.bnd = take(8 * (size_t)tb.n * (p.Cv + 1));
     long long nb = (VN + kSortTile - 1) / kSortTile;
     if (nb < 1) nb = 1;
     {
@@ -1689,6 +1765,8 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
         gmax = g > gmax ? g : gmax;
     }
     const int nchunks = n_views * p.Cv;
+    long long *bnd = (long long *)(ws + p.bnd);
+    { k_chunk_bounds<<<1, kBoundThreads, 0, st>>>(n_views, p.Cv, N, T, offs, d_tile_limit, bnd); count_launches(1); }
     const void *kc = rgb_dtype == GS_F32 ? (const void *)k_pre_count<GS_F32>
                      : rgb_dtype == GS_BF16 ? (const void *)k_pre_count<GS_BF16> : (const void *)k_pre_count<GS_F16>;
     if (gmax > 48 * 1024) cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gmax);
@@ -1697,11 +1775,11 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     const void *cov_splats = d_tile_limit ? nullptr : d_splats;
     uint32_t *Mv_used = d_tile_limit ? nullptr : Mv;
     if (rgb_dtype == GS_F32)
-        { k_pre_count<GS_F32><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, offs, Mc, Mv); count_launches(1); }
+        { k_pre_count<GS_F32><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, bnd, Mc, Mv); count_launches(1); }
     else if (rgb_dtype == GS_BF16)
-        { k_pre_count<GS_BF16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, offs, Mc, Mv); count_launches(1); }
+        { k_pre_count<GS_BF16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, bnd, Mc, Mv); count_launches(1); }
     else
-        { k_pre_count<GS_F16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, offs, Mc, Mv); count_launches(1); }
+        { k_pre_count<GS_F16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, bnd, Mc, Mv); count_launches(1); }
     {
         int nblk = 0;
         for (int v = 0; v < n_views; ++v) nblk += cdiv(tb.v[v].TX * tb.v[v].TY, 32);
@@ -1720,7 +1798,7 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
         }
         const size_t smem = sizeof(uint32_t) * ((size_t)p.Tmax + gmax1);
         if (smem > 48 * 1024) cudaFuncSetAttribute(k_pre_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        { k_pre_place<<<nchunks, kPlaceThreads, smem, st>>>(tb, N, p.Cv, p.Tmax, order, rect, offs, Mc, lastc, tstart,
+        { k_pre_place<<<nchunks, kPlaceThreads, smem, st>>>(tb, N, p.Cv, p.Tmax, order, rect, bnd, Mc, lastc, tstart,
                                                  tstart + T, capacity, d_vals, d_depth,
                                                  reinterpret_cast<unsigned long long *>(d_keys)); count_launches(1); }
     }
