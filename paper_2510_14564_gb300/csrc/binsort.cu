@@ -1187,6 +1187,7 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
 // their end, so images and gradients are those of the full lists.
 // ---------------------------------------------------------------------------
 constexpr int kPreChunks = 608;
+constexpr int kPreMinChunksPerView = 152;
 constexpr int kPreMaxTiles = 16384;               // cursor row of at most 64 KB
 constexpr float kCovScale = 4096.0f;              // fixed-point units of -ln(1 - alpha)
 constexpr uint32_t kCovTarget = 10u * 4096u;      // ln(1e4) = 9.21, plus margin
@@ -1218,23 +1219,52 @@ __device__ __forceinline__ uint32_t core_rect(const void *splats, uint32_t g, sh
 // Record bounds of every chunk of every view: bounds[v (Cv + 1) + k] = first
 // record of chunk k of view v, chunk k starting at instance fraction f(k/Cv)
 // of the view.  Placement work is in the part of the lists that is kept; with
-// per-tile limits (the previous step's processed counts) the kept share s of
-// instances is estimated as sum(2 limit + 64) / instances (an overestimate
+// per-tile limits (the previous step's processed counts) the kept share s of a
+// view's instances is estimated as sum(2 limit + 64) / instances (an overestimate
 // where lists are cut), and the first half of the chunks splits the first s
 // of the instances evenly, the second half the rest with quadratic growth
 // (starting small, so an underestimate costs little).  Without limits the chunks grow cubically
 // (fine at the front of the depth order, where lists are cut).  One CTA.
 constexpr int kBoundThreads = 1024;
-__global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(int n_views, int Cv, int N, int T,
-                                                                const unsigned long long *__restrict__ offs,
-                                                                const int32_t *__restrict__ limit,
-                                                                long long *__restrict__ bounds) {
+
+// First index j in [lo, hi) with a[j] >= key (hi if none), by one warp: 32
+// evenly spaced probes per round narrow the range 32-fold.
+__device__ __forceinline__ long long warp_lower_bound(const unsigned long long *a, long long lo, long long hi,
+                                                      unsigned long long key) {
+    const int l = threadIdx.x & 31;
+    while (hi > lo) {
+        const long long step = (hi - lo + 31) / 32;
+        const long long p = lo + l * step;
+        const bool pred = p >= hi || __ldg(a + p) >= key;       // monotone in the lane index
+        const unsigned bal = __ballot_sync(0xffffffffu, pred);
+        if (step == 1 || (bal & 1u)) {
+            // step 1: every position probed; lane 0 true: lo itself
+            return bal ? min(hi, lo + (long long)(__ffs(bal) - 1) * step) : hi;
+        }
+        const int f = bal ? __ffs(bal) - 1 : 32;                // a[lo + (f-1) step] < key <= a[lo + f step]
+        const long long nlo = lo + (long long)(f - 1) * step + 1;
+        const long long nhi = min(hi, lo + (long long)f * step);
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// Kept share of each view's instances estimated from the limits (the
+// previous step's processed counts): sum over the view's tiles of
+// 2 limit + 64, over the view's instances; one CTA per view.  -1 without
+// limits.
+__global__ void __launch_bounds__(kBoundThreads) k_view_share(TileBatch tb, int N,
+                                                              const unsigned long long *__restrict__ offs,
+                                                              const int32_t *__restrict__ limit,
+                                                              double *__restrict__ share) {
     __shared__ double s_part[kBoundThreads / 32];
-    __shared__ double s_share;
+    const int v = blockIdx.x;
+    const int Tv = tb.v[v].TX * tb.v[v].TY, tbase = tb.v[v].tile_base;
     double est = 0.0;
     if (limit)
-        for (int t = threadIdx.x; t < T; t += kBoundThreads) {
-            const int lm = __ldg(limit + t);
+        for (int t = threadIdx.x; t < Tv; t += kBoundThreads) {
+            const int lm = __ldg(limit + tbase + t);
             if (lm > 0) est += 2.0 * lm + 64.0;
         }
     est = warp_sum(est);
@@ -1243,33 +1273,41 @@ __global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(int n_views, int
     if (threadIdx.x == 0) {
         double sum = 0.0;
         for (int q = 0; q < kBoundThreads / 32; ++q) sum += s_part[q];
-        const double total = (double)offs[(long long)n_views * N];
-        s_share = (limit && total > 0.0) ? fmin(0.5, fmax(0.01, sum / total)) : -1.0;
+        const long long s0 = (long long)v * N;
+        const double total = (double)(offs[s0 + N] - offs[s0]);
+        share[v] = (limit && total > 0.0) ? fmin(0.5, fmax(0.01, sum / total)) : -1.0;
     }
-    __syncthreads();
-    const double share = s_share;
+}
+
+// One boundary per warp.
+__global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(int n_views, int Cv, int N,
+                                                                const unsigned long long *__restrict__ offs,
+                                                                const double *__restrict__ view_share,
+                                                                long long *__restrict__ bounds) {
+    const int j = blockIdx.x * (kBoundThreads / 32) + (threadIdx.x >> 5);
+    if (j >= n_views * (Cv + 1)) return;
+    const int v = j / (Cv + 1), k = j % (Cv + 1);
+    const double share = view_share[v];
     const int half = Cv / 2;
-    for (int j = threadIdx.x; j < n_views * (Cv + 1); j += kBoundThreads) {
-        const int v = j / (Cv + 1), k = j % (Cv + 1);
-        const long long s0 = (long long)v * N, s1 = s0 + N;
-        const unsigned long long i0 = offs[s0], span = offs[s1] - i0;
-        unsigned long long b;
-        if (k >= Cv) {
-            b = i0 + span;
-        } else if (share < 0.0 || half < 1) {
-            b = chunk_bound(i0, span, k, Cv, true);
+    const long long s0 = (long long)v * N, s1 = s0 + N;
+    const unsigned long long i0 = offs[s0], span = offs[s1] - i0;
+    unsigned long long b;
+    if (k >= Cv) {
+        b = i0 + span;
+    } else if (share < 0.0 || half < 1) {
+        b = chunk_bound(i0, span, k, Cv, true);
+    } else {
+        double f;
+        if (k <= half) {
+            f = share * (double)k / (double)half;
         } else {
-            double f;
-            if (k <= half) {
-                f = share * (double)k / (double)half;
-            } else {
-                const double y = (double)(k - half) / (double)(Cv - half);
-                f = share + (1.0 - share) * y * y;
-            }
-            b = i0 + (unsigned long long)((double)span * f);
+            const double y = (double)(k - half) / (double)(Cv - half);
+            f = share + (1.0 - share) * y * y;
         }
-        bounds[j] = lower_bound_u64(offs, s0, s1, b);
+        b = i0 + (unsigned long long)((double)span * f);
     }
+    const long long r = warp_lower_bound(offs, s0, s1, b);
+    if ((threadIdx.x & 31) == 0) bounds[j] = r;
 }
 
 // Per chunk: instance counts and the coverage bound per tile (2D difference
@@ -1610,7 +1648,7 @@ __global__ void k_range_counts(const uint2 *__restrict__ ranges, int T, uint32_t
 }
 
 struct PrePlan {
-    size_t dk0, dk1, dv0, dv1, cnt, offs, mc, mv, full, lastc, kept, tstart, bnd, hist, part, misc, bytes;
+    size_t dk0, dk1, dv0, dv1, cnt, offs, mc, mv, full, lastc, kept, tstart, bnd, vshare, hist, part, misc, bytes;
     int Cv, Tmax;
     bool ok;
 };
@@ -1623,6 +1661,7 @@ static PrePlan make_pre_plan(long long VN, const TileBatch &tb) {
     for (int v = 0; v < tb.n; ++v) p.Tmax = tb.v[v].TX * tb.v[v].TY > p.Tmax ? tb.v[v].TX * tb.v[v].TY : p.Tmax;
     p.ok = p.Tmax <= kPreMaxTiles;
     p.Cv = (kPreChunks + tb.n - 1) / tb.n;
+    if (p.Cv < kPreMinChunksPerView) p.Cv = kPreMinChunksPerView;   // several views: at least this many each
     p.dk0 = take(4 * VN); p.dk1 = take(4 * VN); p.dv0 = take(4 * VN); p.dv1 = take(4 * VN);
     p.cnt = take(4 * VN);
     p.offs = take(8 * (VN + 1));
@@ -1633,6 +1672,7 @@ static PrePlan make_pre_plan(long long VN, const TileBatch &tb) {
     p.kept = take(4 * (size_t)tb.total_tiles);
     p.tstart = take(8 * (size_t)(tb.total_tiles + 1));
     p.bnd = take(8 * (size_t)tb.n * (p.Cv + 1));
+    p.vshare = take(8 * (size_t)tb.n);
     long long nb = (VN + kSortTile - 1) / kSortTile;
     if (nb < 1) nb = 1;
     {
@@ -1766,7 +1806,9 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     }
     const int nchunks = n_views * p.Cv;
     long long *bnd = (long long *)(ws + p.bnd);
-    { k_chunk_bounds<<<1, kBoundThreads, 0, st>>>(n_views, p.Cv, N, T, offs, d_tile_limit, bnd); count_launches(1); }
+    double *vshare = (double *)(ws + p.vshare);
+    { k_view_share<<<n_views, kBoundThreads, 0, st>>>(tb, N, offs, d_tile_limit, vshare); count_launches(1); }
+    { k_chunk_bounds<<<cdiv(n_views * (p.Cv + 1), kBoundThreads / 32), kBoundThreads, 0, st>>>(n_views, p.Cv, N, offs, vshare, bnd); count_launches(1); }
     const void *kc = rgb_dtype == GS_F32 ? (const void *)k_pre_count<GS_F32>
                      : rgb_dtype == GS_BF16 ? (const void *)k_pre_count<GS_BF16> : (const void *)k_pre_count<GS_F16>;
     if (gmax > 48 * 1024) cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gmax);

@@ -245,6 +245,9 @@ class Frame:
         return self.dparams
 
     def l1(self, target: torch.Tensor) -> torch.Tensor:
+        if target.numel() != 3 * self.P or target.dtype != torch.float32 or not target.is_cuda:
+            raise ValueError(f"L1 target must be a float32 CUDA tensor of 3 x {self.P} values "
+                             f"(every view's pixels), got {tuple(target.shape)} {target.dtype}")
         L.gs_l1_loss(3 * self.P, self.img, target, self.loss, self.dimg)
         return self.loss
 
@@ -297,6 +300,9 @@ class Trainer:
             self.sh_shadow = None
         self.frame = Frame(cams, N, rgb_dtype=rgb_dtype, sh_dtype=sh_storage, schedule=schedule,
                            device=params_flat.device, prefix=prefix)
+        if targets.numel() != 3 * self.frame.P:
+            raise ValueError(f"targets must hold 3 x {self.frame.P} values (every view's pixels, "
+                             f"view after view), got {targets.numel()}")
         self.targets = targets
 
     def params_for_kernels(self) -> dict:

@@ -149,3 +149,17 @@ def test_bf16_training_step_updates_master_and_shadow():
     assert torch.equal(a.sh_shadow.view(-1), sh_a.to(torch.bfloat16))
     moved = (a.p - torch.from_numpy(scene.flat()).cuda()).abs()
     assert moved.max() > 0
+
+
+def test_target_of_the_wrong_size_is_refused():
+    """The L1 target covers every view's pixels; a target for one view of a
+    two-view batch is refused on the host, before the L1 kernel runs."""
+    scene = S.uniform_scene(500, 1)
+    cams = S.ring_cameras(2, [(64, 48), (48, 32)])
+    one_view = torch.zeros(3 * 64 * 48, device="cuda")
+    with pytest.raises(ValueError):
+        P.Trainer(cams, P.to_device_params(scene), scene.n, one_view)
+    both = torch.zeros(3 * (64 * 48 + 48 * 32), device="cuda")
+    tr = P.Trainer(cams, P.to_device_params(scene), scene.n, both)
+    with pytest.raises(ValueError):
+        tr.step(targets=one_view)
