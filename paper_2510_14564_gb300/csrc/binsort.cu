@@ -1603,7 +1603,10 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
             n_keep += tot;
         }
         __syncthreads();
-        // 2. each warp places the kept records' tiles in its own rows, in order
+        // 2. each warp places the kept records' tiles in its own rows, in order.
+        //    The (record, tile) pairs of 32 records are flattened record by
+        //    record and handled 32 at a time: pairs on the same tile get slots
+        //    in lane order, which is record order.
         for (int j0 = 0; j0 < n_keep; j0 += 32) {
             const int j = j0 + l;
             uint32_t gj = 0;
@@ -1611,29 +1614,44 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
             if (j < n_keep) { gj = s_g[j]; r = s_rc[j]; }
             const int y0w = r.y + ((w - r.y) % kPlaceWarps + kPlaceWarps) % kPlaceWarps;
             const int hw = r.w > y0w ? (r.w - y0w + kPlaceWarps - 1) / kPlaceWarps : 0;
-            const int cnt = (r.z - r.x) * hw;
-            unsigned has = __ballot_sync(0xffffffffu, cnt > 0);
-            while (has) {
-                const int o = __ffs(has) - 1;
-                has &= has - 1;
-                const int x0 = __shfl_sync(0xffffffffu, (int)r.x, o);
-                const int yw = __shfl_sync(0xffffffffu, y0w, o);
-                const int wd = __shfl_sync(0xffffffffu, (int)(r.z - r.x), o);
-                const int c = __shfl_sync(0xffffffffu, cnt, o);
+            const int wd = r.z - r.x;
+            const int cnt = wd > 0 ? wd * hw : 0;
+            int inc = cnt;                                      // inclusive scan of the counts
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (l >= o) inc += t;
+            }
+            const int total = __shfl_sync(0xffffffffu, inc, 31);
+            const int excl = inc - cnt;
+            for (int q0 = 0; q0 < total; q0 += 32) {
+                const int pidx = q0 + l;
+                int k = 0;                                      // lanes whose pairs all precede pidx
+#pragma unroll
+                for (int sh = 16; sh > 0; sh >>= 1)
+                    if (__shfl_sync(0xffffffffu, inc, k + sh - 1) <= pidx) k += sh;
+                const int o = k < 31 ? k : 31;                  // the record owning pair pidx
+                const int ox = __shfl_sync(0xffffffffu, (int)r.x, o);
+                const int oyw = __shfl_sync(0xffffffffu, y0w, o);
+                const int owd = __shfl_sync(0xffffffffu, wd, o);
+                const int oex = __shfl_sync(0xffffffffu, excl, o);
                 const uint32_t gid = __shfl_sync(0xffffffffu, gj, o);
-                const float rw = 1.0f / (float)wd;
-                for (int q = l; q < c; q += 32) {
-                    int rr = (int)((float)q * rw);
-                    rr += (rr + 1) * wd <= q;
-                    rr -= rr * wd > q;
-                    const int t = (yw + kPlaceWarps * rr) * TX + x0 + (q - rr * wd);
-                    const uint32_t pos = s_cur[t];
-                    if (pos != 0xffffffffu) {
-                        s_cur[t] = pos + 1;
-                        vals[pos] = gid;
-                        if (keys)
-                            keys[pos] = ((unsigned long long)(tbase + t) << 32) | __float_as_uint(__ldg(depth + gid));
-                    }
+                const bool valid = pidx < total;
+                int t = -1;
+                uint32_t cur = 0xffffffffu;
+                if (valid) {
+                    const int loc = pidx - oex;
+                    const int rr = loc / owd;
+                    t = (oyw + kPlaceWarps * rr) * TX + ox + (loc - rr * owd);
+                    cur = s_cur[t];
+                }
+                const bool act = cur != 0xffffffffu;
+                const unsigned peers = __match_any_sync(0xffffffffu, act ? t : -1);
+                if (act) {
+                    const uint32_t pos = cur + __popc(peers & lanemask_lt());
+                    vals[pos] = gid;
+                    if (keys) keys[pos] = ((unsigned long long)(tbase + t) << 32) | __float_as_uint(__ldg(depth + gid));
+                    if ((peers >> l) == 1u) s_cur[t] = cur + __popc(peers);   // the last pair on this tile
                 }
                 __syncwarp();
             }
