@@ -1111,10 +1111,8 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
         const int nchunks = n_views * p.Cv;
         const int p1_blocks = cdiv(nchunks, kP1Warps);
         const size_t p1_smem = sizeof(uint32_t) * (size_t)(p.TYmax + 1) * kP1Warps;
-        if (p1_smem > 48 * 1024) {
-            cudaFuncSetAttribute(k_p1_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem);
-            cudaFuncSetAttribute(k_p1_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem);
-        }
+        allow_dynamic_smem((const void *)k_p1_count, p1_smem);
+        allow_dynamic_smem((const void *)k_p1_place, p1_smem);
         { k_p1_count<<<p1_blocks, 32 * kP1Warps, p1_smem, st>>>(tb, N, p.Cv, p.TYmax, order, rect, offs, M1); count_launches(1); }
         exclusive_scan<uint32_t, unsigned long long>(M1, O1, p.m1n, (unsigned long long *)part, O1 + p.m1n, st);
         { k_finish_count<<<1, 1, 0, st>>>(O1 + p.m1n, capacity, d_n_instances, count, d_err_word); count_launches(1); }
@@ -1829,7 +1827,7 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     { k_chunk_bounds<<<cdiv(n_views * (p.Cv + 1), kBoundThreads / 32), kBoundThreads, 0, st>>>(n_views, p.Cv, N, offs, vshare, bnd); count_launches(1); }
     const void *kc = rgb_dtype == GS_F32 ? (const void *)k_pre_count<GS_F32>
                      : rgb_dtype == GS_BF16 ? (const void *)k_pre_count<GS_BF16> : (const void *)k_pre_count<GS_F16>;
-    if (gmax > 48 * 1024) cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gmax);
+    allow_dynamic_smem(kc, gmax);
     const short4 *rect = reinterpret_cast<const short4 *>(d_rect);
     // the coverage bound needs no history; with per-tile limits it is not computed
     const void *cov_splats = d_tile_limit ? nullptr : d_splats;
@@ -1857,7 +1855,7 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
             gmax1 = g > gmax1 ? g : gmax1;
         }
         const size_t smem = sizeof(uint32_t) * ((size_t)p.Tmax + gmax1);
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k_pre_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_dynamic_smem((const void *)k_pre_place, smem);      // 25 KB of its own static arrays
         { k_pre_place<<<nchunks, kPlaceThreads, smem, st>>>(tb, N, p.Cv, p.Tmax, order, rect, bnd, Mc, lastc, tstart,
                                                  tstart + T, capacity, d_vals, d_depth,
                                                  reinterpret_cast<unsigned long long *>(d_keys)); count_launches(1); }

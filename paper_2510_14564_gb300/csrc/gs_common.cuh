@@ -147,6 +147,16 @@ __device__ __forceinline__ void set_err(int *ew, unsigned bits) {
 // Host-side count of kernel launches issued by the library (gs_launch_count).
 void count_launches(int n);
 
+// Allow `dyn` bytes of dynamic shared memory for `kernel`: above 48 KB of
+// static + dynamic shared memory a launch needs the opt-in attribute, which is
+// set to the dynamic size the launch will ask for.
+inline void allow_dynamic_smem(const void *kernel, size_t dyn) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;   // the launch reports the error
+    if (fa.sharedSizeBytes + dyn > 48 * 1024)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
 inline int launch_status() {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;

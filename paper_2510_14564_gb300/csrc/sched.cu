@@ -406,7 +406,7 @@ extern "C" int gs_sched_order(const float *d_cost, int n, int32_t *d_order, void
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (n <= kSmallOrder) {
         const size_t smem = sizeof(uint32_t) * (5 * (size_t)kSmallOrder + 32 * 256);
-        cudaFuncSetAttribute(k_order_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_dynamic_smem((const void *)k_order_small, smem);
         { k_order_small<<<1, kOrderThreads, smem, st>>>(d_cost, n, d_order); count_launches(1); }
         return launch_status();
     }

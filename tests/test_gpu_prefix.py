@@ -19,6 +19,9 @@ pytestmark = pytest.mark.gpu
 CASES = {
     "uniform-10k-256x256": lambda: (S.uniform_scene(10_000, 0), [S.front_camera(256, 256)]),
     "skewed-200k-640x480": lambda: (S.skewed_scene(200_000, 0), [S.front_camera(640, 480)]),
+    # 3600 tiles: the placement's shared memory (static + per-tile arrays) is
+    # above 48 KB while its dynamic part alone is below
+    "skewed-60k-1280x720": lambda: (S.skewed_scene(60_000, 1), [S.front_camera(1280, 720)]),
     "skewed-60k-3views": lambda: (S.skewed_scene(60_000, 3),
                                   S.ring_cameras(3, [(320, 240), (200, 300), (256, 256)])),
 }
