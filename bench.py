@@ -371,7 +371,10 @@ def schedule_diagnostics(f, L, torch, reps=5) -> dict:
                         f.tile_nproc, None, f.err)
 
     def bwd(o):
-        L.gs_render_bwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, sch(o), f.dimg, f.T_final, f.n_proc,
+        s = sch(o)
+        if s is not None:
+            s["split"] = f.split
+        L.gs_render_bwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, s, f.dimg, f.T_final, f.n_proc,
                         f.tile_nproc, f.grad2d, f.err)
 
     out = {"fwd_ms": {"raster": best(lambda: fwd(None)), "count": best(lambda: fwd(o_count)),

@@ -225,6 +225,9 @@ typedef struct {
     int *d_queue;
     long long budget_ns;
     const int32_t *d_n_order;  /* device count of tiles in d_order; NULL = all T tiles */
+    int32_t *d_split;          /* gs_render_bwd only: one device int of scratch; non-NULL lets the
+                                  heaviest head-of-order tiles be taken in four strips (images and
+                                  gradients are unchanged up to the order of additions) */
 } gs_schedule;
 
 /* a3. Forward blending (Sec. II-A blending equation), one CTA per 16x16 tile.
@@ -345,6 +348,18 @@ int gs_mlp_grad(const float *d_w32, const float *d_feats, const uint64_t *d_tile
 int gs_mlp_train_step(float *d_w32, void *d_w16, float *d_m, float *d_v, int t, float lr,
                       const float *d_feats, const uint64_t *d_tile_ns, const float *d_target, int n,
                       float *d_grad, float *d_loss, gs_stream_t stream);
+
+/* a8, the count order as judge of the learned one (Sec. IV: tile cost drives
+ * the balanced partition).  Over n_pairs seeded pairs of tiles (i, j), drawn
+ * by a counter-based 32-bit mix of seed and the pair index, skipping pairs
+ * where a tile time is 0 (empty tile) or both times are equal, d_out[0]
+ * gains 2 when d_a orders the pair as d_tile_ns does, 1 when d_a ties, 0
+ * otherwise; d_out[1] the same for d_b[i * b_stride] (e.g. the instance-
+ * count feature in the [T, 8] feature array, b_stride 8).  d_out is
+ * 2 x uint64 on the device, ADDED to (zero it first).  Integer results:
+ * exact. */
+int gs_rank_judge(const float *d_a, const float *d_b, int b_stride, const uint64_t *d_tile_ns, int n,
+                  int n_pairs, uint32_t seed, unsigned long long *d_out, gs_stream_t stream);
 
 /* d_cost[i] = (float) d_counts[i] for n entries. */
 int gs_int_cost(const int32_t *d_counts, int n, float *d_cost, gs_stream_t stream);

@@ -28,7 +28,8 @@ EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_project", "gs_bin
            "gs_bin_sort_prefix_workspace", "gs_bin_sort_prefix", "gs_bin_sort_prefix_repair",
            "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_project_bwd", "gs_project_bwd_adam", "gs_adam_step",
            "gs_adam_flat", "gs_tile_features", "gs_mlp_predict", "gs_mlp_grad",
-           "gs_mlp_train_step", "gs_int_cost", "gs_range_cost", "gs_sched_order_workspace", "gs_sched_order"]
+           "gs_mlp_train_step", "gs_rank_judge", "gs_int_cost", "gs_range_cost", "gs_sched_order_workspace",
+           "gs_sched_order"]
 
 
 class GsError(RuntimeError):
@@ -47,7 +48,7 @@ class GsCamera(ctypes.Structure):
 class GsSchedule(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("d_order", ctypes.c_void_p),
                 ("d_queue", ctypes.c_void_p), ("budget_ns", ctypes.c_longlong),
-                ("d_n_order", ctypes.c_void_p)]
+                ("d_n_order", ctypes.c_void_p), ("d_split", ctypes.c_void_p)]
 
 
 _lib = None
@@ -95,6 +96,7 @@ def lib():
         L.gs_mlp_predict.argtypes = [VP, VP, I32, VP, VP]
         L.gs_mlp_grad.argtypes = [VP, VP, VP, VP, I32, VP, VP, VP]
         L.gs_mlp_train_step.argtypes = [VP, VP, VP, VP, I32, F32, VP, VP, VP, I32, VP, VP, VP]
+        L.gs_rank_judge.argtypes = [VP, VP, I32, VP, I32, I32, ctypes.c_uint32, VP, VP]
         L.gs_int_cost.argtypes = [VP, I32, VP, VP]
         L.gs_range_cost.argtypes = [VP, I32, VP, VP]
         L.gs_sched_order_workspace.argtypes = [I32, P(SZ)]
@@ -233,6 +235,7 @@ def _sched(sched):
     s.d_queue = ptr(sched.get("queue"))
     s.budget_ns = int(sched.get("budget_ns", 0))
     s.d_n_order = ptr(sched.get("n_order"))
+    s.d_split = ptr(sched.get("split"))
     return ctypes.byref(s), s
 
 
@@ -315,6 +318,11 @@ def gs_mlp_train_step(w32, w16, m, v, t, lr, feats, tile_ns, target, n, grad, lo
     check(lib().gs_mlp_train_step(ptr(w32), ptr(w16), ptr(m), ptr(v), int(t), float(lr), ptr(feats),
                                   ptr(tile_ns), ptr(target), int(n), ptr(grad), ptr(loss),
                                   stream_ptr(stream)), "gs_mlp_train_step")
+
+
+def gs_rank_judge(a, b, b_stride, tile_ns, n, n_pairs, seed, out, stream=None):
+    check(lib().gs_rank_judge(ptr(a), ptr(b), int(b_stride), ptr(tile_ns), int(n), int(n_pairs),
+                              int(seed) & 0xFFFFFFFF, ptr(out), stream_ptr(stream)), "gs_rank_judge")
 
 
 def gs_int_cost(counts, n, cost, stream=None):

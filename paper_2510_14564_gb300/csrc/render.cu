@@ -4,7 +4,11 @@
 // sorted Gaussians of a pixel, one 16x16 pixel block per CTA (Sec. IV-C1).
 // The forward pass takes one pixel per thread (256 threads); the reverse
 // pass four vertically adjacent pixels per thread (64 threads, each warp a
-// 16x8 block), which divides its warp reductions and atomics per pixel by 4.  Per
+// 16x8 block), which divides its warp reductions and atomics per pixel by 4;
+// with a work order, the tiles heavier than a CTA's share of the work, taken
+// from the head of the order (the costliest), are split into four 16x4 strips
+// of one pixel per thread, so that a heavy tile does not hold one CTA for four
+// times as long.  Per
 // batch of 256 list entries the threads stage the splat records into shared
 // memory (the per-tile batch loading of Sec. V-C, with each record's geometry
 // and colour contiguous), then every pixel walks the batch.
@@ -74,8 +78,11 @@ struct TileCtx {
     float x0, y0;
 };
 
+// part < 0: the whole tile, PPT vertically adjacent pixels per thread;
+// part k >= 0: strip k of PPT strips of rows, one pixel per thread.
 template <int PPT>
-__device__ __forceinline__ TileCtx<PPT> tile_ctx(const TileBatch &tb, const uint2 *ranges, int tile) {
+__device__ __forceinline__ TileCtx<PPT> tile_ctx(const TileBatch &tb, const uint2 *ranges, int tile,
+                                                 int part = -1) {
     TileCtx<PPT> c;
     c.tile = tile;
     c.view = view_of_tile(tb, tile);
@@ -83,9 +90,16 @@ __device__ __forceinline__ TileCtx<PPT> tile_ctx(const TileBatch &tb, const uint
     int lt = tile - vt.tile_base;
     int tx = lt % vt.TX, ty = lt / vt.TX;
     c.px = tx * kTile + (threadIdx.x & (kTile - 1));
-    c.py = ty * kTile + PPT * (threadIdx.x / kTile);
+    if (part < 0) {
+        c.py = ty * kTile + PPT * (threadIdx.x / kTile);
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) c.in[p] = c.px < vt.W && c.py + p < vt.H;
+        for (int p = 0; p < PPT; ++p) c.in[p] = c.px < vt.W && c.py + p < vt.H;
+    } else {
+        c.py = ty * kTile + part * (kTile / PPT) + (int)(threadIdx.x / kTile);
+        c.in[0] = c.px < vt.W && c.py < vt.H;
+#pragma unroll
+        for (int p = 1; p < PPT; ++p) c.in[p] = false;
+    }
     c.range = __ldg(ranges + tile);
     c.x0 = (float)(tx * kTile);
     c.y0 = (float)(ty * kTile);
@@ -98,6 +112,7 @@ struct SchedArgs {
     int *queue;
     long long budget_ns;
     const int *n_order;    // device count of tiles in order (null: all tiles)
+    const int *split_head; // reverse pass: device count of head-of-order tiles taken in strips (null: none)
 };
 
 // Fetch the next tile for this CTA; -1 when the queue is exhausted.
@@ -119,6 +134,40 @@ __device__ __forceinline__ int next_tile(const SchedArgs &sa, int total_tiles, i
     }
     __syncthreads();
     int t = *s_tile;
+    __syncthreads();
+    return t;
+}
+
+// Next work item of the reverse pass: a tile and a part (-1: the whole tile;
+// 0..K-1: one of K strips of rows, one pixel per thread).  The first
+// split_head tiles of the order -- the costliest -- are taken as K strips
+// each, so that no single tile keeps one CTA busy for long.  -1 when done.
+template <int K>
+__device__ __forceinline__ int next_item(const SchedArgs &sa, int total_tiles, int *s_tile, int *s_part,
+                                         unsigned long long t_start, int *err_word, int iter, int &part) {
+    part = -1;
+    if (sa.mode == GS_SCHED_RASTER) return iter == 0 ? (int)blockIdx.x : -1;
+    if (threadIdx.x == 0) {
+        int t = -1, pt = -1;
+        if (sa.budget_ns > 0 && iter > 0 &&
+            (long long)(globaltimer() - t_start) > sa.budget_ns) {
+            set_err(err_word, GS_EW_TIMEOUT);
+        } else {
+            const int q = atomicAdd(sa.queue, 1);
+            const int bound = sa.n_order ? min(*sa.n_order, total_tiles) : total_tiles;
+            const int H = (K > 1 && sa.split_head) ? min(*sa.split_head, bound) : 0;
+            int pos;
+            if (q < K * H) { pos = q / K; pt = q % K; }
+            else pos = q - (K - 1) * H;
+            t = pos < bound ? __ldg(sa.order + pos) : -1;
+            if (t >= total_tiles || t < -1) { set_err(err_word, GS_EW_BOUNDS); t = -1; }
+        }
+        *s_tile = t;
+        *s_part = pt;
+    }
+    __syncthreads();
+    const int t = *s_tile;
+    part = *s_part;
     __syncthreads();
     return t;
 }
@@ -300,7 +349,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_render_fwd(TileBatch tb, con
 }
 
 template <int DT, int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 8) k_render_bwd(
+__global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 8) k_render_bwd(
     TileBatch tb, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
     const void *__restrict__ splats, SchedArgs sa, const float *__restrict__ dimg,
     const float *__restrict__ T_final, const int *__restrict__ n_proc, const int *__restrict__ tile_nproc,
@@ -308,12 +357,13 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 8) k_render_bwd
     constexpr int NT = kTilePix / PPT;
     __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch];
     __shared__ int s_warp[PPT * NT / 32];
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_part;
     const unsigned long long t_start = globaltimer();
     for (int iter = 0;; ++iter) {
-        const int tile = next_tile(sa, tb.total_tiles, &s_tile, t_start, err_word, iter);
+        int part;
+        const int tile = next_item<PPT>(sa, tb.total_tiles, &s_tile, &s_part, t_start, err_word, iter, part);
         if (tile < 0) break;
-        const TileCtx<PPT> c = tile_ctx<PPT>(tb, ranges, tile);
+        const TileCtx<PPT> c = tile_ctx<PPT>(tb, ranges, tile, part);
         const ViewTiles &vt = tb.v[c.view];
         const float pcx = (float)c.px + 0.5f;
         float pcy[PPT], T[PPT], G0[PPT], G1[PPT], G2[PPT], bgdot[PPT], R0[PPT], R1[PPT], R2[PPT];
@@ -418,6 +468,39 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 2 ? 6 : 8) k_render_bwd
     }
 }
 
+// Tiles of the reverse pass worth splitting: those whose processed count
+// exceeds the mean load of a CTA (the sum of all tiles' counts over the
+// number of CTAs): one CTA would stay busy with such a tile after the others
+// ran out of work.  One CTA; writes the count to *split_head.
+__global__ void __launch_bounds__(1024) k_split_head(const int *__restrict__ tile_nproc, int T, int n_cta,
+                                                     int cap, int *__restrict__ split_head) {
+    __shared__ long long s_sum[32];
+    __shared__ int s_cnt[32];
+    __shared__ long long s_total;
+    long long sum = 0;
+    for (int t = threadIdx.x; t < T; t += 1024) sum += max(0, __ldg(tile_nproc + t));
+    sum = warp_sum(sum);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tot = 0;
+        for (int q = 0; q < 32; ++q) tot += s_sum[q];
+        s_total = tot;
+    }
+    __syncthreads();
+    const long long per_cta = s_total / max(1, n_cta);
+    int cnt = 0;
+    for (int t = threadIdx.x; t < T; t += 1024) cnt += (long long)__ldg(tile_nproc + t) > per_cta;
+    cnt = warp_sum(cnt);
+    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int q = 0; q < 32; ++q) c += s_cnt[q];
+        *split_head = min(c, cap);
+    }
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -429,6 +512,7 @@ static int fill_sched(const gs_schedule *sched, const TileBatch &tb, SchedArgs *
     sa->queue = nullptr;
     sa->budget_ns = 0;
     sa->n_order = nullptr;
+    sa->split_head = nullptr;
     *grid = tb.total_tiles;
     if (!sched || sched->mode == GS_SCHED_RASTER) return GS_OK;
     if (sched->mode != GS_SCHED_ORDER || !sched->d_order || !sched->d_queue) return GS_ERR_ARG;
@@ -502,6 +586,12 @@ extern "C" int gs_render_bwd(const gs_camera *cams, int n_views, const uint32_t 
     int rc = fill_sched(sched, tb, &sa, &grid, st, kern, kTilePix / kBwdPPT, 0);
     if (rc != GS_OK) return rc;
     if (grid < 1) return GS_OK;
+    if (sa.mode == GS_SCHED_ORDER && sched->d_split) {
+        // as many head-of-order tiles as there are tiles heavier than a CTA's
+        // share of the work are taken in strips (the order puts the costliest first)
+        { k_split_head<<<1, 1024, 0, st>>>(d_tile_nproc, tb.total_tiles, grid, grid, sched->d_split); count_launches(1); }
+        sa.split_head = sched->d_split;
+    }
     const uint2 *rg = reinterpret_cast<const uint2 *>(d_tile_ranges);
     if (rgb_dtype == GS_F32)
         { k_render_bwd<GS_F32, kBwdPPT><<<grid, kTilePix / kBwdPPT, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_dimg, d_T_final, d_n_proc, d_tile_nproc, d_grad2d, d_err_word); count_launches(1); }

@@ -302,6 +302,46 @@ __global__ void __launch_bounds__(kOrderThreads) k_order_small(const float *__re
     for (int i = threadIdx.x; i < n; i += kOrderThreads) order[i] = (int32_t)va[i];
 }
 
+// Seeded pair of tiles k of a judge round (counter-based: a 32-bit mix of the
+// seed and the pair index).
+__device__ __forceinline__ uint32_t judge_mix(uint32_t x) {
+    x ^= x >> 16; x *= 0x85EBCA6Bu;
+    x ^= x >> 13; x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x;
+}
+
+// Agreement of two tile scores with the measured tile times over seeded
+// pairs of live tiles: +2 for a pair ordered as the times are, +1 for tied
+// scores, 0 otherwise.
+__global__ void __launch_bounds__(256) k_rank_judge(const float *__restrict__ a, const float *__restrict__ b,
+                                                    int b_stride, const unsigned long long *__restrict__ ns, int n,
+                                                    int n_pairs, uint32_t seed,
+                                                    unsigned long long *__restrict__ out) {
+    __shared__ unsigned long long s_a[8], s_b[8];
+    unsigned long long ca = 0, cb = 0;
+    for (int k = blockIdx.x * 256 + threadIdx.x; k < n_pairs; k += gridDim.x * 256) {
+        const int i = (int)(judge_mix(seed ^ (2u * (uint32_t)k) * 0x9E3779B9u) % (uint32_t)n);
+        const int j = (int)(judge_mix(seed ^ (2u * (uint32_t)k + 1u) * 0x9E3779B9u) % (uint32_t)n);
+        const unsigned long long ti = ns[i], tj = ns[j];
+        if (ti == 0 || tj == 0 || ti == tj) continue;
+        const bool up = ti > tj;
+        const float ai = a[i], aj = a[j], bi = b[(long long)i * b_stride], bj = b[(long long)j * b_stride];
+        ca += ai == aj ? 1u : ((ai > aj) == up ? 2u : 0u);
+        cb += bi == bj ? 1u : ((bi > bj) == up ? 2u : 0u);
+    }
+    ca = warp_sum(ca);
+    cb = warp_sum(cb);
+    if ((threadIdx.x & 31) == 0) { s_a[threadIdx.x >> 5] = ca; s_b[threadIdx.x >> 5] = cb; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long ta = 0, tb = 0;
+        for (int w = 0; w < 8; ++w) { ta += s_a[w]; tb += s_b[w]; }
+        atomicAdd(out, ta);
+        atomicAdd(out + 1, tb);
+    }
+}
+
 __global__ void k_range_cost(const uint2 *__restrict__ r, int n, float *__restrict__ cost) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) { uint2 v = r[i]; cost[i] = (float)(v.y - v.x); }
@@ -415,5 +455,17 @@ extern "C" int gs_sched_order(const float *d_cost, int n, int32_t *d_order, void
     uint32_t *k0 = (uint32_t *)ws, *v0 = (uint32_t *)(ws + al);
     { k_cost_keys<<<cdiv(n, 256), 256, 0, st>>>(d_cost, n, k0, v0); count_launches(1); }
     radix_sort_pairs(k0, v0, reinterpret_cast<uint32_t *>(d_order), n, 32, ws + 2 * al, st);
+    return launch_status();
+}
+
+extern "C" int gs_rank_judge(const float *d_a, const float *d_b, int b_stride, const uint64_t *d_tile_ns, int n,
+                             int n_pairs, uint32_t seed, unsigned long long *d_out, gs_stream_t stream) {
+    if (n < 0 || n_pairs < 0 || b_stride < 1 || !d_out) return GS_ERR_ARG;
+    if (n == 0 || n_pairs == 0) return GS_OK;
+    if (!d_a || !d_b || !d_tile_ns) return GS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int grid = min(cdiv(n_pairs, 256), 256);
+    { k_rank_judge<<<grid, 256, 0, st>>>(d_a, d_b, b_stride, reinterpret_cast<const unsigned long long *>(d_tile_ns), n,
+                                         n_pairs, seed, d_out); count_launches(1); }
     return launch_status();
 }

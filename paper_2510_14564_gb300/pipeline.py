@@ -59,6 +59,11 @@ class Schedule:
     train_every: int = 4
     bwd_order: str = "forward"
     seed: int = 0
+    # learned mode: the count order judges the learned one (on seeded pairs of
+    # tiles, which score orders them as their measured times do more often)
+    # and is used until the MLP wins; False leaves the choice to the caller
+    judge: bool = True
+    judge_pairs: int = 65536
 
 
 class Frame:
@@ -111,6 +116,7 @@ class Frame:
             self.reserve(capacity)
         # scheduler state
         self.queue = torch.zeros(1, dtype=torch.int32, device=d)
+        self.split = torch.zeros(1, dtype=torch.int32, device=d)   # heavy tiles the reverse pass splits
         self.feats = torch.zeros(self.T * 8, dtype=torch.float32, device=d)
         self.cost = torch.zeros(self.T, dtype=torch.float32, device=d)
         self.order_f = torch.arange(self.T, dtype=torch.int32, device=d)
@@ -130,7 +136,11 @@ class Frame:
         self.mlp_loss = torch.zeros(1, dtype=torch.float32, device=d)
         self.mlp_t = 0
         self.pred = torch.zeros(self.T, dtype=torch.float32, device=d)
-        self.use_learned = self.sched.mode == "learned"
+        self.use_learned = self.sched.mode == "learned" and not self.sched.judge
+        self.judge = torch.zeros(2, dtype=torch.int64, device=self.dev)
+        self.judge_host = torch.zeros(2, dtype=torch.int64).pin_memory()
+        self.judge_event = None
+        self.judge_rounds = 0
         self.step_count = 0
 
     # -- buffers -----------------------------------------------------------
@@ -196,10 +206,10 @@ class Frame:
         if self.sched.mode == "raster":
             return None
         if self.sched.bwd_order == "forward":
-            return {"mode": L.GS_SCHED_ORDER, "order": self.order_f, "queue": self.queue}
+            return {"mode": L.GS_SCHED_ORDER, "order": self.order_f, "queue": self.queue, "split": self.split}
         L.gs_int_cost(self.tile_nproc, self.T, self.cost)
         L.gs_sched_order(self.cost, self.T, self.order_b, self.order_ws)
-        return {"mode": L.GS_SCHED_ORDER, "order": self.order_b, "queue": self.queue}
+        return {"mode": L.GS_SCHED_ORDER, "order": self.order_b, "queue": self.queue, "split": self.split}
 
     def render(self, timing: bool = False, mark=None) -> None:
         s = self._sched_fwd()
@@ -260,9 +270,28 @@ class Frame:
         if not self.use_learned:
             L.gs_tile_features(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype,
                                self.sched.feature_cap, self.feats, self.mlp_w16, self.pred)
+        if self.sched.judge:
+            self._judge()
         L.gs_mlp_train_step(self.mlp_w32, self.mlp_w16, self.mlp_m, self.mlp_v, self.mlp_t,
                             self.sched.mlp_lr, self.feats, self.tile_ns, None, self.T, self.mlp_g,
                             self.mlp_loss)
+
+    def _judge(self) -> None:
+        """Score the MLP's prediction and the instance count against the tile
+        times just measured; the verdict of the previous round, read without
+        waiting (pinned copy + event), picks the order."""
+        if self.judge_event is not None and self.judge_event.query():
+            learned, count = self.judge_host.tolist()
+            self.use_learned = learned > count
+            self.judge_event = None
+        if self.judge_event is None:
+            self.judge.zero_()
+            L.gs_rank_judge(self.pred, self.feats, 8, self.tile_ns, self.T, self.sched.judge_pairs,
+                            self.sched.seed * 7919 + self.judge_rounds, self.judge)
+            self.judge_rounds += 1
+            self.judge_host.copy_(self.judge, non_blocking=True)
+            self.judge_event = torch.cuda.Event()
+            self.judge_event.record()
 
     def check_errors(self) -> int:
         return int(self.err.item())

@@ -98,7 +98,7 @@ def test_images_identical_across_schedules(mode):
     cams = S.ring_cameras(4, S.uneven_sizes(4, (200, 150), (320, 240)))
     ref, views = _frame(scene, cams, P.Schedule("raster"))
     ref.render()
-    fr, _ = _frame(scene, cams, P.Schedule(mode))
+    fr, _ = _frame(scene, cams, P.Schedule(mode, judge=False))      # the learned order itself
     fr.render(timing=True)
     torch.cuda.synchronize()
     assert torch.equal(ref.img, fr.img)
@@ -171,3 +171,48 @@ def test_learned_cost_model_gain():
     print(f"render makespan (ms): raster {t['raster']:.3f}, count order {t['count']:.3f}, "
           f"learned order {t['learned']:.3f}; order cost: count {t_order_count:.3f}, "
           f"learned {t_order_learned:.3f}")
+
+
+def _mix(x):
+    x &= 0xFFFFFFFF
+    x ^= x >> 16
+    x = (x * 0x85EBCA6B) & 0xFFFFFFFF
+    x ^= x >> 13
+    x = (x * 0xC2B2AE35) & 0xFFFFFFFF
+    x ^= x >> 16
+    return x
+
+
+def test_rank_judge_counts_exactly():
+    """gs_rank_judge against the same seeded pairs counted in Python: +2 for a
+    pair ordered as the times are, +1 for tied scores; pairs with an empty
+    tile or equal times are skipped.  A score equal to the times earns 2 per
+    counted pair, its negation 0."""
+    rng = np.random.default_rng(11)
+    n, pairs, seed = 777, 20000, 12345
+    ns = rng.integers(0, 50, n).astype(np.uint64)             # zeros (empty tiles) and ties
+    a = rng.normal(size=n).astype(np.float32)
+    b = np.zeros((n, 8), np.float32)
+    b[:, 0] = rng.integers(0, 5, n)                           # many ties
+    exp = [0, 0]
+    counted = 0
+    for k in range(pairs):
+        i = _mix(seed ^ ((2 * k * 0x9E3779B9) & 0xFFFFFFFF)) % n
+        j = _mix(seed ^ (((2 * k + 1) * 0x9E3779B9) & 0xFFFFFFFF)) % n
+        ti, tj = int(ns[i]), int(ns[j])
+        if ti == 0 or tj == 0 or ti == tj:
+            continue
+        counted += 1
+        for q, (si, sj) in enumerate(((a[i], a[j]), (b[i, 0], b[j, 0]))):
+            exp[q] += 1 if si == sj else (2 if (si > sj) == (ti > tj) else 0)
+    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    d_ns = torch.from_numpy(ns.view(np.int64)).cuda()
+    L.gs_rank_judge(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), 8, d_ns, n, pairs, seed, out)
+    torch.cuda.synchronize()
+    assert out.cpu().tolist() == exp
+    same = torch.from_numpy(ns.astype(np.float32)).cuda()
+    out.zero_()
+    L.gs_rank_judge(same, -same, 1, d_ns, n, pairs, seed, out)
+    torch.cuda.synchronize()
+    assert counted > pairs // 2
+    assert out.cpu().tolist() == [2 * counted, 0]
