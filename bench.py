@@ -40,12 +40,12 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # Valid only while the kernel sources hash as they did when captured.
 MEASURED_TRAFFIC = {
     "project_bwd_adam": {
-        "bytes_per_gaussian": (0.8400720 + 0.4822640 + 1.8720535 + 1.9520630) * 1e9 / 3e6,
+        "bytes_per_gaussian": (0.840154 + 0.483711 + 1.872072 + 1.952328) * 1e9 / 3e6,
         "sources": {
             "paper_2510_14564_gb300/csrc/project.cu":
                 "5ae04c54b1467bafd4f19124cf10b8f4e50dc820838fa29302985fe8b87c787d",
             "paper_2510_14564_gb300/csrc/gs_common.cuh":
-                "7b566d05e89e1f2b0e3eff97194528e114567584a1a832cbd05301dc8fdefb80",
+                "0030d55b8fab3ccb7ca6285c29977af8f502d986272319b6f97e525d5ed769b4",
         },
     },
 }
