@@ -126,7 +126,13 @@ class Frame:
         rng = np.random.Generator(np.random.PCG64(self.sched.seed))
         w = np.zeros(MLP_W, np.float32)
         w[:256] = rng.normal(0, math.sqrt(2.0 / 8), 256)
-        w[288:320] = rng.normal(0, math.sqrt(1.0 / 32), 32)
+        # hidden unit 0 passes f0 = log1p(instances) to the output, the others
+        # start small: the untrained MLP orders tiles as the count does, and
+        # training moves it from there
+        w[0:8] = 0.0
+        w[0] = 1.0
+        w[288] = 1.0
+        w[289:320] = rng.normal(0, 0.05, 31)
         w[320] = 10.0                      # log(ns) of a typical tile
         self.mlp_w32 = torch.from_numpy(w).to(d)
         self.mlp_w16 = self.mlp_w32.to(torch.float16)
