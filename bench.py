@@ -40,10 +40,10 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # Valid only while the kernel sources hash as they did when captured.
 MEASURED_TRAFFIC = {
     "project_bwd_adam": {
-        "bytes_per_gaussian": (0.840154 + 0.483711 + 1.872072 + 1.952328) * 1e9 / 3e6,
+        "bytes_per_gaussian": (0.843597 + 0.649045 + 1.872040 + 1.952119) * 1e9 / 3e6,
         "sources": {
             "paper_2510_14564_gb300/csrc/project.cu":
-                "5ae04c54b1467bafd4f19124cf10b8f4e50dc820838fa29302985fe8b87c787d",
+                "e14e6ad10839e7a22e6dcf6326919d18f9c950c58a9907b898aaa7f6e1954adb",
             "paper_2510_14564_gb300/csrc/gs_common.cuh":
                 "0030d55b8fab3ccb7ca6285c29977af8f502d986272319b6f97e525d5ed769b4",
         },

@@ -752,7 +752,7 @@ __global__ void __launch_bounds__(128) k_project_bwd1(ViewGeom cam, int N, const
 // zero on clamped channels) and the view direction u -- written over the
 // Gaussian's consumed 2D-gradient record (entries 0..5).
 template <int SDT>
-__global__ void __launch_bounds__(128, 4) k_bwd_adam_geom(ViewGeom cam, int N, const void *__restrict__ sh,
+__global__ void __launch_bounds__(128, SDT == GS_F32 ? 4 : 6) k_bwd_adam_geom(ViewGeom cam, int N, const void *__restrict__ sh,
                                                        const int *__restrict__ touched,
                                                        float *__restrict__ grad2d, float *__restrict__ dparams,
                                                        AdamArgs a) {
@@ -763,7 +763,8 @@ __global__ void __launch_bounds__(128, 4) k_bwd_adam_geom(ViewGeom cam, int N, c
     float *__restrict__ p = a.p;
     float *__restrict__ m = a.m;
     float *__restrict__ v = a.v;
-    // every load of this Gaussian first (one round trip to memory)
+    // every load of this Gaussian first (one round trip to memory); 16-bit SH
+    // (fewer words held) leaves room for 6 CTAs per SM, FP32 SH for 4
     const int hit = __ldg(touched + i);
     float4 *rec = reinterpret_cast<float4 *>(grad2d + 12 * i);
     const float4 ga = rec[0], gb = rec[1], gc = rec[2];
