@@ -284,7 +284,7 @@ class Frame:
 
     def _judge(self) -> None:
         """Score the MLP's prediction and the instance count against the tile
-        times just measured; the verdict of the previous round, read without
+        times just measured; the verdict of the previous scoring, read without
         waiting (pinned copy + event), picks the order."""
         if self.judge_event is not None and self.judge_event.query():
             learned, count = self.judge_host.tolist()
