@@ -135,6 +135,27 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# replicas (one process per GPU): time = the slowest rank's, value = the
+# steps all ranks ran over that time
+# ---------------------------------------------------------------------------
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The largest of the ranks' times (every rank gets it)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(steps: int, ms_max: float, world: int) -> float:
+    """Steps per second of the whole job: every rank ran `steps` steps, the
+    job took the slowest rank's time."""
+    return world * steps / (ms_max / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1) -> dict:
@@ -231,11 +252,7 @@ def run_ours(args):
             torch.cuda.profiler.stop()
         launches = L.gs_launch_count() - l0
         barrier()
-        ms = t0.elapsed_time(t1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(t0.elapsed_time(t1), world, "cuda")
         if stage_times is not None:
             for (n0, e0), (_, e1) in zip(marks[:-1], marks[1:]):
                 if n0 != "end":
@@ -247,7 +264,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         plain.step()
     plain_ms, _ = timed(plain, args.steps)
-    plain_ips = args.steps / (plain_ms / 1e3)
+    plain_ips = replica_throughput(args.steps, plain_ms, 1)
     plain_stages = {}
     timed(plain, args.steps, stage_times=plain_stages)
     assert plain.frame.check_errors() == 0, "kernel error word set (plain path)"
@@ -265,9 +282,9 @@ def run_ours(args):
     with Clocks(local) as clk:
         ms, launches = timed(tr, args.steps, stage_times=stages, profile=True)
     clocks = clk.summary()
-    ips = args.steps / (ms / 1e3)
+    ips = replica_throughput(args.steps, ms, 1)
     e2e_ms, _ = timed(tr, args.steps, e2e=True)
-    e2e_ips = args.steps / (e2e_ms / 1e3)
+    e2e_ips = replica_throughput(args.steps, e2e_ms, 1)
     # the fwd+bwd iteration alone (projection .. projection backward + L1, no Adam)
     st = torch.cuda.current_stream()
     for _ in range(3):
@@ -280,7 +297,8 @@ def run_ours(args):
         tr.iteration()
     a1.record(st)
     torch.cuda.synchronize()
-    it_ips = args.steps / (a0.elapsed_time(a1) / 1e3)
+    barrier()
+    it_ips = args.steps / (max_over_ranks(a0.elapsed_time(a1), world, "cuda") / 1e3)
     assert tr.frame.check_errors() == 0, "kernel error word set (learned path)"
 
     f = tr.frame
