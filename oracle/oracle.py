@@ -316,3 +316,69 @@ def forward(cam, scene, window=None, margin_alpha=1e-4, margin_T=1e-3) -> dict:
     r = render(cam, kp, proj, window, margin_alpha, margin_T)
     r.update(kp=kp, proj=proj)
     return r
+
+
+def densify_prune(flat, m, v, grad_norm, n, logit_threshold, n_clone):
+    """One densification step of dynamic training (density control, Sec. III-B,
+    in its plain clone-and-prune form).  Written out from its definition:
+
+    - keep Gaussian i iff its opacity logit >= logit_threshold (FP32 values,
+      compared as stored: the threshold is the FP32 logit of the minimum
+      opacity);
+    - rank the kept Gaussians by screen-space gradient norm g_i, descending,
+      ties by index (g_i <= 0 or NaN counts as 0), and clone the first
+      c = min(n_clone, kept) of them;
+    - the new count must be a multiple of 4 (the grouped layout's alignment):
+      drop the last (kept + c) mod 4 clones when there are that many, else pad
+      with copies of the first kept Gaussian made invisible (logit -30);
+    - output: the kept Gaussians in index order, then the clones in rank
+      order, then the pads, in the grouped layout of the new count; clones and
+      pads start with zero Adam moments, kept Gaussians keep theirs.
+
+    Returns (flat', m', v', n')."""
+    flat, m, v = (np.asarray(a, np.float32) for a in (flat, m, v))
+    widths = (3, 3, 4, 1, 48)
+    def groups(a, count):
+        out, o = [], 0
+        for w in widths:
+            out.append(a[o:o + w * count].reshape(count, w))
+            o += w * count
+        return out
+    P, M, V = groups(flat, n), groups(m, n), groups(v, n)
+    logit = P[3][:, 0]
+    keep = np.flatnonzero(logit >= np.float32(logit_threshold))
+    g = np.asarray(grad_norm, np.float32)
+    g = np.where(g > 0, g, np.float32(0))
+    ranked = sorted(keep.tolist(), key=lambda i: (-float(g[i]), i))
+    c = min(int(n_clone), len(keep))
+    r = (len(keep) + c) % 4
+    if r and c >= r:
+        c -= r
+    clones = ranked[:c]
+    pad = (-(len(keep) + c)) % 4 if len(keep) else 0
+    src = keep.tolist() + clones + ([int(keep[0])] * pad if pad else [])
+    n2 = len(src)
+    fresh = np.array([False] * len(keep) + [True] * (c + pad))
+    outP, outM, outV = [], [], []
+    for gi in range(5):
+        pg = P[gi][src].copy() if n2 else np.zeros((0, widths[gi]), np.float32)
+        if gi == 3 and pad:
+            pg[len(keep) + c:, 0] = np.float32(-30.0)
+        mg = M[gi][src].copy() if n2 else np.zeros((0, widths[gi]), np.float32)
+        vg = V[gi][src].copy() if n2 else np.zeros((0, widths[gi]), np.float32)
+        if n2:
+            mg[fresh] = 0.0
+            vg[fresh] = 0.0
+        outP.append(pg.ravel())
+        outM.append(mg.ravel())
+        outV.append(vg.ravel())
+    return np.concatenate(outP), np.concatenate(outM), np.concatenate(outV), n2
+
+
+def screen_grad_norm(grad2d, n_views, n):
+    """Screen-space gradient statistic that selects the Gaussians to clone
+    (adaptive density control, Sec. II-A): for Gaussian i, the sum over views
+    of the Euclidean norm of (dL/du, dL/dv), entries 0 and 1 of its record
+    (view v, Gaussian i at record v n + i, 12 floats per record)."""
+    g = np.asarray(grad2d, np.float64).reshape(n_views, n, 12)
+    return np.sqrt(g[:, :, 0] ** 2 + g[:, :, 1] ** 2).sum(axis=0)

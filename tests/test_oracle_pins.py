@@ -545,3 +545,77 @@ def test_tile_features_saturation_sum():
         cov = min(1.0, math.pi * math.sqrt(1 / dconic) / 256)
         Th *= 1 - min(0.99, pr["opac"][k] * cov)
     assert f[5] == pytest.approx(math.log1p(acc), rel=1e-12)
+
+
+# --- densification (clone + prune) ------------------------------------------
+def _dp_scene(n, seed):
+    rng = np.random.default_rng(seed)
+    flat = rng.normal(size=59 * n).astype(np.float32)
+    m = rng.normal(size=59 * n).astype(np.float32)
+    v = rng.random(59 * n).astype(np.float32)
+    return flat, m, v
+
+
+def test_densify_prune_by_hand():
+    """Eight Gaussians, logits chosen around the threshold, gradients with a
+    tie: the kept ones in index order, then the two largest gradients (the tie
+    broken by index), moments zeroed for the clones only."""
+    n = 8
+    flat, m, v = _dp_scene(n, 0)
+    thr = np.float32(-5.0)
+    flat[10 * n:11 * n] = np.array([-6, -5, 0, 3, -5.0000005, 1, -7, 2], np.float32)
+    g = np.array([0.9, 0.1, 0.5, 0.5, 9.0, np.nan, 0.2, 0.3], np.float32)
+    f2, m2, v2, n2 = O.densify_prune(flat, m, v, g, n, thr, 2)
+    keep = [1, 2, 3, 5, 7]                        # logit >= -5 (index 4 is just below)
+    clones = [2, 3]                               # g: 0.5 (2), 0.5 (3): the tie by index; NaN is 0
+    # 5 kept + 2 clones = 7; dropping 3 clones is impossible, so one pad: 8
+    assert n2 == 8
+    src = keep + clones + [keep[0]]
+    for gi, (o, w) in enumerate(((0, 3), (3, 3), (6, 4), (10, 1), (11, 48))):
+        got = f2[o * n2:(o + w) * n2].reshape(n2, w)
+        ref = flat[o * n:(o + w) * n].reshape(n, w)[src]
+        if gi == 3:
+            ref = ref.copy()
+            ref[7, 0] = -30.0
+        assert np.array_equal(got, ref)
+        mg = m2[o * n2:(o + w) * n2].reshape(n2, w)
+        assert np.array_equal(mg[:5], m[o * n:(o + w) * n].reshape(n, w)[keep])
+        assert not mg[5:].any()
+
+
+def test_densify_prune_count_and_alignment():
+    rng = np.random.default_rng(3)
+    for n in (4, 100, 1000):
+        flat, m, v = _dp_scene(n, n)
+        g = rng.random(n).astype(np.float32)
+        for k in (0, 1, 3, n // 50, n):
+            f2, m2, v2, n2 = O.densify_prune(flat, m, v, g, n, np.float32(-1.0), k)
+            kept = int((flat[10 * n:11 * n] >= -1.0).sum())
+            assert n2 % 4 == 0 and kept <= n2 <= kept + min(k, kept) + 3
+            assert f2.size == 59 * n2 and m2.size == 59 * n2 and v2.size == 59 * n2
+
+
+def test_densify_prune_keeps_no_pruned_clone_and_handles_all_pruned():
+    n = 12
+    flat, m, v = _dp_scene(n, 5)
+    flat[10 * n:11 * n] = -10.0
+    f2, m2, v2, n2 = O.densify_prune(flat, m, v, np.ones(n, np.float32), n, np.float32(-5.0), 4)
+    assert n2 == 0 and f2.size == 0
+    flat[10 * n + 3] = 0.0                          # one survivor with the smallest gradient
+    g = np.arange(n, dtype=np.float32)
+    f2, m2, v2, n2 = O.densify_prune(flat, m, v, g, n, np.float32(-5.0), 4)
+    # kept {3}; clones {3} (pruned ones never cloned); 1 + 1 = 2 -> 2 pads
+    assert n2 == 4
+    lg = f2[10 * n2:11 * n2]
+    assert lg[0] == lg[1] == 0.0 and lg[2] == lg[3] == -30.0
+
+
+def test_screen_grad_norm_by_hand():
+    """Two views, two Gaussians: 3-4-5 and 5-12-13 right triangles; entries
+    other than 0 and 1 of a record do not count."""
+    g = np.zeros((2, 2, 12))
+    g[0, 0, :2] = (3, 4)
+    g[1, 0, :2] = (-5, 12)
+    g[0, 1, :2] = (0, -2)
+    g[:, :, 2:] = 7.0
+    assert np.allclose(O.screen_grad_norm(g.ravel(), 2, 2), [5 + 13, 2])
