@@ -354,6 +354,102 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_dynamic(args):
+    """Dynamic training: every step is a training step (forward, L1, backward,
+    Adam over all views) followed by one clone-and-prune (clone the 2% of
+    Gaussians with the largest accumulated screen-space gradient, drop those
+    with opacity below 0.005), so the Gaussian count changes from step to
+    step and every buffer follows it.  Reports steps/s over the timed steps,
+    the count trajectory, per-stage times and the clone-and-prune's HBM
+    rate (parameters, both moments and the 16-bit shadow read and written
+    once)."""
+    import torch
+
+    from paper_2510_14564_gb300 import _lib as L
+    from paper_2510_14564_gb300 import pipeline as P
+    from paper_2510_14564_gb300 import scenes as S
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    L.lib()
+    w = S.WORKLOADS[args.workload]
+    scene, cams = S.make_workload(args.workload, seed=0)
+    N0 = scene.n
+    tgt_host = torch.from_numpy(np.concatenate([S.random_image(c.W, c.H, seed=1 + v).ravel()
+                                                for v, c in enumerate(cams)])).pin_memory()
+    tgt = tgt_host.cuda()
+    lr = tuple(x * args.lr_scale for x in P.DEFAULT_LR)
+    tr = P.Trainer(cams, torch.from_numpy(scene.flat()).cuda(), N0, tgt, rgb_dtype=L.GS_BF16,
+                   sh_storage=L.GS_BF16, schedule=P.Schedule(mode="learned"), lr=lr)
+    del scene
+    tr.track_screen_grad()
+    frac, min_op = w["dynamic"]["clone_frac"], w["dynamic"]["min_opacity"]
+    for _ in range(args.calib):
+        tr.step()
+    for _ in range(args.warmup):
+        tr.step()
+        tr.densify(frac, min_op)
+    st = torch.cuda.current_stream()
+    marks, counts, densify_ms = [], [tr.N], []
+
+    def mark(name):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(st)
+        marks.append((name, e))
+
+    torch.cuda.synchronize()
+    l0 = L.gs_launch_count()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        t0.record(st)
+        for _ in range(args.steps):
+            tr.step(mark=mark)
+            d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            d0.record(st)
+            n_before = tr.N
+            tr.densify(frac, min_op)
+            d1.record(st)
+            densify_ms.append((d0, d1, n_before, tr.N))
+            counts.append(tr.N)
+        t1.record(st)
+        torch.cuda.synchronize()
+    launches = L.gs_launch_count() - l0
+    assert tr.frame.check_errors() == 0, "kernel error word set (dynamic training)"
+    ms = t0.elapsed_time(t1)
+    stages = {}
+    for (n0, e0), (_, e1) in zip(marks[:-1], marks[1:]):
+        if n0 != "end":
+            stages.setdefault(n0, []).append(e0.elapsed_time(e1))
+    dms = [a.elapsed_time(b) for a, b, _, _ in densify_ms]
+    # clone-and-prune traffic: params, m, v read (N) and written (N'), the
+    # 16-bit shadow written, the gradient statistic and sort keys read
+    dbytes = [(3 * 59 * 4) * (n + n2) + 96 * n2 + 4 * n for _, _, n, n2 in densify_ms]
+    dach = statistics.mean(b / (t / 1e3) / 1e9 for b, t in zip(dbytes, dms))
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ips = args.steps / (ms / 1e3)
+    out = {
+        "metric": "dynamic training steps/s (training step + clone/prune) @6M Gaussians, 4 views 1920x1080",
+        "value": round(ips, 3), "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded skewed-density scene, random-init parameters)",
+        "config": {"workload": args.workload, "gaussians_start": N0, "gaussians_timed_first": counts[0],
+                   "gaussians_timed_last": counts[-1], "gaussians_mean": round(statistics.mean(counts)),
+                   "clone_frac": frac, "min_opacity": min_op, "views": [[c.W, c.H] for c in cams],
+                   "schedule": "learned" if tr.frame.use_learned else "count (judge fallback)",
+                   "storage": "bf16 SH + bf16 colour, fp32 blending and gradients",
+                   "adam_lr_scale": args.lr_scale, "mlp_calibration_steps": args.calib,
+                   "l2": "inputs larger than L2", "graphs": "none (eager launches; the count is read back)"},
+        "stage_ms": {**{k: round(statistics.mean(v), 4) for k, v in stages.items()},
+                     "densify": round(statistics.mean(dms), 4)},
+        "roofline": {"kernel": "densify", "bound": "hbm", "achieved": round(dach, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(dach / hbm, 4), "traffic": None,
+                     "algorithmic_bytes": int(statistics.mean(dbytes)), "peak_source": peak_kind},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
 def schedule_diagnostics(f, L, torch, reps=5) -> dict:
     """Render makespans (best of `reps`, ms) of the forward and backward
     passes under the raster, count and learned tile orders (orders computed
@@ -523,10 +619,16 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def _workloads() -> dict:
+    from paper_2510_14564_gb300 import scenes as S
+    return S.WORKLOADS
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 300; 20 for a dynamic-training workload, whose count grows)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -538,8 +640,18 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
+        args.steps = 300 if args.steps is None else args.steps
         run_reference(args)
+    elif "dynamic" in _workloads().get(args.workload, {}):
+        args.steps = 20 if args.steps is None else args.steps
+        w = _workloads()[args.workload]
+        grown = w["n"] * (1 + w["dynamic"]["clone_frac"]) ** (args.warmup + args.steps)
+        if grown > 32e6:
+            ap.error(f"{args.warmup + args.steps} clone-and-prune steps could grow the count to "
+                     f"{grown / 1e6:.0f}M Gaussians; at most 32M are allowed")
+        run_dynamic(args)
     else:
+        args.steps = 300 if args.steps is None else args.steps
         run_ours(args)
 
 

@@ -311,6 +311,48 @@ int gs_adam_step(int N, float *d_params, const float *d_grads, float *d_m, float
 int gs_adam_flat(long long n, float *d_p, const float *d_g, float *d_m, float *d_v, float lr,
                  float b1, float b2, float eps, int t, gs_stream_t stream);
 
+/* a9. Dynamic training: one clone-and-prune step between training steps, the
+ * plain form of the adaptive density control of 3DGS training (Sec. II-A:
+ * Gaussians are cloned where reconstruction is poor and pruned where they
+ * contribute nothing).
+ *
+ * gs_grad2d_norm ADDS to d_out[i] (N floats, zeroed by the caller before the
+ * first step it covers) the screen-space gradient norm of Gaussian i summed
+ * over views, sum_v |(dL/du, dL/dv)|, read from entries 0 and 1 of the
+ * records of d_grad2d [V*N, 12] (view v, Gaussian i at record v*N + i) as
+ * gs_render_bwd leaves them.  Call it before gs_project_bwd_adam, which
+ * consumes d_grad2d for one view.
+ *
+ * gs_densify: from N Gaussians (grouped layout, 59 N floats; Adam moments
+ * d_m, d_v the same) and a per-Gaussian gradient statistic d_grad_norm:
+ *   - Gaussian i is kept iff its opacity logit >= logit_threshold (the logit
+ *     of the minimum opacity, compared in FP32);
+ *   - the kept ones are ranked by d_grad_norm descending, ties by index
+ *     (values <= 0 and NaN rank as 0), and the first c = min(n_clone, kept)
+ *     are cloned;
+ *   - the new count n2 is a multiple of 4 (every group stays 16-byte
+ *     aligned): the last (kept + c) mod 4 clones are dropped when there are
+ *     that many, else copies of the first kept Gaussian with logit -30
+ *     (opacity ~1e-13, invisible) pad the count;
+ *   - output, in the grouped layout of n2 (59 n2 floats) in d_params_out,
+ *     d_m_out, d_v_out: the kept Gaussians in index order, the clones in rank
+ *     order, the pads; clones and pads start with zero moments.  With
+ *     d_sh_shadow_out, the SH group is also written there as [n2,16,3] in
+ *     shadow_dtype (GS_BF16 or GS_F16, rounded to nearest).
+ * n2 is written to *d_n_out on the device (0 when nothing is kept); the host
+ * reads it when it needs the new count.  capacity (Gaussians) bounds n2; the
+ * output buffers hold 59 * capacity floats (N + n_clone + 3 always
+ * suffices).  If n2 would exceed it, GS_EW_CAPACITY is set in *d_err_word,
+ * *d_n_out is 0 and nothing is written.  Output buffers must not alias the
+ * inputs.  d_workspace: gs_densify_workspace(N) bytes. */
+int gs_grad2d_norm(int n_views, int N, const float *d_grad2d, float *d_out, gs_stream_t stream);
+int gs_densify_workspace(int N, size_t *bytes);
+int gs_densify(int N, const float *d_params, const float *d_m, const float *d_v,
+               const float *d_grad_norm, float logit_threshold, int n_clone, long long capacity,
+               float *d_params_out, float *d_m_out, float *d_v_out, void *d_sh_shadow_out,
+               int shadow_dtype, int32_t *d_n_out, void *d_workspace, size_t workspace_bytes,
+               int *d_err_word, gs_stream_t stream);
+
 /* a8. Learned tile-cost scheduler.  The paper balances rendering work by a
  * region density rho = active Gaussians / pixels (Sec. IV-C2); here a small
  * MLP predicts each tile's render cost from eight tile statistics and the

@@ -29,7 +29,7 @@ EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_project", "gs_bin
            "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_project_bwd", "gs_project_bwd_adam", "gs_adam_step",
            "gs_adam_flat", "gs_tile_features", "gs_mlp_predict", "gs_mlp_grad",
            "gs_mlp_train_step", "gs_rank_judge", "gs_int_cost", "gs_range_cost", "gs_sched_order_workspace",
-           "gs_sched_order"]
+           "gs_sched_order", "gs_grad2d_norm", "gs_densify_workspace", "gs_densify"]
 
 
 class GsError(RuntimeError):
@@ -101,6 +101,9 @@ def lib():
         L.gs_range_cost.argtypes = [VP, I32, VP, VP]
         L.gs_sched_order_workspace.argtypes = [I32, P(SZ)]
         L.gs_sched_order.argtypes = [VP, I32, VP, VP, SZ, VP]
+        L.gs_grad2d_norm.argtypes = [I32, I32, VP, VP, VP]
+        L.gs_densify_workspace.argtypes = [I32, P(SZ)]
+        L.gs_densify.argtypes = [I32, VP, VP, VP, VP, F32, I32, I64, VP, VP, VP, VP, I32, VP, VP, SZ, VP, VP]
         for name in EXPORTS:
             if name not in ("gs_version", "gs_strerror", "gs_launch_count"):
                 getattr(L, name).restype = I32
@@ -294,6 +297,26 @@ def gs_adam_step(N, params, grads, m, v, lr6, b1, b2, eps, t, sh_shadow=None, sh
 def gs_adam_flat(n, p, g, m, v, lr, b1, b2, eps, t, stream=None):
     check(lib().gs_adam_flat(int(n), ptr(p), ptr(g), ptr(m), ptr(v), float(lr), float(b1), float(b2),
                              float(eps), int(t), stream_ptr(stream)), "gs_adam_flat")
+
+
+def gs_grad2d_norm(n_views, N, grad2d, out, stream=None):
+    check(lib().gs_grad2d_norm(int(n_views), int(N), ptr(grad2d), ptr(out), stream_ptr(stream)),
+          "gs_grad2d_norm")
+
+
+def gs_densify_workspace(N) -> int:
+    out = SZ(0)
+    check(lib().gs_densify_workspace(int(N), ctypes.byref(out)), "gs_densify_workspace")
+    return int(out.value)
+
+
+def gs_densify(N, params, m, v, grad_norm, logit_threshold, n_clone, capacity, params_out, m_out, v_out,
+               sh_shadow_out, shadow_dtype, n_out, workspace, err_word, stream=None):
+    check(lib().gs_densify(int(N), ptr(params), ptr(m), ptr(v), ptr(grad_norm), float(logit_threshold),
+                           int(n_clone), int(capacity), ptr(params_out), ptr(m_out), ptr(v_out),
+                           ptr(sh_shadow_out), int(shadow_dtype), ptr(n_out), ptr(workspace),
+                           workspace.numel() * workspace.element_size(), ptr(err_word), stream_ptr(stream)),
+          "gs_densify")
 
 
 def gs_tile_features(cams, tile_ranges, vals, splats, rgb_dtype, cap, feats, w16=None, pred=None,

@@ -176,6 +176,165 @@ extern "C" int gs_adam_flat(long long n, float *d_p, const float *d_g, float *d_
                        reinterpret_cast<cudaStream_t>(stream));
 }
 
+// ---------------------------------------------------------------------------
+// Dynamic training: clone and prune (density control, Sec. III-B, in its
+// plain form)
+// ---------------------------------------------------------------------------
+namespace gs {
+
+// Sort keys of the two orders: by descending gradient norm among the kept
+// Gaussians (pruned ones last), and kept-before-pruned (one bit).
+__global__ void k_dp_keys(int N, const float *__restrict__ logits, const float *__restrict__ gnorm, float thr,
+                          uint32_t *__restrict__ kg, uint32_t *__restrict__ vg, uint32_t *__restrict__ kk,
+                          uint32_t *__restrict__ vk, unsigned int *__restrict__ n_kept) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool keep = false;
+    if (i < N) {
+        keep = logits[i] >= thr;
+        const float g0 = gnorm[i];
+        const float g = g0 > 0.0f ? g0 : 0.0f;                    // NaN and negatives count as 0
+        kg[i] = keep ? 0x7FFFFFFFu - __float_as_uint(g) : 0xFFFFFFFFu;
+        vg[i] = (uint32_t)i;
+        kk[i] = keep ? 0u : 1u;
+        vk[i] = (uint32_t)i;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, keep);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_kept, (unsigned)__popc(b));
+}
+
+// Clones c and pads so that the new count is a multiple of 4 (see gs_densify).
+__global__ void k_dp_count(const unsigned int *__restrict__ n_kept, int n_clone, long long cap,
+                           int *__restrict__ out3, int32_t *__restrict__ n_out, int *err_word) {
+    const int kept = (int)*n_kept;
+    int c = min(n_clone, kept);
+    const int r = (kept + c) % 4;
+    if (r && c >= r) c -= r;
+    const int pad = kept ? (4 - (kept + c) % 4) % 4 : 0;
+    int n2 = kept + c + pad;
+    if ((long long)n2 > cap) { set_err(err_word, GS_EW_CAPACITY); n2 = 0; }
+    out3[0] = kept;
+    out3[1] = c;
+    out3[2] = n2;
+    *n_out = n2;
+}
+
+// Output entry b of the grouped layout of the new count n2 (one thread per
+// entry, so writes are coalesced): destination Gaussian d takes, in order,
+// the kept Gaussians by index, the clones by rank, then the pads (copies of
+// the first kept Gaussian with logit -30); clones and pads get zero moments.
+template <int SDT>
+__global__ void k_dp_scatter(int N, const int *__restrict__ cnt, const uint32_t *__restrict__ by_keep,
+                             const uint32_t *__restrict__ by_grad, const float *__restrict__ p,
+                             const float *__restrict__ m, const float *__restrict__ v, float *__restrict__ p2,
+                             float *__restrict__ m2, float *__restrict__ v2, void *__restrict__ shadow) {
+    const int kept = cnt[0], c = cnt[1];
+    const long long o = cnt[2], n = N, total = 59 * o;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < total;
+         b += (long long)gridDim.x * blockDim.x) {
+        int g, w;
+        long long base_out, base_in;
+        if (b < 3 * o) { g = 0; w = 3; base_out = 0; base_in = 0; }
+        else if (b < 6 * o) { g = 1; w = 3; base_out = 3 * o; base_in = 3 * n; }
+        else if (b < 10 * o) { g = 2; w = 4; base_out = 6 * o; base_in = 6 * n; }
+        else if (b < 11 * o) { g = 3; w = 1; base_out = 10 * o; base_in = 10 * n; }
+        else { g = 4; w = 48; base_out = 11 * o; base_in = 11 * n; }
+        const long long e = b - base_out;
+        const int d = (int)(e / w), k = (int)(e - (long long)d * w);
+        const bool fresh = d >= kept, pad = d >= kept + c;
+        const long long s = d < kept ? by_keep[d] : (!pad ? by_grad[d - kept] : by_keep[0]);
+        const long long a = base_in + w * s + k;
+        const float val = (g == 3 && pad) ? -30.0f : p[a];
+        p2[b] = val;
+        m2[b] = fresh ? 0.0f : m[a];
+        v2[b] = fresh ? 0.0f : v[a];
+        if (SDT == GS_BF16 && g == 4) reinterpret_cast<__nv_bfloat16 *>(shadow)[e] = __float2bfloat16_rn(val);
+        if (SDT == GS_F16 && g == 4) reinterpret_cast<__half *>(shadow)[e] = __float2half_rn(val);
+    }
+}
+
+// Screen-space gradient norm per Gaussian, summed over views and added to
+// out: sum_v |(dL/du, dL/dv)|.
+__global__ void k_grad2d_norm(int n_views, int N, const float *__restrict__ g2, float *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float s = 0.0f;
+    for (int vi = 0; vi < n_views; ++vi) {
+        const float2 uv = __ldg(reinterpret_cast<const float2 *>(g2 + 12 * ((long long)vi * N + i)));
+        s += sqrtf(uv.x * uv.x + uv.y * uv.y);
+    }
+    out[i] += s;
+}
+
+struct DpPlan {
+    size_t kg, vg, kk, vk, sg, sk, scratch, misc, bytes;
+};
+
+static DpPlan dp_plan(int N) {
+    DpPlan q;
+    size_t o = 0;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    auto take = [&](size_t b) { size_t r = o; o += al(b); return r; };
+    const size_t a = 4 * (size_t)(N > 0 ? N : 1);
+    q.kg = take(a); q.vg = take(a); q.kk = take(a); q.vk = take(a); q.sg = take(a); q.sk = take(a);
+    q.scratch = take(radix_sort_workspace(N > 0 ? N : 1));
+    q.misc = take(64);
+    q.bytes = o;
+    return q;
+}
+
+}  // namespace gs
+
+extern "C" int gs_densify_workspace(int N, size_t *bytes) {
+    if (N < 0 || !bytes) return GS_ERR_ARG;
+    *bytes = gs::dp_plan(N).bytes;
+    return GS_OK;
+}
+
+extern "C" int gs_densify(int N, const float *d_params, const float *d_m, const float *d_v,
+                          const float *d_grad_norm, float logit_threshold, int n_clone, long long capacity,
+                          float *d_params_out, float *d_m_out, float *d_v_out, void *d_sh_shadow_out,
+                          int shadow_dtype, int32_t *d_n_out, void *d_workspace, size_t workspace_bytes,
+                          int *d_err_word, gs_stream_t stream) {
+    using namespace gs;
+    if (N < 0 || n_clone < 0 || capacity < 0 || !d_n_out) return GS_ERR_ARG;
+    if (d_sh_shadow_out && shadow_dtype != GS_BF16 && shadow_dtype != GS_F16) return GS_ERR_ARG;
+    if (N > 0 && (!d_params || !d_m || !d_v || !d_grad_norm || !d_params_out || !d_m_out || !d_v_out ||
+                  !d_workspace))
+        return GS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (N == 0) { cudaMemsetAsync(d_n_out, 0, sizeof(int32_t), st); return launch_status(); }
+    const DpPlan q = dp_plan(N);
+    if (workspace_bytes < q.bytes) return GS_ERR_CAPACITY;
+    char *ws = reinterpret_cast<char *>(d_workspace);
+    uint32_t *kg = (uint32_t *)(ws + q.kg), *vg = (uint32_t *)(ws + q.vg), *kk = (uint32_t *)(ws + q.kk),
+             *vk = (uint32_t *)(ws + q.vk), *sg = (uint32_t *)(ws + q.sg), *sk = (uint32_t *)(ws + q.sk);
+    unsigned int *n_kept = (unsigned int *)(ws + q.misc);
+    int *cnt = (int *)(ws + q.misc + 16);
+    cudaMemsetAsync(n_kept, 0, sizeof(unsigned int), st);
+    const long long n = N;
+    { k_dp_keys<<<cdiv(N, 256), 256, 0, st>>>(N, d_params + 10 * n, d_grad_norm, logit_threshold, kg, vg, kk, vk, n_kept); count_launches(1); }
+    radix_sort_pairs(kg, vg, sg, N, 32, ws + q.scratch, st);      // by descending gradient, ties by index
+    radix_sort_pairs(kk, vk, sk, N, 1, ws + q.scratch, st);       // kept first, in index order
+    { k_dp_count<<<1, 1, 0, st>>>(n_kept, n_clone, capacity, cnt, d_n_out, d_err_word); count_launches(1); }
+    const long long most = min(capacity, n + (long long)n_clone + 3);
+    const int grid = (int)max(1ll, min((59 * most + 255) / 256, 152ll * 16));
+    if (!d_sh_shadow_out)
+        { k_dp_scatter<GS_F32><<<grid, 256, 0, st>>>(N, cnt, sk, sg, d_params, d_m, d_v, d_params_out, d_m_out, d_v_out, nullptr); count_launches(1); }
+    else if (shadow_dtype == GS_BF16)
+        { k_dp_scatter<GS_BF16><<<grid, 256, 0, st>>>(N, cnt, sk, sg, d_params, d_m, d_v, d_params_out, d_m_out, d_v_out, d_sh_shadow_out); count_launches(1); }
+    else
+        { k_dp_scatter<GS_F16><<<grid, 256, 0, st>>>(N, cnt, sk, sg, d_params, d_m, d_v, d_params_out, d_m_out, d_v_out, d_sh_shadow_out); count_launches(1); }
+    return launch_status();
+}
+
+extern "C" int gs_grad2d_norm(int n_views, int N, const float *d_grad2d, float *d_out, gs_stream_t stream) {
+    using namespace gs;
+    if (n_views < 1 || N < 0 || (N > 0 && (!d_grad2d || !d_out)) || !aligned(d_grad2d, 8)) return GS_ERR_ARG;
+    if (N == 0) return GS_OK;
+    { k_grad2d_norm<<<cdiv(N, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(n_views, N, d_grad2d, d_out); count_launches(1); }
+    return launch_status();
+}
+
 namespace gs {
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }

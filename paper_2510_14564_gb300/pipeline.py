@@ -83,15 +83,10 @@ class Frame:
         self.sh_dtype = sh_dtype
         self.sched = schedule or Schedule()
         d = self.dev
-        VN = max(1, self.V * self.N)       # non-empty buffers even for N = 0
         self.T = sum(c.n_tiles for c in self.cams)
         self.P = sum(c.W * c.H for c in self.cams)
-        nb = L.SPLAT_BYTES[rgb_dtype]
-        self.splats = torch.empty(VN * nb // 4, dtype=torch.float32, device=d)
-        self.depth = torch.empty(VN, dtype=torch.float32, device=d)
-        self.rect = torch.empty(VN * 4, dtype=torch.int16, device=d)
-        self.touched = torch.empty(VN, dtype=torch.int32, device=d)
-        self.radius = torch.empty(VN, dtype=torch.int32, device=d)
+        self.gcap = 0
+        self._alloc_gaussians(self.N)
         self.err = torch.zeros(1, dtype=torch.int32, device=d)
         self.n_inst = torch.zeros(1, dtype=torch.int64, device=d)
         self.ranges = torch.empty(self.T * 2, dtype=torch.int32, device=d)
@@ -106,8 +101,6 @@ class Frame:
         self.tile_ns = torch.zeros(self.T, dtype=torch.int64, device=d)
         self.dimg = torch.empty(3 * self.P, dtype=torch.float32, device=d)
         self.loss = torch.zeros(1, dtype=torch.float32, device=d)
-        self.grad2d = torch.empty(VN * 12, dtype=torch.float32, device=d)
-        self.dparams = torch.empty(PARAM_FLOATS * max(1, self.N), dtype=torch.float32, device=d)
         self.capacity = 0
         self.vals = None
         self.keys = None
@@ -150,18 +143,64 @@ class Frame:
         self.step_count = 0
 
     # -- buffers -----------------------------------------------------------
+    def _alloc_gaussians(self, N: int) -> None:
+        """Per-Gaussian buffers for up to N Gaussians in every view (non-empty
+        even for N = 0); the kernels index them by the current N."""
+        d = self.dev
+        self.gcap = max(1, int(N))
+        VN = self.V * self.gcap
+        nb = L.SPLAT_BYTES[self.rgb_dtype]
+        self.splats = torch.empty(VN * nb // 4, dtype=torch.float32, device=d)
+        self.depth = torch.empty(VN, dtype=torch.float32, device=d)
+        self.rect = torch.empty(VN * 4, dtype=torch.int16, device=d)
+        self.touched = torch.empty(VN, dtype=torch.int32, device=d)
+        self.radius = torch.empty(VN, dtype=torch.int32, device=d)
+        self.grad2d = torch.empty(VN * 12, dtype=torch.float32, device=d)
+        self.dparams = torch.empty(PARAM_FLOATS * self.gcap, dtype=torch.float32, device=d)
+
+    def resize(self, N: int) -> None:
+        """A new Gaussian count (after clone and prune).  Per-Gaussian buffers
+        and the instance capacity (which grows in proportion to the count)
+        are enlarged with 25% slack when they must grow and never shrunk; the
+        binning workspace is checked against the new count.  Per-tile history
+        (last processed counts, scheduler state) is kept: the prefix repair
+        covers lists that grew past it."""
+        N = int(N)
+        if N == self.N:
+            return
+        if N > self.gcap:
+            self._alloc_gaussians(N + N // 4)
+        old, self.N = self.N, N
+        if self.vals is None:
+            return
+        need = int(self.capacity * N / max(1, old)) + 1 if N > old else self.capacity
+        if need > self.capacity:
+            self.reserve(min(int(need * 1.25), 0xF0000000), with_keys=self.keys is not None)
+        else:
+            self._size_ws()
+
     def reserve(self, capacity: int, with_keys: bool = False) -> None:
         capacity = int(max(capacity, 1))
         if capacity <= self.capacity and (not with_keys or self.keys is not None):
             return
         self.capacity = max(capacity, self.capacity)
+        self.vals = None                  # release before allocating the larger buffers
+        self.keys = None
+        self.ws = None
         self.vals = torch.empty(self.capacity, dtype=torch.int32, device=self.dev)
         self.keys = torch.empty(self.capacity, dtype=torch.int64, device=self.dev) if with_keys else None
+        self._size_ws()
+
+    def _size_ws(self) -> None:
+        """Binning workspace for the current count and capacity (reallocated
+        only when it must grow)."""
         if self.prefix:
             nbytes = L.gs_bin_sort_prefix_workspace(self.cams, self.N, self.capacity)
         else:
             nbytes = L.gs_bin_sort_workspace(self.cams, self.N, self.capacity)
-        self.ws = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device=self.dev)
+        if self.ws is None or self.ws.numel() * 4 < nbytes + 256:
+            self.ws = None
+            self.ws = torch.empty(nbytes // 4 + 64, dtype=torch.float32, device=self.dev)
 
     # -- forward -----------------------------------------------------------
     def project(self, params: dict) -> None:
@@ -339,6 +378,53 @@ class Trainer:
             raise ValueError(f"targets must hold 3 x {self.frame.P} values (every view's pixels, "
                              f"view after view), got {targets.numel()}")
         self.targets = targets
+        self.grad_norm = None             # screen-space gradient statistic, when tracked
+
+    def track_screen_grad(self, on: bool = True) -> None:
+        """Accumulate, every step, each Gaussian's screen-space gradient norm
+        summed over views (the statistic densify() clones by)."""
+        self.grad_norm = torch.zeros(max(1, self.N), dtype=torch.float32, device=self.p.device) if on else None
+
+    def densify(self, clone_frac: float = 0.02, min_opacity: float = 0.005) -> int:
+        """One clone-and-prune step between training steps (adaptive density
+        control of 3DGS training in its plain form, Sec. II-A): drop the
+        Gaussians with opacity below min_opacity, clone the
+        floor(clone_frac N) kept ones with the largest accumulated
+        screen-space gradient (trimmed or padded to a multiple of 4; see
+        gs_densify), clones starting with zero Adam moments.  Parameters,
+        moments, the 16-bit SH shadow and the frame's buffers move to the new
+        count, which is read back (4 bytes) and returned; the statistic
+        restarts from zero."""
+        n_clone = int(clone_frac * self.N)
+        thr = float(np.float32(math.log(min_opacity / (1.0 - min_opacity))))
+        cap = self.N + n_clone + 3
+        dev = self.p.device
+        p2 = torch.empty(PARAM_FLOATS * cap, dtype=torch.float32, device=dev)
+        m2 = torch.empty_like(p2)
+        v2 = torch.empty_like(p2)
+        sh2 = None
+        if self.sh_shadow is not None:
+            sh2 = torch.empty(48 * cap, dtype=self.sh_shadow.dtype, device=dev)
+        gn = self.grad_norm if self.grad_norm is not None else torch.zeros(max(1, self.N), device=dev)
+        ws = torch.empty(L.gs_densify_workspace(self.N) // 4 + 64, dtype=torch.float32, device=dev)
+        n_out = torch.zeros(1, dtype=torch.int32, device=dev)
+        f = self.frame
+        L.gs_densify(self.N, self.p, self.m, self.v, gn, thr, n_clone, cap, p2, m2, v2, sh2, self.sh_storage,
+                     n_out, ws, f.err)
+        n2 = int(n_out.item())
+        if f.check_errors():
+            raise L.GsError(f"gs_densify reported error bits {f.check_errors():#x}")
+        self.N = n2
+        self.p = p2[:PARAM_FLOATS * n2]
+        self.m = m2[:PARAM_FLOATS * n2]
+        self.v = v2[:PARAM_FLOATS * n2]
+        self.views = param_views(self.p, n2)
+        if sh2 is not None:
+            self.sh_shadow = sh2[:48 * n2]
+        f.resize(n2)
+        if self.grad_norm is not None:
+            self.track_screen_grad(True)
+        return n2
 
     def params_for_kernels(self) -> dict:
         d = dict(self.views)
@@ -377,6 +463,9 @@ class Trainer:
         mk("render_bwd")
         L.gs_render_bwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, s, f.dimg, f.T_final, f.n_proc,
                         f.tile_nproc, f.grad2d, f.err)
+        if self.grad_norm is not None:
+            mk("grad_stat")
+            L.gs_grad2d_norm(len(f.cams), self.N, f.grad2d, self.grad_norm)
         pk_sh = self.sh_shadow if self.sh_shadow is not None else pk["sh"]
         self.t += 1
         if len(f.cams) == 1:

@@ -204,6 +204,10 @@ WORKLOADS = {
     "skewed-3M-1600x1060": dict(n=3_000_000, kind="skewed", views=[(1600, 1060)]),
     # scheduler workload: 1.5M skewed, 16 views from 800x600 to 1920x1080
     "skewed-1.5M-16views": dict(n=1_500_000, kind="skewed", views=uneven_sizes(16), ring=True),
+    # dynamic training: 6M skewed, 4 views at 1920x1080, a clone-and-prune
+    # after every step (2% clones, opacity < 0.005 dropped)
+    "dynamic-6M-4x1920x1080": dict(n=6_000_000, kind="skewed", views=[(1920, 1080)] * 4, ring=True,
+                                   dynamic=dict(clone_frac=0.02, min_opacity=0.005)),
 }
 
 
