@@ -161,7 +161,7 @@ def test_trainer_densifies_and_keeps_training():
     assert np.array_equal(tr.p.cpu().numpy(), p_ref)
     assert np.array_equal(tr.m.cpu().numpy(), m_ref)
     assert np.array_equal(tr.v.cpu().numpy(), v_ref)
-    assert torch.equal(tr.sh_shadow.view(torch.int16),
+    assert torch.equal(tr.sh_shadow.cpu().view(torch.int16),
                        torch.from_numpy(p_ref[11 * n2:]).to(torch.bfloat16).view(torch.int16))
     for _ in range(2):
         loss = tr.step()
