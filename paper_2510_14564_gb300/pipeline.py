@@ -102,6 +102,7 @@ class Frame:
         self.dimg = torch.empty(3 * self.P, dtype=torch.float32, device=d)
         self.loss = torch.zeros(1, dtype=torch.float32, device=d)
         self.capacity = 0
+        self.inst_per_gaussian = 0.0
         self.vals = None
         self.keys = None
         self.ws = None
@@ -170,14 +171,13 @@ class Frame:
             return
         if N > self.gcap:
             self._alloc_gaussians(N + N // 4)
-        old, self.N = self.N, N
+        self.N = N
         if self.vals is None:
             return
-        need = int(self.capacity * N / max(1, old)) + 1 if N > old else self.capacity
+        need = int(self.inst_per_gaussian * N) + 65536
         if need > self.capacity:
             self.reserve(min(int(need * 1.25), 0xF0000000), with_keys=self.keys is not None)
-        else:
-            self._size_ws()
+        self._size_ws()
 
     def reserve(self, capacity: int, with_keys: bool = False) -> None:
         capacity = int(max(capacity, 1))
@@ -226,6 +226,7 @@ class Frame:
             need = int(self.n_inst.item())
             if self.prefix:          # room for repairs: the full lists
                 need = max(need, int(self.tile_count.sum().item()))
+            self.inst_per_gaussian = need / max(1, self.N)     # scales the capacity when the count changes
             self.reserve(int(need * 1.25) + 65536, with_keys=want_keys)
             self.err.bitwise_and_(~L.GS_EW_CAPACITY)      # the sizing pass overflowed on purpose
         elif want_keys and self.keys is None:
