@@ -1936,6 +1936,133 @@ __global__ void __launch_bounds__(256) k_rep_fill(TileBatch tb, int N, long long
     }
 }
 
+// The same rebuild spread over the GPU: each view's records (in depth order)
+// are cut into S segments of L records, and one CTA takes one (segment,
+// flagged tile) item at a time, segment-major so that the CTAs running
+// together read the same segment from L2.  The records' rectangles are first
+// gathered into depth order (8 coalesced bytes per record, empty for
+// untouched records); a count pass per (segment, tile), then a fill pass that
+// starts each segment after the hits of the tile's earlier segments, write
+// each tile's list in depth order.  Work is flagged
+// tiles x records and nothing runs when no tile is flagged.
+constexpr int kRepSegMin = 16384;   // records per segment, at least
+constexpr int kRepSegsMax = 256;    // segments per view, at most
+constexpr int kRepGrid = 152 * 8;
+
+__global__ void __launch_bounds__(256) k_rep_gather(const int32_t *__restrict__ flag_count,
+                                                    const uint32_t *__restrict__ order,
+                                                    const short4 *__restrict__ rect,
+                                                    const int *__restrict__ touched, long long VN,
+                                                    short4 *__restrict__ rs) {
+    if (*flag_count <= 0) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < VN;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t g = order[i];
+        rs[i] = __ldg(touched + g) > 0 ? __ldg(rect + g) : make_short4(0, 0, 0, 0);
+    }
+}
+
+struct RepItem {
+    int f, k, tx, ty;
+    long long s0, s1;
+};
+
+__device__ __forceinline__ RepItem rep_item(const TileBatch &tb, int N, int L, int F, long long w,
+                                            const int32_t *__restrict__ flag_tiles) {
+    RepItem it;
+    it.k = (int)(w / F);
+    it.f = (int)(w - (long long)it.k * F);
+    const int t = flag_tiles[it.f];
+    const int v = view_of_tile(tb, t);
+    const int lt = t - tb.v[v].tile_base;
+    it.tx = lt % tb.v[v].TX;
+    it.ty = lt / tb.v[v].TX;
+    it.s0 = (long long)v * N + (long long)it.k * L;
+    const long long vend = (long long)(v + 1) * N;
+    it.s1 = it.s0 + L < vend ? it.s0 + L : vend;
+    return it;
+}
+
+__device__ __forceinline__ bool rect_holds(short4 rc, int tx, int ty) {
+    return rc.x <= tx && tx < rc.z && rc.y <= ty && ty < rc.w;
+}
+
+__global__ void __launch_bounds__(256) k_rep_seg_count(TileBatch tb, int N, int L, int S,
+                                                       const int32_t *__restrict__ flag_tiles,
+                                                       const int32_t *__restrict__ flag_count,
+                                                       const uint32_t *__restrict__ rep_start,
+                                                       const short4 *__restrict__ rs,
+                                                       uint32_t *__restrict__ seg_cnt) {
+    __shared__ int s_w[8];
+    const int F = *flag_count;
+    const long long items = F > 0 ? (long long)F * S : 0;
+    for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+        const RepItem it = rep_item(tb, N, L, F, w, flag_tiles);
+        int c = 0;
+        if (rep_start[it.f] != 0xffffffffu)
+            for (long long i = it.s0 + threadIdx.x; i < it.s1; i += 256) c += rect_holds(rs[i], it.tx, it.ty);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) tot += s_w[k];
+            seg_cnt[(long long)it.f * S + it.k] = (uint32_t)tot;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_rep_seg_fill(TileBatch tb, int N, int L, int S,
+                                                      const int32_t *__restrict__ flag_tiles,
+                                                      const int32_t *__restrict__ flag_count,
+                                                      const uint32_t *__restrict__ rep_start,
+                                                      const uint32_t *__restrict__ full,
+                                                      const uint32_t *__restrict__ seg_cnt,
+                                                      const uint32_t *__restrict__ order,
+                                                      const short4 *__restrict__ rs,
+                                                      uint32_t *__restrict__ vals, int *err_word) {
+    __shared__ int s_w[8];
+    const int F = *flag_count;
+    const long long items = F > 0 ? (long long)F * S : 0;
+    for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+        const RepItem it = rep_item(tb, N, L, F, w, flag_tiles);
+        const uint32_t at0 = rep_start[it.f];
+        if (at0 == 0xffffffffu) continue;                  // the same for the whole CTA
+        const uint32_t end = at0 + full[flag_tiles[it.f]];
+        // this segment's start: the hits of the tile's earlier segments (S <= 256)
+        int before = threadIdx.x < it.k ? (int)seg_cnt[(long long)it.f * S + threadIdx.x] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = before;
+        __syncthreads();
+        uint32_t at = at0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) at += (uint32_t)s_w[k];
+        __syncthreads();
+        for (long long i0 = it.s0; i0 < it.s1; i0 += 256) {
+            const long long i = i0 + threadIdx.x;
+            const bool hit = i < it.s1 && rect_holds(rs[i], it.tx, it.ty);
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            const int wp = threadIdx.x >> 5;
+            if ((threadIdx.x & 31) == 0) s_w[wp] = __popc(bal);
+            __syncthreads();
+            int base = 0, tot = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) { base += k < wp ? s_w[k] : 0; tot += s_w[k]; }
+            if (hit) {
+                const uint32_t pos = at + (uint32_t)base + (uint32_t)__popc(bal & lanemask_lt());
+                if (pos < end) vals[pos] = order[i];
+                else set_err(err_word, GS_EW_BOUNDS);
+            }
+            at += (uint32_t)tot;
+            __syncthreads();
+        }
+    }
+}
+
 extern "C" int gs_bin_sort_prefix_repair(const gs_camera *cams, int n_views, int N,
                                          const int16_t *d_rect, const int32_t *d_touched,
                                          const int32_t *d_flag_tiles, const int32_t *d_flag_count,
@@ -1959,7 +2086,26 @@ extern "C" int gs_bin_sort_prefix_repair(const gs_camera *cams, int n_views, int
     uint32_t *rep_start = (uint32_t *)(ws + p.kept);  // kept counts are no longer needed
     { k_rep_alloc<<<1, 1, 0, st>>>(d_flag_tiles, d_flag_count, full, d_n_instances, capacity,
                                    reinterpret_cast<uint2 *>(d_tile_ranges), rep_start, d_err_word); count_launches(1); }
-    { k_rep_fill<<<64, 256, 0, st>>>(tb, N, VN, d_flag_tiles, d_flag_count, rep_start, order,
-                                     reinterpret_cast<const short4 *>(d_rect), d_touched, d_vals); count_launches(1); }
+    const short4 *rect = reinterpret_cast<const short4 *>(d_rect);
+    // segments: at least kRepSegMin records, at most kRepSegsMax per view; the
+    // gathered rectangles reuse the depth keys' space and the segment counts
+    // the record offsets' (both dead once the lists are placed)
+    long long L = (N + kRepSegsMax - 1) / kRepSegsMax;
+    L = (L + 255) / 256 * 256;
+    if (L < kRepSegMin) L = kRepSegMin;
+    const int S = (int)((N + L - 1) / L);
+    const int T = tb.total_tiles;
+    if (8 * (size_t)VN <= p.dv0 - p.dk0 && 4 * (size_t)T * S <= p.mc - p.offs) {
+        short4 *rs = (short4 *)(ws + p.dk0);
+        uint32_t *seg = (uint32_t *)(ws + p.offs);
+        const int gg = (int)(cdiv(VN, 256) < 152 * 16 ? cdiv(VN, 256) : 152 * 16);
+        { k_rep_gather<<<gg, 256, 0, st>>>(d_flag_count, order, rect, d_touched, VN, rs); count_launches(1); }
+        { k_rep_seg_count<<<kRepGrid, 256, 0, st>>>(tb, N, (int)L, S, d_flag_tiles, d_flag_count, rep_start, rs, seg); count_launches(1); }
+        { k_rep_seg_fill<<<kRepGrid, 256, 0, st>>>(tb, N, (int)L, S, d_flag_tiles, d_flag_count, rep_start, full, seg,
+                                                   order, rs, d_vals, d_err_word); count_launches(1); }
+    } else {
+        { k_rep_fill<<<64, 256, 0, st>>>(tb, N, VN, d_flag_tiles, d_flag_count, rep_start, order, rect, d_touched,
+                                         d_vals); count_launches(1); }
+    }
     return launch_status();
 }
