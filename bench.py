@@ -400,6 +400,7 @@ def run_dynamic(args):
     l0 = L.gs_launch_count()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        torch.cuda.profiler.start()     # a profiler started with --profile-from-start off sees only this
         t0.record(st)
         for _ in range(args.steps):
             tr.step(mark=mark)
@@ -412,6 +413,7 @@ def run_dynamic(args):
             counts.append(tr.N)
         t1.record(st)
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     launches = L.gs_launch_count() - l0
     assert tr.frame.check_errors() == 0, "kernel error word set (dynamic training)"
     ms = t0.elapsed_time(t1)

@@ -1949,12 +1949,34 @@ constexpr int kRepSegMin = 16384;   // records per segment, at least
 constexpr int kRepSegsMax = 256;    // segments per view, at most
 constexpr int kRepGrid = 152 * 8;
 
-__global__ void __launch_bounds__(256) k_rep_gather(const int32_t *__restrict__ flag_count,
-                                                    const uint32_t *__restrict__ order,
+// The first thread also places the tiles' lists after the kept entries, as
+// k_rep_alloc does (one launch less on the steps that repair nothing).
+__global__ void __launch_bounds__(256) k_rep_gather(const int32_t *__restrict__ flag_tiles,
+                                                    const int32_t *__restrict__ flag_count,
+                                                    const uint32_t *__restrict__ full,
+                                                    const long long *__restrict__ n_inst, long long cap,
+                                                    uint2 *__restrict__ ranges, uint32_t *__restrict__ rep_start,
+                                                    int *err_word, const uint32_t *__restrict__ order,
                                                     const short4 *__restrict__ rect,
                                                     const int *__restrict__ touched, long long VN,
                                                     short4 *__restrict__ rs) {
-    if (*flag_count <= 0) return;
+    const int n = *flag_count;
+    if (n <= 0) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long at = (unsigned long long)*n_inst;
+        for (int i = 0; i < n; ++i) {
+            const int t = flag_tiles[i];
+            const unsigned long long c = full[t];
+            if ((long long)(at + c) > cap) {
+                set_err(err_word, GS_EW_CAPACITY);
+                rep_start[i] = 0xffffffffu;
+                continue;
+            }
+            rep_start[i] = (uint32_t)at;
+            ranges[t] = make_uint2((uint32_t)at, (uint32_t)(at + c));
+            at += c;
+        }
+    }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < VN;
          i += (long long)gridDim.x * blockDim.x) {
         const uint32_t g = order[i];
@@ -2084,8 +2106,6 @@ extern "C" int gs_bin_sort_prefix_repair(const gs_camera *cams, int n_views, int
     const uint32_t *order = (const uint32_t *)(ws + (n_views > 1 ? p.dv1 : p.dv0));
     const uint32_t *full = (const uint32_t *)(ws + p.full);
     uint32_t *rep_start = (uint32_t *)(ws + p.kept);  // kept counts are no longer needed
-    { k_rep_alloc<<<1, 1, 0, st>>>(d_flag_tiles, d_flag_count, full, d_n_instances, capacity,
-                                   reinterpret_cast<uint2 *>(d_tile_ranges), rep_start, d_err_word); count_launches(1); }
     const short4 *rect = reinterpret_cast<const short4 *>(d_rect);
     // segments: at least kRepSegMin records, at most kRepSegsMax per view; the
     // gathered rectangles reuse the depth keys' space and the segment counts
@@ -2098,12 +2118,16 @@ extern "C" int gs_bin_sort_prefix_repair(const gs_camera *cams, int n_views, int
     if (8 * (size_t)VN <= p.dv0 - p.dk0 && 4 * (size_t)T * S <= p.mc - p.offs) {
         short4 *rs = (short4 *)(ws + p.dk0);
         uint32_t *seg = (uint32_t *)(ws + p.offs);
-        const int gg = (int)(cdiv(VN, 256) < 152 * 16 ? cdiv(VN, 256) : 152 * 16);
-        { k_rep_gather<<<gg, 256, 0, st>>>(d_flag_count, order, rect, d_touched, VN, rs); count_launches(1); }
+        const int gg = (int)(cdiv(VN, 256) < 152 * 8 ? cdiv(VN, 256) : 152 * 8);
+        { k_rep_gather<<<gg, 256, 0, st>>>(d_flag_tiles, d_flag_count, full, d_n_instances, capacity,
+                                           reinterpret_cast<uint2 *>(d_tile_ranges), rep_start, d_err_word, order,
+                                           rect, d_touched, VN, rs); count_launches(1); }
         { k_rep_seg_count<<<kRepGrid, 256, 0, st>>>(tb, N, (int)L, S, d_flag_tiles, d_flag_count, rep_start, rs, seg); count_launches(1); }
         { k_rep_seg_fill<<<kRepGrid, 256, 0, st>>>(tb, N, (int)L, S, d_flag_tiles, d_flag_count, rep_start, full, seg,
                                                    order, rs, d_vals, d_err_word); count_launches(1); }
     } else {
+        { k_rep_alloc<<<1, 1, 0, st>>>(d_flag_tiles, d_flag_count, full, d_n_instances, capacity,
+                                       reinterpret_cast<uint2 *>(d_tile_ranges), rep_start, d_err_word); count_launches(1); }
         { k_rep_fill<<<64, 256, 0, st>>>(tb, N, VN, d_flag_tiles, d_flag_count, rep_start, order, rect, d_touched,
                                          d_vals); count_launches(1); }
     }
