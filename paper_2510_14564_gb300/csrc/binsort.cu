@@ -1942,7 +1942,7 @@ __global__ void __launch_bounds__(256) k_rep_fill(TileBatch tb, int N, long long
 // together read the same segment from L2.  The records' rectangles are first
 // gathered into depth order (8 coalesced bytes per record, empty for
 // untouched records); a count pass per (segment, tile), then a fill pass that
-// starts each segment after the hits of the tile's earlier segments, write
+// starts each segment after the hits of the tile's earlier segments, writes
 // each tile's list in depth order.  Work is flagged
 // tiles x records and nothing runs when no tile is flagged.
 constexpr int kRepSegMin = 16384;   // records per segment, at least
@@ -2037,6 +2037,10 @@ __global__ void __launch_bounds__(256) k_rep_seg_count(TileBatch tb, int N, int 
     }
 }
 
+// Each warp takes one eighth of the segment: it counts its hits, the CTA
+// adds up where each warp starts, and every warp then places its hits with
+// warp ballots alone (no CTA barrier per record batch).  Segments without a
+// hit for the tile are skipped.
 __global__ void __launch_bounds__(256) k_rep_seg_fill(TileBatch tb, int N, int L, int S,
                                                       const int32_t *__restrict__ flag_tiles,
                                                       const int32_t *__restrict__ flag_count,
@@ -2046,41 +2050,46 @@ __global__ void __launch_bounds__(256) k_rep_seg_fill(TileBatch tb, int N, int L
                                                       const uint32_t *__restrict__ order,
                                                       const short4 *__restrict__ rs,
                                                       uint32_t *__restrict__ vals, int *err_word) {
-    __shared__ int s_w[8];
+    __shared__ uint32_t s_before[8], s_cnt[8];
     const int F = *flag_count;
     const long long items = F > 0 ? (long long)F * S : 0;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     for (long long w = blockIdx.x; w < items; w += gridDim.x) {
         const RepItem it = rep_item(tb, N, L, F, w, flag_tiles);
         const uint32_t at0 = rep_start[it.f];
-        if (at0 == 0xffffffffu) continue;                  // the same for the whole CTA
+        const uint32_t *cnt = seg_cnt + (long long)it.f * S;
+        if (at0 == 0xffffffffu || cnt[it.k] == 0u) continue;      // the same for the whole CTA
         const uint32_t end = at0 + full[flag_tiles[it.f]];
-        // this segment's start: the hits of the tile's earlier segments (S <= 256)
-        int before = threadIdx.x < it.k ? (int)seg_cnt[(long long)it.f * S + threadIdx.x] : 0;
+        // hits of the tile's earlier segments (S <= 256: one per thread)
+        uint32_t before = threadIdx.x < it.k ? cnt[threadIdx.x] : 0u;
+        // this warp's share of the segment, in whole batches of 32 records
+        const long long len = it.s1 - it.s0;
+        const long long per = (len + 255) / 256 * 32;
+        const long long a = it.s0 + wp * per;
+        const long long b = a + per < it.s1 ? a + per : it.s1;
+        uint32_t c = 0;
+        for (long long i = a + lane; i < b; i += 32) c += rect_holds(rs[i], it.tx, it.ty);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
-        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = before;
+        for (int o = 16; o > 0; o >>= 1) {
+            before += __shfl_xor_sync(0xffffffffu, before, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (lane == 0) { s_before[wp] = before; s_cnt[wp] = c; }
         __syncthreads();
-        uint32_t at = at0;
+        uint32_t pos = at0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) at += (uint32_t)s_w[k];
+        for (int k = 0; k < 8; ++k) pos += s_before[k] + (k < wp ? s_cnt[k] : 0u);
         __syncthreads();
-        for (long long i0 = it.s0; i0 < it.s1; i0 += 256) {
-            const long long i = i0 + threadIdx.x;
-            const bool hit = i < it.s1 && rect_holds(rs[i], it.tx, it.ty);
+        for (long long i0 = a; i0 < b; i0 += 32) {
+            const long long i = i0 + lane;
+            const bool hit = i < b && rect_holds(rs[i], it.tx, it.ty);
             const unsigned bal = __ballot_sync(0xffffffffu, hit);
-            const int wp = threadIdx.x >> 5;
-            if ((threadIdx.x & 31) == 0) s_w[wp] = __popc(bal);
-            __syncthreads();
-            int base = 0, tot = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) { base += k < wp ? s_w[k] : 0; tot += s_w[k]; }
             if (hit) {
-                const uint32_t pos = at + (uint32_t)base + (uint32_t)__popc(bal & lanemask_lt());
-                if (pos < end) vals[pos] = order[i];
+                const uint32_t q = pos + (uint32_t)__popc(bal & lanemask_lt());
+                if (q < end) vals[q] = order[i];
                 else set_err(err_word, GS_EW_BOUNDS);
             }
-            at += (uint32_t)tot;
-            __syncthreads();
+            pos += (uint32_t)__popc(bal);
         }
     }
 }
