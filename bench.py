@@ -452,6 +452,87 @@ def run_dynamic(args):
     print(json.dumps(out), flush=True)
 
 
+def run_colour_ablation(args):
+    """Colour-layout ablation of the forward pass (the reordering-based
+    memory access of Sec. V): the same lists rendered with the colour planar
+    or interleaved, read in the blend loop or batch-loaded into shared
+    memory, beside the production kernel (colour inside the staged splat
+    record).  FP32 records; kept prefixes from the guaranteed bound of a
+    first step (nothing flagged).  Each render is timed alone with CUDA
+    events after an L2 flush; the images are checked equal bit for bit."""
+    import torch
+
+    from paper_2510_14564_gb300 import _lib as L
+    from paper_2510_14564_gb300 import pipeline as P
+    from paper_2510_14564_gb300 import scenes as S
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    L.lib()
+    scene, cams = S.make_workload(args.workload, seed=0)
+    N = scene.n
+    params = P.to_device_params(scene)
+    fr = P.Frame(cams, N, rgb_dtype=L.GS_F32, prefix=True)
+    fr.project(P.param_views(params, N))
+    fr.bin_sort()
+    fr.render()
+    torch.cuda.synchronize()
+    assert fr.check_errors() == 0 and int(fr.flag_count.item()) == 0
+    VN = fr.V * N
+    planar = torch.empty(3 * VN, dtype=torch.float32, device="cuda")
+    inter = torch.empty(3 * VN, dtype=torch.float32, device="cuda")
+    L.gs_colour_arrays(VN, fr.splats, planar, inter)
+    ref = fr.img.clone()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")     # 256 MB > L2
+    img = torch.empty_like(fr.img)
+    T = torch.empty_like(fr.T_final)
+    npx = torch.empty_like(fr.n_proc)
+    tn = torch.empty_like(fr.tile_nproc)
+
+    def production():
+        L.gs_render_fwd(fr.cams, fr.ranges, fr.vals, fr.splats, L.GS_F32, None, img, T, npx, tn, None, fr.err)
+
+    runs = {"production_record": production}
+    for name, layout in L.COLOUR_LAYOUTS.items():
+        col = planar if "planar" in name else inter
+        runs[name] = (lambda layout=layout, col=col: L.gs_render_fwd_colour(
+            fr.cams, N, fr.ranges, fr.vals, fr.splats, layout, col, img, T, npx))
+    st = torch.cuda.current_stream()
+    times, equal = {}, {}
+    for name, fn in runs.items():
+        for _ in range(3):
+            fn()
+        ms = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        times[name] = statistics.median(ms)
+        equal[name] = bool(torch.equal(img, ref))
+    torch.cuda.profiler.start()         # one launch of each, for a profiler started with --profile-from-start off
+    for fn in runs.values():
+        fn()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    base = times["planar_global"]
+    out = {
+        "metric": "forward-pass ms by colour layout (planar/interleaved x blend-loop/staged)",
+        "unit": "ms", "higher_is_better": False, "steps": args.steps, "dtype": "f32",
+        "data": "synthetic (seeded skewed-density scene, random-init parameters)",
+        "config": {"workload": args.workload, "gaussians": N, "views": [[c.W, c.H] for c in cams],
+                   "instances_kept": int(fr.n_inst.item()), "schedule": "raster, one CTA per tile",
+                   "l2": "flushed before every timed render (256 MB write)"},
+        "render_ms": {k: round(v, 4) for k, v in times.items()},
+        "speedup_vs_planar_global": {k: round(base / v, 3) for k, v in times.items()},
+        "images_equal_to_production": equal,
+        "gpu_launches_per_render": 1,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def schedule_diagnostics(f, L, torch, reps=5) -> dict:
     """Render makespans (best of `reps`, ms) of the forward and backward
     passes under the raster, count and learned tile orders (orders computed
@@ -636,12 +717,17 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--calib", type=int, default=40, help="untimed MLP calibration steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--colour-ablation", action="store_true",
+                    help="time the forward pass under four colour layouts (prints its own JSON line)")
     ap.add_argument("--lr-scale", type=float, default=1e-3,
                     help="scale of the Adam learning rates (keeps the scene fixed over the run)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    if args.impl == "reference":
+    if args.colour_ablation:
+        args.steps = 20 if args.steps is None else args.steps
+        run_colour_ablation(args)
+    elif args.impl == "reference":
         args.steps = 300 if args.steps is None else args.steps
         run_reference(args)
     elif "dynamic" in _workloads().get(args.workload, {}):

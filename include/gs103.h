@@ -249,6 +249,39 @@ int gs_render_fwd(const gs_camera *cams, int n_views, const uint32_t *d_tile_ran
                   int32_t *d_flag_tiles, int32_t *d_flag_count, int *d_err_word,
                   gs_stream_t stream);
 
+/* a3, colour-layout ablation (Sec. V: batch loading, reordering into
+ * per-Gaussian RGB, coalesced access).  Not on the training path: it
+ * measures what the layout of the colour costs the forward pass.
+ *
+ * gs_colour_arrays copies the colour of VN FP32 splat records (GS_F32
+ * records from gs_project) into d_planar [3, VN] (all R, then all G, then
+ * all B) and/or d_interleaved [VN, 3] (R G B per Gaussian); either may be
+ * NULL.
+ *
+ * gs_render_fwd_colour is gs_render_fwd with FP32 records and one CTA per
+ * tile in raster order, except that the colour of each list entry is read
+ * from d_colour (laid out as the layout says) instead of from the record:
+ *   GS_COLOUR_PLANAR_GLOBAL       planar, read in the blend loop by every
+ *                                 pixel that blends the Gaussian;
+ *   GS_COLOUR_INTERLEAVED_GLOBAL  interleaved, read the same way;
+ *   GS_COLOUR_PLANAR_STAGED       planar, loaded into shared memory with the
+ *                                 batch's geometry;
+ *   GS_COLOUR_INTERLEAVED_STAGED  interleaved, loaded the same way.
+ * Writes d_img, d_T_final and d_n_proc as gs_render_fwd does, equal bit for
+ * bit for every layout (and to gs_render_fwd on the same records).  Full
+ * lists, or kept prefixes none of whose pixels ran out (the ablation does
+ * not flag tiles). */
+#define GS_COLOUR_PLANAR_GLOBAL 0
+#define GS_COLOUR_INTERLEAVED_GLOBAL 1
+#define GS_COLOUR_PLANAR_STAGED 2
+#define GS_COLOUR_INTERLEAVED_STAGED 3
+int gs_colour_arrays(long long VN, const void *d_splats_f32, float *d_planar, float *d_interleaved,
+                     gs_stream_t stream);
+int gs_render_fwd_colour(const gs_camera *cams, int n_views, int N, const uint32_t *d_tile_ranges,
+                         const uint32_t *d_vals, const void *d_splats_f32, int layout,
+                         const float *d_colour, float *d_img, float *d_T_final, int32_t *d_n_proc,
+                         gs_stream_t stream);
+
 /* a4. L1 loss over n floats: *d_loss (device float, overwritten)
  * = mean |img - tgt|; d_dimg = sign(img - tgt)/n with sign(0) = 0. */
 int gs_l1_loss(long long n, const float *d_img, const float *d_tgt, float *d_loss,

@@ -19,6 +19,9 @@ LIB_PATH = PKG / "_build" / "libgs103.so"
 GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_NONFINITE = range(6)
 GS_F32, GS_BF16, GS_F16 = 0, 1, 2
 GS_EW_NONFINITE, GS_EW_CAPACITY, GS_EW_TIMEOUT, GS_EW_BOUNDS = 1, 2, 4, 8
+GS_COLOUR_PLANAR_GLOBAL, GS_COLOUR_INTERLEAVED_GLOBAL, GS_COLOUR_PLANAR_STAGED, GS_COLOUR_INTERLEAVED_STAGED = 0, 1, 2, 3
+COLOUR_LAYOUTS = {"planar_global": GS_COLOUR_PLANAR_GLOBAL, "interleaved_global": GS_COLOUR_INTERLEAVED_GLOBAL,
+                  "planar_staged": GS_COLOUR_PLANAR_STAGED, "interleaved_staged": GS_COLOUR_INTERLEAVED_STAGED}
 GS_SCHED_RASTER, GS_SCHED_ORDER = 0, 1
 GS_MAX_VIEWS = 64
 SPLAT_BYTES = {GS_F32: 48, GS_BF16: 32, GS_F16: 32}
@@ -29,7 +32,8 @@ EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_project", "gs_bin
            "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_project_bwd", "gs_project_bwd_adam", "gs_adam_step",
            "gs_adam_flat", "gs_tile_features", "gs_mlp_predict", "gs_mlp_grad",
            "gs_mlp_train_step", "gs_rank_judge", "gs_int_cost", "gs_range_cost", "gs_sched_order_workspace",
-           "gs_sched_order", "gs_grad2d_norm", "gs_densify_workspace", "gs_densify"]
+           "gs_sched_order", "gs_grad2d_norm", "gs_densify_workspace", "gs_densify",
+           "gs_colour_arrays", "gs_render_fwd_colour"]
 
 
 class GsError(RuntimeError):
@@ -102,6 +106,8 @@ def lib():
         L.gs_sched_order_workspace.argtypes = [I32, P(SZ)]
         L.gs_sched_order.argtypes = [VP, I32, VP, VP, SZ, VP]
         L.gs_grad2d_norm.argtypes = [I32, I32, VP, VP, VP]
+        L.gs_colour_arrays.argtypes = [I64, VP, VP, VP, VP]
+        L.gs_render_fwd_colour.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, I32, VP, VP, VP, VP, VP]
         L.gs_densify_workspace.argtypes = [I32, P(SZ)]
         L.gs_densify.argtypes = [I32, VP, VP, VP, VP, F32, I32, I64, VP, VP, VP, VP, I32, VP, VP, SZ, VP, VP]
         for name in EXPORTS:
@@ -317,6 +323,18 @@ def gs_densify(N, params, m, v, grad_norm, logit_threshold, n_clone, capacity, p
                            ptr(sh_shadow_out), int(shadow_dtype), ptr(n_out), ptr(workspace),
                            workspace.numel() * workspace.element_size(), ptr(err_word), stream_ptr(stream)),
           "gs_densify")
+
+
+def gs_colour_arrays(VN, splats, planar, interleaved, stream=None):
+    check(lib().gs_colour_arrays(int(VN), ptr(splats), ptr(planar), ptr(interleaved), stream_ptr(stream)),
+          "gs_colour_arrays")
+
+
+def gs_render_fwd_colour(cams, N, tile_ranges, vals, splats, layout, colour, img, T_final, n_proc, stream=None):
+    ca = camera_array(cams)
+    check(lib().gs_render_fwd_colour(ca, len(cams), int(N), ptr(tile_ranges), ptr(vals), ptr(splats), int(layout),
+                                     ptr(colour), ptr(img), ptr(T_final), ptr(n_proc), stream_ptr(stream)),
+          "gs_render_fwd_colour")
 
 
 def gs_tile_features(cams, tile_ranges, vals, splats, rgb_dtype, cap, feats, w16=None, pred=None,

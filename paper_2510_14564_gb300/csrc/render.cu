@@ -601,3 +601,181 @@ extern "C" int gs_render_bwd(const gs_camera *cams, int n_views, const uint32_t 
         { k_render_bwd<GS_F16, kBwdPPT><<<grid, kTilePix / kBwdPPT, 0, st>>>(tb, rg, d_vals, d_splats, sa, d_dimg, d_T_final, d_n_proc, d_tile_nproc, d_grad2d, d_err_word); count_launches(1); }
     return launch_status();
 }
+
+// ---------------------------------------------------------------------------
+// Colour-layout ablation of the forward pass (Sec. V: batch loading, data
+// reordering, coalesced access).  The geometry of every list entry is staged
+// as in k_render_fwd (from FP32 records, without their colour words); the
+// colour comes from a separate array in one of four ways:
+//   planar, global       [R_1..R_n][G_1..G_n][B_1..B_n], read in the blend
+//                        loop by every pixel that blends the Gaussian;
+//   interleaved, global  [R_1 G_1 B_1 .. R_n G_n B_n], read the same way;
+//   planar, staged       batch-loaded into shared memory with the geometry;
+//   interleaved, staged  the same from the interleaved array (Sec. V's end
+//                        state).
+// The arithmetic and its order are those of k_render_fwd with one pixel per
+// thread, so every layout gives the same image bit for bit.  One CTA per
+// tile in raster order; not on the training path.
+// ---------------------------------------------------------------------------
+namespace gs {
+
+template <int CL>
+__device__ __forceinline__ float3 colour_of(const float *__restrict__ colour, long long VN, uint32_t id) {
+    if (CL == GS_COLOUR_PLANAR_GLOBAL || CL == GS_COLOUR_PLANAR_STAGED)
+        return make_float3(__ldg(colour + id), __ldg(colour + VN + id), __ldg(colour + 2 * VN + id));
+    const float *p = colour + 3ll * id;
+    return make_float3(__ldg(p), __ldg(p + 1), __ldg(p + 2));
+}
+
+template <int CL>
+__device__ __forceinline__ int stage_colour_batch(const uint32_t *vals, const SplatF32 *splats,
+                                                  const float *colour, long long VN, const TileCtx<1> &c,
+                                                  int j0, int j1, float4 *s_a, float4 *s_b, float4 *s_c,
+                                                  int *s_warp) {
+    constexpr bool kStaged = CL == GS_COLOUR_PLANAR_STAGED || CL == GS_COLOUR_INTERLEAVED_STAGED;
+    const int w = threadIdx.x >> 5;
+    const int j = j0 + threadIdx.x;
+    bool keep = false;
+    uint32_t id = 0;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 b = make_float2(0.f, 0.f);
+    if (j < j1) {
+        id = __ldg(vals + j);
+        const SplatF32 *p = splats + id;
+        a = __ldg(&p->g0);
+        b = __ldg(reinterpret_cast<const float2 *>(&p->g1));
+        keep = tile_bound(a.x, a.y, a.z, a.w, b.x, b.y, c.x0, c.y0) >= kCullLog2;
+    }
+    float3 rgb = make_float3(0.f, 0.f, 0.f);
+    if (kStaged && keep) rgb = colour_of<CL>(colour, VN, id);
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if ((threadIdx.x & 31) == 0) s_warp[w] = __popc(bal);
+    __syncthreads();
+    int pre = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < kTilePix / 32; ++q) {
+        const int cnt = s_warp[q];
+        total += cnt;
+        pre += q < w ? cnt : 0;
+    }
+    if (keep) {
+        const int pos = pre + __popc(bal & lanemask_lt_r());
+        s_a[pos] = a;
+        s_b[pos] = make_float4(b.x, b.y, rgb.x, rgb.y);
+        s_c[pos] = make_float4(rgb.z, __int_as_float(j - (int)c.range.x), __uint_as_float(id), 0.f);
+    }
+    __syncthreads();
+    return total;
+}
+
+template <int CL>
+__global__ void __launch_bounds__(kTilePix, 4) k_render_fwd_colour(TileBatch tb, const uint2 *__restrict__ ranges,
+                                                               const uint32_t *__restrict__ vals,
+                                                               const SplatF32 *__restrict__ splats,
+                                                               const float *__restrict__ colour, long long VN,
+                                                               float *__restrict__ img,
+                                                               float *__restrict__ T_final,
+                                                               int *__restrict__ n_proc) {
+    constexpr bool kStaged = CL == GS_COLOUR_PLANAR_STAGED || CL == GS_COLOUR_INTERLEAVED_STAGED;
+    __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch];
+    __shared__ int s_warp[kTilePix / 32];
+    const int tile = blockIdx.x;
+    const TileCtx<1> c = tile_ctx<1>(tb, ranges, tile);
+    const float pcx = (float)c.px + 0.5f, pcy = (float)c.py + 0.5f;
+    float T = 1.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
+    int last = 0;
+    bool done = !c.in[0];
+    for (int j0 = (int)c.range.x; j0 < (int)c.range.y; j0 += kBatch) {
+        if (__syncthreads_count(done) == kTilePix) break;
+        const int j1 = min(j0 + kBatch, (int)c.range.y);
+        const int n = stage_colour_batch<CL>(vals, splats, colour, VN, c, j0, j1, s_a, s_b, s_c, s_warp);
+        if (done) continue;
+        for (int k = 0; k < n; ++k) {
+            const float4 a = s_a[k];
+            const float4 b = s_b[k];
+            float q;
+            const float araw = pair_alpha_raw(a.z, a.w, b.x, b.y, pcx - a.x, pcy - a.y, &q);
+            const float alpha = fminf(kAlphaMax, araw);
+            if (alpha < kAlphaMin) continue;
+            const float Tn = T * (1.0f - alpha);
+            if (Tn < kTMin) { done = true; break; }
+            const float4 cc = s_c[k];
+            float3 rgb;
+            if (kStaged) rgb = make_float3(b.z, b.w, cc.x);
+            else rgb = colour_of<CL>(colour, VN, __float_as_uint(cc.z));
+            const float w = alpha * T;
+            Cr = fmaf(rgb.x, w, Cr);
+            Cg = fmaf(rgb.y, w, Cg);
+            Cb = fmaf(rgb.z, w, Cb);
+            T = Tn;
+            last = __float_as_int(cc.y) + 1;
+        }
+    }
+    if (!c.in[0]) return;
+    const ViewTiles &vt = tb.v[c.view];
+    const long long HW = (long long)vt.W * vt.H;
+    float *im = img + 3 * vt.pix_base;
+    const long long q = (long long)c.py * vt.W + c.px;
+    im[q] = fmaf(T, vt.bg[0], Cr);
+    im[HW + q] = fmaf(T, vt.bg[1], Cg);
+    im[2 * HW + q] = fmaf(T, vt.bg[2], Cb);
+    T_final[vt.pix_base + q] = T;
+    n_proc[vt.pix_base + q] = last;
+}
+
+// Colour of each FP32 splat record into the planar and interleaved arrays.
+__global__ void k_colour_arrays(long long VN, const SplatF32 *__restrict__ splats, float *__restrict__ planar,
+                                float *__restrict__ inter) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < VN;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 g1 = __ldg(&splats[i].g1);
+        const float bl = __ldg(&splats[i].g2).x;
+        if (planar) { planar[i] = g1.z; planar[VN + i] = g1.w; planar[2 * VN + i] = bl; }
+        if (inter) { inter[3 * i] = g1.z; inter[3 * i + 1] = g1.w; inter[3 * i + 2] = bl; }
+    }
+}
+
+}  // namespace gs
+
+extern "C" int gs_colour_arrays(long long VN, const void *d_splats_f32, float *d_planar, float *d_interleaved,
+                                gs_stream_t stream) {
+    if (VN < 0 || (VN > 0 && !d_splats_f32) || !aligned(d_splats_f32, 16)) return GS_ERR_ARG;
+    if (VN == 0 || (!d_planar && !d_interleaved)) return GS_OK;
+    const int grid = (int)((VN + 255) / 256 < 152 * 16 ? (VN + 255) / 256 : 152 * 16);
+    { k_colour_arrays<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+          VN, reinterpret_cast<const SplatF32 *>(d_splats_f32), d_planar, d_interleaved); count_launches(1); }
+    return launch_status();
+}
+
+extern "C" int gs_render_fwd_colour(const gs_camera *cams, int n_views, int N, const uint32_t *d_tile_ranges,
+                                    const uint32_t *d_vals, const void *d_splats_f32, int layout,
+                                    const float *d_colour, float *d_img, float *d_T_final, int32_t *d_n_proc,
+                                    gs_stream_t stream) {
+    TileBatch tb;
+    if (make_tile_batch(cams, n_views, &tb) != GS_OK) return GS_ERR_ARG;
+    if (N < 0 || !d_tile_ranges || !d_vals || !d_splats_f32 || !d_colour || !d_img || !d_T_final || !d_n_proc)
+        return GS_ERR_ARG;
+    if (!aligned(d_splats_f32, 16) || !aligned(d_tile_ranges, 8)) return GS_ERR_ARG;
+    if (layout < GS_COLOUR_PLANAR_GLOBAL || layout > GS_COLOUR_INTERLEAVED_STAGED) return GS_ERR_ARG;
+    if (tb.total_tiles == 0) return GS_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint2 *rg = reinterpret_cast<const uint2 *>(d_tile_ranges);
+    const SplatF32 *sp = reinterpret_cast<const SplatF32 *>(d_splats_f32);
+    const long long VN = (long long)n_views * N;
+    const int g = tb.total_tiles;
+    switch (layout) {
+    case GS_COLOUR_PLANAR_GLOBAL:
+        { k_render_fwd_colour<GS_COLOUR_PLANAR_GLOBAL><<<g, kTilePix, 0, st>>>(tb, rg, d_vals, sp, d_colour, VN, d_img, d_T_final, d_n_proc); count_launches(1); }
+        break;
+    case GS_COLOUR_INTERLEAVED_GLOBAL:
+        { k_render_fwd_colour<GS_COLOUR_INTERLEAVED_GLOBAL><<<g, kTilePix, 0, st>>>(tb, rg, d_vals, sp, d_colour, VN, d_img, d_T_final, d_n_proc); count_launches(1); }
+        break;
+    case GS_COLOUR_PLANAR_STAGED:
+        { k_render_fwd_colour<GS_COLOUR_PLANAR_STAGED><<<g, kTilePix, 0, st>>>(tb, rg, d_vals, sp, d_colour, VN, d_img, d_T_final, d_n_proc); count_launches(1); }
+        break;
+    default:
+        { k_render_fwd_colour<GS_COLOUR_INTERLEAVED_STAGED><<<g, kTilePix, 0, st>>>(tb, rg, d_vals, sp, d_colour, VN, d_img, d_T_final, d_n_proc); count_launches(1); }
+        break;
+    }
+    return launch_status();
+}
