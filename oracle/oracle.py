@@ -382,3 +382,156 @@ def screen_grad_norm(grad2d, n_views, n):
     (view v, Gaussian i at record v n + i, 12 floats per record)."""
     g = np.asarray(grad2d, np.float64).reshape(n_views, n, 12)
     return np.sqrt(g[:, :, 0] ** 2 + g[:, :, 1] ** 2).sum(axis=0)
+
+
+# ---------------------------------------------------------------------------
+# Workload-sensitive density control (Sec. III-C), written from its
+# definitions with brute-force pairwise distances.  Distances are FP32, each
+# squared distance summed as (dx^2 + dy^2) + dz^2 with every operation
+# rounded (no fused multiply-add), so the integer decisions they feed
+# (neighbour counts, nearest neighbours) are reproducible bit for bit.
+# ---------------------------------------------------------------------------
+
+def _pair_d2(P, rows):
+    """FP32 squared distances from points `rows` to every point, [len(rows), n]."""
+    d = [(P[None, :, a] - P[rows, None, a]).astype(np.float32) for a in range(3)]
+    return ((d[0] * d[0] + d[1] * d[1]).astype(np.float32) + d[2] * d[2]).astype(np.float32)
+
+
+def density_stats(means, r, k, chunk=512):
+    """Per point: local density rho_p = #{q != p : |q - p| <= r} (Sec. III-C1,
+    squared distances against fl32(r) * fl32(r)); the mean distance to the k
+    nearest other points, d_bar = (sum of the k smallest distances, ascending,
+    in FP32) / k (fewer when fewer points exist, 0 with none, Sec. III-C2); the
+    nearest neighbour (ties by index, -1 with none) and its distance."""
+    P = np.ascontiguousarray(means, np.float32)
+    n = P.shape[0]
+    r2 = np.float32(np.float32(r) * np.float32(r))
+    rho = np.zeros(n, np.int64)
+    dbar = np.zeros(n, np.float32)
+    nn = np.full(n, -1, np.int64)
+    dnn = np.zeros(n, np.float32)
+    kk = min(k, n - 1)
+    for a in range(0, n, chunk):
+        rows = np.arange(a, min(n, a + chunk))
+        d2 = _pair_d2(P, rows)
+        d2[np.arange(len(rows)), rows] = np.inf                  # not its own neighbour
+        rho[rows] = (d2 <= r2).sum(axis=1)
+        if kk <= 0:
+            continue
+        order = np.argsort(d2, axis=1, kind="stable")[:, :kk]    # ties by index
+        near = np.sqrt(np.take_along_axis(d2, order, axis=1)).astype(np.float32)
+        acc = np.zeros(len(rows), np.float32)
+        for j in range(kk):
+            acc = (acc + near[:, j]).astype(np.float32)
+        dbar[rows] = (acc / np.float32(kk)).astype(np.float32)
+        nn[rows] = order[:, 0]
+        dnn[rows] = near[:, 0]
+    return rho, dbar, nn, dnn
+
+
+def density_thresholds(rho, dnn, alpha, beta, gamma):
+    """rho_low = mu - alpha sigma, rho_high = mu + beta sigma over the local
+    densities (Sec. III-C1; population standard deviation), and the merge
+    radius d_merge = mu_d + gamma sigma_d over the nearest-neighbour
+    distances (Sec. III-C3), in FP64: mu = S1 / n, sigma = sqrt(max(0,
+    S2 / n - mu^2)) from exact integer sums for rho."""
+    n = len(rho)
+    if n == 0:
+        return 0.0, 0.0, 0.0
+    s1, s2 = int(np.sum(rho)), int(np.sum(rho.astype(object) ** 2))
+    mu = float(s1) / n
+    var = float(s2) / n - mu * mu
+    sd = float(np.sqrt(max(var, 0.0)))
+    lo, hi = mu - alpha * sd, mu + beta * sd
+    if n < 2:
+        return lo, hi, 0.0
+    d = dnn.astype(np.float64)
+    mu_d = float(d.sum()) / n
+    var_d = float((d * d).sum()) / n - mu_d * mu_d
+    return lo, hi, mu_d + gamma * float(np.sqrt(max(var_d, 0.0)))
+
+
+def density_control(flat, m, v, n, r, k, alpha, beta, alpha_d, delta, gamma, z, u):
+    """One round of workload-sensitive density control (Sec. III-C).
+
+    - thresholds from the local densities (density_thresholds);
+    - every point with rho < rho_low spawns one new point (Sec. III-C2):
+      p_new = p + sigma_p z + delta (2 u - 1), sigma_p = alpha_d d_bar_p, with
+      the draws z ~ N(0, 1)^3 and u ~ U[0, 1)^3 given; the rest of the new
+      Gaussian is a copy of its parent;
+    - a point with rho > rho_high merges with its nearest neighbour when the
+      two are each other's nearest neighbour, both have rho > rho_high and
+      their distance is <= d_merge (Sec. III-C3): position = opacity-weighted
+      centroid (weights sigmoid(logit)), log-scale = log of the mean scale per
+      axis, every other parameter from the more opaque of the two (larger
+      logit, ties to the lower index);
+    - output (grouped layout of the new count): the untouched points in index
+      order, the merged points in the order of their lower index, the new
+      points in the order of their parents, then padding to a multiple of 4
+      (copies of output point 0 with logit -30); merged, new and padding
+      points start with zero Adam moments.
+    Returns (flat', m', v', n', info)."""
+    flat, m, v = (np.asarray(a, np.float32) for a in (flat, m, v))
+    widths = (3, 3, 4, 1, 48)
+    def groups(a, count):
+        out, o = [], 0
+        for w in widths:
+            out.append(a[o:o + w * count].reshape(count, w))
+            o += w * count
+        return out
+    Pg, Mg, Vg = groups(flat, n), groups(m, n), groups(v, n)
+    means = Pg[0]
+    rho, dbar, nn, dnn = density_stats(means, r, k)
+    lo, hi, dm = density_thresholds(rho, dnn, alpha, beta, gamma)
+    low = rho.astype(np.float64) < lo
+    high = rho.astype(np.float64) > hi
+    head = np.zeros(n, bool)
+    gone = np.zeros(n, bool)
+    for i in range(n):
+        j = int(nn[i])
+        if j > i and high[i] and high[j] and nn[j] == i and float(dnn[i]) <= dm:
+            head[i] = True
+            gone[j] = True
+    keep = ~(head | gone)
+    z, u = np.asarray(z, np.float32), np.asarray(u, np.float32)
+    rows = []                      # (parameters, fresh) per output point, group by group
+    def point(i):
+        return [g[i].copy() for g in Pg]
+    for i in np.flatnonzero(keep):
+        rows.append(([g[i].copy() for g in Pg], [g[i].copy() for g in Mg], [g[i].copy() for g in Vg]))
+    for i in np.flatnonzero(head):
+        j = int(nn[i])
+        pi, pj = point(i), point(j)
+        li, lj = pi[3][0], pj[3][0]
+        wi = np.float32(1.0) / (np.float32(1.0) + np.exp(-li, dtype=np.float32))
+        wj = np.float32(1.0) / (np.float32(1.0) + np.exp(-lj, dtype=np.float32))
+        pos = ((wi * pi[0] + wj * pj[0]) / (wi + wj)).astype(np.float32)
+        ls = np.log(np.float32(0.5) * (np.exp(pi[1]) + np.exp(pj[1]))).astype(np.float32)
+        src = pi if li >= lj else pj
+        q = [pos, ls] + [src[g].copy() for g in (2, 3, 4)]
+        rows.append((q, [np.zeros(w, np.float32) for w in widths], [np.zeros(w, np.float32) for w in widths]))
+    f32 = np.float32
+    for i in np.flatnonzero(low):
+        pi = point(i)
+        s = f32(f32(alpha_d) * dbar[i])
+        jit = (f32(2.0) * u[i] - f32(1.0)).astype(np.float32)
+        pos = ((means[i] + (s * z[i]).astype(np.float32)).astype(np.float32)
+               + (f32(delta) * jit).astype(np.float32)).astype(np.float32)
+        q = [pos] + [pi[g].copy() for g in (1, 2, 3, 4)]
+        rows.append((q, [np.zeros(w, np.float32) for w in widths], [np.zeros(w, np.float32) for w in widths]))
+    pad = (-len(rows)) % 4 if rows else 0
+    for _ in range(pad):
+        q = [g.copy() for g in rows[0][0]]
+        q[3] = np.array([-30.0], np.float32)
+        rows.append((q, [np.zeros(w, np.float32) for w in widths], [np.zeros(w, np.float32) for w in widths]))
+    n2 = len(rows)
+    outs = []
+    for which in range(3):
+        parts = [np.stack([row[which][g] for row in rows]).ravel() if n2 else np.zeros(0, np.float32)
+                 for g in range(5)]
+        outs.append(np.concatenate(parts).astype(np.float32))
+    info = dict(rho=rho, dbar=dbar, nn=nn, dnn=dnn, rho_low=lo, rho_high=hi, d_merge=dm,
+                low=low, high=high, head=head, gone=gone, n_keep=int(keep.sum()),
+                n_merged=int(head.sum()), n_new=int(low.sum()), pad=pad)
+    return outs[0], outs[1], outs[2], n2, info

@@ -191,6 +191,15 @@ def random_cotangent(shape, seed: int = 7) -> np.ndarray:
     return rng.normal(0.0, 1.0, size=shape).astype(np.float32)
 
 
+def density_draws(n: int, seed: int = 11):
+    """Seeded random draws of one density-control round: per point three
+    standard normals z and three uniforms u in [0, 1) (float32, [n, 3] each)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z = rng.normal(0.0, 1.0, size=(n, 3)).astype(np.float32)
+    u = rng.random(size=(n, 3), dtype=np.float32)
+    return z, u
+
+
 # ---------------------------------------------------------------------------
 # Named workloads (sizes and structure only).
 # ---------------------------------------------------------------------------

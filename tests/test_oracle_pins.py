@@ -619,3 +619,120 @@ def test_screen_grad_norm_by_hand():
     g[0, 1, :2] = (0, -2)
     g[:, :, 2:] = 7.0
     assert np.allclose(O.screen_grad_norm(g.ravel(), 2, 2), [5 + 13, 2])
+
+
+# -- workload-sensitive density control (Sec. III-C) -------------------------
+
+def _line_points():
+    # binary-exact coordinates: distances 0.125, 0.25, 0.75, 0.875 are exact
+    return np.array([[0.0, 0, 0], [0.125, 0, 0], [0.25, 0, 0], [1.0, 0, 0]], np.float32)
+
+
+def test_density_stats_on_a_line_by_hand():
+    rho, dbar, nn, dnn = O.density_stats(_line_points(), r=0.2, k=2)
+    assert rho.tolist() == [1, 2, 1, 0]
+    assert dbar.tolist() == [0.1875, 0.125, 0.1875, 0.8125]
+    assert nn.tolist() == [1, 0, 1, 2]                 # point 1: two at 0.125, the lower index wins
+    assert dnn.tolist() == [0.125, 0.125, 0.125, 0.75]
+
+
+def test_density_thresholds_closed_form():
+    rho = np.array([1, 2, 1, 0])
+    dnn = np.array([0.125, 0.125, 0.125, 0.75], np.float32)
+    lo, hi, dm = O.density_thresholds(rho, dnn, alpha=1.0, beta=2.0, gamma=0.5)
+    sd = np.sqrt(6 / 4 - 1.0)
+    assert np.isclose(lo, 1 - sd, rtol=0, atol=1e-15) and np.isclose(hi, 1 + 2 * sd, rtol=0, atol=1e-15)
+    mu_d = 1.125 / 4
+    sd_d = np.sqrt((3 * 0.125 ** 2 + 0.75 ** 2) / 4 - mu_d ** 2)
+    assert np.isclose(dm, mu_d + 0.5 * sd_d, rtol=0, atol=1e-15)
+
+
+def test_density_stats_on_a_cubic_lattice():
+    a = 0.5
+    g = np.arange(5, dtype=np.float32) * np.float32(a)
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    rho, dbar, nn, dnn = O.density_stats(P, r=0.6, k=6)
+    idx = np.arange(125).reshape(5, 5, 5)
+    inner = idx[1:4, 1:4, 1:4].ravel()
+    assert np.all(rho[inner] == 6)                     # the six face neighbours
+    assert np.all(dbar[inner] == np.float32(a))
+    corner = idx[0, 0, 0]
+    assert rho[corner] == 3
+    assert np.all(dnn == np.float32(a))
+
+
+def _two_clusters(n_dense=40, n_far=6, seed=0, n_core=20):
+    """A tight core inside a looser cluster (high densities there) and a few
+    far, isolated points (density 0)."""
+    rng = np.random.default_rng(seed)
+    core = rng.normal(0.0, 0.003, (n_core, 3))
+    dense = rng.normal(0.0, 0.02, (n_dense, 3))
+    far = rng.uniform(-1, 1, (n_far, 3)) + np.array([3.0, 0, 0])
+    return np.concatenate([core, dense, far]).astype(np.float32)
+
+
+def test_density_control_formulas_by_hand():
+    P = _two_clusters()
+    n = len(P)
+    rng = np.random.default_rng(1)
+    flat = rng.normal(0, 1, 59 * n).astype(np.float32)
+    flat[:3 * n] = P.ravel()
+    m = rng.normal(0, 1, 59 * n).astype(np.float32)
+    v = rng.random(59 * n).astype(np.float32)
+    z = rng.normal(0, 1, (n, 3)).astype(np.float32)
+    u = rng.random((n, 3)).astype(np.float32)
+    r, k, ad, delta = 0.03, 3, 1.5, 0.01
+    p2, m2, v2, n2, info = O.density_control(flat, m, v, n, r, k, 1.0, 1.0, ad, delta, 1.0, z, u)
+    # every far point is alone within r: rho 0 < rho_low, so each spawns one point
+    assert info["low"][60:].all() and info["n_new"] >= 6
+    assert info["n_merged"] > 0
+    assert n2 == info["n_keep"] + info["n_merged"] + info["n_new"] + info["pad"] and n2 % 4 == 0
+    G = lambda a, cnt: np.split(a, np.cumsum([3 * cnt, 3 * cnt, 4 * cnt, cnt]))
+    out = G(p2, n2)
+    mo, vo = G(m2, n2), G(v2, n2)
+    means2 = out[0].reshape(n2, 3)
+    # untouched points come first, unchanged, with their moments
+    keep = np.flatnonzero(~(info["head"] | info["gone"]))
+    assert np.array_equal(means2[:len(keep)], P[keep])
+    assert np.array_equal(mo[4].reshape(n2, 48)[:len(keep)], m[11 * n:].reshape(n, 48)[keep])
+    # merged points: opacity-weighted centroid, log of the mean scale, zero moments
+    heads = np.flatnonzero(info["head"])
+    i = heads[0]
+    j = int(info["nn"][i])
+    lg = flat[10 * n:11 * n].astype(np.float64)
+    w = 1 / (1 + np.exp(-lg))
+    want = (w[i] * P[i] + w[j] * P[j]) / (w[i] + w[j])
+    got = means2[len(keep)]
+    assert np.allclose(got, want, rtol=0, atol=1e-6)
+    ls = flat[3 * n:6 * n].reshape(n, 3).astype(np.float64)
+    assert np.allclose(out[1].reshape(n2, 3)[len(keep)], np.log((np.exp(ls[i]) + np.exp(ls[j])) / 2), atol=1e-6)
+    better = i if lg[i] >= lg[j] else j
+    assert np.array_equal(out[4].reshape(n2, 48)[len(keep)], flat[11 * n:].reshape(n, 48)[better])
+    assert not mo[0].reshape(n2, 3)[len(keep)].any()
+    # new points: p + alpha_d dbar z + delta (2u - 1), the rest copied from the parent
+    first_new = len(keep) + len(heads)
+    lows = np.flatnonzero(info["low"])
+    a = lows[0]
+    want = P[a].astype(np.float64) + ad * float(info["dbar"][a]) * z[a] + delta * (2.0 * u[a] - 1.0)
+    assert np.allclose(means2[first_new], want, rtol=0, atol=1e-6)
+    assert np.array_equal(out[4].reshape(n2, 48)[first_new], flat[11 * n:].reshape(n, 48)[a])
+    # padding: invisible copies
+    if info["pad"]:
+        assert out[3][-1] == np.float32(-30.0)
+
+
+def test_density_control_merges_only_mutual_pairs_in_dense_regions():
+    P = _two_clusters(60, 4, seed=3)
+    n = len(P)
+    flat = np.zeros(59 * n, np.float32)
+    flat[:3 * n] = P.ravel()
+    z = np.zeros((n, 3), np.float32)
+    u = np.full((n, 3), 0.5, np.float32)
+    _, _, _, n2, info = O.density_control(flat, flat * 0, flat * 0, n, 0.03, 3, 1.0, 1.0, 1.5, 0.0, 1.0, z, u)
+    assert info["head"].any() and info["low"].any()
+    for i in np.flatnonzero(info["head"]):
+        j = info["nn"][i]
+        assert info["nn"][j] == i and info["high"][i] and info["high"][j] and j > i
+        assert info["dnn"][i] <= info["d_merge"]
+    assert not (info["head"] & info["gone"]).any()
+    assert not (info["low"] & (info["head"] | info["gone"])).any()
