@@ -533,6 +533,76 @@ def run_colour_ablation(args):
     print(json.dumps(out), flush=True)
 
 
+def run_density_control(args):
+    """One round of workload-sensitive density control (Sec. III-C) on the
+    benchmark scene: local densities within r, thresholds, k-nearest
+    dispersion, spawned and merged Gaussians written into buffers of the new
+    count.  Reports ms per round and for the statistics alone (CUDA events),
+    the classes' sizes and the thresholds."""
+    import torch
+
+    from paper_2510_14564_gb300 import _lib as L
+    from paper_2510_14564_gb300 import scenes as S
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    L.lib()
+    scene, _ = S.make_workload(args.workload, seed=0)
+    N = scene.n
+    r, k, alpha_d, delta = args.density_r, 3, 1.5, 0.2 * args.density_r
+    p = torch.from_numpy(scene.flat()).cuda()
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    z, u = (torch.from_numpy(a.ravel()).cuda() for a in S.density_draws(N))
+    cap = 2 * N + 3
+    p2 = torch.empty(59 * cap, device="cuda")
+    m2, v2 = torch.empty_like(p2), torch.empty_like(p2)
+    sh = torch.empty(48 * cap, dtype=torch.bfloat16, device="cuda")
+    n_out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    thr = torch.zeros(3, dtype=torch.float64, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(L.gs_density_workspace(N) // 4 + 64, dtype=torch.float32, device="cuda")
+    rho = torch.empty(N, dtype=torch.int32, device="cuda")
+    nn = torch.empty_like(rho)
+    dbar = torch.empty(N, device="cuda")
+    dnn = torch.empty_like(dbar)
+
+    def control():
+        L.gs_density_control(N, p, m, v, z, u, r, k, 1.0, 1.0, alpha_d, delta, 1.0, cap, p2, m2, v2, sh,
+                             L.GS_BF16, n_out, thr, ws, err)
+
+    def stats():
+        L.gs_density_stats(N, p, r, k, rho, dbar, nn, dnn, (1.0, 1.0, 1.0), thr, ws)
+
+    st = torch.cuda.current_stream()
+    res = {}
+    for name, fn in (("round", control), ("stats", stats)):
+        for _ in range(args.warmup):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(args.steps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(b) / args.steps
+    assert int(err.item()) == 0
+    lo, hi, dm = (float(x) for x in thr.cpu())
+    rh = rho.cpu().numpy()
+    out = {
+        "metric": "density-control round ms (densities, thresholds, kNN dispersion, spawn and merge)",
+        "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+        "data": "synthetic (seeded skewed-density scene; seeded normal and uniform draws)",
+        "config": {"workload": args.workload, "gaussians": N, "r": r, "k": k, "alpha": 1.0, "beta": 1.0,
+                   "gamma": 1.0, "alpha_d": alpha_d, "delta": delta},
+        "round_ms": round(res["round"], 3), "stats_ms": round(res["stats"], 3),
+        "gaussians_out": int(n_out.item()), "rho_low": lo, "rho_high": hi, "d_merge": dm,
+        "low": int((rh < lo).sum()), "high": int((rh > hi).sum()), "rho_mean": float(rh.mean()),
+        "rho_max": int(rh.max()),
+    }
+    print(json.dumps(out), flush=True)
+
+
 def schedule_diagnostics(f, L, torch, reps=5) -> dict:
     """Render makespans (best of `reps`, ms) of the forward and backward
     passes under the raster, count and learned tile orders (orders computed
@@ -719,12 +789,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--colour-ablation", action="store_true",
                     help="time the forward pass under four colour layouts (prints its own JSON line)")
+    ap.add_argument("--density-control", action="store_true",
+                    help="time one round of workload-sensitive density control (prints its own JSON line)")
+    ap.add_argument("--density-r", type=float, default=0.005, help="neighbour radius of the density control")
     ap.add_argument("--lr-scale", type=float, default=1e-3,
                     help="scale of the Adam learning rates (keeps the scene fixed over the run)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    if args.colour_ablation:
+    if args.density_control:
+        args.steps = 10 if args.steps is None else args.steps
+        run_density_control(args)
+    elif args.colour_ablation:
         args.steps = 20 if args.steps is None else args.steps
         run_colour_ablation(args)
     elif args.impl == "reference":

@@ -386,6 +386,54 @@ int gs_densify(int N, const float *d_params, const float *d_m, const float *d_v,
                int shadow_dtype, int32_t *d_n_out, void *d_workspace, size_t workspace_bytes,
                int *d_err_word, gs_stream_t stream);
 
+/* Workload-sensitive density control (Sec. III-C), one round.  Positions are
+ * the first 3N floats of the grouped layout ([N, 3], finite).  Squared
+ * distances are (dx^2 + dy^2) + dz^2 in FP32 with every operation rounded.
+ *
+ * gs_density_stats: per point, the local density rho (other points with
+ * squared distance <= fl(r * r), Sec. III-C1), the mean distance d_bar to the
+ * k nearest other points (1 <= k <= 8; the k smallest distances added in
+ * ascending order, then divided by k; fewer when fewer points exist, 0 with
+ * none, Sec. III-C2), the nearest other point (ties to the lower index; -1
+ * with none) and its distance.  With d_thresholds (device, 3 doubles) and
+ * thr_params (host, 3 floats: alpha, beta, gamma >= 0) it also writes, in
+ * FP64, rho_low = mu - alpha sigma and rho_high = mu + beta sigma (mu, sigma
+ * the mean and population standard deviation of rho, from exact integer
+ * sums) and d_merge = mu_d + gamma sigma_d over the nearest-neighbour
+ * distances (Sec. III-C3; summed in FP64 in no fixed order).
+ *
+ * gs_density_control: from N Gaussians (grouped layout; moments d_m, d_v the
+ * same; draws d_z ~ N(0,1) and d_u ~ U[0,1), [N, 3] each):
+ *   - a point with rho < rho_low spawns one point at
+ *     p + (alpha_d d_bar) z + delta (2u - 1), every other parameter copied;
+ *   - a point with rho > rho_high whose nearest neighbour is also above
+ *     rho_high, has it as its own nearest neighbour and lies within d_merge
+ *     merges with it: position = opacity-weighted centroid (weights
+ *     sigmoid(logit)), log-scale = log(mean of the two scales) per axis, the
+ *     rest from the larger logit (ties to the lower index);
+ *   - output, grouped layout of the new count n2 in d_params_out, d_m_out,
+ *     d_v_out (and the SH group in d_sh_shadow_out as [n2,16,3] of
+ *     shadow_dtype, if given): untouched points in index order, merged points
+ *     in the order of their lower index, spawned points in the order of their
+ *     parents, then copies of output point 0 with logit -30 up to a multiple
+ *     of 4; merged, spawned and padding points have zero moments.
+ * n2 goes to *d_n_out (device); rho_low, rho_high, d_merge to d_thresholds if
+ * given.  capacity (Gaussians) bounds n2 (2N + 3 always suffices); beyond it
+ * GS_EW_CAPACITY is set, *d_n_out = 0 and nothing is written.  Outputs must
+ * not alias inputs.  d_workspace: gs_density_workspace(N) bytes (it holds a
+ * cell table of 2^24 + 1 entries; the grid's cells are at least 1.0001 r and
+ * grow until at most 2^24 cover the points' bounding box). */
+int gs_density_workspace(int N, size_t *bytes);
+int gs_density_stats(int N, const float *d_means, float r, int k, int32_t *d_rho, float *d_dbar,
+                     int32_t *d_nn, float *d_dnn, const float *thr_params, double *d_thresholds,
+                     void *d_workspace, size_t workspace_bytes, gs_stream_t stream);
+int gs_density_control(int N, const float *d_params, const float *d_m, const float *d_v,
+                       const float *d_z, const float *d_u, float r, int k, float alpha, float beta,
+                       float alpha_d, float delta, float gamma, long long capacity,
+                       float *d_params_out, float *d_m_out, float *d_v_out, void *d_sh_shadow_out,
+                       int shadow_dtype, int32_t *d_n_out, double *d_thresholds, void *d_workspace,
+                       size_t workspace_bytes, int *d_err_word, gs_stream_t stream);
+
 /* a8. Learned tile-cost scheduler.  The paper balances rendering work by a
  * region density rho = active Gaussians / pixels (Sec. IV-C2); here a small
  * MLP predicts each tile's render cost from eight tile statistics and the

@@ -419,7 +419,13 @@ def density_stats(means, r, k, chunk=512):
         rho[rows] = (d2 <= r2).sum(axis=1)
         if kk <= 0:
             continue
-        order = np.argsort(d2, axis=1, kind="stable")[:, :kk]    # ties by index
+        # the kk smallest by (distance, index): every entry up to the kk-th
+        # smallest value is a candidate, ordered by value then index
+        kth = np.partition(d2, kk - 1, axis=1)[:, kk - 1]
+        order = np.empty((len(rows), kk), np.int64)
+        for t in range(len(rows)):
+            cand = np.flatnonzero(d2[t] <= kth[t])
+            order[t] = cand[np.lexsort((cand, d2[t, cand]))][:kk]
         near = np.sqrt(np.take_along_axis(d2, order, axis=1)).astype(np.float32)
         acc = np.zeros(len(rows), np.float32)
         for j in range(kk):
@@ -428,6 +434,24 @@ def density_stats(means, r, k, chunk=512):
         nn[rows] = order[:, 0]
         dnn[rows] = near[:, 0]
     return rho, dbar, nn, dnn
+
+
+def density_point(means, i, r, k):
+    """density_stats for the single point i against every point (for sampled
+    checks of large inputs): (rho, d_bar, nearest index, nearest distance)."""
+    P = np.ascontiguousarray(means, np.float32)
+    d2 = _pair_d2(P, np.array([i]))[0]
+    d2[i] = np.inf
+    r2 = np.float32(np.float32(r) * np.float32(r))
+    kk = min(k, len(P) - 1)
+    if kk <= 0:
+        return int((d2 <= r2).sum()), np.float32(0), -1, np.float32(0)
+    order = np.lexsort((np.arange(len(P)), d2))[:kk]
+    near = np.sqrt(d2[order]).astype(np.float32)
+    acc = np.float32(0)
+    for x in near:
+        acc = np.float32(acc + x)
+    return int((d2 <= r2).sum()), np.float32(acc / np.float32(kk)), int(order[0]), near[0]
 
 
 def density_thresholds(rho, dnn, alpha, beta, gamma):

@@ -33,7 +33,8 @@ EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_project", "gs_bin
            "gs_adam_flat", "gs_tile_features", "gs_mlp_predict", "gs_mlp_grad",
            "gs_mlp_train_step", "gs_rank_judge", "gs_int_cost", "gs_range_cost", "gs_sched_order_workspace",
            "gs_sched_order", "gs_grad2d_norm", "gs_densify_workspace", "gs_densify",
-           "gs_colour_arrays", "gs_render_fwd_colour"]
+           "gs_colour_arrays", "gs_render_fwd_colour", "gs_density_workspace", "gs_density_stats",
+           "gs_density_control"]
 
 
 class GsError(RuntimeError):
@@ -107,6 +108,10 @@ def lib():
         L.gs_sched_order.argtypes = [VP, I32, VP, VP, SZ, VP]
         L.gs_grad2d_norm.argtypes = [I32, I32, VP, VP, VP]
         L.gs_colour_arrays.argtypes = [I64, VP, VP, VP, VP]
+        L.gs_density_workspace.argtypes = [I32, P(SZ)]
+        L.gs_density_stats.argtypes = [I32, VP, F32, I32, VP, VP, VP, VP, P(F32), VP, VP, SZ, VP]
+        L.gs_density_control.argtypes = [I32, VP, VP, VP, VP, VP, F32, I32, F32, F32, F32, F32, F32, I64, VP, VP,
+                                         VP, VP, I32, VP, VP, VP, SZ, VP, VP]
         L.gs_render_fwd_colour.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, I32, VP, VP, VP, VP, VP]
         L.gs_densify_workspace.argtypes = [I32, P(SZ)]
         L.gs_densify.argtypes = [I32, VP, VP, VP, VP, F32, I32, I64, VP, VP, VP, VP, I32, VP, VP, SZ, VP, VP]
@@ -335,6 +340,32 @@ def gs_render_fwd_colour(cams, N, tile_ranges, vals, splats, layout, colour, img
     check(lib().gs_render_fwd_colour(ca, len(cams), int(N), ptr(tile_ranges), ptr(vals), ptr(splats), int(layout),
                                      ptr(colour), ptr(img), ptr(T_final), ptr(n_proc), stream_ptr(stream)),
           "gs_render_fwd_colour")
+
+
+def gs_density_workspace(N) -> int:
+    out = SZ(0)
+    check(lib().gs_density_workspace(int(N), ctypes.byref(out)), "gs_density_workspace")
+    return int(out.value)
+
+
+def gs_density_stats(N, means, r, k, rho, dbar, nn, dnn, thr_params=None, thresholds=None, workspace=None,
+                     stream=None):
+    tp = (F32 * 3)(*[float(x) for x in thr_params]) if thr_params is not None else None
+    check(lib().gs_density_stats(int(N), ptr(means), float(r), int(k), ptr(rho), ptr(dbar), ptr(nn), ptr(dnn), tp,
+                                 ptr(thresholds), ptr(workspace),
+                                 workspace.numel() * workspace.element_size() if workspace is not None else 0,
+                                 stream_ptr(stream)), "gs_density_stats")
+
+
+def gs_density_control(N, params, m, v, z, u, r, k, alpha, beta, alpha_d, delta, gamma, capacity, params_out,
+                       m_out, v_out, sh_shadow_out, shadow_dtype, n_out, thresholds, workspace, err_word,
+                       stream=None):
+    check(lib().gs_density_control(int(N), ptr(params), ptr(m), ptr(v), ptr(z), ptr(u), float(r), int(k),
+                                   float(alpha), float(beta), float(alpha_d), float(delta), float(gamma),
+                                   int(capacity), ptr(params_out), ptr(m_out), ptr(v_out), ptr(sh_shadow_out),
+                                   int(shadow_dtype), ptr(n_out), ptr(thresholds), ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), ptr(err_word),
+                                   stream_ptr(stream)), "gs_density_control")
 
 
 def gs_tile_features(cams, tile_ranges, vals, splats, rgb_dtype, cap, feats, w16=None, pred=None,
