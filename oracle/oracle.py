@@ -559,3 +559,44 @@ def density_control(flat, m, v, n, r, k, alpha, beta, alpha_d, delta, gamma, z, 
                 low=low, high=high, head=head, gone=gone, n_keep=int(keep.sum()),
                 n_merged=int(head.sum()), n_new=int(low.sum()), pad=pad)
     return outs[0], outs[1], outs[2], n2, info
+
+
+# ---------------------------------------------------------------------------
+# Colour hashing of the Gaussians listed per 16x16 tile (Sec. IV-C1).
+# ---------------------------------------------------------------------------
+
+def colour_bucket(rgb):
+    """Bucket of each colour: every channel to 8 bits as floor(fl32(fl32(c *
+    255) + 0.5)) clamped to [0, 255], quantised to c_q = floor(c8 / 256 * 16)
+    (16 levels), hash = R_q * 256 + G_q * 16 + B_q in [0, 4095]."""
+    c = np.asarray(rgb, np.float32)
+    c8 = np.floor((c * np.float32(255.0)).astype(np.float32) + np.float32(0.5)).astype(np.int64)
+    c8 = np.clip(c8, 0, 255)
+    q = np.floor(c8 / 256.0 * 16.0).astype(np.int64)
+    return q[..., 0] * 256 + q[..., 1] * 16 + q[..., 2]
+
+
+def colour_buckets(ranges, vals, rgb, lo):
+    """Bucket-wise aggregation over every tile's list (Sec. IV-C1): per bucket
+    the number of (tile, Gaussian) entries, the sums of their colours and of
+    their opacities 2^lo (FP64), and per tile the number of distinct buckets
+    among its entries."""
+    ranges = np.asarray(ranges, np.int64).reshape(-1, 2)
+    vals = np.asarray(vals, np.int64)
+    h_all = colour_bucket(rgb)
+    count = np.zeros(4096, np.int64)
+    sums = np.zeros((4, 4096), np.float64)
+    distinct = np.zeros(len(ranges), np.int64)
+    rgb64 = np.asarray(rgb, np.float32).astype(np.float64)
+    op = np.exp2(np.asarray(lo, np.float32).astype(np.float64))
+    for t, (a, b) in enumerate(ranges):
+        ids = vals[a:b]
+        if len(ids) == 0:
+            continue
+        h = h_all[ids]
+        np.add.at(count, h, 1)
+        for ch in range(3):
+            np.add.at(sums[ch], h, rgb64[ids, ch])
+        np.add.at(sums[3], h, op[ids])
+        distinct[t] = len(np.unique(h))
+    return count, sums, distinct

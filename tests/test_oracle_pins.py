@@ -736,3 +736,32 @@ def test_density_control_merges_only_mutual_pairs_in_dense_regions():
         assert info["dnn"][i] <= info["d_merge"]
     assert not (info["head"] & info["gone"]).any()
     assert not (info["low"] & (info["head"] | info["gone"])).any()
+
+
+# -- colour hashing (Sec. IV-C1) ---------------------------------------------
+
+def test_colour_quantisation_matches_the_formula_and_bounds():
+    c8 = np.arange(256)
+    rgb = np.stack([c8, c8, c8], -1).astype(np.float32) / np.float32(255.0)
+    h = O.colour_bucket(rgb)
+    q = c8 >> 4                                          # floor(c / 256 * 16) for 8-bit c
+    assert np.array_equal(h, q * 256 + q * 16 + q)
+    assert O.colour_bucket(np.array([1.0, 1.0, 1.0], np.float32)) == 4095      # c = 255 -> 15
+    assert O.colour_bucket(np.array([0.0, 0.0, 0.0], np.float32)) == 0
+    assert O.colour_bucket(np.array([2.0, -1.0, 0.5], np.float32)) == 15 * 256 + 0 + 8   # clamped; 0.5 -> 128 -> 8
+    rng = np.random.default_rng(0)
+    hh = O.colour_bucket(rng.uniform(-0.5, 1.5, (10000, 3)).astype(np.float32))
+    assert hh.min() >= 0 and hh.max() <= 4095
+
+
+def test_colour_buckets_by_hand():
+    rgb = np.array([[1.0, 0.0, 0.0], [0.99, 0.01, 0.02], [0.0, 0.0, 1.0]], np.float32)
+    lo = np.array([-1.0, -2.0, 0.0], np.float32)        # opacities 0.5, 0.25, 1
+    ranges = np.array([[0, 3], [3, 3], [3, 5]])
+    vals = np.array([0, 1, 2, 1, 1])
+    count, sums, distinct = O.colour_buckets(ranges, vals, rgb, lo)
+    red, blue = 15 * 256, 15
+    assert count[red] == 4 and count[blue] == 1 and count.sum() == 5
+    assert np.isclose(sums[0, red], 1.0 + 3 * 0.99) and np.isclose(sums[3, red], 0.5 + 3 * 0.25)
+    assert np.isclose(sums[3, blue], 1.0)
+    assert distinct.tolist() == [2, 0, 1]
