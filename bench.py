@@ -603,6 +603,63 @@ def run_density_control(args):
     print(json.dumps(out), flush=True)
 
 
+def run_colour_buckets(args):
+    """Colour hashing of the tile lists (Sec. IV-C1) on the benchmark view:
+    the full lists and the kept prefixes of a training step (16-bit records),
+    each hashed into the 4096 buckets.  Reports ms (CUDA events), entries per
+    second, the mean number of distinct buckets per non-empty tile and the
+    share of entries whose tile holds another entry of the same bucket."""
+    import torch
+
+    from paper_2510_14564_gb300 import _lib as L
+    from paper_2510_14564_gb300 import pipeline as P
+    from paper_2510_14564_gb300 import scenes as S
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    L.lib()
+    scene, cams = S.make_workload(args.workload, seed=0)
+    N = scene.n
+    views = P.param_views(P.to_device_params(scene), N)
+    st = torch.cuda.current_stream()
+    res = {}
+    for name, prefix in (("full_lists", False), ("kept_prefixes", True)):
+        fr = P.Frame(cams, N, rgb_dtype=L.GS_BF16, prefix=prefix)
+        fr.project(views)
+        fr.bin_sort()
+        if prefix:                     # a step's history: prefixes cut at twice the processed counts
+            fr.render()
+            fr.bin_sort()
+        count = torch.zeros(4096, dtype=torch.int64, device="cuda")
+        sums = torch.zeros(4 * 4096, dtype=torch.float64, device="cuda")
+        distinct = torch.zeros(fr.T, dtype=torch.int32, device="cuda")
+        run = lambda: L.gs_colour_buckets(fr.T, fr.ranges, fr.vals, fr.splats, L.GS_BF16, count, sums, distinct)
+        for _ in range(args.warmup):
+            run()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(args.steps):
+            run()
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        lens = (fr.ranges.view(-1, 2)[:, 1] - fr.ranges.view(-1, 2)[:, 0]).double()
+        d = distinct.double()
+        entries = float(lens.sum())
+        res[name] = {"ms": round(ms, 4), "entries": int(entries),
+                     "entries_per_s": round(entries / (ms / 1e3), 1),
+                     "mean_distinct_buckets_per_tile": round(float(d[lens > 0].mean()), 2),
+                     "share_in_shared_bucket": round(1.0 - float(d.sum()) / max(entries, 1.0), 4)}
+        del fr
+        torch.cuda.empty_cache()
+    out = {"metric": "colour hashing of tile lists (4096 buckets), ms per pass", "unit": "ms",
+           "higher_is_better": False, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+           "data": "synthetic (seeded skewed-density scene, random-init parameters)",
+           "config": {"workload": args.workload, "gaussians": N, "records": "bf16 colour"},
+           "passes": res}
+    print(json.dumps(out), flush=True)
+
+
 def schedule_diagnostics(f, L, torch, reps=5) -> dict:
     """Render makespans (best of `reps`, ms) of the forward and backward
     passes under the raster, count and learned tile orders (orders computed
@@ -789,6 +846,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--colour-ablation", action="store_true",
                     help="time the forward pass under four colour layouts (prints its own JSON line)")
+    ap.add_argument("--colour-buckets", action="store_true",
+                    help="time the colour hashing of the tile lists (prints its own JSON line)")
     ap.add_argument("--density-control", action="store_true",
                     help="time one round of workload-sensitive density control (prints its own JSON line)")
     ap.add_argument("--density-r", type=float, default=0.005, help="neighbour radius of the density control")
@@ -797,7 +856,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    if args.density_control:
+    if args.colour_buckets:
+        args.steps = 10 if args.steps is None else args.steps
+        run_colour_buckets(args)
+    elif args.density_control:
         args.steps = 10 if args.steps is None else args.steps
         run_density_control(args)
     elif args.colour_ablation:

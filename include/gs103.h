@@ -386,6 +386,22 @@ int gs_densify(int N, const float *d_params, const float *d_m, const float *d_v,
                int shadow_dtype, int32_t *d_n_out, void *d_workspace, size_t workspace_bytes,
                int *d_err_word, gs_stream_t stream);
 
+/* Colour hashing of the Gaussians listed per tile (Sec. IV-C1).  For every
+ * entry of every tile's list [d_tile_ranges[t].x, .y) (the lists of
+ * gs_bin_sort or gs_bin_sort_prefix) the colour of its splat record
+ * (rgb_dtype as gs_render_fwd; 16-bit colours widened) goes to 8 bits per
+ * channel as floor(fl32(fl32(c * 255) + 0.5)) clamped to [0, 255], is
+ * quantised to c_q = c8 >> 4 (= floor(c8 / 256 * 16)) and hashed to
+ * R_q * 256 + G_q * 16 + B_q in [0, 4095].  Per bucket, ADDED to d_count
+ * [4096] and d_sums [4, 4096] (sums of R, G, B and of the opacity
+ * 2^lo of the record; the caller zeroes both): the number of entries and the
+ * sums, accumulated per tile in shared memory and then across tiles (FP32
+ * per tile, FP64 across, in no fixed order).  d_tile_distinct [n_tiles]
+ * receives the number of distinct buckets among each tile's entries. */
+int gs_colour_buckets(int n_tiles, const uint32_t *d_tile_ranges, const uint32_t *d_vals,
+                      const void *d_splats, int rgb_dtype, unsigned long long *d_count, double *d_sums,
+                      int32_t *d_tile_distinct, gs_stream_t stream);
+
 /* Workload-sensitive density control (Sec. III-C), one round.  Positions are
  * the first 3N floats of the grouped layout ([N, 3], finite).  Squared
  * distances are (dx^2 + dy^2) + dz^2 in FP32 with every operation rounded.

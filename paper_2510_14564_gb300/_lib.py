@@ -34,7 +34,7 @@ EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_project", "gs_bin
            "gs_mlp_train_step", "gs_rank_judge", "gs_int_cost", "gs_range_cost", "gs_sched_order_workspace",
            "gs_sched_order", "gs_grad2d_norm", "gs_densify_workspace", "gs_densify",
            "gs_colour_arrays", "gs_render_fwd_colour", "gs_density_workspace", "gs_density_stats",
-           "gs_density_control"]
+           "gs_density_control", "gs_colour_buckets"]
 
 
 class GsError(RuntimeError):
@@ -109,6 +109,7 @@ def lib():
         L.gs_grad2d_norm.argtypes = [I32, I32, VP, VP, VP]
         L.gs_colour_arrays.argtypes = [I64, VP, VP, VP, VP]
         L.gs_density_workspace.argtypes = [I32, P(SZ)]
+        L.gs_colour_buckets.argtypes = [I32, VP, VP, VP, I32, VP, VP, VP, VP]
         L.gs_density_stats.argtypes = [I32, VP, F32, I32, VP, VP, VP, VP, P(F32), VP, VP, SZ, VP]
         L.gs_density_control.argtypes = [I32, VP, VP, VP, VP, VP, F32, I32, F32, F32, F32, F32, F32, I64, VP, VP,
                                          VP, VP, I32, VP, VP, VP, SZ, VP, VP]
@@ -366,6 +367,11 @@ def gs_density_control(N, params, m, v, z, u, r, k, alpha, beta, alpha_d, delta,
                                    int(shadow_dtype), ptr(n_out), ptr(thresholds), ptr(workspace),
                                    workspace.numel() * workspace.element_size(), ptr(err_word),
                                    stream_ptr(stream)), "gs_density_control")
+
+
+def gs_colour_buckets(n_tiles, tile_ranges, vals, splats, rgb_dtype, count, sums, tile_distinct, stream=None):
+    check(lib().gs_colour_buckets(int(n_tiles), ptr(tile_ranges), ptr(vals), ptr(splats), int(rgb_dtype), ptr(count),
+                                  ptr(sums), ptr(tile_distinct), stream_ptr(stream)), "gs_colour_buckets")
 
 
 def gs_tile_features(cams, tile_ranges, vals, splats, rgb_dtype, cap, feats, w16=None, pred=None,

@@ -19,7 +19,7 @@ CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 BUILD = PKG / "_build"
 LIB = BUILD / "libgs103.so"
-SOURCES = ["project.cu", "binsort.cu", "render.cu", "train.cu", "sched.cu", "density.cu"]
+SOURCES = ["project.cu", "binsort.cu", "render.cu", "train.cu", "sched.cu", "density.cu", "colour_hash.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
