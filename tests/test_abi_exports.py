@@ -54,3 +54,27 @@ def test_host_only_calls(lib_path):
     assert L.gs_sched_order_workspace(6700) > 6700 * 16
     with pytest.raises(L.GsError):
         L.gs_bin_sort_workspace([cam], -1, 10)
+
+
+def test_host_checks_of_the_later_entry_points(lib_path):
+    """Argument checks that return before any device work (raw calls: the
+    binding's wrappers ask torch for the current stream)."""
+    from paper_2510_14564_gb300 import _lib as L
+    from paper_2510_14564_gb300 import scenes as S
+    lib = L.lib()
+    assert L.gs_densify_workspace(1000) > 4 * 1000 * 6
+    assert L.gs_density_workspace(1000) > 4 * (1 << 24)          # the cell table
+    with pytest.raises(L.GsError):
+        L.gs_density_workspace(-1)
+    z = [None] * 4
+    assert lib.gs_density_stats(10, None, 0.0, 3, *z, None, None, None, 0, None) == L.GS_ERR_ARG   # r > 0
+    assert lib.gs_density_stats(10, None, 0.1, 9, *z, None, None, None, 0, None) == L.GS_ERR_ARG   # k <= 8
+    assert lib.gs_density_stats(10, None, 0.1, 3, *z, None, None, None, 0, None) == L.GS_ERR_ARG   # null buffers
+    assert lib.gs_colour_buckets(1, None, None, None, 7, None, None, None, None) == L.GS_ERR_ARG   # record type
+    assert lib.gs_colour_buckets(0, None, None, None, 0, None, None, None, None) == L.GS_OK        # no tiles
+    cams = L.camera_array([S.front_camera(64, 48)])
+    assert lib.gs_render_fwd_colour(cams, 1, 10, None, None, None, 0, None, None, None, None, None) == L.GS_ERR_ARG
+    assert lib.gs_densify(-1, None, None, None, None, 0.0, 0, 0, None, None, None, None, 1, None, None, 0,
+                          None, None) == L.GS_ERR_ARG
+    assert lib.gs_densify(10, None, None, None, None, 0.0, 0, 100, None, None, None, None, 9, None, None, 0,
+                          None, None) == L.GS_ERR_ARG                # null output count / bad shadow type

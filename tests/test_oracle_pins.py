@@ -765,3 +765,13 @@ def test_colour_buckets_by_hand():
     assert np.isclose(sums[0, red], 1.0 + 3 * 0.99) and np.isclose(sums[3, red], 0.5 + 3 * 0.25)
     assert np.isclose(sums[3, blue], 1.0)
     assert distinct.tolist() == [2, 0, 1]
+
+
+def test_density_point_agrees_with_the_full_statistics():
+    """The per-point form used for sampled checks of large inputs gives the
+    rows of the all-points form, including ties and the nearest index."""
+    P = np.concatenate([_two_clusters(30, 5, seed=7), _line_points()])
+    P = np.concatenate([P, P[:4]])                        # exact duplicates: zero distances, ties
+    rho, dbar, nn, dnn = O.density_stats(P, r=0.03, k=4)
+    for i in (0, 3, 17, 33, 50, 55, len(P) - 1):
+        assert O.density_point(P, i, 0.03, 4) == (rho[i], dbar[i], nn[i], dnn[i])
