@@ -318,6 +318,36 @@ def forward(cam, scene, window=None, margin_alpha=1e-4, margin_T=1e-3) -> dict:
     return r
 
 
+# 16-bit storage formats of the precision path (SH coefficients and colours
+# stored in BF16 or FP16, everything computed from them in wider precision):
+# (significand bits including the implicit one, minimum normal exponent,
+# largest finite value).
+STORAGE_FORMATS = {
+    "bf16": (8, -126, (2.0 - 2.0 ** -7) * 2.0 ** 127),
+    "f16": (11, -14, 65504.0),
+}
+
+
+def round_storage(x, kind: str) -> np.ndarray:
+    """The value a 16-bit storage format holds for x: the nearest value of the
+    format, ties to the even significand (IEEE 754 roundTiesToEven), values
+    beyond the overflow threshold to infinity; returned as float64.
+
+    Written from the definition of a binary floating-point format with p
+    significand bits and minimum exponent emin: below 2^(emin + 1) the
+    spacing is the subnormal one, 2^(emin - p + 1); in [2^e, 2^(e + 1)) it is
+    2^(e - p + 1).  Dividing by that power of two is exact, np.rint rounds
+    half to even, and multiplying back is exact."""
+    p, emin, vmax = STORAGE_FORMATS[kind]
+    x = np.asarray(x, np.float64)
+    _, e = np.frexp(np.abs(x))                 # |x| = m 2^e with m in [0.5, 1)
+    ulp = np.ldexp(1.0, np.maximum(e - 1, emin) - (p - 1))
+    with np.errstate(invalid="ignore", over="ignore"):
+        r = np.rint(x / ulp) * ulp
+        r = np.where(np.abs(r) > vmax, np.copysign(np.inf, x), r)
+    return np.where(np.isfinite(x), r, x)
+
+
 def densify_prune(flat, m, v, grad_norm, n, logit_threshold, n_clone):
     """One densification step of dynamic training (density control, Sec. III-B,
     in its plain clone-and-prune form).  Written out from its definition:

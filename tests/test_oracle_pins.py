@@ -775,3 +775,65 @@ def test_density_point_agrees_with_the_full_statistics():
     rho, dbar, nn, dnn = O.density_stats(P, r=0.03, k=4)
     for i in (0, 3, 17, 33, 50, 55, len(P) - 1):
         assert O.density_point(P, i, 0.03, 4) == (rho[i], dbar[i], nn[i], dnn[i])
+
+
+# -- 16-bit storage of the precision path (SH and colours in BF16 / FP16) -----
+
+def _bf16_grid():
+    """Every finite non-negative BF16 value, by enumerating bit patterns (a
+    BF16 value is a binary32 value whose low 16 bits are zero), ascending,
+    with the pattern of each."""
+    bits = np.arange(0, 0x7F80, dtype=np.uint32)
+    return (bits << np.uint32(16)).view(np.float32).astype(np.float64), bits
+
+
+def _nearest_even_on_grid(x, grid, bits):
+    """Brute-force rounding to a sorted grid: the nearer neighbour, on a tie
+    the one whose pattern is even."""
+    i = np.clip(np.searchsorted(grid, x), 1, len(grid) - 1)
+    lo, hi = grid[i - 1], grid[i]
+    dlo, dhi = x - lo, hi - x
+    pick_hi = (dhi < dlo) | ((dhi == dlo) & (bits[i] % 2 == 0))
+    return np.where(pick_hi, hi, lo)
+
+
+def test_bf16_rounding_against_brute_force_on_the_whole_grid():
+    grid, bits = _bf16_grid()
+    rng = np.random.default_rng(0)
+    x = np.concatenate([
+        np.exp(rng.uniform(np.log(1e-40), np.log(3e38), 200_000)),     # every binade, subnormals too
+        rng.uniform(0.0, 4.0, 100_000),                                 # colours and SH
+        (grid[1:-1] + grid[2:]) / 2,                                    # every exact midpoint: ties
+    ])
+    x = x[x < grid[-1]]
+    want = _nearest_even_on_grid(x, grid, bits)
+    assert np.array_equal(O.round_storage(x, "bf16"), want)
+    assert np.array_equal(O.round_storage(-x, "bf16"), -want)          # symmetric
+    assert np.array_equal(O.round_storage(grid, "bf16"), grid)         # representable values stay
+
+
+def test_bf16_rounding_by_hand():
+    r = lambda v: float(O.round_storage(v, "bf16"))
+    assert r(1.0 + 2.0 ** -8) == 1.0                    # tie, 1.0 has the even significand
+    assert r(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6    # tie, rounds up to the even one
+    assert r(1.0 + 2.0 ** -8 + 2.0 ** -30) == 1.0 + 2.0 ** -7   # just past the tie
+    assert r(0.5 - 2.0 ** -11) == 0.5                   # rounds up across a power of two
+    assert r(3.5e38) == math.inf and r(-3.5e38) == -math.inf
+    assert r(0.0) == 0.0 and math.isnan(r(math.nan))
+
+
+def test_f16_rounding_matches_numpy_half():
+    rng = np.random.default_rng(1)
+    h = np.arange(0, 0x7C00, dtype=np.uint16).view(np.float16).astype(np.float64)   # every finite half
+    x = np.concatenate([
+        np.exp(rng.uniform(np.log(1e-9), np.log(7e4), 200_000)),
+        rng.uniform(0.0, 4.0, 100_000),
+        (h[1:-1] + h[2:]) / 2,                                          # ties
+        [65519.0, 65520.0, 65535.0, 1e5],                               # around overflow
+    ])
+    x = np.concatenate([x, -x])
+    with np.errstate(over="ignore"):
+        want = x.astype(np.float16).astype(np.float64)
+    assert np.array_equal(O.round_storage(x, "f16"), want)
+    assert float(O.round_storage(1.0 + 2.0 ** -11, "f16")) == 1.0      # tie to even
+    assert float(O.round_storage(65520.0, "f16")) == math.inf
