@@ -36,8 +36,9 @@ WORKLOAD = "skewed-3M-1600x1060"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 
 # DRAM bytes (read + write) per Gaussian of the dominant call, from one ncu
-# capture of the full-size workload (profiles/project_bwd_adam_skewed-3M-1600x1060.md).
-# Valid only while the kernel sources hash as they did when captured.
+# capture of the full-size workload (the summary of that capture is kept with
+# the profiles).  Valid only while the kernel sources hash as they did when
+# captured.
 MEASURED_TRAFFIC = {
     "project_bwd_adam": {
         "bytes_per_gaussian": (0.843597 + 0.649045 + 1.872040 + 1.952119) * 1e9 / 3e6,

@@ -102,6 +102,30 @@ const char *gs_strerror(int status);
  * (a host-side counter; thread-safe). */
 long long gs_launch_count(void);
 
+/* Zero n_bytes at d_ptr on the stream (a memset, not a kernel launch): the
+ * accumulating outputs (gs_render_bwd's d_grad2d, gs_render_fwd's
+ * d_flag_count, gs_rank_judge's d_out, gs_grad2d_norm's d_out) start from
+ * zero.  d_ptr NULL with n_bytes > 0: GS_ERR_ARG. */
+int gs_zero(void *d_ptr, size_t n_bytes, gs_stream_t stream);
+
+/* Bounded device waits (no paper counterpart: a property of this library).
+ * The depth sort inside gs_bin_sort, gs_bin_sort_noalloc and
+ * gs_bin_sort_prefix is a onesweep radix sort: each 4096-key tile of a digit
+ * pass reads the digit counts of earlier tiles from status words those tiles
+ * publish (decoupled look-back).  A tile reads at most `reads` status words
+ * per digit; past that it gives up, sets GS_EW_TIMEOUT in *err_word and goes
+ * on with the counts it has.  The call then completes with an unspecified
+ * instance order, but every buffer it leaves still holds record indices in
+ * [0, V*N) and every count is consistent with them, so no later kernel reads
+ * or writes out of bounds.  A healthy look-back makes a few hundred reads at
+ * most; 0 makes every tile but the first give up at once (how the tests
+ * reach this path without a stuck GPU).  The limit is process-wide and
+ * applies to calls made after gs_set_wait_limit returns; reads < 0 returns
+ * GS_ERR_ARG.  gs_get_wait_limit returns the limit in force. */
+#define GS_WAIT_LIMIT_DEFAULT (1LL << 20)
+int gs_set_wait_limit(long long reads);
+long long gs_get_wait_limit(void);
+
 /* a1. Projection and SH colour (Sec. II-A projection equation).
  * In:  N Gaussians' parameters (grouped layout above; d_sh may instead be a
  *      separate [N,16,3] array of dtype sh_dtype = GS_F32, GS_BF16 or GS_F16).

@@ -27,7 +27,7 @@ GS_MAX_VIEWS = 64
 SPLAT_BYTES = {GS_F32: 48, GS_BF16: 32, GS_F16: 32}
 
 # Every symbol include/gs103.h declares.
-EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_bin_sort_noalloc",
+EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_set_wait_limit", "gs_get_wait_limit", "gs_zero", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_bin_sort_noalloc",
            "gs_bin_sort_prefix_workspace", "gs_bin_sort_prefix", "gs_bin_sort_prefix_repair",
            "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_project_bwd", "gs_project_bwd_adam", "gs_adam_step",
            "gs_adam_flat", "gs_tile_features", "gs_mlp_predict", "gs_mlp_grad",
@@ -75,6 +75,9 @@ def lib():
         P = ctypes.POINTER
         L.gs_version.restype = I32
         L.gs_launch_count.restype = I64
+        L.gs_set_wait_limit.argtypes = [I64]
+        L.gs_zero.argtypes = [VP, SZ, VP]
+        L.gs_get_wait_limit.restype = I64
         L.gs_strerror.restype = ctypes.c_char_p
         L.gs_strerror.argtypes = [I32]
         L.gs_project.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, VP, VP, I32, VP, I32, VP, VP, VP,
@@ -117,7 +120,7 @@ def lib():
         L.gs_densify_workspace.argtypes = [I32, P(SZ)]
         L.gs_densify.argtypes = [I32, VP, VP, VP, VP, F32, I32, I64, VP, VP, VP, VP, I32, VP, VP, SZ, VP, VP]
         for name in EXPORTS:
-            if name not in ("gs_version", "gs_strerror", "gs_launch_count"):
+            if name not in ("gs_version", "gs_strerror", "gs_launch_count", "gs_get_wait_limit"):
                 getattr(L, name).restype = I32
         _lib = L
     return _lib
@@ -176,6 +179,19 @@ def gs_strerror(status: int) -> str:
 
 def gs_launch_count() -> int:
     return int(lib().gs_launch_count())
+
+
+def gs_zero(t, stream=None) -> None:
+    """Zero a tensor's bytes on the stream (cudaMemsetAsync in the library)."""
+    check(lib().gs_zero(ptr(t), t.numel() * t.element_size(), stream_ptr(stream)), "gs_zero")
+
+
+def gs_set_wait_limit(reads: int) -> None:
+    check(lib().gs_set_wait_limit(int(reads)), "gs_set_wait_limit")
+
+
+def gs_get_wait_limit() -> int:
+    return int(lib().gs_get_wait_limit())
 
 
 def gs_project(cams, N, means, log_scales, quats, opacity_logits, sh, sh_dtype, splats, rgb_dtype,

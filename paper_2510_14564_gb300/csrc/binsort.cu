@@ -12,6 +12,7 @@
 // Stability carries the depth order (and the index order of equal depths)
 // through step 4, so the result equals the 64-bit sort.  Tile ranges come
 // from the boundaries of the sorted tile ids.
+#include <atomic>
 #include <mutex>
 
 #include "gs_common.cuh"
@@ -163,7 +164,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_downsweep(
 constexpr uint32_t kLbAgg = 1u << 30;            // status word: tile's own count is ready
 constexpr uint32_t kLbPre = 2u << 30;            // status word: inclusive prefix is ready
 constexpr uint32_t kLbVal = (1u << 30) - 1u;
-constexpr int kLbSpinLimit = 1 << 20;
+
+// Status-word reads a tile may make in one digit's look-back before it gives
+// up (gs_set_wait_limit).  A healthy look-back reads a few hundred at most.
+static std::atomic<long long> g_wait_limit{GS_WAIT_LIMIT_DEFAULT};
 
 __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(256) k_onesweep_hist(const uint32_t *__restric
 __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, uint32_t n, int shift, const uint32_t *__restrict__ ghist,
-    uint32_t *status, uint32_t *tile_counter, int *err_word) {
+    uint32_t *status, uint32_t *tile_counter, long long wait_limit, int *err_word) {
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_wh[8][kRadix];
@@ -245,15 +249,15 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
         const uint32_t gbase = block_excl_scan_256(__ldg(ghist + d), s_warp2);
         uint32_t excl = 0;
         if (bid > 0) {
-            long long j = (long long)bid - 1;
-            int spins = 0;
+            long long j = (long long)bid - 1, reads = 0;
             while (j >= 0) {
+                // bounded: after wait_limit reads the tile goes on with the
+                // counts it has (an unspecified order, still a set of valid
+                // record indices) and reports GS_EW_TIMEOUT
+                if (++reads > wait_limit) { set_err(err_word, GS_EW_TIMEOUT); break; }
                 const uint32_t v = ld_relaxed(status + (size_t)j * kRadix + d);
                 const uint32_t f = v & ~kLbVal;
-                if (f == 0u) {
-                    if (++spins > kLbSpinLimit) { set_err(err_word, GS_EW_TIMEOUT); break; }
-                    continue;
-                }
+                if (f == 0u) continue;
                 excl += v & kLbVal;
                 if (f == kLbPre) break;
                 --j;
@@ -427,12 +431,17 @@ static void exclusive_scan(const Tin *in, Tout *out, long long n, Tout *partials
 // ---------------------------------------------------------------------------
 // Binning kernels
 // ---------------------------------------------------------------------------
+// Depth keys and record indices of the depth sort.  The indices go to both
+// value buffers of the sort's ping-pong, so that every value buffer holds
+// record indices only, whatever a sort cut short by a timeout leaves there.
 __global__ void k_depth_keys(const float *__restrict__ depth, const int *__restrict__ touched,
-                             long long n, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                             long long n, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                             uint32_t *__restrict__ vals2) {
     long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     keys[j] = touched[j] > 0 ? __float_as_uint(depth[j]) : 0xffffffffu;
     vals[j] = (uint32_t)j;
+    vals2[j] = (uint32_t)j;
 }
 
 __global__ void k_gather_counts(const uint32_t *__restrict__ order, const int *__restrict__ touched,
@@ -950,7 +959,7 @@ static void radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
 static const uint32_t *depth_order(const float *d_depth, const int32_t *d_touched, long long VN, int N,
                                    int n_views, uint32_t *dk0, uint32_t *dk1, uint32_t *dv0, uint32_t *dv1,
                                    uint32_t *hist, void *part, int *err_word, cudaStream_t st) {
-    { k_depth_keys<<<cdiv(VN, 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0); count_launches(1); }
+    { k_depth_keys<<<cdiv(VN, 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0, dv1); count_launches(1); }
     uint32_t *ka = dk0, *kb = dk1, *va = dv0, *vb = dv1;
     if (VN < (long long)kLbVal) {
         // onesweep: status words of the four passes, the four histograms and
@@ -963,7 +972,8 @@ static const uint32_t *depth_order(const float *d_depth, const int32_t *d_touche
             { k_onesweep_hist<<<hb, 256, 0, st>>>(ka, (uint32_t)VN, ghist); count_launches(1); }
             for (int pass = 0; pass < 4; ++pass) {
                 { k_onesweep_pass<<<(int)nb, kSortThreads, 0, st>>>(ka, va, kb, vb, (uint32_t)VN, 8 * pass, ghist + kRadix * pass,
-                                                                   status + (size_t)kRadix * nb * pass, counters + pass, err_word);
+                                                                   status + (size_t)kRadix * nb * pass, counters + pass,
+                                                                   g_wait_limit.load(), err_word);
                   count_launches(1); }
                 uint32_t *t = ka; ka = kb; kb = t;
                 t = va; va = vb; vb = t;
@@ -2142,3 +2152,14 @@ extern "C" int gs_bin_sort_prefix_repair(const gs_camera *cams, int n_views, int
     }
     return launch_status();
 }
+
+// ---------------------------------------------------------------------------
+// Bounded waits
+// ---------------------------------------------------------------------------
+extern "C" int gs_set_wait_limit(long long reads) {
+    if (reads < 0) return GS_ERR_ARG;
+    g_wait_limit.store(reads);
+    return GS_OK;
+}
+
+extern "C" long long gs_get_wait_limit(void) { return g_wait_limit.load(); }

@@ -344,6 +344,13 @@ extern "C" long long gs_launch_count(void) { return gs::g_launches.load(std::mem
 
 extern "C" int gs_version(void) { return GS_VERSION; }
 
+extern "C" int gs_zero(void *d_ptr, size_t n_bytes, gs_stream_t stream) {
+    if (n_bytes == 0) return GS_OK;
+    if (!d_ptr) return GS_ERR_ARG;
+    return cudaMemsetAsync(d_ptr, 0, n_bytes, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? GS_OK
+                                                                                                       : GS_ERR_CUDA;
+}
+
 extern "C" const char *gs_strerror(int status) {
     switch (status) {
         case GS_OK: return "ok";

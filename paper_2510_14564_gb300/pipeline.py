@@ -142,6 +142,10 @@ class Frame:
         self.judge_event = None
         self.judge_rounds = 0
         self.step_count = 0
+        # the error word, read back each step without waiting (pinned copy +
+        # event): an instance-capacity overflow raises, never passes silently
+        self.err_host = torch.zeros(1, dtype=torch.int32).pin_memory()
+        self.err_event = None
 
     # -- buffers -----------------------------------------------------------
     def _alloc_gaussians(self, N: int) -> None:
@@ -218,7 +222,24 @@ class Frame:
             L.gs_bin_sort(self.cams, self.N, self.depth, self.rect, self.touched, capacity, self.vals,
                           self.ranges, keys, self.n_inst, self.ws, self.err)
 
+    def _watch_errors(self, issue: bool) -> None:
+        """Check the error word read back after the previous step's render,
+        and (issue=True) start the read-back of this step's.  A capacity
+        overflow there means that step rendered cut lists: raise rather than
+        train on them."""
+        if self.err_event is not None and self.err_event.query():
+            bits = int(self.err_host.item())
+            self.err_event = None
+            if bits & L.GS_EW_CAPACITY:
+                raise L.GsError(f"instance capacity {self.capacity} was exceeded (error word {bits:#x}): "
+                                "the lists of that step were cut; reserve() a larger capacity")
+        if issue and self.err_event is None:
+            self.err_host.copy_(self.err, non_blocking=True)
+            self.err_event = torch.cuda.Event()
+            self.err_event.record()
+
     def bin_sort(self, want_keys: bool = False) -> None:
+        self._watch_errors(issue=False)
         if self.vals is None:
             # first call: size the instance buffers from the exact count
             self.reserve(1)
@@ -267,7 +288,7 @@ class Frame:
                             self.T_final, self.n_proc, self.tile_nproc, tns, self.err)
             return
         # kept prefixes: check that no pixel ran past one, rebuild and re-render any that did
-        self.flag_count.zero_()
+        L.gs_zero(self.flag_count)
         L.gs_render_fwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, s, self.img,
                         self.T_final, self.n_proc, self.tile_nproc, tns, self.err,
                         tile_count=self.tile_count, flag_tiles=self.flag_tiles, flag_count=self.flag_count)
@@ -278,6 +299,7 @@ class Frame:
                "n_order": self.flag_count}
         L.gs_render_fwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, rep, self.img,
                         self.T_final, self.n_proc, self.tile_nproc, tns, self.err)
+        self._watch_errors(issue=True)
 
     def forward(self, params: dict, timing: bool = False) -> torch.Tensor:
         self.project(params)
@@ -287,7 +309,7 @@ class Frame:
 
     # -- backward ----------------------------------------------------------
     def backward(self, params: dict, dimg: torch.Tensor, mark=None) -> torch.Tensor:
-        self.grad2d.zero_()
+        L.gs_zero(self.grad2d[:self.V * self.N * 12])
         s = self._sched_bwd()
         if mark:
             mark("render_bwd")
@@ -331,7 +353,7 @@ class Frame:
             self.use_learned = learned > count
             self.judge_event = None
         if self.judge_event is None:
-            self.judge.zero_()
+            L.gs_zero(self.judge)
             L.gs_rank_judge(self.pred, self.feats, 8, self.tile_ns, self.T, self.sched.judge_pairs,
                             self.sched.seed * 7919 + self.judge_rounds, self.judge)
             self.judge_rounds += 1
@@ -415,6 +437,11 @@ class Trainer:
         n2 = int(n_out.item())
         if f.check_errors():
             raise L.GsError(f"gs_densify reported error bits {f.check_errors():#x}")
+        if f.vals is not None and self.N > 0:
+            # instances per Gaussian of the latest binning (full lists), which
+            # resize() scales the instance capacity by
+            need = int(f.tile_count.sum().item()) if f.prefix else int(f.n_inst.item())
+            f.inst_per_gaussian = need / self.N
         self.N = n2
         self.p = p2[:PARAM_FLOATS * n2]
         self.m = m2[:PARAM_FLOATS * n2]
@@ -459,7 +486,7 @@ class Trainer:
         mk("l1")
         f.l1(self.targets if targets is None else targets)
         mk("sched_bwd")
-        f.grad2d.zero_()
+        L.gs_zero(f.grad2d[:f.V * self.N * 12])
         s = f._sched_bwd()
         mk("render_bwd")
         L.gs_render_bwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, s, f.dimg, f.T_final, f.n_proc,

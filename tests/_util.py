@@ -62,3 +62,94 @@ def oracle_lists(cam, kp) -> tuple:
         off += len(ids)
         vals.append(ids)
     return (np.concatenate(vals) if vals else np.zeros(0, np.uint32)), ranges
+
+
+# ---------------------------------------------------------------------------
+# 16-bit storage (SH coefficients and record colours in BF16 / FP16)
+# ---------------------------------------------------------------------------
+
+STORAGE_KIND = {1: "bf16", 2: "f16"}       # GS_BF16, GS_F16
+# FP32 evaluation of a colour (16 SH terms, each with a few ulp of error)
+# stays well inside this distance of the FP64 value
+COLOUR_MARGIN = 8e-6
+GROUPS = dict(means=(0, 3), log_scales=(3, 6), quats=(6, 10), logits=(10, 11), sh=(11, 59))
+
+
+def storage_scene(scene, cams, dtype, margin=COLOUR_MARGIN, rounds=40, only=None):
+    """A copy of `scene` prepared for parity of the 16-bit storage path.
+
+    The SH coefficients are rounded to the storage format (what the GPU
+    reads).  The GPU evaluates each colour in FP32 and rounds it to the
+    record's 16-bit format; the oracle evaluates it in FP64 and rounds it
+    with O.round_storage.  The two agree unless the colour lies within FP32
+    error of a point where that rounding changes (a midpoint between two
+    16-bit values) or of the max(0, .) clamp.  While some visible (Gaussian,
+    channel) of some view lies within `margin` of one, its DC coefficient is
+    raised by 0.004 (then rounded), which moves the colour by at least 5.6e-4.
+    `only` (indices) limits the preparation to the Gaussians a comparison
+    reads.  This prepares the input from the oracle's own colours only."""
+    kind = STORAGE_KIND[dtype]
+    sc = scene.subset(np.arange(scene.n))
+    sc.sh = O.round_storage(sc.sh, kind).astype(np.float32)
+    idx = np.arange(sc.n) if only is None else np.asarray(only, np.int64)
+    for _ in range(rounds):
+        sub = sc.subset(idx)
+        bad = np.zeros((sub.n, 3), bool)
+        for cam in cams:
+            kp = O.keypath(cam, sub)
+            pr = O.project(cam, sub, kp)
+            pre = pr["rgb_pre"]
+            flip = (O.round_storage(np.maximum(pre - margin, 0.0), kind)
+                    != O.round_storage(np.maximum(pre + margin, 0.0), kind))
+            bad |= (flip | (np.abs(pre) < margin)) & (kp["touched"] > 0)[:, None]
+        if not bad.any():
+            return sc
+        i, ch = np.nonzero(bad)
+        sc.sh[idx[i], 0, ch] = O.round_storage(sc.sh[idx[i], 0, ch].astype(np.float64) + 0.004, kind)
+    raise AssertionError("colours still next to a rounding point after the nudges")
+
+
+def storage_refs(sc, cams, dtype, window=None):
+    """Oracle of the 16-bit storage path for each view: FP64 projection of
+    the (already rounded) SH, the record colour rounded to the storage format,
+    FP64 blending of that colour."""
+    kind = STORAGE_KIND[dtype]
+    refs = []
+    for cam in cams:
+        kp = O.keypath(cam, sc)
+        pr = dict(O.project(cam, sc, kp))
+        pr["rgb"] = O.round_storage(pr["rgb"], kind)
+        refs.append(dict(kp=kp, proj=pr, r=O.render(cam, kp, pr, window)))
+    return refs
+
+
+def rel_errors(got, ref, floor: float = 1e-2):
+    """(max error / max |ref|, median relative error over entries with
+    |ref| >= floor max |ref|), pooled over the columns of one group."""
+    got = np.asarray(got, np.float64).reshape(len(got), -1)
+    ref = np.asarray(ref, np.float64).reshape(len(ref), -1)
+    scale = np.abs(ref).max(axis=0, keepdims=True)
+    scale = np.where(scale > 0, scale, 1.0)
+    err = np.abs(got - ref)
+    big = np.abs(ref) >= floor * scale
+    rel = err[big] / np.abs(ref[big])
+    return float((err / scale).max()), float(np.median(rel)) if rel.size else 0.0
+
+
+def blending_at_flagged(cam, kp, proj, flag, margin=1e-3):
+    """Gaussians that blend at some flagged pixel (alpha there at least
+    (1 - margin)/255): the only ones whose gradient a decision flipped at
+    that pixel can change.  A Gaussian gets gradient from a pixel only where
+    it blends, and a flipped decision at a pixel changes the transmittance and
+    the colour behind of exactly the Gaussians blending there."""
+    out = np.zeros(kp["depth"].shape[0], bool)
+    for y, x in np.argwhere(flag != 0):
+        ids = O.tile_list(kp, x // 16, y // 16).astype(np.int64)
+        if ids.size == 0:
+            continue
+        dx = x + 0.5 - proj["mean2d"][ids, 0]
+        dy = y + 0.5 - proj["mean2d"][ids, 1]
+        A, B, C = proj["conic"][ids, 0], proj["conic"][ids, 1], proj["conic"][ids, 2]
+        alpha = np.minimum(0.99, proj["opac"][ids] * np.exp(-0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy))
+        out[ids[alpha >= (1.0 - margin) / 255.0]] = True
+    return out

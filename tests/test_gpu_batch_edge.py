@@ -183,6 +183,37 @@ def test_timeout_budget_sets_error_without_hanging():
     assert fr.check_errors() & L.GS_EW_TIMEOUT
 
 
+def test_depth_sort_wait_limit_sets_error_and_returns():
+    """The onesweep depth sort's look-back reads are bounded (gs_set_wait_limit).
+    At 0 every tile after the first gives up at once: the call returns,
+    GS_EW_TIMEOUT is set, and the lists it leaves hold record indices only.
+    With the default limit restored the same call is exact again."""
+    scene = S.uniform_scene(10_000, 0)           # 10k records: three 4096-key tiles per digit pass
+    cam = S.front_camera(256, 256)
+    fr, _ = _frame(scene, [cam])
+    I = int(fr.n_inst.item())
+    want = fr.vals[:I].clone()
+    assert L.gs_get_wait_limit() == 1 << 20 and fr.check_errors() == 0
+    try:
+        L.gs_set_wait_limit(0)
+        assert L.gs_get_wait_limit() == 0
+        fr.err.zero_()
+        fr.bin_sort()
+        torch.cuda.synchronize()
+        assert fr.check_errors() & L.GS_EW_TIMEOUT
+        got = fr.vals[:min(I, fr.capacity)]
+        assert int(got.min()) >= 0 and int(got.max()) < scene.n
+    finally:
+        L.gs_set_wait_limit(1 << 20)
+    fr.err.zero_()
+    fr.bin_sort()
+    torch.cuda.synchronize()
+    assert fr.check_errors() == 0
+    assert int(fr.n_inst.item()) == I and torch.equal(fr.vals[:I], want)
+    with pytest.raises(L.GsError):
+        L.gs_set_wait_limit(-1)
+
+
 def test_argument_errors_are_reported():
     cam = S.front_camera(64, 64)
     fr = P.Frame([cam], 8)

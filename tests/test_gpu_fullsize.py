@@ -11,7 +11,7 @@ from oracle import oracle as O
 from paper_2510_14564_gb300 import _lib as L
 from paper_2510_14564_gb300 import pipeline as P
 from paper_2510_14564_gb300 import scenes as S
-from tests._util import GRAD_RTOL, IMG_ATOL, rel_check
+from tests._util import GRAD_RTOL, GROUPS, IMG_ATOL, rel_check, storage_refs, storage_scene
 
 pytestmark = pytest.mark.gpu
 
@@ -91,24 +91,63 @@ def test_fullsize_fp32_count_path(full):
         assert np.all(gg[~hit] == 0.0), name
 
 
+def _crop_gaussians(cam, kp, win):
+    """Visible Gaussians whose tile rectangle meets the crop's tiles."""
+    x0, y0, x1, y1 = (v // 16 for v in win)
+    r = kp["rect"]
+    return np.flatnonzero((kp["touched"] > 0) & (r[:, 0] < x1) & (r[:, 2] > x0) & (r[:, 1] < y1) & (r[:, 3] > y0))
+
+
 def test_fullsize_bf16_learned_path(full):
+    """The benchmark's precision path at full size: BF16 SH and colours,
+    kept-prefix binning, the learned order a few steps in.  The centre crop's
+    image, reverse pass, projection backward and fused backward + Adam
+    against the oracle of the storage path (same rounded SH, colours rounded
+    to BF16; tests/test_gpu_half_grad.py)."""
     scene, cam, kp, _ = full
-    tr = _trainer(scene, [cam], "learned", L.GS_BF16)
-    for _ in range(3):                      # the benchmark's configuration, a few steps in
-        tr.frame.forward(tr.params_for_kernels(), timing=True)
-        tr.frame.train_scheduler()
-    tr.frame.use_learned = True
-    tr.frame.forward(tr.params_for_kernels(), timing=True)
-    torch.cuda.synchronize()
-    assert tr.frame.check_errors() == 0
-    sc16 = scene.subset(np.arange(scene.n))
-    sc16.sh = torch.from_numpy(scene.sh).to(torch.bfloat16).float().numpy()
-    kp16 = O.keypath(cam, sc16)
-    pr16 = O.project(cam, sc16, kp16)
     win = _crop(cam)
+    sc = storage_scene(scene, [cam], L.GS_BF16, only=_crop_gaussians(cam, kp, win))
+    tr = _trainer(sc, [cam], "learned", L.GS_BF16)
+    f = tr.frame
+    for _ in range(3):                      # the benchmark's configuration, a few steps in
+        f.forward(tr.params_for_kernels(), timing=True)
+        f.train_scheduler()
+    f.use_learned = True
+    pk = tr.params_for_kernels()
+    f.forward(pk, timing=True)
+    torch.cuda.synchronize()
+    assert f.check_errors() == 0
+    ref = storage_refs(sc, [cam], L.GS_BF16, window=win)[0]
+    r, kp16, pr16 = ref["r"], ref["kp"], ref["proj"]
     x0, y0, x1, y1 = win
-    r = O.render(cam, kp16, pr16, window=win)
     ok = r["flag"][y0:y1, x0:x1] == 0
-    img = tr.frame.image(0).cpu().numpy()[:, y0:y1, x0:x1]
-    ref = r["img"][:, y0:y1, x0:x1]
-    assert np.all(np.abs(img - ref)[:, ok] <= (2.0 ** -8 * ref + IMG_ATOL)[:, ok])
+    print(f"\nflagged crop pixels: {1 - ok.mean():.2%}")
+    assert ok.mean() > 0.95
+    img = f.image(0).cpu().numpy()[:, y0:y1, x0:x1]
+    assert np.abs(img - r["img"][:, y0:y1, x0:x1])[:, ok].max() <= IMG_ATOL
+    # gradients of a cotangent on the crop
+    d = np.zeros((3, cam.H, cam.W), np.float32)
+    dc = S.random_cotangent((3, y1 - y0, x1 - x0), seed=8) * 1e-3
+    dc[:, ~ok] = 0.0
+    d[:, y0:y1, x0:x1] = dc
+    d_t = torch.from_numpy(d.ravel()).cuda()
+    g2 = O.render_bwd(cam, kp16, pr16, d.astype(np.float64), window=win)
+    gref = O.project_bwd(cam, sc, kp16, g2)
+    n = sc.n
+    hit = np.abs(g2).sum(1) > 0
+    assert hit.sum() > 100
+    g = f.backward(pk, d_t).cpu().numpy()
+    # the fused call the training step makes (BF16 shadow read and rewritten)
+    f.grad2d.zero_()
+    L.gs_render_bwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, None, d_t, f.T_final, f.n_proc,
+                    f.tile_nproc, f.grad2d, f.err)
+    gB = torch.empty(59 * n, device="cuda")
+    L.gs_project_bwd_adam([cam], n, tr.p, tr.sh_shadow, L.GS_BF16, f.touched, f.grad2d, tr.m, tr.v,
+                          tr.lr, P.ADAM_B1, P.ADAM_B2, P.ADAM_EPS, 1, tr.sh_shadow, L.GS_BF16, gB)
+    gb = gB.cpu().numpy()
+    for name, (a, b) in GROUPS.items():
+        gr = gref[a * n:b * n].reshape(n, -1)
+        for what, got in (("chain", g), ("fused", gb)):
+            gg = got[a * n:b * n].reshape(n, -1)
+            rel_check(gg[hit], gr[hit], GRAD_RTOL, f"{what}.{name}")
+            assert np.all(gg[~hit] == 0.0), f"{what}.{name}"

@@ -4,10 +4,10 @@ blending, projection backward and Adam.  One view takes the fused projection
 backward + Adam kernel, two views the separate calls.
 
 Pixels the oracle flags (a discrete decision within rounding of a threshold)
-may legitimately differ; every Gaussian listed in a tile holding one is left
-out of the comparison.  The target is pushed away from the oracle image
-where they are close, so the sign of the L1 gradient is the same on both
-sides."""
+may legitimately differ; every Gaussian that blends at one of them is left
+out of the comparison (at least 90% of the Gaussians stay in).  The target
+is pushed away from the oracle image where they are close, so the sign of
+the L1 gradient is the same on both sides."""
 import numpy as np
 import pytest
 
@@ -17,7 +17,7 @@ from oracle import oracle as O
 from paper_2510_14564_gb300 import _lib as L
 from paper_2510_14564_gb300 import pipeline as P
 from paper_2510_14564_gb300 import scenes as S
-from tests._util import GRAD_RTOL, rel_check
+from tests._util import GRAD_RTOL, blending_at_flagged, rel_check
 
 pytestmark = pytest.mark.gpu
 
@@ -52,15 +52,15 @@ def _oracle_step(scene, cams, seed):
         d *= d.size / n_total                  # the loss is the mean over every view's pixels
         g2 = O.render_bwd(cam, r["kp"], r["proj"], d)
         grads += O.project_bwd(cam, scene, r["kp"], g2)
-        for y, x in np.argwhere(r["flag"] != 0):
-            excluded[O.tile_list(r["kp"], x // 16, y // 16)] = True
+        excluded |= blending_at_flagged(cam, r["kp"], r["proj"], r["flag"])
     return tgts, grads, excluded
 
 
 def _check(tr, scene, p0, grads, excluded, b1=P.ADAM_B1):
     n = scene.n
     keep = ~excluded
-    assert keep.sum() > 0.5 * n
+    print(f"\nGaussians compared: {keep.mean():.1%}")
+    assert keep.mean() >= 0.9
     m = tr.m.cpu().numpy().astype(np.float64)
     p = tr.p.cpu().numpy().astype(np.float64)
     g_gpu = m / (1.0 - b1)                    # first step from m = 0: m = (1 - b1) g
