@@ -551,6 +551,48 @@ long long orc_render_fwd(const orc_cam *cam, int n, const int *rect, const int *
 }
 
 /*
+ * Forward render of the pixel window from explicit tile lists: tile t of the
+ * view (row-major) blends the splats ids[ranges[2t] .. ranges[2t+1]) in that
+ * order, with the same per-pixel rules as orc_render_fwd (blend_pixel).  The
+ * splat arrays (mean2d, conic, opac, rgb) are indexed by those ids; with the
+ * lists of orc_tile_list this is orc_render_fwd.
+ */
+long long orc_render_lists(const orc_cam *cam, const long long *ranges, const unsigned *ids,
+                           const double *mean2d, const double *conic, const double *opac,
+                           const double *rgb, int x0, int y0, int x1, int y1, double margin_alpha,
+                           double margin_T, double *img, double *T_final, int *n_proc,
+                           unsigned char *flag)
+{
+    orc_scene sc = {cam, 0, NULL, NULL, NULL, mean2d, conic, opac, rgb, margin_alpha, margin_T};
+    const int W = cam->W, H = cam->H, TX = tiles_x(cam);
+    const int tx0 = x0 / ORC_TILE, tx1 = (x1 + ORC_TILE - 1) / ORC_TILE;
+    const int ty0 = y0 / ORC_TILE, ty1 = (y1 + ORC_TILE - 1) / ORC_TILE;
+    const int ntiles = (tx1 - tx0) * (ty1 - ty0);
+    long long pairs = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : pairs)
+    for (int it = 0; it < ntiles; ++it) {
+        int tx = tx0 + it % (tx1 - tx0), ty = ty0 + it / (tx1 - tx0);
+        const long long t = (long long)ty * TX + tx;
+        const unsigned *list = ids + ranges[2 * t];
+        const long long len = ranges[2 * t + 1] - ranges[2 * t];
+        for (int py = ty * ORC_TILE; py < (ty + 1) * ORC_TILE; ++py)
+            for (int px = tx * ORC_TILE; px < (tx + 1) * ORC_TILE; ++px) {
+                if (px < x0 || px >= x1 || py < y0 || py >= y1 || px >= W || py >= H) continue;
+                double c[3], T;
+                int fl;
+                long long last = blend_pixel(&sc, list, len, px, py, c, &T, &fl, NULL, NULL);
+                size_t p = (size_t)py * W + px;
+                for (int ch = 0; ch < 3; ++ch) img[(size_t)ch * W * H + p] = c[ch];
+                T_final[p] = T;
+                n_proc[p] = (int)last;
+                flag[p] = (unsigned char)fl;
+                pairs += last;
+            }
+    }
+    return pairs;
+}
+
+/*
  * Reverse mode of the blending for the pixel window, given dL/dimg ([3, H, W]).
  * Accumulates into grad2d ([n, 9], zeroed by the caller) the derivatives with
  * respect to (u, v, A, B, C, opacity, r, g, b), where the conic enters as

@@ -76,6 +76,9 @@ def lib():
         L.orc_render_fwd.restype = I64
         L.orc_render_fwd.argtypes = ([P(OrcCam), I32, P(I32), P(I32), P(F32)] + [P(F64)] * 4 +
                                      [I32] * 4 + [F64, F64, P(F64), P(F64), P(I32), P(U8)])
+        L.orc_render_lists.restype = I64
+        L.orc_render_lists.argtypes = ([P(OrcCam), P(I64), P(U32)] + [P(F64)] * 4 + [I32] * 4 +
+                                       [F64, F64, P(F64), P(F64), P(I32), P(U8)])
         L.orc_render_bwd.argtypes = ([P(OrcCam), I32, P(I32), P(I32), P(F32)] + [P(F64)] * 4 +
                                      [I32] * 4 + [P(F64), P(F64)])
         L.orc_project_bwd.argtypes = [P(OrcCam), I32] + [P(F64)] * 5 + [P(I32), P(F64), P(F64)]
@@ -213,6 +216,30 @@ def render(cam, kp: dict, proj: dict, window=None, margin_alpha: float = 1e-4,
                                  _p(kp["depth"], F32), _p(m2, F64), _p(co, F64), _p(op, F64),
                                  _p(rgb, F64), x0, y0, x1, y1, margin_alpha, margin_T,
                                  _p(img, F64), _p(T, F64), _p(nproc, I32), _p(flag, U8))
+    return dict(img=img, T_final=T, n_proc=nproc, flag=flag, pairs=int(pairs))
+
+
+def render_lists(cam, ranges, ids, splats: dict, window=None, margin_alpha: float = 1e-4,
+                 margin_T: float = 1e-3) -> dict:
+    """FP64 forward blend of the pixel window from explicit tile lists: tile t
+    (row-major) blends splats ids[ranges[t, 0]:ranges[t, 1]] in that order
+    (splats: mean2d [m, 2], conic [m, 3], opac [m], rgb [m, 3]), with the
+    per-pixel rules of render()."""
+    x0, y0, x1, y1 = _window(cam, window)
+    W, H = cam.W, cam.H
+    img = np.zeros((3, H, W))
+    T = np.zeros((H, W))
+    nproc = np.zeros((H, W), np.int32)
+    flag = np.zeros((H, W), np.uint8)
+    rg = np.ascontiguousarray(np.asarray(ranges, np.int64).reshape(-1, 2))
+    idv = np.ascontiguousarray(np.asarray(ids, np.uint32))
+    if idv.size == 0:
+        idv = np.zeros(1, np.uint32)
+    m2, co, op, rgb = (_c64(splats[k]) for k in ("mean2d", "conic", "opac", "rgb"))
+    c = cam_struct(cam)
+    pairs = lib().orc_render_lists(ctypes.byref(c), _p(rg, I64), _p(idv, U32), _p(m2, F64), _p(co, F64),
+                                   _p(op, F64), _p(rgb, F64), x0, y0, x1, y1, margin_alpha, margin_T,
+                                   _p(img, F64), _p(T, F64), _p(nproc, I32), _p(flag, U8))
     return dict(img=img, T_final=T, n_proc=nproc, flag=flag, pairs=int(pairs))
 
 
@@ -604,6 +631,54 @@ def colour_bucket(rgb):
     c8 = np.clip(c8, 0, 255)
     q = np.floor(c8 / 256.0 * 16.0).astype(np.int64)
     return q[..., 0] * 256 + q[..., 1] * 16 + q[..., 2]
+
+
+def colour_merge(ranges, vals, record_rgb, splats: dict):
+    """Similarity-based sampling and merging of tile lists (Sec. IV-C1), one
+    16x16 tile at a time.  A tile's entries are grouped by the bucket of
+    their record colour (colour_bucket); each bucket is represented by its
+    first entry in list (depth) order, which keeps that Gaussian's position,
+    shape and place in the list, and takes the bucket's averaged colour
+    (mean of the members' record colours) and accumulated opacity
+    min(1, sum of the members' opacities); the other members are dropped.
+
+    ranges [T, 2] and vals: the tile lists; record_rgb [n, 3]: the colour
+    each record holds (hashed and averaged); splats: FP64 mean2d, conic,
+    opac of the n Gaussians.  Returns (ranges', ids', reps, src, members):
+    the merged lists (tile after tile, ids' indexing reps), the
+    representatives (mean2d, conic, opac, rgb; FP64), the Gaussian each
+    representative stands at and its member count."""
+    ranges = np.asarray(ranges, np.int64).reshape(-1, 2)
+    vals = np.asarray(vals, np.int64)
+    rec = np.asarray(record_rgb, np.float32)
+    h_all = colour_bucket(rec)
+    rgb64 = rec.astype(np.float64)
+    op = np.asarray(splats["opac"], np.float64)
+    out_ranges = np.zeros_like(ranges)
+    src, members, rgb, opac = [], [], [], []
+    for t, (a, b) in enumerate(ranges):
+        out_ranges[t, 0] = len(src)
+        first = {}                                  # bucket -> representative number
+        for g in vals[a:b]:
+            h = int(h_all[g])
+            if h not in first:
+                first[h] = len(src)
+                src.append(int(g))
+                members.append(0)
+                rgb.append(np.zeros(3))
+                opac.append(0.0)
+            r = first[h]
+            members[r] += 1
+            rgb[r] = rgb[r] + rgb64[g]
+            opac[r] += op[g]
+        out_ranges[t, 1] = len(src)
+    src = np.asarray(src, np.int64)
+    members = np.asarray(members, np.int64)
+    reps = dict(mean2d=np.asarray(splats["mean2d"], np.float64)[src].reshape(-1, 2),
+                conic=np.asarray(splats["conic"], np.float64)[src].reshape(-1, 3),
+                opac=np.minimum(1.0, np.asarray(opac, np.float64)),
+                rgb=np.asarray(rgb, np.float64).reshape(-1, 3) / np.maximum(members, 1)[:, None])
+    return out_ranges, np.arange(len(src), dtype=np.uint32), reps, src, members
 
 
 def colour_buckets(ranges, vals, rgb, lo):

@@ -837,3 +837,64 @@ def test_f16_rounding_matches_numpy_half():
     assert np.array_equal(O.round_storage(x, "f16"), want)
     assert float(O.round_storage(1.0 + 2.0 ** -11, "f16")) == 1.0      # tie to even
     assert float(O.round_storage(65520.0, "f16")) == math.inf
+
+
+# -- similarity-based sampling and merging of tile lists (Sec. IV-C1) ----------
+
+def test_render_lists_with_the_oracle_lists_is_render():
+    """Blending explicit tile lists that are the oracle's own lists, with each
+    Gaussian's attributes, gives render() bit for bit."""
+    scene = S.uniform_scene(400, 2)
+    cam = S.front_camera(96, 64)
+    r = O.forward(cam, scene)
+    ranges, ids = [], []
+    for t in range(cam.n_tiles):
+        lst = O.tile_list(r["kp"], t % cam.tiles_x, t // cam.tiles_x)
+        ranges.append((len(ids), len(ids) + len(lst)))
+        ids.extend(lst.tolist())
+    rl = O.render_lists(cam, ranges, np.asarray(ids, np.uint32), r["proj"])
+    for k in ("img", "T_final", "n_proc", "flag"):
+        assert np.array_equal(rl[k], r[k]), k
+
+
+def test_colour_merge_by_hand():
+    # tile 0: red (0.9, 0.1, 0.1) and red (0.92, 0.08, 0.11) share bucket
+    # (14, 1, 1); blue is alone; tile 1: the second red only
+    rgb = np.array([[0.9, 0.1, 0.1], [0.2, 0.3, 0.95], [0.92, 0.08, 0.11]], np.float32)
+    sp = dict(mean2d=np.array([[1.0, 2.0], [3.0, 4.0], [5.0, 6.0]]),
+              conic=np.array([[1.0, 0.1, 2.0], [3.0, 0.2, 4.0], [5.0, 0.3, 6.0]]),
+              opac=np.array([0.7, 0.4, 0.6]))
+    ranges = np.array([[0, 3], [3, 4], [4, 4]])
+    vals = np.array([0, 1, 2, 2])
+    out_r, ids, reps, src, members = O.colour_merge(ranges, vals, rgb, sp)
+    assert out_r.tolist() == [[0, 2], [2, 3], [3, 3]]
+    assert src.tolist() == [0, 1, 2] and members.tolist() == [2, 1, 1]
+    assert np.allclose(reps["rgb"][0], (rgb[0].astype(np.float64) + rgb[2]) / 2)
+    assert reps["opac"][0] == 1.0                     # 0.7 + 0.6, accumulated and capped
+    assert reps["opac"][1] == 0.4 and reps["opac"][2] == 0.6
+    assert np.array_equal(reps["mean2d"][0], sp["mean2d"][0])       # the first member's place
+    assert np.array_equal(reps["conic"][2], sp["conic"][2])
+
+
+def test_colour_merge_of_two_coincident_splats_closed_form():
+    """Two coincident isotropic splats of one colour merge into one of
+    opacity min(1, 2 o): at the centre the pixel is min(0.99, 2 o) c, where
+    the exact blend gives c (a + a (1 - a)), a = o."""
+    cam = S.front_camera(32, 32)
+    c, o, s2 = 0.6, 0.3, 9.0
+    sp = dict(mean2d=np.array([[16.5, 16.5], [16.5, 16.5]]),
+              conic=np.array([[1 / s2, 0.0, 1 / s2]] * 2), opac=np.array([o, o]))
+    rgb = np.array([[c, c, c], [c, c, c]], np.float32)
+    ranges = np.zeros((cam.n_tiles, 2), np.int64)
+    t = (16 // 16) * cam.tiles_x + 16 // 16
+    ranges[t:] = 2
+    ranges[t, 0] = 0
+    out_r, ids, reps, src, members = O.colour_merge(ranges, np.array([0, 1]), rgb, sp)
+    assert members.tolist() == [2] and reps["opac"][0] == 2 * o
+    m = O.render_lists(cam, out_r, ids, dict(reps, rgb=reps["rgb"]))
+    e = O.render_lists(cam, ranges, np.array([0, 1], np.uint32), dict(sp, rgb=rgb.astype(np.float64)))
+    cf = float(np.float32(c))
+    assert m["img"][0, 16, 16] == pytest.approx(min(0.99, 2 * o) * cf, rel=1e-12)
+    assert e["img"][0, 16, 16] == pytest.approx(cf * (o + o * (1 - o)), rel=1e-12)
+    # a pixel 2 sigma away: alpha = 2 o exp(-2)
+    assert m["img"][0, 16, 22] == pytest.approx(2 * o * math.exp(-0.5 * 36 / s2) * cf, rel=1e-12)
