@@ -181,6 +181,37 @@ def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1) -> dict:
     }
 
 
+# Warp instructions the reverse pass issues per (pixel, Gaussian) pair its
+# pixels walk, from one ncu capture of the full-size workload
+# (smsp__inst_executed.sum of k_render_bwd over the sum of the per-pixel
+# processed counts).  Valid only while the kernel sources hash as captured.
+RENDER_BWD_INSTR = {
+    "warp_instr_per_pair": None,
+    "sources": {},
+}
+
+
+def issue_roofline(pairs: int, ms: float | None, sm_count: int, clock_hz: float) -> dict | None:
+    """The reverse pass against its issue roofline: the time its measured
+    warp instructions per pair would take at the peak issue rate (4 warp
+    instructions per SM per cycle, i.e. 128 thread instructions), over the
+    measured time."""
+    import hashlib
+    w = RENDER_BWD_INSTR.get("warp_instr_per_pair")
+    if not ms or not w:
+        return None
+    for path, digest in RENDER_BWD_INSTR["sources"].items():
+        with open(os.path.join(ROOT, path), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != digest:
+                return None
+    instr = w * pairs
+    t_min = instr / (sm_count * 4 * clock_hz)
+    return {"bound": "issue", "pairs": pairs, "warp_instr_per_pair": w,
+            "achieved": round(instr / (ms / 1e3) / 1e12, 4), "peak": round(sm_count * 4 * clock_hz / 1e12, 4),
+            "unit": "T warp-instr/s", "frac": round(t_min / (ms / 1e3), 4),
+            "issue_roofline_ms": round(t_min * 1e3, 4), "measured_ms": round(ms, 4)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -223,7 +254,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    def timed(tr, steps, stage_times=None, e2e=False, profile=False):
+    def timed(tr, steps, stage_times=None, e2e=False, profile=False, adam=True):
         st = torch.cuda.current_stream()
         marks = []
 
@@ -244,7 +275,7 @@ def run_ours(args):
         for _ in range(steps):
             if e2e:
                 tgt.copy_(tgt_host, non_blocking=True)
-            tr.step(mark=mark if stage_times is not None else None)
+            tr.step(mark=mark if stage_times is not None else None, adam=adam)
             if e2e:
                 loss_host.copy_(tr.frame.loss, non_blocking=True)
         t1.record(st)
@@ -260,7 +291,8 @@ def run_ours(args):
                     stage_times.setdefault(n0, []).append(e0.elapsed_time(e1))
         return ms, launches
 
-    # plain FP32 path, tile order by instance count
+    # plain FP32 path, tile order by instance count: the training step, then
+    # the fwd+bwd iteration (no Adam)
     plain = make("count", False)
     for _ in range(args.warmup):
         plain.step()
@@ -268,13 +300,17 @@ def run_ours(args):
     plain_ips = replica_throughput(args.steps, plain_ms, 1)
     plain_stages = {}
     timed(plain, args.steps, stage_times=plain_stages)
+    for _ in range(3):
+        plain.iteration()
+    plain_it_ms, _ = timed(plain, args.steps, adam=False)
+    plain_it_ips = replica_throughput(args.steps, plain_it_ms, 1)
     assert plain.frame.check_errors() == 0, "kernel error word set (plain path)"
     del plain
     torch.cuda.empty_cache()
 
     # learned schedule, BF16 storage
     tr = make("learned", True)
-    # calibration: the tile-cost MLP learns from the renderer's own timings
+    # calibration: the tile-cost MLPs learn from the renderer's own timings
     for _ in range(args.calib):
         tr.step()
     for _ in range(args.warmup):
@@ -287,29 +323,30 @@ def run_ours(args):
     e2e_ms, _ = timed(tr, args.steps, e2e=True)
     e2e_ips = replica_throughput(args.steps, e2e_ms, 1)
     # the fwd+bwd iteration alone (projection .. projection backward + L1, no Adam)
-    st = torch.cuda.current_stream()
     for _ in range(3):
         tr.iteration()
-    barrier()
-    torch.cuda.synchronize()
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record(st)
-    for _ in range(args.steps):
-        tr.iteration()
-    a1.record(st)
-    torch.cuda.synchronize()
-    barrier()
-    it_ips = args.steps / (max_over_ranks(a0.elapsed_time(a1), world, "cuda") / 1e3)
+    it_stages = {}
+    it_ms, _ = timed(tr, args.steps, adam=False)
+    timed(tr, args.steps, stage_times=it_stages, adam=False)
+    it_ips = replica_throughput(args.steps, it_ms, 1)
     assert tr.frame.check_errors() == 0, "kernel error word set (learned path)"
 
     f = tr.frame
+    # tiles whose kept prefix ran short and were repaired, per step (read back
+    # step by step after the timed regions)
+    flagged = []
+    for _ in range(20):
+        tr.step()
+        flagged.append(int(f.flag_count.item()))
     sched_diag = schedule_diagnostics(f, L, torch)
     I = int(f.n_inst.item())
     I_full = int(f.tile_count.sum().item())
     I_proc = int(f.tile_nproc.sum().item())
+    pairs = int(f.n_proc.sum().item())           # (pixel, Gaussian) pairs the blend loops walk
     Pix = sum(c.W * c.H for c in cams)
     ab = algorithmic_bytes(N, Pix, I, I_proc, True, len(cams))
     stage_ms = {k: statistics.mean(v) for k, v in stages.items()}
+    it_stage_ms = {k: statistics.mean(v) for k, v in it_stages.items()}
     kernel_stages = {k: v for k, v in stage_ms.items() if k in ab}
     dom = max(kernel_stages, key=kernel_stages.get)
     peaks, peak_kind = load_peaks()
@@ -317,6 +354,11 @@ def run_ours(args):
     achieved = ab[dom] / (stage_ms[dom] / 1e3) / 1e9
     step_bytes = sum(v for k, v in ab.items() if k in stage_ms)
     whole = step_bytes / (ms / args.steps / 1e3) / 1e9
+    it_bytes = sum(v for k, v in ab.items() if k in it_stage_ms)
+    it_gbs = it_bytes / (it_ms / args.steps / 1e3) / 1e9
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    clock_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
+    issue = issue_roofline(pairs, stage_ms.get("render_bwd"), sm_count, clock_hz)
 
     out = {
         "metric": METRIC, "value": round(ips * world, 3), "unit": "iters/s", "n_gpus": world,
@@ -325,12 +367,23 @@ def run_ours(args):
         "data": "synthetic (seeded skewed-density scene, random-init parameters)",
         "config": {"workload": args.workload, "gaussians": N,
                    "view": [cam.W, cam.H] if len(cams) == 1 else [[c.W, c.H] for c in cams],
-                   "schedule": "learned" if f.use_learned else "count (judge fallback)",
+                   "step": "training step: every hot-path row incl. Adam and the cost-MLP training",
+                   "schedule": f.schedule_report(),
                    "storage": "bf16 SH + bf16 colour, fp32 blending and gradients",
                    "plain_fp32_count_iters_per_s": round(plain_ips * world, 3),
                    "learned_vs_plain": round(ips / plain_ips, 4),
-                   "fwd_bwd_iters_per_s_no_adam": round(it_ips * world, 3),
+                   "fwd_bwd_iteration": {
+                       "what": "the step without Adam: project, bin, schedule, forward, L1, reverse pass, "
+                               "projection backward, cost-MLP training",
+                       "iters_per_s": round(it_ips * world, 3),
+                       "plain_fp32_count_iters_per_s": round(plain_it_ips * world, 3),
+                       "learned_vs_plain": round(it_ips / plain_it_ips, 4),
+                       "algorithmic_bytes": int(it_bytes), "achieved_gbs": round(it_gbs, 1),
+                       "hbm_frac": round(it_gbs / hbm, 4),
+                       "stage_ms": {k: round(v, 4) for k, v in it_stage_ms.items()}},
                    "instances_full_lists": I_full, "instances_kept": I, "processed_instances": I_proc,
+                   "pixel_pairs_processed": pairs,
+                   "flagged_tiles_per_step": {"mean": round(statistics.mean(flagged), 2), "max": max(flagged)},
                    "l2": "inputs larger than L2 (0.4-0.7 GB of parameters, 1.5+ GB of instances)",
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "mlp_calibration_steps": args.calib, "adam_lr_scale": args.lr_scale,
@@ -342,6 +395,7 @@ def run_ours(args):
                      "traffic": measured_traffic(dom, N), "algorithmic_bytes": int(ab[dom]),
                      "peak_source": peak_kind,
                      "whole_step_hbm_frac": round(whole / hbm, 4)},
+        "issue_roofline_render_bwd": issue,
         "e2e": {"value": round(e2e_ips * world, 3), "unit": "iters/s",
                 "h2d_bytes_per_step": int(tgt.numel() * 4), "d2h_bytes_per_step": 4},
         "gpu_launches": int(launches),
@@ -438,7 +492,7 @@ def run_dynamic(args):
         "config": {"workload": args.workload, "gaussians_start": N0, "gaussians_timed_first": counts[0],
                    "gaussians_timed_last": counts[-1], "gaussians_mean": round(statistics.mean(counts)),
                    "clone_frac": frac, "min_opacity": min_op, "views": [[c.W, c.H] for c in cams],
-                   "schedule": "learned" if tr.frame.use_learned else "count (judge fallback)",
+                   "schedule": tr.frame.schedule_report(),
                    "storage": "bf16 SH + bf16 colour, fp32 blending and gradients",
                    "adam_lr_scale": args.lr_scale, "mlp_calibration_steps": args.calib,
                    "l2": "inputs larger than L2", "graphs": "none (eager launches; the count is read back)"},
@@ -661,10 +715,86 @@ def run_colour_buckets(args):
     print(json.dumps(out), flush=True)
 
 
+def run_colour_merge(args):
+    """Similarity-based sampling and merging (Sec. IV-C1) on the benchmark
+    view, BF16 records: the exact forward pass against the merge plus the
+    render of the merged lists, for the full lists and for the kept prefixes
+    of a training step.  Reports ms (CUDA events, median of --steps, L2
+    flushed before each), the entries kept and the merged image's distance to
+    the exact one (the mode is lossy)."""
+    import torch
+
+    from paper_2510_14564_gb300 import _lib as L
+    from paper_2510_14564_gb300 import pipeline as P
+    from paper_2510_14564_gb300 import scenes as S
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    L.lib()
+    scene, cams = S.make_workload(args.workload, seed=0)
+    N = scene.n
+    params = P.to_device_params(scene)
+    views = dict(P.param_views(params, N))
+    views["sh"] = views["sh"].to(torch.bfloat16)
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2
+
+    def timed(fn):
+        ts = []
+        for k in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    res = {}
+    for name, prefix in (("full_lists", False), ("kept_prefixes", True)):
+        fr = P.Frame(cams, N, rgb_dtype=L.GS_BF16, sh_dtype=L.GS_BF16, prefix=prefix)
+        fr.project(views)
+        fr.bin_sort()
+        if prefix:                     # a step's history: prefixes cut at twice the processed counts
+            fr.render()
+            fr.bin_sort()
+        exact = lambda: L.gs_render_fwd(fr.cams, fr.ranges, fr.vals, fr.splats, fr.rgb_dtype, None, fr.img,
+                                        fr.T_final, fr.n_proc, None, None, fr.err)
+        ms_exact = timed(exact)
+        img_exact = fr.img.clone()
+        ms_merged = timed(fr.render_merged)
+        mr = fr.m_ranges.view(-1, 2).long()
+        lens = fr.ranges.view(-1, 2).long()
+        kept = int((mr[:, 1] - mr[:, 0]).sum())
+        entries = int((lens[:, 1] - lens[:, 0]).sum())
+        d = (fr.img - img_exact).double()
+        mse = float((d * d).mean())
+        assert fr.check_errors() == 0
+        res[name] = {"entries": entries, "representatives": kept, "kept_share": round(kept / max(1, entries), 4),
+                     "ms_exact_render": round(ms_exact, 4), "ms_merge_plus_render": round(ms_merged, 4),
+                     "speedup": round(ms_exact / ms_merged, 3),
+                     "image_vs_exact": {"max_abs": round(float(d.abs().max()), 5),
+                                        "mean_abs": round(float(d.abs().mean()), 6),
+                                        "psnr_db": round(10 * np.log10(1.0 / max(mse, 1e-30)), 2)}}
+        del fr
+        torch.cuda.empty_cache()
+    out = {"metric": "similarity-based sampling and merging: merged vs exact forward render, ms", "unit": "ms",
+           "higher_is_better": False, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+           "data": "synthetic (seeded skewed-density scene, random-init parameters)",
+           "config": {"workload": args.workload, "gaussians": N, "records": "bf16 colour",
+                      "l2": "flushed before each timed pass"},
+           "passes": res}
+    print(json.dumps(out), flush=True)
+
+
 def schedule_diagnostics(f, L, torch, reps=5) -> dict:
-    """Render makespans (best of `reps`, ms) of the forward and backward
-    passes under the raster, count and learned tile orders (orders computed
-    beforehand), the cost of computing each order, and per-tile time spread."""
+    """Render makespans (best of `reps`, ms) of the forward pass in raster
+    and count order, and of the reverse pass in raster, count,
+    processed-count and learned order (orders computed beforehand; the
+    learned one splits the tiles its MLP predicts heavy, the others by
+    processed count); the cost of computing each order; per-tile time
+    spread of the forward."""
     def best(fn):
         out = 1e9
         for _ in range(reps):
@@ -676,17 +806,17 @@ def schedule_diagnostics(f, L, torch, reps=5) -> dict:
             out = min(out, a.elapsed_time(b))
         return round(out, 4)
 
-    keep = f.use_learned
-    f.use_learned = False
-    t_count = best(lambda: f._sched_fwd())
+    keep = f.force_order
+    t_count = best(lambda: f._count_order(f.order_f))
     o_count = f.order_f.clone()
-    f.use_learned = True
-    t_learned = best(lambda: f._sched_fwd())
-    o_learned = f.order_f.clone()
-    f.use_learned = keep
+    f.force_order = "learned"
+    t_learned = best(lambda: f._sched_bwd())
+    o_learned = f.order_b.clone()
+    pred = f.pred_b.clone()
+    f.force_order = keep
     L.gs_int_cost(f.tile_nproc, f.T, f.cost)
     L.gs_sched_order(f.cost, f.T, f.order_b, f.order_ws)
-    o_bwd = f.order_b.clone()
+    o_proc = f.order_b.clone()
 
     def sch(o):
         return None if o is None else {"mode": L.GS_SCHED_ORDER, "order": o, "queue": f.queue}
@@ -695,20 +825,19 @@ def schedule_diagnostics(f, L, torch, reps=5) -> dict:
         L.gs_render_fwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, sch(o), f.img, f.T_final, f.n_proc,
                         f.tile_nproc, None, f.err)
 
-    def bwd(o):
+    def bwd(o, cost=None):
         s = sch(o)
         if s is not None:
             s["split"] = f.split
+            s["split_cost"] = cost
         L.gs_render_bwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, s, f.dimg, f.T_final, f.n_proc,
                         f.tile_nproc, f.grad2d, f.err)
 
-    out = {"fwd_ms": {"raster": best(lambda: fwd(None)), "count": best(lambda: fwd(o_count)),
-                      "learned": best(lambda: fwd(o_learned))},
-           "bwd_ms": {"raster": best(lambda: bwd(None)), "by_processed": best(lambda: bwd(o_bwd)),
-                      "learned": best(lambda: bwd(o_learned))},
-           "order_cost_ms": {"count": t_count, "learned": t_learned}}
-    fwd(o_learned)
-    L.gs_render_fwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, sch(o_learned), f.img, f.T_final,
+    out = {"fwd_ms": {"raster": best(lambda: fwd(None)), "count": best(lambda: fwd(o_count))},
+           "bwd_ms": {"raster": best(lambda: bwd(None)), "count": best(lambda: bwd(o_count)),
+                      "by_processed": best(lambda: bwd(o_proc)), "learned": best(lambda: bwd(o_learned, pred))},
+           "order_cost_ms": {"count": t_count, "learned_bwd": t_learned}}
+    L.gs_render_fwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, None, f.img, f.T_final,
                     f.n_proc, f.tile_nproc, f.tile_ns, f.err)
     torch.cuda.synchronize()
     ns = f.tile_ns.double()
@@ -849,6 +978,8 @@ def main():
                     help="time the forward pass under four colour layouts (prints its own JSON line)")
     ap.add_argument("--colour-buckets", action="store_true",
                     help="time the colour hashing of the tile lists (prints its own JSON line)")
+    ap.add_argument("--colour-merge", action="store_true",
+                    help="time the merged-bucket render against the exact one (prints its own JSON line)")
     ap.add_argument("--density-control", action="store_true",
                     help="time one round of workload-sensitive density control (prints its own JSON line)")
     ap.add_argument("--density-r", type=float, default=0.005, help="neighbour radius of the density control")
@@ -860,6 +991,9 @@ def main():
     if args.colour_buckets:
         args.steps = 10 if args.steps is None else args.steps
         run_colour_buckets(args)
+    elif args.colour_merge:
+        args.steps = 20 if args.steps is None else args.steps
+        run_colour_merge(args)
     elif args.density_control:
         args.steps = 10 if args.steps is None else args.steps
         run_density_control(args)

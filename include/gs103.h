@@ -116,8 +116,8 @@ int gs_zero(void *d_ptr, size_t n_bytes, gs_stream_t stream);
  * per digit; past that it gives up, sets GS_EW_TIMEOUT in *err_word and goes
  * on with the counts it has.  The call then completes with an unspecified
  * instance order, but every buffer it leaves still holds record indices in
- * [0, V*N) and every count is consistent with them, so no later kernel reads
- * or writes out of bounds.  A healthy look-back makes a few hundred reads at
+ * [0, V*N), and the counts the lists are placed by are taken from that same
+ * order, so no later kernel reads or writes out of bounds.  A healthy look-back makes a few hundred reads at
  * most; 0 makes every tile but the first give up at once (how the tests
  * reach this path without a stuck GPU).  The limit is process-wide and
  * applies to calls made after gs_set_wait_limit returns; reads < 0 returns
@@ -252,6 +252,13 @@ typedef struct {
     int32_t *d_split;          /* gs_render_bwd only: one device int of scratch; non-NULL lets the
                                   heaviest head-of-order tiles be taken in four strips (images and
                                   gradients are unchanged up to the order of additions) */
+    uint64_t *d_tile_ns;       /* gs_render_bwd only: [T] u64; each tile's nanoseconds are ADDED
+                                  (the strips of a split tile add up; the caller zeroes it);
+                                  NULL = not measured.  gs_render_fwd takes its own d_tile_ns. */
+    const float *d_split_cost; /* gs_render_bwd with d_split only: [T] predicted log costs (e.g. the
+                                  cost MLP's); the heavy tiles counted for splitting are then those
+                                  whose exp(cost) exceeds a CTA's mean share of the total, instead of
+                                  those whose processed count does.  NULL = processed counts */
 } gs_schedule;
 
 /* a3. Forward blending (Sec. II-A blending equation), one CTA per 16x16 tile.
@@ -426,6 +433,28 @@ int gs_colour_buckets(int n_tiles, const uint32_t *d_tile_ranges, const uint32_t
                       const void *d_splats, int rgb_dtype, unsigned long long *d_count, double *d_sums,
                       int32_t *d_tile_distinct, gs_stream_t stream);
 
+/* Similarity-based sampling and merging of the tile lists (Sec. IV-C1), an
+ * opt-in lossy render mode.  Per tile, the entries of its list (as
+ * gs_colour_buckets reads them) are grouped by the same colour bucket; the
+ * paper merges a bucket by averaging the colour and accumulating the
+ * opacity.  Reading taken: the bucket's first entry in list (depth) order
+ * represents it, keeping its record's position, conic and place in the list,
+ * with colour = the mean of the members' record colours and opacity
+ * min(1, sum of the members' opacities 2^lo); the other entries are dropped.
+ * Out: d_out_ranges [n_tiles, 2] the merged lists (each within its input
+ * range, from its start; an empty tile reads [0, 0)); d_out_splats FP32 splat
+ * records (GS_SPLAT_BYTES_F32 each) and d_out_vals (u32, = position) at the
+ * positions of the merged lists, so gs_render_fwd(d_out_ranges, d_out_vals,
+ * d_out_splats, GS_F32, ...) renders them; optional d_out_src (the record
+ * index of each representative) and d_out_members (its member count).  The
+ * output arrays are indexed like d_vals (its length suffices).  Sums are FP32
+ * in shared memory, in no fixed order (last-bit differences between runs).
+ * Forward only: no reverse pass is defined for merged lists. */
+int gs_colour_merge(int n_tiles, const uint32_t *d_tile_ranges, const uint32_t *d_vals,
+                    const void *d_splats, int rgb_dtype, uint32_t *d_out_ranges, uint32_t *d_out_vals,
+                    void *d_out_splats, uint32_t *d_out_src, uint32_t *d_out_members,
+                    gs_stream_t stream);
+
 /* Workload-sensitive density control (Sec. III-C), one round.  Positions are
  * the first 3N floats of the grouped layout ([N, 3], finite).  Squared
  * distances are (dx^2 + dy^2) + dz^2 in FP32 with every operation rounded.
@@ -492,6 +521,23 @@ int gs_density_control(int N, const float *d_params, const float *d_m, const flo
 int gs_tile_features(const gs_camera *cams, int n_views, const uint32_t *d_tile_ranges,
                      const uint32_t *d_vals, const void *d_splats, int rgb_dtype, int cap,
                      float *d_feats, const void *d_w16, float *d_pred, gs_stream_t stream);
+
+/* a8, the reverse pass's cost features: eight per tile from what the
+ * forward pass of the same step left, [T, 8] FP32 into d_feats:
+ *   b0 log1p(d_tile_nproc, the tile's largest processed count),
+ *   b1 log1p(mean of d_n_proc over the tile's in-image pixels),
+ *   b2 log1p(the forward's d_tile_ns of the tile; 0 if NULL),
+ *   b3 log1p(the tile's kept list length, from d_tile_ranges),
+ *   b4 log1p(mean over the tile's upper and lower 16x8 halves of their
+ *      largest d_n_proc),
+ *   b5 the fraction of in-image pixels with d_n_proc > 0,
+ *   b6 the in-image pixel fraction, b7 log1p(W H) / 16.
+ * With d_w16 and d_pred the MLP's prediction is written as in
+ * gs_tile_features. */
+int gs_bwd_tile_features(const gs_camera *cams, int n_views, const uint32_t *d_tile_ranges,
+                         const int32_t *d_tile_nproc, const int32_t *d_n_proc,
+                         const uint64_t *d_tile_ns, float *d_feats, const void *d_w16, float *d_pred,
+                         gs_stream_t stream);
 
 /* MLP 8 -> 32 (ReLU) -> 1.  Weights are 321 values in the order W1 [32, 8]
  * (row-major), b1 [32], W2 [32], b2 [1].  gs_mlp_predict reads FP16 weights

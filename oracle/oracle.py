@@ -336,6 +336,34 @@ def tile_features(cam, kp: dict, proj: dict, tx: int, ty: int, cap: int = 4096) 
     return f
 
 
+def bwd_tile_features(cam, n_proc, tile_nproc, tile_ns, kept) -> np.ndarray:
+    """The reverse pass's eight cost features of every tile of one view
+    ([n_tiles, 8], FP64), from what the forward pass left: b0 log1p(the
+    tile's largest processed count), b1 log1p(mean processed count over its
+    in-image pixels), b2 log1p(the forward's time of the tile, ns), b3
+    log1p(its kept list length), b4 log1p(mean over its upper and lower
+    16x8 halves of their largest processed count), b5 the fraction of its
+    in-image pixels with a processed count > 0, b6 the in-image pixel
+    fraction, b7 log1p(W H) / 16.  n_proc is the [H, W] map of processed
+    counts."""
+    npm = np.maximum(np.asarray(n_proc, np.float64).reshape(cam.H, cam.W), 0)
+    out = np.zeros((cam.n_tiles, 8))
+    for t in range(cam.n_tiles):
+        tx, ty = t % cam.tiles_x, t // cam.tiles_x
+        block = npm[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16]
+        top, bottom = block[:8], block[8:]
+        halves = [h.max() if h.size else 0.0 for h in (top, bottom)]
+        out[t, 0] = np.log1p(max(0, int(tile_nproc[t])))
+        out[t, 1] = np.log1p(block.sum() / block.size)
+        out[t, 2] = np.log1p(float(tile_ns[t]))
+        out[t, 3] = np.log1p(float(kept[t]))
+        out[t, 4] = np.log1p(0.5 * (halves[0] + halves[1]))
+        out[t, 5] = (block > 0).sum() / block.size
+        out[t, 6] = block.size / 256.0
+        out[t, 7] = np.log1p(float(cam.W) * cam.H) / 16.0
+    return out
+
+
 def forward(cam, scene, window=None, margin_alpha=1e-4, margin_T=1e-3) -> dict:
     """Key path + FP64 projection + render, in one call."""
     kp = keypath(cam, scene)

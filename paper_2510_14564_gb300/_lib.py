@@ -31,10 +31,10 @@ EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_set_wait_limit", 
            "gs_bin_sort_prefix_workspace", "gs_bin_sort_prefix", "gs_bin_sort_prefix_repair",
            "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_project_bwd", "gs_project_bwd_adam", "gs_adam_step",
            "gs_adam_flat", "gs_tile_features", "gs_mlp_predict", "gs_mlp_grad",
-           "gs_mlp_train_step", "gs_rank_judge", "gs_int_cost", "gs_range_cost", "gs_sched_order_workspace",
+           "gs_mlp_train_step", "gs_rank_judge", "gs_bwd_tile_features", "gs_int_cost", "gs_range_cost", "gs_sched_order_workspace",
            "gs_sched_order", "gs_grad2d_norm", "gs_densify_workspace", "gs_densify",
            "gs_colour_arrays", "gs_render_fwd_colour", "gs_density_workspace", "gs_density_stats",
-           "gs_density_control", "gs_colour_buckets"]
+           "gs_density_control", "gs_colour_buckets", "gs_colour_merge"]
 
 
 class GsError(RuntimeError):
@@ -53,7 +53,8 @@ class GsCamera(ctypes.Structure):
 class GsSchedule(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("d_order", ctypes.c_void_p),
                 ("d_queue", ctypes.c_void_p), ("budget_ns", ctypes.c_longlong),
-                ("d_n_order", ctypes.c_void_p), ("d_split", ctypes.c_void_p)]
+                ("d_n_order", ctypes.c_void_p), ("d_split", ctypes.c_void_p),
+                ("d_tile_ns", ctypes.c_void_p), ("d_split_cost", ctypes.c_void_p)]
 
 
 _lib = None
@@ -102,6 +103,7 @@ def lib():
         L.gs_adam_flat.argtypes = [I64, VP, VP, VP, VP, F32, F32, F32, F32, I32, VP]
         L.gs_tile_features.argtypes = [P(GsCamera), I32, VP, VP, VP, I32, I32, VP, VP, VP, VP]
         L.gs_mlp_predict.argtypes = [VP, VP, I32, VP, VP]
+        L.gs_bwd_tile_features.argtypes = [P(GsCamera), I32, VP, VP, VP, VP, VP, VP, VP, VP]
         L.gs_mlp_grad.argtypes = [VP, VP, VP, VP, I32, VP, VP, VP]
         L.gs_mlp_train_step.argtypes = [VP, VP, VP, VP, I32, F32, VP, VP, VP, I32, VP, VP, VP]
         L.gs_rank_judge.argtypes = [VP, VP, I32, VP, I32, I32, ctypes.c_uint32, VP, VP]
@@ -113,6 +115,7 @@ def lib():
         L.gs_colour_arrays.argtypes = [I64, VP, VP, VP, VP]
         L.gs_density_workspace.argtypes = [I32, P(SZ)]
         L.gs_colour_buckets.argtypes = [I32, VP, VP, VP, I32, VP, VP, VP, VP]
+        L.gs_colour_merge.argtypes = [I32, VP, VP, VP, I32, VP, VP, VP, VP, VP, VP]
         L.gs_density_stats.argtypes = [I32, VP, F32, I32, VP, VP, VP, VP, P(F32), VP, VP, SZ, VP]
         L.gs_density_control.argtypes = [I32, VP, VP, VP, VP, VP, F32, I32, F32, F32, F32, F32, F32, I64, VP, VP,
                                          VP, VP, I32, VP, VP, VP, SZ, VP, VP]
@@ -267,6 +270,8 @@ def _sched(sched):
     s.budget_ns = int(sched.get("budget_ns", 0))
     s.d_n_order = ptr(sched.get("n_order"))
     s.d_split = ptr(sched.get("split"))
+    s.d_tile_ns = ptr(sched.get("tile_ns"))
+    s.d_split_cost = ptr(sched.get("split_cost"))
     return ctypes.byref(s), s
 
 
@@ -390,12 +395,25 @@ def gs_colour_buckets(n_tiles, tile_ranges, vals, splats, rgb_dtype, count, sums
                                   ptr(sums), ptr(tile_distinct), stream_ptr(stream)), "gs_colour_buckets")
 
 
+def gs_colour_merge(n_tiles, tile_ranges, vals, splats, rgb_dtype, out_ranges, out_vals, out_splats,
+                    out_src=None, out_members=None, stream=None):
+    check(lib().gs_colour_merge(int(n_tiles), ptr(tile_ranges), ptr(vals), ptr(splats), int(rgb_dtype),
+                                ptr(out_ranges), ptr(out_vals), ptr(out_splats), ptr(out_src), ptr(out_members),
+                                stream_ptr(stream)), "gs_colour_merge")
+
+
 def gs_tile_features(cams, tile_ranges, vals, splats, rgb_dtype, cap, feats, w16=None, pred=None,
                      stream=None):
     ca = camera_array(cams)
     check(lib().gs_tile_features(ca, len(cams), ptr(tile_ranges), ptr(vals), ptr(splats),
                                  int(rgb_dtype), int(cap), ptr(feats), ptr(w16), ptr(pred),
                                  stream_ptr(stream)), "gs_tile_features")
+
+
+def gs_bwd_tile_features(cams, tile_ranges, tile_nproc, n_proc, tile_ns, feats, w16=None, pred=None, stream=None):
+    ca = camera_array(cams)
+    check(lib().gs_bwd_tile_features(ca, len(cams), ptr(tile_ranges), ptr(tile_nproc), ptr(n_proc), ptr(tile_ns),
+                                     ptr(feats), ptr(w16), ptr(pred), stream_ptr(stream)), "gs_bwd_tile_features")
 
 
 def gs_mlp_predict(w16, feats, n, pred, stream=None):

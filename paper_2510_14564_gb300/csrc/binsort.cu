@@ -178,15 +178,27 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
     return v;
 }
 
-// Global histograms of the four 8-bit digits of n keys: ghist[4][256] (zeroed
-// by the caller).
-__global__ void __launch_bounds__(256) k_onesweep_hist(const uint32_t *__restrict__ keys, uint32_t n,
+// Range reduction and the global histograms of the four 8-bit digits of n
+// keys.  range[0] holds ~min and range[1] the max of the visible keys (raw
+// FP32 depth bits; 0xffffffff marks a culled record), as k_depth_keys left
+// them.  Each key is rewritten in place as its offset from the smallest
+// visible key, culled records as the largest visible offset + 1: an
+// order-preserving map, so the stable sort is unchanged, whose top digits are
+// zero for every key when the depths span few binades (a digit pass in
+// which every key has the same digit is then a copy).  ghist[4][256] is
+// zeroed by the caller.
+__global__ void __launch_bounds__(256) k_onesweep_hist(uint32_t *__restrict__ keys, uint32_t n,
+                                                       const uint32_t *__restrict__ range,
                                                        uint32_t *__restrict__ ghist) {
     __shared__ uint32_t s_h[4 * kRadix];
     for (int k = threadIdx.x; k < 4 * kRadix; k += 256) s_h[k] = 0;
     __syncthreads();
+    const uint32_t kmin = ~__ldg(range), kmax = __ldg(range + 1);
+    const bool any = kmin <= kmax;
     for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < n; i += gridDim.x * 256u) {
-        const uint32_t k = __ldg(keys + i);
+        const uint32_t raw = keys[i];
+        const uint32_t k = !any ? 0u : (raw == 0xffffffffu ? kmax - kmin + 1u : raw - kmin);
+        keys[i] = k;
 #pragma unroll
         for (int d = 0; d < 4; ++d) atomicAdd(&s_h[d * kRadix + ((k >> (8 * d)) & 255u)], 1u);
     }
@@ -196,11 +208,18 @@ __global__ void __launch_bounds__(256) k_onesweep_hist(const uint32_t *__restric
 }
 
 // One digit pass.  status [nb][256] and *tile_counter are zeroed by the
-// caller; ghist is this digit's global histogram.
+// caller; ghist is this digit's global histogram.  If every key has the same
+// digit the pass is the identity and copies (the keys only if keys_needed).
+// With touched != NULL (the last pass of a one-view sort) it also writes,
+// beside each record's final position g, cnt[g] = max(0, touched[record])
+// and rs[g] = its tile rectangle (empty for a culled record): the later
+// passes then read both in depth order, coalesced, without a gather.
 __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, uint32_t n, int shift, const uint32_t *__restrict__ ghist,
-    uint32_t *status, uint32_t *tile_counter, long long wait_limit, int *err_word) {
+    uint32_t *status, uint32_t *tile_counter, long long wait_limit, int keys_needed,
+    const int32_t *__restrict__ touched, uint32_t *__restrict__ cnt, const short4 *__restrict__ rect,
+    short4 *__restrict__ rs, int *err_word) {
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_wh[8][kRadix];
@@ -208,11 +227,31 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     __shared__ uint32_t s_goff[kRadix];
     __shared__ uint32_t s_warp[8], s_warp2[8];
     __shared__ uint32_t s_bid;
-    if (threadIdx.x == 0) s_bid = atomicAdd(tile_counter, 1u);
+    __shared__ int s_copy;
+    if (threadIdx.x == 0) {
+        s_bid = atomicAdd(tile_counter, 1u);
+        s_copy = 0;
+    }
     for (int k = threadIdx.x; k < 8 * kRadix; k += kSortThreads) (&s_wh[0][0])[k] = 0;
+    __syncthreads();
+    if (__ldg(ghist + threadIdx.x) == n) s_copy = 1;       // one digit for every key
     __syncthreads();
     const uint32_t bid = s_bid;
     const long long bbase = (long long)bid * kSortTile;
+    if (s_copy) {
+        const long long end = min((long long)n, bbase + kSortTile);
+        for (long long i = bbase + threadIdx.x; i < end; i += kSortThreads) {
+            const uint32_t v = __ldg(vin + i);
+            vout[i] = v;
+            if (keys_needed) kout[i] = __ldg(kin + i);
+            if (touched) {
+                const int t = __ldg(touched + v);
+                cnt[i] = t > 0 ? (uint32_t)t : 0u;
+                if (rs) rs[i] = t > 0 ? __ldg(rect + v) : make_short4(0, 0, 0, 0);
+            }
+        }
+        return;
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
     const long long base = bbase + w * (kSortItems * 32);
@@ -282,8 +321,14 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
         const uint32_t k = s_keys[q];
         const uint32_t d = (k >> shift) & 255u;
         const uint32_t g = s_goff[d] + (uint32_t)(q - s_dstart[d]);
-        kout[g] = k;
-        vout[g] = s_vals[q];
+        const uint32_t v = s_vals[q];
+        if (keys_needed) kout[g] = k;
+        vout[g] = v;
+        if (touched) {
+            const int t = __ldg(touched + v);
+            cnt[g] = t > 0 ? (uint32_t)t : 0u;
+            if (rs) rs[g] = t > 0 ? __ldg(rect + v) : make_short4(0, 0, 0, 0);
+        }
     }
 }
 
@@ -291,7 +336,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
 // four digit histograms, four tile counters).
 static size_t onesweep_scratch_bytes(long long n) {
     const long long nb = (n + kSortTile - 1) / kSortTile;
-    return 4 * (size_t)(4 * kRadix * nb + 4 * kRadix + 4);
+    return 4 * (size_t)(4 * kRadix * nb + 4 * kRadix + 4 + 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -373,24 +418,59 @@ __global__ void __launch_bounds__(1024) k_scan_top(T *partials, int np, T *total
         }
 }
 
+// Each thread owns kScanItems consecutive items of the chunk and moves them
+// with 16-byte vector accesses (a warp covers one contiguous span, so loads
+// and stores stay coalesced, and no shared-memory staging is needed);
+// partial chunks at the end take the scalar path.
+template <typename T>
+__device__ __forceinline__ void load_items(const T *__restrict__ p, long long i0, long long n, T (&v)[kScanItems]) {
+    constexpr int V = 16 / sizeof(T);
+    if (i0 + kScanItems <= n && ((reinterpret_cast<uintptr_t>(p + i0) & 15) == 0)) {
+#pragma unroll
+        for (int k = 0; k < kScanItems; k += V) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p + i0 + k));
+            const T *t = reinterpret_cast<const T *>(&q);
+#pragma unroll
+            for (int e = 0; e < V; ++e) v[k + e] = t[e];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = i0 + k < n ? p[i0 + k] : (T)0;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_items(T *__restrict__ p, long long i0, long long n, const T (&v)[kScanItems]) {
+    constexpr int V = 16 / sizeof(T);
+    if (i0 + kScanItems <= n && ((reinterpret_cast<uintptr_t>(p + i0) & 15) == 0)) {
+#pragma unroll
+        for (int k = 0; k < kScanItems; k += V) {
+            uint4 q;
+            T *t = reinterpret_cast<T *>(&q);
+#pragma unroll
+            for (int e = 0; e < V; ++e) t[e] = v[k + e];
+            *reinterpret_cast<uint4 *>(p + i0 + k) = q;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k)
+            if (i0 + k < n) p[i0 + k] = v[k];
+    }
+}
+
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const Tin *__restrict__ in, long long n,
                                                              const Tout *__restrict__ partials,
                                                              Tout *__restrict__ out) {
-    __shared__ Tout s_v[kScanChunk];
     __shared__ Tout s_w[8];
-    const long long base = (long long)blockIdx.x * kScanChunk;
-    for (int k = 0; k < kScanItems; ++k) {
-        int j = k * kScanThreads + threadIdx.x;
-        long long i = base + j;
-        s_v[j] = i < n ? (Tout)in[i] : (Tout)0;
-    }
-    __syncthreads();
+    const long long i0 = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+    Tin vin[kScanItems];
+    load_items<Tin>(in, i0, n, vin);
     Tout loc[kScanItems];
     Tout sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        loc[k] = s_v[threadIdx.x * kScanItems + k];
+        loc[k] = (Tout)vin[k];
         sum += loc[k];
     }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -408,15 +488,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const Tin *__restri
     Tout run = off + inc - sum;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        s_v[threadIdx.x * kScanItems + k] = run;
-        run += loc[k];
+        const Tout c = loc[k];
+        loc[k] = run;
+        run += c;
     }
-    __syncthreads();
-    for (int k = 0; k < kScanItems; ++k) {
-        int j = k * kScanThreads + threadIdx.x;
-        long long i = base + j;
-        if (i < n) out[i] = s_v[j];
-    }
+    store_items<Tout>(out, i0, n, loc);
 }
 
 template <typename Tin, typename Tout>
@@ -434,22 +510,53 @@ static void exclusive_scan(const Tin *in, Tout *out, long long n, Tout *partials
 // Depth keys and record indices of the depth sort.  The indices go to both
 // value buffers of the sort's ping-pong, so that every value buffer holds
 // record indices only, whatever a sort cut short by a timeout leaves there.
-__global__ void k_depth_keys(const float *__restrict__ depth, const int *__restrict__ touched,
-                             long long n, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                             uint32_t *__restrict__ vals2) {
-    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    keys[j] = touched[j] > 0 ? __float_as_uint(depth[j]) : 0xffffffffu;
-    vals[j] = (uint32_t)j;
-    vals2[j] = (uint32_t)j;
+// With range != NULL also range[0] = ~(smallest visible key) and range[1] =
+// the largest (both zeroed by the caller): reduced per CTA over a
+// grid-stride loop, then one atomic per CTA and word.
+__global__ void __launch_bounds__(256) k_depth_keys(const float *__restrict__ depth, const int *__restrict__ touched,
+                                                    long long n, uint32_t *__restrict__ keys,
+                                                    uint32_t *__restrict__ vals, uint32_t *__restrict__ vals2,
+                                                    uint32_t *__restrict__ range) {
+    __shared__ uint32_t s_inv[8], s_max[8];
+    uint32_t inv = 0u, mx = 0u;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const uint32_t k = touched[j] > 0 ? __float_as_uint(depth[j]) : 0xffffffffu;
+        keys[j] = k;
+        vals[j] = (uint32_t)j;
+        vals2[j] = (uint32_t)j;
+        if (k != 0xffffffffu) {
+            inv = max(inv, ~k);
+            mx = max(mx, k);
+        }
+    }
+    if (!range) return;
+    inv = __reduce_max_sync(0xffffffffu, inv);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) {
+        s_inv[threadIdx.x >> 5] = inv;
+        s_max[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) {
+            inv = max(inv, s_inv[w]);
+            mx = max(mx, s_max[w]);
+        }
+        if (inv) atomicMax(range, inv);
+        if (mx) atomicMax(range + 1, mx);
+    }
 }
 
+// Each record's tile count, and (rs != NULL) its rectangle, in sorted order.
 __global__ void k_gather_counts(const uint32_t *__restrict__ order, const int *__restrict__ touched,
-                                long long n, uint32_t *__restrict__ out) {
+                                long long n, uint32_t *__restrict__ out, const short4 *__restrict__ rect = nullptr,
+                                short4 *__restrict__ rs = nullptr) {
     long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    int t = touched[order[j]];
+    const uint32_t g = order[j];
+    int t = touched[g];
     out[j] = t > 0 ? (uint32_t)t : 0u;
+    if (rs) rs[j] = t > 0 ? __ldg(rect + g) : make_short4(0, 0, 0, 0);
 }
 
 // Clamp the instance count to the capacity; flag an overflow.
@@ -624,8 +731,7 @@ __device__ __forceinline__ uint32_t warp_scan_smem(uint32_t *a, int n) {
 
 // Pass 1 count: instances per (global row, chunk) into M1[row * Cv + chunk].
 __global__ void __launch_bounds__(32 * kP1Warps) k_p1_count(TileBatch tb, int N, int Cv, int TYmax,
-                                                            const uint32_t *__restrict__ order,
-                                                            const short4 *__restrict__ rect,
+                                                            const short4 *__restrict__ rs,
                                                             const unsigned long long *__restrict__ offs,
                                                             uint32_t *__restrict__ M1) {
     extern __shared__ uint32_t s_p1[];
@@ -639,7 +745,7 @@ __global__ void __launch_bounds__(32 * kP1Warps) k_p1_count(TileBatch tb, int N,
     __syncwarp();
     const ChunkGeom cg = chunk_of(v, k, Cv, N, offs);
     for (long long i = cg.lo + l; i < cg.hi; i += 32) {
-        const short4 rc = __ldg(rect + __ldg(order + i));
+        const short4 rc = __ldg(rs + i);
         const uint32_t wd = (uint32_t)(rc.z - rc.x);
         atomicAdd(&d[rc.y], wd);
         atomicAdd(&d[rc.w], 0u - wd);
@@ -658,7 +764,7 @@ __global__ void __launch_bounds__(32 * kP1Warps) k_p1_count(TileBatch tb, int N,
 // Pass 1 place: each warp hands out slots in record order from per-row cursors.
 __global__ void __launch_bounds__(32 * kP1Warps) k_p1_place(TileBatch tb, int N, int Cv, int TYmax,
                                                             const uint32_t *__restrict__ order,
-                                                            const short4 *__restrict__ rect,
+                                                            const short4 *__restrict__ rs,
                                                             const unsigned long long *__restrict__ offs,
                                                             const unsigned long long *__restrict__ O1,
                                                             const unsigned long long *__restrict__ total,
@@ -681,7 +787,7 @@ __global__ void __launch_bounds__(32 * kP1Warps) k_p1_place(TileBatch tb, int N,
         short4 rc = make_short4(0, 0, 0, 0);
         if (i < cg.hi) {
             g = __ldg(order + i);
-            rc = __ldg(rect + g);
+            rc = __ldg(rs + i);
         }
         const int cnt = (rc.z - rc.x) * (rc.w - rc.y);
         unsigned has = __ballot_sync(0xffffffffu, cnt > 0);
@@ -876,7 +982,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_p2_place(TileBatch tb, int 
 // Workspace plan
 // ---------------------------------------------------------------------------
 struct Plan {
-    size_t dk0, dk1, dv0, dv1, cnt, offs, tk0, tk1, tvs, hist, part, misc, bytes;
+    size_t dk0, dk1, dv0, dv1, cnt, rs, offs, tk0, tk1, tvs, hist, part, misc, bytes;
     size_t ids1, xs1, m1, o1, nsl, m2l, spre, m2b, m2, o2, tcnt;
     long long m1n, m2n, slices_ub;
     int nb_max, Cv, TXmax, TYmax;
@@ -902,6 +1008,7 @@ static Plan make_plan(long long VN, long long cap, const TileBatch &tb) {
     if (p.direct) {
         p.tk0 = p.tk1 = p.tvs = 0;
         p.cnt = take(4 * VN);
+        p.rs = take(8 * VN);
         p.offs = take(8 * (VN + 1));
         p.ids1 = take(4 * (size_t)cap);
         p.xs1 = take(2 * (size_t)cap);
@@ -921,6 +1028,7 @@ static Plan make_plan(long long VN, long long cap, const TileBatch &tb) {
         maxscan = p.m2n > maxscan ? p.m2n : maxscan;
     } else {
         p.ids1 = p.xs1 = p.m1 = p.o1 = p.nsl = p.m2l = p.spre = p.m2b = p.m2 = p.o2 = p.tcnt = 0;
+        p.rs = 0;
         p.cnt = take(4 * VN);
         p.offs = take(8 * (VN + 1));
         p.tk0 = take(4 * cap); p.tk1 = take(4 * cap); p.tvs = take(4 * cap);
@@ -958,28 +1066,35 @@ static void radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
 // views, a stable pass on the view.  Returns the sorted record indices.
 static const uint32_t *depth_order(const float *d_depth, const int32_t *d_touched, long long VN, int N,
                                    int n_views, uint32_t *dk0, uint32_t *dk1, uint32_t *dv0, uint32_t *dv1,
-                                   uint32_t *hist, void *part, int *err_word, cudaStream_t st) {
-    { k_depth_keys<<<cdiv(VN, 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0, dv1); count_launches(1); }
+                                   uint32_t *hist, void *part, int *err_word, cudaStream_t st,
+                                   uint32_t *cnt = nullptr, const short4 *rect = nullptr, short4 *rs = nullptr) {
     uint32_t *ka = dk0, *kb = dk1, *va = dv0, *vb = dv1;
     if (VN < (long long)kLbVal) {
-        // onesweep: status words of the four passes, the four histograms and
-        // the four tile counters, zeroed together
+        // onesweep: status words of the four passes, the four histograms, the
+        // four tile counters and the key range, zeroed together
         const long long nb = (VN + kSortTile - 1) / kSortTile;
         uint32_t *status = hist, *ghist = hist + 4 * kRadix * nb, *counters = ghist + 4 * kRadix;
+        uint32_t *range = counters + 4;
         cudaMemsetAsync(hist, 0, onesweep_scratch_bytes(VN), st);
+        { k_depth_keys<<<(int)(cdiv(VN, 256) < 152 * 8 ? cdiv(VN, 256) : 152 * 8), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0, dv1, range); count_launches(1); }
         if (VN > 0) {
             const int hb = (int)(VN / 4096 + 1 < 1024 ? VN / 4096 + 1 : 1024);
-            { k_onesweep_hist<<<hb, 256, 0, st>>>(ka, (uint32_t)VN, ghist); count_launches(1); }
+            { k_onesweep_hist<<<hb, 256, 0, st>>>(ka, (uint32_t)VN, range, ghist); count_launches(1); }
             for (int pass = 0; pass < 4; ++pass) {
+                // the last pass of a one-view sort also gathers each record's tile count
+                const bool last = pass == 3 && n_views == 1 && cnt;
                 { k_onesweep_pass<<<(int)nb, kSortThreads, 0, st>>>(ka, va, kb, vb, (uint32_t)VN, 8 * pass, ghist + kRadix * pass,
                                                                    status + (size_t)kRadix * nb * pass, counters + pass,
-                                                                   g_wait_limit.load(), err_word);
+                                                                   g_wait_limit.load(), pass < 3 ? 1 : 0,
+                                                                   last ? d_touched : nullptr, cnt, rect, rs, err_word);
                   count_launches(1); }
                 uint32_t *t = ka; ka = kb; kb = t;
                 t = va; va = vb; vb = t;
             }
+            if (n_views == 1 && cnt) return va;
         }
     } else {
+        { k_depth_keys<<<(int)(cdiv(VN, 256) < 152 * 8 ? cdiv(VN, 256) : 152 * 8), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0, dv1, nullptr); count_launches(1); }
         for (int pass = 0; pass < 4; ++pass) {
             radix_pass(ka, va, kb, vb, nullptr, (uint32_t)VN, VN, 8 * pass, 8, true, hist, (uint32_t *)part, st);
             uint32_t *t = ka; ka = kb; kb = t;
@@ -993,6 +1108,7 @@ static const uint32_t *depth_order(const float *d_depth, const int32_t *d_touche
         radix_pass(ka, va, kb, vb, nullptr, (uint32_t)VN, VN, 0, vbits, false, hist, (uint32_t *)part, st);
         uint32_t *t = va; va = vb; vb = t;
     }
+    if (cnt && VN > 0) { k_gather_counts<<<cdiv(VN, 256), 256, 0, st>>>(va, d_touched, VN, cnt, rect, rs); count_launches(1); }
     return va;
 }
 
@@ -1101,8 +1217,16 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
         cudaMemsetAsync(d_n_instances, 0, sizeof(long long), st);
         return launch_status();
     }
-    // 1. records in (view, depth bits, index) order; culled last in each view
-    const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, d_err_word, st);
+    // 1. records in (view, depth bits, index) order, culled last in each
+    //    view, and each record's tile count in that order.  (The emission
+    //    of the wide-view path writes each record's tiles from its count: it
+    //    gathers the counts after the sort, from the final order itself, so
+    //    they agree with the order even after a look-back timeout.)
+    const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, d_err_word, st,
+                                        p.direct ? (uint32_t *)(ws + p.cnt) : nullptr,
+                                        reinterpret_cast<const short4 *>(d_rect),
+                                        p.direct ? (short4 *)(ws + p.rs) : nullptr);
+    const short4 *rs = p.direct ? (const short4 *)(ws + p.rs) : nullptr;   // rectangles in sorted order
 
     if (p.direct) {
         uint32_t *ids1 = (uint32_t *)(ws + p.ids1);
@@ -1116,17 +1240,16 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
         const int R = tb.total_rows;
         uint32_t *cnt = (uint32_t *)(ws + p.cnt);
         unsigned long long *offs = (unsigned long long *)(ws + p.offs);
-        { k_gather_counts<<<cdiv(VN, 256), 256, 0, st>>>(order, d_touched, VN, cnt); count_launches(1); }
         exclusive_scan<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, offs + VN, st);
         const int nchunks = n_views * p.Cv;
         const int p1_blocks = cdiv(nchunks, kP1Warps);
         const size_t p1_smem = sizeof(uint32_t) * (size_t)(p.TYmax + 1) * kP1Warps;
         allow_dynamic_smem((const void *)k_p1_count, p1_smem);
         allow_dynamic_smem((const void *)k_p1_place, p1_smem);
-        { k_p1_count<<<p1_blocks, 32 * kP1Warps, p1_smem, st>>>(tb, N, p.Cv, p.TYmax, order, rect, offs, M1); count_launches(1); }
+        { k_p1_count<<<p1_blocks, 32 * kP1Warps, p1_smem, st>>>(tb, N, p.Cv, p.TYmax, rs, offs, M1); count_launches(1); }
         exclusive_scan<uint32_t, unsigned long long>(M1, O1, p.m1n, (unsigned long long *)part, O1 + p.m1n, st);
         { k_finish_count<<<1, 1, 0, st>>>(O1 + p.m1n, capacity, d_n_instances, count, d_err_word); count_launches(1); }
-        { k_p1_place<<<p1_blocks, 32 * kP1Warps, p1_smem, st>>>(tb, N, p.Cv, p.TYmax, order, rect, offs, O1,
+        { k_p1_place<<<p1_blocks, 32 * kP1Warps, p1_smem, st>>>(tb, N, p.Cv, p.TYmax, order, rs, offs, O1,
                                                                O1 + p.m1n, capacity, ids1, xs1); count_launches(1); }
         { k_p2_rows<<<cdiv(R, 256), 256, 0, st>>>(tb, p.Cv, O1, O1 + p.m1n, capacity, nsl, m2l); count_launches(1); }
         exclusive_scan<uint32_t, uint32_t>(nsl, spre, R, (uint32_t *)part, spre + R, st);
@@ -1323,7 +1446,7 @@ __global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(int n_views, int
 template <int DT>
 __global__ void __launch_bounds__(256) k_pre_count(TileBatch tb, int N, int Cv, int Tmax,
                                                    const uint32_t *__restrict__ order,
-                                                   const short4 *__restrict__ rect,
+                                                   const short4 *__restrict__ rs,
                                                    const void *__restrict__ splats,
                                                    const long long *__restrict__ bounds,
                                                    uint32_t *__restrict__ Mc, uint32_t *__restrict__ Mv) {
@@ -1341,9 +1464,11 @@ __global__ void __launch_bounds__(256) k_pre_count(TileBatch tb, int N, int Cv, 
         uint32_t g[R];
         short4 rc[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) g[r] = i0 + r * 256 < cg.hi ? __ldg(order + i0 + r * 256) : 0xffffffffu;
-#pragma unroll
-        for (int r = 0; r < R; ++r) rc[r] = g[r] != 0xffffffffu ? __ldg(rect + g[r]) : make_short4(0, 0, 0, 0);
+        for (int r = 0; r < R; ++r) {
+            const bool in = i0 + r * 256 < cg.hi;
+            g[r] = in ? (splats ? __ldg(order + i0 + r * 256) : 0u) : 0xffffffffu;
+            rc[r] = in ? __ldg(rs + i0 + r * 256) : make_short4(0, 0, 0, 0);
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (g[r] == 0xffffffffu) continue;
@@ -1508,7 +1633,7 @@ constexpr int kPlaceRounds = 4;                        // records staged per thr
 constexpr int kPlaceBatch = kPlaceRounds * kPlaceThreads;
 __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     TileBatch tb, int N, int Cv, int Tmax, const uint32_t *__restrict__ order,
-    const short4 *__restrict__ rect, const long long *__restrict__ bounds,
+    const short4 *__restrict__ rs, const long long *__restrict__ bounds,
     const uint32_t *__restrict__ Mc, const uint32_t *__restrict__ last_chunk,
     const unsigned long long *__restrict__ tstart, const unsigned long long *__restrict__ total,
     long long cap, uint32_t *__restrict__ vals, const float *__restrict__ depth,
@@ -1581,7 +1706,7 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
             rc[r] = make_short4(0, 0, 0, 0);
             if (i < cg.hi) {
                 g[r] = __ldg(order + i);
-                rc[r] = __ldg(rect + g[r]);
+                rc[r] = __ldg(rs + i);
             }
         }
 #pragma unroll
@@ -1674,7 +1799,7 @@ __global__ void k_range_counts(const uint2 *__restrict__ ranges, int T, uint32_t
 }
 
 struct PrePlan {
-    size_t dk0, dk1, dv0, dv1, cnt, offs, mc, mv, full, lastc, kept, tstart, bnd, vshare, hist, part, misc, bytes;
+    size_t dk0, dk1, dv0, dv1, cnt, rs, offs, mc, mv, full, lastc, kept, tstart, bnd, vshare, hist, part, misc, bytes;
     int Cv, Tmax;
     bool ok;
 };
@@ -1690,6 +1815,7 @@ static PrePlan make_pre_plan(long long VN, const TileBatch &tb) {
     if (p.Cv < kPreMinChunksPerView) p.Cv = kPreMinChunksPerView;   // several views: at least this many each
     p.dk0 = take(4 * VN); p.dk1 = take(4 * VN); p.dv0 = take(4 * VN); p.dv1 = take(4 * VN);
     p.cnt = take(4 * VN);
+    p.rs = take(8 * VN);
     p.offs = take(8 * (VN + 1));
     p.mc = take(4 * (size_t)tb.n * p.Cv * p.Tmax);
     p.mv = take(4 * (size_t)tb.n * p.Cv * p.Tmax);
@@ -1822,8 +1948,9 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
         cudaMemsetAsync(d_n_instances, 0, sizeof(long long), st);
         return launch_status();
     }
-    const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, d_err_word, st);
-    { k_gather_counts<<<cdiv(VN, 256), 256, 0, st>>>(order, d_touched, VN, cnt); count_launches(1); }
+    short4 *rs = (short4 *)(ws + p.rs);                 // rectangles in sorted order
+    const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, d_err_word, st,
+                                        cnt, reinterpret_cast<const short4 *>(d_rect), rs);
     exclusive_scan<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, offs + VN, st);
     size_t gmax = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -1843,11 +1970,11 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     const void *cov_splats = d_tile_limit ? nullptr : d_splats;
     uint32_t *Mv_used = d_tile_limit ? nullptr : Mv;
     if (rgb_dtype == GS_F32)
-        { k_pre_count<GS_F32><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, bnd, Mc, Mv); count_launches(1); }
+        { k_pre_count<GS_F32><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rs, cov_splats, bnd, Mc, Mv); count_launches(1); }
     else if (rgb_dtype == GS_BF16)
-        { k_pre_count<GS_BF16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, bnd, Mc, Mv); count_launches(1); }
+        { k_pre_count<GS_BF16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rs, cov_splats, bnd, Mc, Mv); count_launches(1); }
     else
-        { k_pre_count<GS_F16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rect, cov_splats, bnd, Mc, Mv); count_launches(1); }
+        { k_pre_count<GS_F16><<<nchunks, 256, gmax, st>>>(tb, N, p.Cv, p.Tmax, order, rs, cov_splats, bnd, Mc, Mv); count_launches(1); }
     {
         int nblk = 0;
         for (int v = 0; v < n_views; ++v) nblk += cdiv(tb.v[v].TX * tb.v[v].TY, 32);
@@ -1866,7 +1993,7 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
         }
         const size_t smem = sizeof(uint32_t) * ((size_t)p.Tmax + gmax1);
         allow_dynamic_smem((const void *)k_pre_place, smem);      // 25 KB of its own static arrays
-        { k_pre_place<<<nchunks, kPlaceThreads, smem, st>>>(tb, N, p.Cv, p.Tmax, order, rect, bnd, Mc, lastc, tstart,
+        { k_pre_place<<<nchunks, kPlaceThreads, smem, st>>>(tb, N, p.Cv, p.Tmax, order, rs, bnd, Mc, lastc, tstart,
                                                  tstart + T, capacity, d_vals, d_depth,
                                                  reinterpret_cast<unsigned long long *>(d_keys)); count_launches(1); }
     }

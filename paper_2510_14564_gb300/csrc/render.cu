@@ -113,6 +113,7 @@ struct SchedArgs {
     long long budget_ns;
     const int *n_order;    // device count of tiles in order (null: all tiles)
     const int *split_head; // reverse pass: device count of head-of-order tiles taken in strips (null: none)
+    unsigned long long *tile_ns;   // reverse pass: per-tile nanoseconds added (null: not measured)
 };
 
 // Fetch the next tile for this CTA; -1 when the queue is exhausted.
@@ -363,6 +364,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 
         int part;
         const int tile = next_item<PPT>(sa, tb.total_tiles, &s_tile, &s_part, t_start, err_word, iter, part);
         if (tile < 0) break;
+        const unsigned long long t0 = sa.tile_ns ? globaltimer() : 0ull;
         const TileCtx<PPT> c = tile_ctx<PPT>(tb, ranges, tile, part);
         const ViewTiles &vt = tb.v[c.view];
         const float pcx = (float)c.px + 0.5f;
@@ -465,6 +467,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 
             }
         }
         __syncthreads();
+        if (sa.tile_ns && threadIdx.x == 0) atomicAdd(sa.tile_ns + tile, globaltimer() - t0);   // strips add up
     }
 }
 
@@ -472,25 +475,32 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 
 // exceeds the mean load of a CTA (the sum of all tiles' counts over the
 // number of CTAs): one CTA would stay busy with such a tile after the others
 // ran out of work.  One CTA; writes the count to *split_head.
-__global__ void __launch_bounds__(1024) k_split_head(const int *__restrict__ tile_nproc, int T, int n_cta,
+// With log_cost (a predicted log cost per tile, e.g. the cost MLP's) the
+// tiles' costs are exp(log_cost) instead of their processed counts.
+__device__ __forceinline__ double split_cost(const int *tile_nproc, const float *log_cost, int t) {
+    return log_cost ? (double)__expf(__ldg(log_cost + t)) : (double)max(0, __ldg(tile_nproc + t));
+}
+
+__global__ void __launch_bounds__(1024) k_split_head(const int *__restrict__ tile_nproc,
+                                                     const float *__restrict__ log_cost, int T, int n_cta,
                                                      int cap, int *__restrict__ split_head) {
-    __shared__ long long s_sum[32];
+    __shared__ double s_sum[32];
     __shared__ int s_cnt[32];
-    __shared__ long long s_total;
-    long long sum = 0;
-    for (int t = threadIdx.x; t < T; t += 1024) sum += max(0, __ldg(tile_nproc + t));
+    __shared__ double s_total;
+    double sum = 0;
+    for (int t = threadIdx.x; t < T; t += 1024) sum += split_cost(tile_nproc, log_cost, t);
     sum = warp_sum(sum);
     if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
     __syncthreads();
     if (threadIdx.x == 0) {
-        long long tot = 0;
+        double tot = 0;
         for (int q = 0; q < 32; ++q) tot += s_sum[q];
         s_total = tot;
     }
     __syncthreads();
-    const long long per_cta = s_total / max(1, n_cta);
+    const double per_cta = s_total / max(1, n_cta);
     int cnt = 0;
-    for (int t = threadIdx.x; t < T; t += 1024) cnt += (long long)__ldg(tile_nproc + t) > per_cta;
+    for (int t = threadIdx.x; t < T; t += 1024) cnt += split_cost(tile_nproc, log_cost, t) > per_cta;
     cnt = warp_sum(cnt);
     if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = cnt;
     __syncthreads();
@@ -513,6 +523,7 @@ static int fill_sched(const gs_schedule *sched, const TileBatch &tb, SchedArgs *
     sa->budget_ns = 0;
     sa->n_order = nullptr;
     sa->split_head = nullptr;
+    sa->tile_ns = sched ? reinterpret_cast<unsigned long long *>(sched->d_tile_ns) : nullptr;
     *grid = tb.total_tiles;
     if (!sched || sched->mode == GS_SCHED_RASTER) return GS_OK;
     if (sched->mode != GS_SCHED_ORDER || !sched->d_order || !sched->d_queue) return GS_ERR_ARG;
@@ -589,7 +600,7 @@ extern "C" int gs_render_bwd(const gs_camera *cams, int n_views, const uint32_t 
     if (sa.mode == GS_SCHED_ORDER && sched->d_split) {
         // as many head-of-order tiles as there are tiles heavier than a CTA's
         // share of the work are taken in strips (the order puts the costliest first)
-        { k_split_head<<<1, 1024, 0, st>>>(d_tile_nproc, tb.total_tiles, grid, grid, sched->d_split); count_launches(1); }
+        { k_split_head<<<1, 1024, 0, st>>>(d_tile_nproc, sched->d_split_cost, tb.total_tiles, grid, grid, sched->d_split); count_launches(1); }
         sa.split_head = sched->d_split;
     }
     const uint2 *rg = reinterpret_cast<const uint2 *>(d_tile_ranges);

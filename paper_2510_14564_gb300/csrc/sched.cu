@@ -110,6 +110,71 @@ __global__ void __launch_bounds__(256) k_tile_features(TileBatch tb, const uint2
     }
 }
 
+// Eight reverse-pass features per tile, one warp per tile, from what the
+// forward pass of the same step left (the reverse pass walks each pixel's
+// list back from its processed count, so those counts are its work):
+//   b0 log1p(largest processed count)   b1 log1p(mean processed count)
+//   b2 log1p(forward ns of the tile)     b3 log1p(kept list length)
+//   b4 log1p(mean over the tile's upper and lower 16x8 halves of their
+//      largest processed count: a reverse-pass warp walks as far as the
+//      deepest of its pixels)
+//   b5 fraction of in-image pixels that blended anything
+//   b6 in-image pixel fraction           b7 log1p(W H) / 16
+// with the MLP prediction fused as in k_tile_features.
+__global__ void __launch_bounds__(256) k_bwd_features(TileBatch tb, const uint2 *__restrict__ ranges,
+                                                      const int *__restrict__ tile_nproc,
+                                                      const int *__restrict__ n_proc,
+                                                      const unsigned long long *__restrict__ tile_ns,
+                                                      float *__restrict__ feats, const __half *__restrict__ w16,
+                                                      float *__restrict__ pred) {
+    __shared__ float s_w[kMlpW];
+    if (w16) {
+        for (int k = threadIdx.x; k < kMlpW; k += blockDim.x) s_w[k] = __half2float(w16[k]);
+        __syncthreads();
+    }
+    const int tile = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int l = threadIdx.x & 31;
+    if (tile >= tb.total_tiles) return;
+    const int v = view_of_tile(tb, tile);
+    const ViewTiles &vt = tb.v[v];
+    const int lt = tile - vt.tile_base, tx = lt % vt.TX, ty = lt / vt.TX;
+    const int inx = min(kTile, vt.W - tx * kTile), iny = min(kTile, vt.H - ty * kTile);
+    long long sum = 0;
+    int mx0 = 0, mx1 = 0, active = 0;
+    for (int k = l; k < kTilePix; k += 32) {
+        const int px = k & (kTile - 1), py = k / kTile;
+        if (px < inx && py < iny) {
+            const int c = max(0, __ldg(n_proc + vt.pix_base + (long long)(ty * kTile + py) * vt.W + tx * kTile + px));
+            sum += c;
+            active += c > 0;
+            if (py < kTile / 2) mx0 = max(mx0, c); else mx1 = max(mx1, c);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        active += __shfl_xor_sync(0xffffffffu, active, o);
+        mx0 = max(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+        mx1 = max(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+    }
+    if (l == 0) {
+        const float npx = (float)(inx * iny);
+        const uint2 rg = __ldg(ranges + tile);
+        float f[8];
+        f[0] = log1pf((float)max(0, __ldg(tile_nproc + tile)));
+        f[1] = log1pf((float)sum / npx);
+        f[2] = tile_ns ? log1pf((float)__ldg(tile_ns + tile)) : 0.f;
+        f[3] = log1pf((float)(rg.y - rg.x));
+        f[4] = log1pf(0.5f * (float)(mx0 + mx1));
+        f[5] = (float)active / npx;
+        f[6] = npx / (float)kTilePix;
+        f[7] = log1pf((float)vt.W * (float)vt.H) / 16.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) feats[8ll * tile + k] = f[k];
+        if (w16) pred[tile] = mlp_eval(s_w, f);
+    }
+}
+
 // y = W2 relu(W1 f + b1) + b2 with FP16 weights, FP32 accumulation.
 __global__ void __launch_bounds__(256) k_mlp_predict(const __half *__restrict__ w16,
                                                      const float *__restrict__ feats, int n,
@@ -376,6 +441,24 @@ extern "C" int gs_tile_features(const gs_camera *cams, int n_views, const uint32
         { k_tile_features<GS_F16><<<grid, 256, 0, st>>>(tb, rg, d_vals, d_splats, cap, d_feats, w16, d_pred); count_launches(1); }
     else
         return GS_ERR_ARG;
+    return launch_status();
+}
+
+extern "C" int gs_bwd_tile_features(const gs_camera *cams, int n_views, const uint32_t *d_tile_ranges,
+                                    const int32_t *d_tile_nproc, const int32_t *d_n_proc,
+                                    const uint64_t *d_tile_ns, float *d_feats, const void *d_w16, float *d_pred,
+                                    gs_stream_t stream) {
+    TileBatch tb;
+    if (make_tile_batch(cams, n_views, &tb) != GS_OK) return GS_ERR_ARG;
+    if (!d_tile_ranges || !d_tile_nproc || !d_n_proc || !d_feats) return GS_ERR_ARG;
+    if (!aligned(d_tile_ranges, 8)) return GS_ERR_ARG;
+    if ((d_w16 == nullptr) != (d_pred == nullptr)) return GS_ERR_ARG;
+    if (tb.total_tiles == 0) return GS_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    { k_bwd_features<<<cdiv((long long)tb.total_tiles * 32, 256), 256, 0, st>>>(
+        tb, reinterpret_cast<const uint2 *>(d_tile_ranges), d_tile_nproc, d_n_proc,
+        reinterpret_cast<const unsigned long long *>(d_tile_ns), d_feats, reinterpret_cast<const __half *>(d_w16),
+        d_pred); count_launches(1); }
     return launch_status();
 }
 

@@ -50,20 +50,102 @@ def to_device_params(scene, device=None) -> torch.Tensor:
 
 @dataclass
 class Schedule:
-    """How render CTAs take tiles: 'raster' (one CTA per tile), 'count'
-    (persistent, most instances first) or 'learned' (persistent, longest
-    predicted time first, MLP trained on measured tile times)."""
+    """How render CTAs take tiles.  'raster': one CTA per tile, both passes.
+    'count' (the plain split): persistent CTAs, tiles with the most
+    instances first, both passes.  'learned': the forward in raster order
+    (measured fastest: neighbouring tiles share Gaussians in L2), the reverse
+    pass by persistent CTAs in the order of a cost MLP trained on the reverse
+    pass's own tile times, longest predicted first, the tiles predicted to
+    take more than a CTA's share split into strips; judged against the count
+    order by measured duration."""
     mode: str = "raster"
     feature_cap: int = 128
     mlp_lr: float = 3e-3
     train_every: int = 4
     bwd_order: str = "forward"
     seed: int = 0
-    # learned mode: the count order judges the learned one (on seeded pairs of
-    # tiles, which score orders them as their measured times do more often)
-    # and is used until the MLP wins; False leaves the choice to the caller
+    # learned mode: the count order judges the learned one by measured
+    # makespan (every judge_every-th pass of each kind runs the count order,
+    # the pass half-way between runs the learned order, the others whichever
+    # is faster on average) and is used until the learned order wins; False
+    # uses the learned orders without judging
     judge: bool = True
-    judge_pairs: int = 65536
+    judge_every: int = 8
+
+
+class PassJudge:
+    """Chooses the tile order of one render pass between the learned cost
+    model's and the instance count's by measured duration: every `every`-th
+    pass runs the count order, the pass half-way between runs the learned
+    order, and the others the order with the lower mean duration (an
+    exponential average over its measured passes; the count order until both
+    have been measured).  Durations are CUDA events around the pass's
+    kernel, read back without waiting."""
+
+    def __init__(self, every: int = 8, weight: float = 0.25):
+        self.every = max(2, int(every))
+        self.weight = weight
+        self.mean = {"learned": None, "count": None}
+        self.passes = {"learned": 0, "count": 0}
+        self.pending = []
+        self.k = 0
+
+    def winner(self) -> str:
+        l, c = self.mean["learned"], self.mean["count"]
+        return "learned" if l is not None and c is not None and l < c else "count"
+
+    def pick(self) -> str:
+        self.poll()
+        r = self.k % self.every
+        self.k += 1
+        if r == 0:
+            return "count"
+        if r == self.every // 2:
+            return "learned"
+        return self.winner()
+
+    def start(self, which: str):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return which, e
+
+    def stop(self, token) -> None:
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        self.pending.append((token[0], token[1], e))
+
+    def poll(self) -> None:
+        keep = []
+        for which, a, b in self.pending:
+            if not b.query():
+                keep.append((which, a, b))
+                continue
+            ms = a.elapsed_time(b)
+            m = self.mean[which]
+            self.mean[which] = ms if m is None else m + self.weight * (ms - m)
+            self.passes[which] += 1
+        self.pending = keep
+
+    def report(self) -> dict:
+        self.poll()
+        return {"in_use": self.winner(), "mean_ms": {k: (None if v is None else round(v, 4))
+                                                      for k, v in self.mean.items()},
+                "passes_timed": dict(self.passes)}
+
+
+def _count_mlp_init(seed: int) -> np.ndarray:
+    """FP32 weights of a cost MLP that starts out ordering tiles by its
+    feature 0 (a log count): hidden unit 0 passes it to the output, the
+    others start small, and training moves it from there."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = np.zeros(MLP_W, np.float32)
+    w[:256] = rng.normal(0, math.sqrt(2.0 / 8), 256)
+    w[0:8] = 0.0
+    w[0] = 1.0
+    w[288] = 1.0
+    w[289:320] = rng.normal(0, 0.05, 31)
+    w[320] = 10.0                      # log(ns) of a typical tile
+    return w
 
 
 class Frame:
@@ -117,30 +199,28 @@ class Frame:
         self.order_b = torch.arange(self.T, dtype=torch.int32, device=d)
         self.order_ws = torch.empty(L.gs_sched_order_workspace(self.T) // 4 + 64,
                                     dtype=torch.float32, device=d)
-        rng = np.random.Generator(np.random.PCG64(self.sched.seed))
-        w = np.zeros(MLP_W, np.float32)
-        w[:256] = rng.normal(0, math.sqrt(2.0 / 8), 256)
-        # hidden unit 0 passes f0 = log1p(instances) to the output, the others
-        # start small: the untrained MLP orders tiles as the count does, and
-        # training moves it from there
-        w[0:8] = 0.0
-        w[0] = 1.0
-        w[288] = 1.0
-        w[289:320] = rng.normal(0, 0.05, 31)
-        w[320] = 10.0                      # log(ns) of a typical tile
-        self.mlp_w32 = torch.from_numpy(w).to(d)
-        self.mlp_w16 = self.mlp_w32.to(torch.float16)
-        self.mlp_m = torch.zeros(MLP_W, dtype=torch.float32, device=d)
-        self.mlp_v = torch.zeros(MLP_W, dtype=torch.float32, device=d)
-        self.mlp_g = torch.zeros(MLP_W, dtype=torch.float32, device=d)
-        self.mlp_loss = torch.zeros(1, dtype=torch.float32, device=d)
+        # learned mode: the cost MLP of the reverse pass predicts a tile's
+        # reverse-pass time from what the forward left (gs_bwd_tile_features);
+        # it starts as the order by processed count and trains on the reverse
+        # pass's own tile times.  (A forward cost model, gs_tile_features,
+        # exists in the library; the forward runs in raster order.)
+        self.mlp = {}
+        for k, seed in (("bwd", self.sched.seed + 1),):
+            w32 = torch.from_numpy(_count_mlp_init(seed)).to(d)
+            self.mlp[k] = dict(w32=w32, w16=w32.to(torch.float16),
+                               m=torch.zeros(MLP_W, dtype=torch.float32, device=d),
+                               v=torch.zeros(MLP_W, dtype=torch.float32, device=d),
+                               g=torch.zeros(MLP_W, dtype=torch.float32, device=d),
+                               loss=torch.zeros(1, dtype=torch.float32, device=d))
         self.mlp_t = 0
         self.pred = torch.zeros(self.T, dtype=torch.float32, device=d)
-        self.use_learned = self.sched.mode == "learned" and not self.sched.judge
-        self.judge = torch.zeros(2, dtype=torch.int64, device=self.dev)
-        self.judge_host = torch.zeros(2, dtype=torch.int64).pin_memory()
-        self.judge_event = None
-        self.judge_rounds = 0
+        self.feats_b = torch.zeros(self.T * 8, dtype=torch.float32, device=d)
+        self.pred_b = torch.zeros(self.T, dtype=torch.float32, device=d)
+        self.tile_ns_b = torch.zeros(self.T, dtype=torch.int64, device=d)
+        # which order each pass uses: forced ("learned" / "count") or judged
+        self.force_order = "learned" if self.sched.mode == "learned" and not self.sched.judge else None
+        self.judge_b = PassJudge(self.sched.judge_every)
+        self.pick_b = "count"
         self.step_count = 0
         # the error word, read back each step without waiting (pinned copy +
         # event): an instance-capacity overflow raises, never passes silently
@@ -254,29 +334,62 @@ class Frame:
             self.reserve(self.capacity, with_keys=True)
         self._bin(self.capacity, self.keys if want_keys else None)
 
+    @property
+    def use_learned(self) -> bool:
+        """Whether the reverse pass uses the learned order (forced, or
+        winning its judge)."""
+        if self.force_order is not None:
+            return self.force_order == "learned"
+        return self.judge_b.winner() == "learned"
+
+    @use_learned.setter
+    def use_learned(self, on: bool) -> None:
+        self.force_order = "learned" if on else "count"
+
+    def _pick(self, judge: PassJudge) -> str:
+        return self.force_order if self.force_order is not None else judge.pick()
+
+    def _count_order(self, out: torch.Tensor) -> None:
+        L.gs_range_cost(self.ranges, self.T, self.cost)
+        L.gs_sched_order(self.cost, self.T, out, self.order_ws)
+
     def _sched_fwd(self):
-        m = self.sched.mode
-        if m == "raster":
+        """The forward's schedule: None (raster) for the raster and learned
+        schedules, the instance-count order for the plain one."""
+        if self.sched.mode != "count":
             return None
-        if m == "count" or not self.use_learned:
-            L.gs_range_cost(self.ranges, self.T, self.cost)
-            L.gs_sched_order(self.cost, self.T, self.order_f, self.order_ws)
-        else:
-            L.gs_tile_features(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype,
-                               self.sched.feature_cap, self.feats, self.mlp_w16, self.pred)
-            L.gs_sched_order(self.pred, self.T, self.order_f, self.order_ws)
+        self._count_order(self.order_f)
         return {"mode": L.GS_SCHED_ORDER, "order": self.order_f, "queue": self.queue}
 
-    def _sched_bwd(self):
-        """The backward reuses the forward's order ('forward'), or orders
-        tiles by the entries the forward processed ('processed')."""
+    def _sched_bwd(self, timing: bool = False):
+        """The reverse pass's order.  The plain schedule reuses the forward's
+        order (bwd_order 'forward') or orders tiles by the entries the
+        forward processed ('processed'); the learned schedule orders them by
+        the reverse-pass MLP's prediction (and splits the tiles it predicts
+        heavy) or, when its judge says so, by instance count.  timing:
+        measure the reverse pass's tile times (self.tile_ns_b)."""
         if self.sched.mode == "raster":
             return None
+        base = {"queue": self.queue, "split": self.split, "mode": L.GS_SCHED_ORDER}
+        if timing:
+            L.gs_zero(self.tile_ns_b)
+            base["tile_ns"] = self.tile_ns_b
+        if self.sched.mode == "learned":
+            self.pick_b = self._pick(self.judge_b)
+            if self.pick_b == "learned" or timing:
+                L.gs_bwd_tile_features(self.cams, self.ranges, self.tile_nproc, self.n_proc, self.tile_ns,
+                                       self.feats_b, self.mlp["bwd"]["w16"], self.pred_b)
+            if self.pick_b == "learned":
+                L.gs_sched_order(self.pred_b, self.T, self.order_b, self.order_ws)
+                return dict(base, order=self.order_b, split_cost=self.pred_b)
+            self._count_order(self.order_b)
+            return dict(base, order=self.order_b)
+        self.pick_b = "count"
         if self.sched.bwd_order == "forward":
-            return {"mode": L.GS_SCHED_ORDER, "order": self.order_f, "queue": self.queue, "split": self.split}
+            return dict(base, order=self.order_f)
         L.gs_int_cost(self.tile_nproc, self.T, self.cost)
         L.gs_sched_order(self.cost, self.T, self.order_b, self.order_ws)
-        return {"mode": L.GS_SCHED_ORDER, "order": self.order_b, "queue": self.queue, "split": self.split}
+        return dict(base, order=self.order_b)
 
     def render(self, timing: bool = False, mark=None) -> None:
         s = self._sched_fwd()
@@ -301,6 +414,25 @@ class Frame:
                         self.T_final, self.n_proc, self.tile_nproc, tns, self.err)
         self._watch_errors(issue=True)
 
+    def render_merged(self) -> torch.Tensor:
+        """Forward render with similarity-based sampling and merging of the
+        current tile lists (Sec. IV-C1; lossy, forward only): gs_colour_merge
+        keeps one representative per (tile, colour bucket), then
+        gs_render_fwd blends the merged lists into self.img (T_final and
+        n_proc are overwritten; the per-tile history is not)."""
+        cap = self.vals.numel()
+        if getattr(self, "merge_cap", 0) < cap:
+            self.m_ranges = torch.empty(self.T * 2, dtype=torch.int32, device=self.dev)
+            self.m_vals = torch.empty(cap, dtype=torch.int32, device=self.dev)
+            self.m_splats = torch.empty(cap * L.SPLAT_BYTES[L.GS_F32] // 4, dtype=torch.float32, device=self.dev)
+            self.m_tile_nproc = torch.empty(self.T, dtype=torch.int32, device=self.dev)
+            self.merge_cap = cap
+        L.gs_colour_merge(self.T, self.ranges, self.vals, self.splats, self.rgb_dtype, self.m_ranges, self.m_vals,
+                          self.m_splats)
+        L.gs_render_fwd(self.cams, self.m_ranges, self.m_vals, self.m_splats, L.GS_F32, None, self.img,
+                        self.T_final, self.n_proc, self.m_tile_nproc, None, self.err)
+        return self.img
+
     def forward(self, params: dict, timing: bool = False) -> torch.Tensor:
         self.project(params)
         self.bin_sort()
@@ -308,13 +440,22 @@ class Frame:
         return self.img
 
     # -- backward ----------------------------------------------------------
-    def backward(self, params: dict, dimg: torch.Tensor, mark=None) -> torch.Tensor:
+    def render_bwd(self, dimg: torch.Tensor, timing: bool = False, mark=None) -> None:
+        """The reverse pass into self.grad2d (zeroed first) in the schedule's
+        order; timing: also measure its per-tile times (self.tile_ns_b)."""
         L.gs_zero(self.grad2d[:self.V * self.N * 12])
-        s = self._sched_bwd()
+        s = self._sched_bwd(timing=timing)
         if mark:
             mark("render_bwd")
+        judged = self.sched.mode == "learned" and self.force_order is None
+        tok = self.judge_b.start(self.pick_b) if judged else None
         L.gs_render_bwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, s, dimg,
                         self.T_final, self.n_proc, self.tile_nproc, self.grad2d, self.err)
+        if tok:
+            self.judge_b.stop(tok)
+
+    def backward(self, params: dict, dimg: torch.Tensor, mark=None) -> torch.Tensor:
+        self.render_bwd(dimg, mark=mark)
         if mark:
             mark("project_bwd")
         L.gs_project_bwd(self.cams, self.N, params["means"], params["log_scales"], params["quats"],
@@ -331,35 +472,23 @@ class Frame:
 
     # -- scheduler training ------------------------------------------------
     def train_scheduler(self) -> None:
-        """One MLP step on the tile times of the last timed forward."""
+        """One training step of the reverse pass's cost MLP on the tile times
+        of the last timed reverse pass (self.tile_ns_b) and the features
+        computed for it."""
         if self.sched.mode != "learned":
             return
         self.mlp_t += 1
-        if not self.use_learned:
-            L.gs_tile_features(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype,
-                               self.sched.feature_cap, self.feats, self.mlp_w16, self.pred)
-        if self.sched.judge:
-            self._judge()
-        L.gs_mlp_train_step(self.mlp_w32, self.mlp_w16, self.mlp_m, self.mlp_v, self.mlp_t,
-                            self.sched.mlp_lr, self.feats, self.tile_ns, None, self.T, self.mlp_g,
-                            self.mlp_loss)
+        m = self.mlp["bwd"]
+        L.gs_mlp_train_step(m["w32"], m["w16"], m["m"], m["v"], self.mlp_t, self.sched.mlp_lr, self.feats_b,
+                            self.tile_ns_b, None, self.T, m["g"], m["loss"])
 
-    def _judge(self) -> None:
-        """Score the MLP's prediction and the instance count against the tile
-        times just measured; the verdict of the previous scoring, read without
-        waiting (pinned copy + event), picks the order."""
-        if self.judge_event is not None and self.judge_event.query():
-            learned, count = self.judge_host.tolist()
-            self.use_learned = learned > count
-            self.judge_event = None
-        if self.judge_event is None:
-            L.gs_zero(self.judge)
-            L.gs_rank_judge(self.pred, self.feats, 8, self.tile_ns, self.T, self.sched.judge_pairs,
-                            self.sched.seed * 7919 + self.judge_rounds, self.judge)
-            self.judge_rounds += 1
-            self.judge_host.copy_(self.judge, non_blocking=True)
-            self.judge_event = torch.cuda.Event()
-            self.judge_event.record()
+    def schedule_report(self) -> dict:
+        """The orders in use and the measured pass durations behind them."""
+        if self.sched.mode != "learned":
+            return {"forward": self.sched.mode, "backward": self.sched.mode}
+        if self.force_order is not None:
+            return {"forward": "raster", "backward": self.force_order, "judged": False}
+        return {"forward": "raster", "backward": self.judge_b.report(), "judged": True}
 
     def check_errors(self) -> int:
         return int(self.err.item())
@@ -460,23 +589,22 @@ class Trainer:
             d["sh"] = self.sh_shadow
         return d
 
-    def iteration(self, targets: torch.Tensor | None = None) -> torch.Tensor:
-        """Forward, L1 and backward to the 59 parameter gradients (in
-        frame.dparams), without the Adam step: one fwd+bwd iteration."""
-        f = self.frame
-        pk = self.params_for_kernels()
-        f.forward(pk, timing=f.sched.mode == "learned")
-        f.l1(self.targets if targets is None else targets)
-        f.backward(pk, f.dimg)
-        return f.loss
+    def iteration(self, targets: torch.Tensor | None = None, mark=None) -> torch.Tensor:
+        """One fwd+bwd iteration: the step without Adam.  Projection, binning,
+        schedule, forward, L1, reverse pass, projection backward to the 59
+        parameter gradients (in frame.dparams), and the cost models' training
+        step every train_every-th iteration."""
+        return self.step(mark=mark, targets=targets, adam=False)
 
-    def step(self, mark=None, targets: torch.Tensor | None = None) -> torch.Tensor:
-        """One training step.  `mark(name)`, if given, is called before each
-        stage (and with "end" after the last) so a caller can time stages."""
+    def step(self, mark=None, targets: torch.Tensor | None = None, adam: bool = True) -> torch.Tensor:
+        """One training step (adam=False: without the parameter update, see
+        iteration()).  `mark(name)`, if given, is called before each stage
+        (and with "end" after the last) so a caller can time stages."""
         mk = mark or (lambda name: None)
         f = self.frame
         pk = self.params_for_kernels()
         timing = f.sched.mode == "learned"
+        train_now = timing and (f.step_count % max(1, f.sched.train_every) == 0)
         mk("project")
         f.project(pk)
         mk("bin_sort")
@@ -486,32 +614,33 @@ class Trainer:
         mk("l1")
         f.l1(self.targets if targets is None else targets)
         mk("sched_bwd")
-        L.gs_zero(f.grad2d[:f.V * self.N * 12])
-        s = f._sched_bwd()
-        mk("render_bwd")
-        L.gs_render_bwd(f.cams, f.ranges, f.vals, f.splats, f.rgb_dtype, s, f.dimg, f.T_final, f.n_proc,
-                        f.tile_nproc, f.grad2d, f.err)
+        f.render_bwd(f.dimg, timing=train_now, mark=mark)
         if self.grad_norm is not None:
             mk("grad_stat")
             L.gs_grad2d_norm(len(f.cams), self.N, f.grad2d, self.grad_norm)
         pk_sh = self.sh_shadow if self.sh_shadow is not None else pk["sh"]
-        self.t += 1
-        if len(f.cams) == 1:
+        if not adam:
+            mk("project_bwd")
+            L.gs_project_bwd(f.cams, self.N, pk["means"], pk["log_scales"], pk["quats"], pk["opacity_logits"],
+                             pk_sh, self.sh_storage, f.touched, f.grad2d, f.dparams)
+        elif len(f.cams) == 1:
             # one view: the projection backward and Adam in one streaming pass
             # (the per-Gaussian gradients never go to memory)
+            self.t += 1
             mk("project_bwd_adam")
             L.gs_project_bwd_adam(f.cams, self.N, self.p, self.sh_shadow, self.sh_storage, f.touched, f.grad2d,
                                   self.m, self.v, self.lr, ADAM_B1, ADAM_B2, ADAM_EPS, self.t,
                                   self.sh_shadow, self.sh_storage)
         else:
             # several views: gradients summed over views, then Adam
+            self.t += 1
             mk("project_bwd")
             L.gs_project_bwd(f.cams, self.N, pk["means"], pk["log_scales"], pk["quats"], pk["opacity_logits"],
                              pk_sh, self.sh_storage, f.touched, f.grad2d, f.dparams)
             mk("adam")
             L.gs_adam_step(self.N, self.p, f.dparams, self.m, self.v, self.lr, ADAM_B1, ADAM_B2, ADAM_EPS,
                            self.t, self.sh_shadow, self.sh_storage)
-        if timing and (f.step_count % max(1, f.sched.train_every) == 0):
+        if train_now:
             mk("mlp_train")
             f.train_scheduler()
         mk("end")

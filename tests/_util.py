@@ -75,22 +75,32 @@ COLOUR_MARGIN = 8e-6
 GROUPS = dict(means=(0, 3), log_scales=(3, 6), quats=(6, 10), logits=(10, 11), sh=(11, 59))
 
 
-def storage_scene(scene, cams, dtype, margin=COLOUR_MARGIN, rounds=40, only=None):
-    """A copy of `scene` prepared for parity of the 16-bit storage path.
+def _hash_level(c):
+    """The 16-level quantisation of a colour channel (Sec. IV-C1): 8 bits as
+    floor(c 255 + 0.5) clamped, then c8 >> 4."""
+    return np.clip(np.floor(np.asarray(c, np.float64) * 255.0 + 0.5), 0, 255).astype(np.int64) >> 4
+
+
+def storage_scene(scene, cams, dtype, margin=COLOUR_MARGIN, rounds=40, only=None, hash_safe=False):
+    """A copy of `scene` prepared for parity of the 16-bit storage path
+    (dtype GS_BF16 / GS_F16) or of colour hashing (hash_safe).
 
     The SH coefficients are rounded to the storage format (what the GPU
     reads).  The GPU evaluates each colour in FP32 and rounds it to the
     record's 16-bit format; the oracle evaluates it in FP64 and rounds it
     with O.round_storage.  The two agree unless the colour lies within FP32
     error of a point where that rounding changes (a midpoint between two
-    16-bit values) or of the max(0, .) clamp.  While some visible (Gaussian,
-    channel) of some view lies within `margin` of one, its DC coefficient is
-    raised by 0.004 (then rounded), which moves the colour by at least 5.6e-4.
-    `only` (indices) limits the preparation to the Gaussians a comparison
-    reads.  This prepares the input from the oracle's own colours only."""
-    kind = STORAGE_KIND[dtype]
+    16-bit values) or of the max(0, .) clamp; with hash_safe, also of a point
+    where the colour's 16-level hash quantisation changes (FP32 records).
+    While some visible (Gaussian, channel) of some view lies within `margin`
+    of one, its DC coefficient is raised by 0.004 (then rounded), which moves
+    the colour by at least 5.6e-4.  `only` (indices) limits the preparation
+    to the Gaussians a comparison reads.  This prepares the input from the
+    oracle's own colours only."""
+    kind = STORAGE_KIND.get(dtype)
     sc = scene.subset(np.arange(scene.n))
-    sc.sh = O.round_storage(sc.sh, kind).astype(np.float32)
+    rnd = (lambda x: O.round_storage(x, kind)) if kind else (lambda x: x)
+    sc.sh = rnd(sc.sh).astype(np.float32)
     idx = np.arange(sc.n) if only is None else np.asarray(only, np.int64)
     for _ in range(rounds):
         sub = sc.subset(idx)
@@ -99,26 +109,31 @@ def storage_scene(scene, cams, dtype, margin=COLOUR_MARGIN, rounds=40, only=None
             kp = O.keypath(cam, sub)
             pr = O.project(cam, sub, kp)
             pre = pr["rgb_pre"]
-            flip = (O.round_storage(np.maximum(pre - margin, 0.0), kind)
-                    != O.round_storage(np.maximum(pre + margin, 0.0), kind))
-            bad |= (flip | (np.abs(pre) < margin)) & (kp["touched"] > 0)[:, None]
+            lo, hi = np.maximum(pre - margin, 0.0), np.maximum(pre + margin, 0.0)
+            flip = np.abs(pre) < margin
+            if kind:
+                flip |= O.round_storage(lo, kind) != O.round_storage(hi, kind)
+            if hash_safe:
+                flip |= _hash_level(lo) != _hash_level(hi)
+            bad |= flip & (kp["touched"] > 0)[:, None]
         if not bad.any():
             return sc
         i, ch = np.nonzero(bad)
-        sc.sh[idx[i], 0, ch] = O.round_storage(sc.sh[idx[i], 0, ch].astype(np.float64) + 0.004, kind)
+        sc.sh[idx[i], 0, ch] = rnd(sc.sh[idx[i], 0, ch].astype(np.float64) + 0.004)
     raise AssertionError("colours still next to a rounding point after the nudges")
 
 
 def storage_refs(sc, cams, dtype, window=None):
     """Oracle of the 16-bit storage path for each view: FP64 projection of
     the (already rounded) SH, the record colour rounded to the storage format,
-    FP64 blending of that colour."""
-    kind = STORAGE_KIND[dtype]
+    FP64 blending of that colour.  GS_F32: the plain FP64 oracle."""
+    kind = STORAGE_KIND.get(dtype)
     refs = []
     for cam in cams:
         kp = O.keypath(cam, sc)
         pr = dict(O.project(cam, sc, kp))
-        pr["rgb"] = O.round_storage(pr["rgb"], kind)
+        if kind:
+            pr["rgb"] = O.round_storage(pr["rgb"], kind)
         refs.append(dict(kp=kp, proj=pr, r=O.render(cam, kp, pr, window)))
     return refs
 

@@ -12,10 +12,13 @@ Two checks of its backward, for FP32 storage and for BF16 SH and colours:
   L = sum(dimg * image).  The forward is piecewise smooth: its discrete
   decisions (tile rectangles, the alpha skip and clamp, the transmittance
   stop, the colour clamp) must not change between p - v and p + v.  Pixels
-  with a blending decision within 5% of its threshold carry no upstream
+  with a blending decision within 10% of its threshold carry no upstream
   gradient, directions whose tile rectangles change (the oracle's FP32 key
-  path, bit-exact with the GPU's) are drawn again, and Gaussians with a
-  colour near the clamp are not perturbed.
+  path, bit-exact with the GPU's) are drawn again, Gaussians with a colour
+  near the clamp are not perturbed (with BF16 colours, which are piecewise
+  constant in the view direction, neither are means or SH), and a mean moves along the viewing axis
+  only when no Gaussian sharing a tile with it lies within 20 steps in depth
+  (the depth order of a tile list must not change either).
 """
 import numpy as np
 import pytest
@@ -31,12 +34,13 @@ from tests._util import GRAD_RTOL, GROUPS, rel_check, storage_refs, storage_scen
 pytestmark = pytest.mark.gpu
 
 N_SUB = 1024
-FD_MARGIN = 5e-2          # flag margin of the FD check (alpha and transmittance, relative)
-FD_RTOL = 5e-3
-# per-group perturbation scale (about 0.5% of a Gaussian's size for the
-# means, 1e-3 of the unit for log-scales, quaternions, logits, SH): alpha
-# moves by well under the flag margin
-STEP = dict(means=1e-4, log_scales=1e-3, quats=1e-3, logits=1e-3, sh=1e-3)
+FD_MARGIN = 0.1           # flag margin of the FD check (alpha and transmittance, relative)
+FD_RTOL, FD_ATOL = 5e-3, 1e-4   # FP32 rounding of the two renders limits the absolute part
+# per-group perturbation scale (about 0.3% of a Gaussian's size for the
+# means, 5e-4 of the unit for log-scales, quaternions, logits, SH): alpha
+# moves by well under the flag margin, and few tile rectangles change
+STEP = dict(means=5e-5, log_scales=5e-4, quats=5e-4, logits=5e-4, sh=5e-4)
+N_DIR, N_MOVED, MAX_TRIES = 6, 12, 30
 TDT = {L.GS_F32: torch.float32, L.GS_BF16: torch.bfloat16}
 
 
@@ -106,14 +110,29 @@ def test_autograd_function_against_oracle_and_finite_differences(subsets, dtype,
     # central differences of the GPU forward
     rng = np.random.default_rng(40 + which)
     smooth = vis & (np.abs(pr["rgb_pre"]).min(axis=1) > 0.02)
-    perturbed = ["means", "log_scales", "quats", "logits"] + (["sh"] if dtype == L.GS_F32 else [])
+    # depth gap to the nearest visible Gaussian whose tile rectangle overlaps
+    rc, dep = kp["rect"], kp["depth"].astype(np.float64)
+    over = ((rc[:, None, 0] < rc[None, :, 2]) & (rc[None, :, 0] < rc[:, None, 2]) &
+            (rc[:, None, 1] < rc[None, :, 3]) & (rc[None, :, 1] < rc[:, None, 3]) & vis[:, None] & vis[None, :])
+    np.fill_diagonal(over, False)
+    gap = np.where(over, np.abs(dep[:, None] - dep[None, :]), np.inf).min(axis=1)
+    depth_free = gap > 20 * 4 * STEP["means"]
+    axis = np.asarray(cam.R, np.float64)[2]             # camera viewing axis in world space
+    # 16-bit colours are piecewise constant in the view direction (a mean's
+    # move crosses their rounding steps), so with BF16 only scales,
+    # rotations and opacities are perturbed
+    perturbed = (["means", "log_scales", "quats", "logits", "sh"] if dtype == L.GS_F32
+                 else ["log_scales", "quats", "logits"])
     done = tries = 0
-    while done < 6 and tries < 24:
+    while done < N_DIR and tries < MAX_TRIES:
         tries += 1
-        ids = rng.choice(np.flatnonzero(smooth), 24, replace=False)
+        ids = rng.choice(np.flatnonzero(smooth), N_MOVED, replace=False)
         v = {name: np.zeros_like(g[name]) for name in GROUPS}
         for name in perturbed:
             v[name][ids] = rng.normal(0.0, 1.0, (len(ids), v[name].shape[1])) * STEP[name]
+        # keep the depth of Gaussians with a close neighbour in depth
+        tied = ids[~depth_free[ids]]
+        v["means"][tied] -= np.outer(v["means"][tied] @ axis, axis)
         sides = []
         for s in (1.0, -1.0):
             scp = sc.subset(np.arange(n))
@@ -139,6 +158,6 @@ def test_autograd_function_against_oracle_and_finite_differences(subsets, dtype,
             step = (getattr(sides[0], attr).astype(np.float64) - getattr(sides[1], attr).astype(np.float64)) / 2
             ad += float((g[name] * step.reshape(n, -1)).sum())
         print(f"direction {done}: autograd {ad:+.6e}, central difference {fd:+.6e}")
-        assert abs(fd - ad) <= FD_RTOL * abs(ad) + 1e-5, (fd, ad)
+        assert abs(fd - ad) <= FD_RTOL * abs(ad) + FD_ATOL, (fd, ad)
         done += 1
-    assert done == 6, f"only {done} of {tries} directions kept the discrete path"
+    assert done == N_DIR, f"only {done} of {tries} directions kept the discrete path"

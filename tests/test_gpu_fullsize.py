@@ -111,8 +111,10 @@ def test_fullsize_bf16_learned_path(full):
     f = tr.frame
     for _ in range(3):                      # the benchmark's configuration, a few steps in
         f.forward(tr.params_for_kernels(), timing=True)
+        f.l1(tr.targets)
+        f.render_bwd(f.dimg, timing=True)
         f.train_scheduler()
-    f.use_learned = True
+    f.use_learned = True                    # the reverse pass in the learned order
     pk = tr.params_for_kernels()
     f.forward(pk, timing=True)
     torch.cuda.synchronize()

@@ -118,59 +118,107 @@ def _spearman(a, b):
     return np.corrcoef(ra, rb)[0, 1]
 
 
-def test_learned_cost_model_gain():
-    """After training on the renderer's own tile times, the MLP ranks tile
-    costs better than the instance count does; the render makespans of the
-    raster, count and learned orders, and the cost of computing each order,
-    are reported."""
-    scene = S.skewed_scene(300_000, 0)
-    cams = S.ring_cameras(8, S.uneven_sizes(8, (400, 300), (960, 540)))
-    fr, _ = _frame(scene, cams, P.Schedule("learned", mlp_lr=3e-3))
-    fr.use_learned = False
-    for _ in range(300):                                     # train on measured tile times
-        fr.render(timing=True)
-        fr.train_scheduler()
-    fr.use_learned = True
-    fr.render(timing=True)
+def test_bwd_features_match_oracle():
+    """gs_bwd_tile_features on a two-view batch (ragged tiles) against the
+    oracle's formula, from the same seeded inputs (processed counts, tile
+    times, kept list lengths); the fused prediction equals gs_mlp_predict."""
+    cams = S.ring_cameras(2, [(200, 136), (72, 40)])
+    rng = np.random.default_rng(21)
+    P_all = sum(c.W * c.H for c in cams)
+    T = sum(c.n_tiles for c in cams)
+    n_proc = rng.integers(0, 400, P_all).astype(np.int32)
+    n_proc[rng.random(P_all) < 0.2] = 0                      # pixels that blended nothing
+    tile_nproc = rng.integers(0, 900, T).astype(np.int32)
+    tile_ns = rng.integers(0, 200_000, T).astype(np.int64)
+    lens = rng.integers(0, 3000, T)
+    starts = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    ranges = np.stack([starts, starts + lens], 1).astype(np.int32)
+    feats = torch.empty(T * 8, device="cuda")
+    w16 = torch.from_numpy(rng.normal(0, 0.3, 321).astype(np.float32)).cuda().half()
+    pred = torch.empty(T, device="cuda")
+    L.gs_bwd_tile_features(cams, torch.from_numpy(ranges.ravel()).cuda(), torch.from_numpy(tile_nproc).cuda(),
+                           torch.from_numpy(n_proc).cuda(), torch.from_numpy(tile_ns).cuda(), feats, w16, pred)
+    ref_pred = torch.empty(T, device="cuda")
+    L.gs_mlp_predict(w16, feats, T, ref_pred)
     torch.cuda.synchronize()
-    ns = fr.tile_ns.cpu().numpy().astype(np.float64)
+    got = feats.cpu().numpy().reshape(T, 8)
+    t0 = p0 = 0
+    for cam in cams:
+        nt, npix = cam.n_tiles, cam.W * cam.H
+        ref = O.bwd_tile_features(cam, n_proc[p0:p0 + npix], tile_nproc[t0:t0 + nt], tile_ns[t0:t0 + nt],
+                                  lens[t0:t0 + nt])
+        assert np.allclose(got[t0:t0 + nt], ref, rtol=1e-6, atol=1e-6)
+        t0 += nt
+        p0 += npix
+    assert torch.allclose(pred, ref_pred, rtol=1e-6, atol=1e-6)
+
+
+def _best(fn, reps=7):
+    best = 1e9
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        best = min(best, s.elapsed_time(e))
+    return best
+
+
+def test_learned_reverse_order_gains_over_the_count_order():
+    """What the trained network gains over the plain count split, where the
+    work order matters: the dense skewed scene of the skewed-density training
+    step (500k Gaussians, 80% in 20 clusters, one 1280x720 view), whose
+    cluster tiles are many times heavier than the rest.  Training steps train
+    the reverse pass's cost MLP on the pass's own tile times; then, best of 7
+    with the orders computed beforehand, the reverse pass in the learned
+    order (heavy tiles split by predicted cost) must beat the instance-count
+    order, and the judge, which compares measured pass durations, must have
+    chosen the learned order.  The processed-count order and the rank
+    correlations of each predictor with the measured tile times are
+    reported beside them."""
+    scene = S.skewed_scene(500_000, 0)
+    cams = [S.front_camera(1280, 720)]
+    tgt = torch.from_numpy(S.random_image(1280, 720, seed=1).ravel()).cuda()
+    tr = P.Trainer(cams, P.to_device_params(scene), scene.n, tgt, rgb_dtype=L.GS_BF16, sh_storage=L.GS_BF16,
+                   schedule=P.Schedule("learned"), lr=tuple(x * 1e-3 for x in P.DEFAULT_LR))
+    for _ in range(200):
+        tr.step()
+    torch.cuda.synchronize()
+    fr = tr.frame
+    assert fr.check_errors() == 0
+    rep = fr.schedule_report()
+    print(f"\njudge after 200 steps: {rep}")
+    keep = fr.force_order
+    fr.force_order = "learned"
+    fr._sched_bwd()
+    o_learned, pred = fr.order_b.clone(), fr.pred_b.clone()
+    fr.force_order = keep
+    fr._count_order(fr.order_f)
+    o_count = fr.order_f.clone()
+    L.gs_int_cost(fr.tile_nproc, fr.T, fr.cost)
+    o_proc = torch.empty_like(fr.order_b)
+    L.gs_sched_order(fr.cost, fr.T, o_proc, fr.order_ws)
+
+    def bwd(o, cost=None):
+        L.gs_render_bwd(fr.cams, fr.ranges, fr.vals, fr.splats, fr.rgb_dtype,
+                        {"mode": L.GS_SCHED_ORDER, "order": o, "queue": fr.queue, "split": fr.split,
+                         "split_cost": cost}, fr.dimg, fr.T_final, fr.n_proc, fr.tile_nproc, fr.grad2d, fr.err)
+
+    tb = {"count": _best(lambda: bwd(o_count)), "by_processed": _best(lambda: bwd(o_proc)),
+          "learned": _best(lambda: bwd(o_learned, pred))}
+    print(f"reverse pass makespan (ms): {tb}")
+    fr.render_bwd(fr.dimg, timing=True)
+    torch.cuda.synchronize()
+    ns = fr.tile_ns_b.cpu().numpy().astype(np.float64)
     live = ns > 0
-    pred = fr.pred.cpu().numpy()
-    count = fr.feats.cpu().numpy().reshape(-1, 8)[:, 0]
-    rho_learned = _spearman(pred[live], ns[live])
-    rho_count = _spearman(count[live], ns[live])
-    print(f"\nSpearman vs measured tile time: learned {rho_learned:.3f}, count {rho_count:.3f}")
-    assert rho_learned > rho_count
-
-    def timed(fn, reps=7):
-        best = 1e9
-        for _ in range(reps):
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record()
-            fn()
-            e.record()
-            torch.cuda.synchronize()
-            best = min(best, s.elapsed_time(e))
-        return best
-
-    orders = {}
-    fr.use_learned = False
-    t_order_count = timed(lambda: fr._sched_fwd())
-    orders["count"] = fr.order_f.clone()
-    fr.use_learned = True
-    t_order_learned = timed(lambda: fr._sched_fwd())
-    orders["learned"] = fr.order_f.clone()
-
-    def render(order):
-        s = None if order is None else {"mode": L.GS_SCHED_ORDER, "order": order, "queue": fr.queue}
-        L.gs_render_fwd(fr.cams, fr.ranges, fr.vals, fr.splats, fr.rgb_dtype, s, fr.img, fr.T_final,
-                        fr.n_proc, fr.tile_nproc, None, fr.err)
-
-    t = {k: timed(lambda o=o: render(o)) for k, o in (("raster", None), ("count", orders["count"]),
-                                                      ("learned", orders["learned"]))}
-    print(f"render makespan (ms): raster {t['raster']:.3f}, count order {t['count']:.3f}, "
-          f"learned order {t['learned']:.3f}; order cost: count {t_order_count:.3f}, "
-          f"learned {t_order_learned:.3f}")
+    f = fr.feats_b.cpu().numpy().reshape(-1, 8)
+    rho = {"learned": _spearman(fr.pred_b.cpu().numpy()[live], ns[live]),
+           "processed": _spearman(f[live, 0], ns[live]), "count": _spearman(f[live, 3], ns[live])}
+    print(f"Spearman vs reverse-pass tile time: {rho}")
+    assert fr.check_errors() == 0
+    assert tb["learned"] < tb["count"]
+    assert rep["backward"]["in_use"] == "learned"
 
 
 def _mix(x):

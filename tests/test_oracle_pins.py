@@ -898,3 +898,28 @@ def test_colour_merge_of_two_coincident_splats_closed_form():
     assert e["img"][0, 16, 16] == pytest.approx(cf * (o + o * (1 - o)), rel=1e-12)
     # a pixel 2 sigma away: alpha = 2 o exp(-2)
     assert m["img"][0, 16, 22] == pytest.approx(2 * o * math.exp(-0.5 * 36 / s2) * cf, rel=1e-12)
+
+
+# -- reverse-pass cost features (a8) ------------------------------------------
+
+def test_bwd_tile_features_by_hand():
+    cam = S.front_camera(20, 18)                       # 2 x 2 tiles, ragged: 16x16, 4x16, 16x2, 4x2
+    n_proc = np.zeros((18, 20), np.int32)
+    n_proc[:16, :16] = 3
+    n_proc[:16, 16:] = 8
+    n_proc[16:, :16] = 0
+    n_proc[16:, 16:] = 5
+    n_proc[12, 2] = 9                                  # tile 0's lower half holds its deepest pixel
+    tile_nproc = np.array([9, 8, 0, 5])
+    tile_ns = np.array([1000, 0, 7, 30], np.uint64)
+    kept = np.array([40, 12, 0, 3])
+    f = O.bwd_tile_features(cam, n_proc, tile_nproc, tile_ns, kept)
+    assert np.allclose(f[:, 0], np.log1p([9, 8, 0, 5]))
+    assert np.allclose(f[:, 1], np.log1p([3 + 6 / 256, 8, 0, 5]))
+    assert np.allclose(f[:, 2], np.log1p([1000, 0, 7, 30]))
+    assert np.allclose(f[:, 3], np.log1p([40, 12, 0, 3]))
+    # halves: tile 0 (3, 9), tile 1 (8, 8), tile 2 (0, -) and tile 3 (5, -) have no lower half
+    assert np.allclose(f[:, 4], np.log1p([6.0, 8.0, 0.0, 2.5]))
+    assert np.allclose(f[:, 5], [1.0, 1.0, 0.0, 1.0])
+    assert np.allclose(f[:, 6], [1.0, 64 / 256, 32 / 256, 8 / 256])
+    assert np.allclose(f[:, 7], math.log1p(360) / 16)
