@@ -154,6 +154,9 @@ int gs_project(const gs_camera *cams, int n_views, int N, const float *d_means,
  * by the 64-bit key (global tile id << 32 | FP32 depth bits), ties by
  * record index (v*N + i); the order is exactly that of a stable sort of that
  * key over index-ordered input.
+ * In: d_depth, d_rect, d_touched as gs_project writes them: a record with
+ * d_touched > 0 covers its rectangle's (xmax-xmin)(ymax-ymin) tiles, a
+ * culled record (d_touched <= 0) has an empty rectangle.
  * Out: d_vals [capacity] u32 record index per sorted instance;
  *      d_tile_ranges [T, 2] u32 [start, end) into d_vals per global tile
  *                    (an empty tile reads [0, 0));

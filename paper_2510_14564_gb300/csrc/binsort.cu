@@ -178,6 +178,12 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
     return v;
 }
 
+// Tiles a record covers: its rectangle's area (gs_project writes touched as
+// exactly that, and an empty rectangle for a culled record).
+__device__ __forceinline__ int rect_area(short4 r) {
+    return r.z > r.x && r.w > r.y ? (r.z - r.x) * (r.w - r.y) : 0;
+}
+
 // Range reduction and the global histograms of the four 8-bit digits of n
 // keys.  range[0] holds ~min and range[1] the max of the visible keys (raw
 // FP32 depth bits; 0xffffffff marks a culled record), as k_depth_keys left
@@ -239,15 +245,39 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     const uint32_t bid = s_bid;
     const long long bbase = (long long)bid * kSortTile;
     if (s_copy) {
+        // four items per thread at a time, every load issued before any use
         const long long end = min((long long)n, bbase + kSortTile);
-        for (long long i = bbase + threadIdx.x; i < end; i += kSortThreads) {
-            const uint32_t v = __ldg(vin + i);
-            vout[i] = v;
-            if (keys_needed) kout[i] = __ldg(kin + i);
-            if (touched) {
-                const int t = __ldg(touched + v);
-                cnt[i] = t > 0 ? (uint32_t)t : 0u;
-                if (rs) rs[i] = t > 0 ? __ldg(rect + v) : make_short4(0, 0, 0, 0);
+        for (long long i0 = bbase + threadIdx.x; i0 < end; i0 += 4 * kSortThreads) {
+            uint32_t v[4];
+            int t[4];
+            short4 rc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long i = i0 + u * kSortThreads;
+                v[u] = i < end ? __ldg(vin + i) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long i = i0 + u * kSortThreads;
+                if (i >= end) continue;
+                vout[i] = v[u];
+                if (keys_needed) kout[i] = __ldg(kin + i);
+                if (touched) {
+                    if (rs) {                       // the count is the rectangle's area
+                        rc[u] = __ldg(rect + v[u]);
+                        t[u] = rect_area(rc[u]);
+                    } else {
+                        t[u] = __ldg(touched + v[u]);
+                    }
+                }
+            }
+            if (!touched) continue;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long i = i0 + u * kSortThreads;
+                if (i >= end) continue;
+                cnt[i] = t[u] > 0 ? (uint32_t)t[u] : 0u;
+                if (rs) rs[i] = t[u] > 0 ? rc[u] : make_short4(0, 0, 0, 0);
             }
         }
         return;
@@ -255,12 +285,18 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
     const long long base = bbase + w * (kSortItems * 32);
+    // every load of the tile first: 2 x kSortItems in flight per thread
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const long long idx = base + it * 32 + l;
         const bool valid = idx < (long long)n;
         key[it] = valid ? __ldg(kin + idx) : 0u;
         val[it] = valid ? __ldg(vin + idx) : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const long long idx = base + it * 32 + l;
+        const bool valid = idx < (long long)n;
         const uint32_t d = valid ? ((key[it] >> shift) & 255u) : kRadix;
         const unsigned peers = warp_peers(d, 8);
         const unsigned rank = __popc(peers & lanemask_lt());
@@ -325,9 +361,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
         if (keys_needed) kout[g] = k;
         vout[g] = v;
         if (touched) {
-            const int t = __ldg(touched + v);
+            const short4 rc = rs ? __ldg(rect + v) : make_short4(0, 0, 0, 0);
+            const int t = rs ? rect_area(rc) : __ldg(touched + v);             // the count is the area
             cnt[g] = t > 0 ? (uint32_t)t : 0u;
-            if (rs) rs[g] = t > 0 ? __ldg(rect + v) : make_short4(0, 0, 0, 0);
+            if (rs) rs[g] = t > 0 ? rc : make_short4(0, 0, 0, 0);
         }
     }
 }
@@ -511,24 +548,49 @@ static void exclusive_scan(const Tin *in, Tout *out, long long n, Tout *partials
 // value buffers of the sort's ping-pong, so that every value buffer holds
 // record indices only, whatever a sort cut short by a timeout leaves there.
 // With range != NULL also range[0] = ~(smallest visible key) and range[1] =
-// the largest (both zeroed by the caller): reduced per CTA over a
-// grid-stride loop, then one atomic per CTA and word.
+// the largest (both zeroed by the caller): reduced per CTA, one atomic per
+// CTA and word.  Four records per thread, with 16-byte accesses where the
+// four are whole and aligned.
 __global__ void __launch_bounds__(256) k_depth_keys(const float *__restrict__ depth, const int *__restrict__ touched,
                                                     long long n, uint32_t *__restrict__ keys,
                                                     uint32_t *__restrict__ vals, uint32_t *__restrict__ vals2,
                                                     uint32_t *__restrict__ range) {
     __shared__ uint32_t s_inv[8], s_max[8];
     uint32_t inv = 0u, mx = 0u;
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
-        const uint32_t k = touched[j] > 0 ? __float_as_uint(depth[j]) : 0xffffffffu;
-        keys[j] = k;
-        vals[j] = (uint32_t)j;
-        vals2[j] = (uint32_t)j;
-        if (k != 0xffffffffu) {
-            inv = max(inv, ~k);
-            mx = max(mx, k);
+    const long long j0 = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    uint32_t k[4];
+    if (j0 + 4 <= n && ((reinterpret_cast<uintptr_t>(depth + j0) | reinterpret_cast<uintptr_t>(touched + j0) |
+                         reinterpret_cast<uintptr_t>(keys + j0) | reinterpret_cast<uintptr_t>(vals + j0) |
+                         reinterpret_cast<uintptr_t>(vals2 + j0)) & 15) == 0) {
+        const float4 d = __ldg(reinterpret_cast<const float4 *>(depth + j0));
+        const int4 t = __ldg(reinterpret_cast<const int4 *>(touched + j0));
+        k[0] = t.x > 0 ? __float_as_uint(d.x) : 0xffffffffu;
+        k[1] = t.y > 0 ? __float_as_uint(d.y) : 0xffffffffu;
+        k[2] = t.z > 0 ? __float_as_uint(d.z) : 0xffffffffu;
+        k[3] = t.w > 0 ? __float_as_uint(d.w) : 0xffffffffu;
+        const uint4 idx = make_uint4((uint32_t)j0, (uint32_t)j0 + 1, (uint32_t)j0 + 2, (uint32_t)j0 + 3);
+        *reinterpret_cast<uint4 *>(keys + j0) = make_uint4(k[0], k[1], k[2], k[3]);
+        *reinterpret_cast<uint4 *>(vals + j0) = idx;
+        *reinterpret_cast<uint4 *>(vals2 + j0) = idx;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long j = j0 + u;
+            k[u] = 0xffffffffu;
+            if (j < n) {
+                k[u] = touched[j] > 0 ? __float_as_uint(depth[j]) : 0xffffffffu;
+                keys[j] = k[u];
+                vals[j] = (uint32_t)j;
+                vals2[j] = (uint32_t)j;
+            }
         }
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (k[u] != 0xffffffffu) {
+            inv = max(inv, ~k[u]);
+            mx = max(mx, k[u]);
+        }
     if (!range) return;
     inv = __reduce_max_sync(0xffffffffu, inv);
     mx = __reduce_max_sync(0xffffffffu, mx);
@@ -1076,7 +1138,7 @@ static const uint32_t *depth_order(const float *d_depth, const int32_t *d_touche
         uint32_t *status = hist, *ghist = hist + 4 * kRadix * nb, *counters = ghist + 4 * kRadix;
         uint32_t *range = counters + 4;
         cudaMemsetAsync(hist, 0, onesweep_scratch_bytes(VN), st);
-        { k_depth_keys<<<(int)(cdiv(VN, 256) < 152 * 8 ? cdiv(VN, 256) : 152 * 8), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0, dv1, range); count_launches(1); }
+        { k_depth_keys<<<cdiv(cdiv(VN, 4), 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0, dv1, range); count_launches(1); }
         if (VN > 0) {
             const int hb = (int)(VN / 4096 + 1 < 1024 ? VN / 4096 + 1 : 1024);
             { k_onesweep_hist<<<hb, 256, 0, st>>>(ka, (uint32_t)VN, range, ghist); count_launches(1); }
@@ -1094,7 +1156,7 @@ static const uint32_t *depth_order(const float *d_depth, const int32_t *d_touche
             if (n_views == 1 && cnt) return va;
         }
     } else {
-        { k_depth_keys<<<(int)(cdiv(VN, 256) < 152 * 8 ? cdiv(VN, 256) : 152 * 8), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0, dv1, nullptr); count_launches(1); }
+        { k_depth_keys<<<cdiv(cdiv(VN, 4), 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0, dv1, nullptr); count_launches(1); }
         for (int pass = 0; pass < 4; ++pass) {
             radix_pass(ka, va, kb, vb, nullptr, (uint32_t)VN, VN, 8 * pass, 8, true, hist, (uint32_t *)part, st);
             uint32_t *t = ka; ka = kb; kb = t;
@@ -1381,44 +1443,63 @@ __device__ __forceinline__ long long warp_lower_bound(const unsigned long long *
     return lo;
 }
 
-// Kept share of each view's instances estimated from the limits (the
-// previous step's processed counts): sum over the view's tiles of
-// 2 limit + 64, over the view's instances; one CTA per view.  -1 without
-// limits.
-__global__ void __launch_bounds__(kBoundThreads) k_view_share(TileBatch tb, int N,
-                                                              const unsigned long long *__restrict__ offs,
-                                                              const int32_t *__restrict__ limit,
-                                                              double *__restrict__ share) {
-    __shared__ double s_part[kBoundThreads / 32];
-    const int v = blockIdx.x;
-    const int Tv = tb.v[v].TX * tb.v[v].TY, tbase = tb.v[v].tile_base;
-    double est = 0.0;
-    if (limit)
-        for (int t = threadIdx.x; t < Tv; t += kBoundThreads) {
-            const int lm = __ldg(limit + tbase + t);
-            if (lm > 0) est += 2.0 * lm + 64.0;
-        }
-    est = warp_sum(est);
-    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = est;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sum = 0.0;
-        for (int q = 0; q < kBoundThreads / 32; ++q) sum += s_part[q];
-        const long long s0 = (long long)v * N;
-        const double total = (double)(offs[s0 + N] - offs[s0]);
-        share[v] = (limit && total > 0.0) ? fmin(0.5, fmax(0.01, sum / total)) : -1.0;
-    }
-}
-
-// One boundary per warp.
-__global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(int n_views, int Cv, int N,
+// One boundary per warp.  The CTA first sums the kept-share estimate of
+// each view its warps cover (the views' limits, a few KB from L2), so no
+// kernel has to run before.
+__global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(TileBatch tb, int Cv, int N,
                                                                 const unsigned long long *__restrict__ offs,
-                                                                const double *__restrict__ view_share,
+                                                                const int32_t *__restrict__ limit,
                                                                 long long *__restrict__ bounds) {
-    const int j = blockIdx.x * (kBoundThreads / 32) + (threadIdx.x >> 5);
+    __shared__ long long s_part[kBoundThreads / 32];
+    __shared__ double s_share[2];
+    const int n_views = tb.n;
+    const int jw0 = blockIdx.x * (kBoundThreads / 32);
+    const int v_first = min(n_views - 1, jw0 / (Cv + 1));
+    const int v_last = min(n_views - 1, (jw0 + kBoundThreads / 32 - 1) / (Cv + 1));
+    // a CTA of 32 warps covers at most two views when every view has at least
+    // 32 boundaries (Cv >= 152 here); more views take the per-warp path below
+    const bool per_cta = v_last - v_first <= 1;
+    if (per_cta) {
+        for (int vv = v_first; vv <= v_last; ++vv) {
+            long long est = 0;
+            if (limit) {
+                const int Tv = tb.v[vv].TX * tb.v[vv].TY, tbase = tb.v[vv].tile_base;
+                for (int t = threadIdx.x; t < Tv; t += kBoundThreads) {
+                    const int lm = __ldg(limit + tbase + t);
+                    if (lm > 0) est += 2ll * lm + 64;
+                }
+            }
+            est = warp_sum(est);
+            if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = est;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                long long sum = 0;
+                for (int q = 0; q < kBoundThreads / 32; ++q) sum += s_part[q];
+                const long long s0 = (long long)vv * N;
+                const double total = (double)(offs[s0 + N] - offs[s0]);
+                s_share[vv - v_first] = (limit && total > 0.0) ? fmin(0.5, fmax(0.01, (double)sum / total)) : -1.0;
+            }
+            __syncthreads();
+        }
+    }
+    const int j = jw0 + (threadIdx.x >> 5);
     if (j >= n_views * (Cv + 1)) return;
     const int v = j / (Cv + 1), k = j % (Cv + 1);
-    const double share = view_share[v];
+    double share = -1.0;
+    if (per_cta) {
+        share = s_share[v - v_first];
+    } else if (limit) {
+        const int Tv = tb.v[v].TX * tb.v[v].TY, tbase = tb.v[v].tile_base;
+        long long est = 0;
+        for (int t = threadIdx.x & 31; t < Tv; t += 32) {
+            const int lm = __ldg(limit + tbase + t);
+            if (lm > 0) est += 2ll * lm + 64;
+        }
+        est = warp_sum(est);
+        const long long s0 = (long long)v * N;
+        const double total = (double)(offs[s0 + N] - offs[s0]);
+        if (total > 0.0) share = fmin(0.5, fmax(0.01, (double)est / total));
+    }
     const int half = Cv / 2;
     const long long s0 = (long long)v * N, s1 = s0 + N;
     const unsigned long long i0 = offs[s0], span = offs[s1] - i0;
@@ -1521,7 +1602,7 @@ __global__ void __launch_bounds__(256) k_pre_count(TileBatch tb, int N, int Cv, 
 // warps before it, and each warp writes its range's prefixes and finds the
 // first chunk of its range that meets the rule; the first warp that found
 // one decides.
-constexpr int kColWarps = 8;
+constexpr int kColWarps = 16;
 __global__ void __launch_bounds__(32 * kColWarps) k_pre_colscan(TileBatch tb, int Cv, int Tmax,
                                                                uint32_t *__restrict__ Mc,
                                                                const uint32_t *__restrict__ Mv,
@@ -1749,6 +1830,7 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
             const int hw = r.w > y0w ? (r.w - y0w + kPlaceWarps - 1) / kPlaceWarps : 0;
             const int wd = r.z - r.x;
             const int cnt = wd > 0 ? wd * hw : 0;
+            if (!__any_sync(0xffffffffu, cnt > 0)) continue;  // none of these records reaches this warp's rows
             int inc = cnt;                                      // inclusive scan of the counts
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -1799,7 +1881,7 @@ __global__ void k_range_counts(const uint2 *__restrict__ ranges, int T, uint32_t
 }
 
 struct PrePlan {
-    size_t dk0, dk1, dv0, dv1, cnt, rs, offs, mc, mv, full, lastc, kept, tstart, bnd, vshare, hist, part, misc, bytes;
+    size_t dk0, dk1, dv0, dv1, cnt, rs, offs, mc, mv, full, lastc, kept, tstart, bnd, hist, part, misc, bytes;
     int Cv, Tmax;
     bool ok;
 };
@@ -1824,7 +1906,6 @@ static PrePlan make_pre_plan(long long VN, const TileBatch &tb) {
     p.kept = take(4 * (size_t)tb.total_tiles);
     p.tstart = take(8 * (size_t)(tb.total_tiles + 1));
     p.bnd = take(8 * (size_t)tb.n * (p.Cv + 1));
-    p.vshare = take(8 * (size_t)tb.n);
     long long nb = (VN + kSortTile - 1) / kSortTile;
     if (nb < 1) nb = 1;
     {
@@ -1959,9 +2040,7 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     }
     const int nchunks = n_views * p.Cv;
     long long *bnd = (long long *)(ws + p.bnd);
-    double *vshare = (double *)(ws + p.vshare);
-    { k_view_share<<<n_views, kBoundThreads, 0, st>>>(tb, N, offs, d_tile_limit, vshare); count_launches(1); }
-    { k_chunk_bounds<<<cdiv(n_views * (p.Cv + 1), kBoundThreads / 32), kBoundThreads, 0, st>>>(n_views, p.Cv, N, offs, vshare, bnd); count_launches(1); }
+    { k_chunk_bounds<<<cdiv(n_views * (p.Cv + 1), kBoundThreads / 32), kBoundThreads, 0, st>>>(tb, p.Cv, N, offs, d_tile_limit, bnd); count_launches(1); }
     const void *kc = rgb_dtype == GS_F32 ? (const void *)k_pre_count<GS_F32>
                      : rgb_dtype == GS_BF16 ? (const void *)k_pre_count<GS_BF16> : (const void *)k_pre_count<GS_F16>;
     allow_dynamic_smem(kc, gmax);

@@ -477,28 +477,28 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 
 // ran out of work.  One CTA; writes the count to *split_head.
 // With log_cost (a predicted log cost per tile, e.g. the cost MLP's) the
 // tiles' costs are exp(log_cost) instead of their processed counts.
-__device__ __forceinline__ double split_cost(const int *tile_nproc, const float *log_cost, int t) {
-    return log_cost ? (double)__expf(__ldg(log_cost + t)) : (double)max(0, __ldg(tile_nproc + t));
+__device__ __forceinline__ float split_cost(const int *tile_nproc, const float *log_cost, int t) {
+    return log_cost ? __expf(__ldg(log_cost + t)) : (float)max(0, __ldg(tile_nproc + t));
 }
 
 __global__ void __launch_bounds__(1024) k_split_head(const int *__restrict__ tile_nproc,
                                                      const float *__restrict__ log_cost, int T, int n_cta,
                                                      int cap, int *__restrict__ split_head) {
-    __shared__ double s_sum[32];
+    __shared__ float s_sum[32];
     __shared__ int s_cnt[32];
-    __shared__ double s_total;
-    double sum = 0;
+    __shared__ float s_total;
+    float sum = 0;
     for (int t = threadIdx.x; t < T; t += 1024) sum += split_cost(tile_nproc, log_cost, t);
     sum = warp_sum(sum);
     if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double tot = 0;
+        float tot = 0;
         for (int q = 0; q < 32; ++q) tot += s_sum[q];
         s_total = tot;
     }
     __syncthreads();
-    const double per_cta = s_total / max(1, n_cta);
+    const float per_cta = s_total / (float)max(1, n_cta);
     int cnt = 0;
     for (int t = threadIdx.x; t < T; t += 1024) cnt += split_cost(tile_nproc, log_cost, t) > per_cta;
     cnt = warp_sum(cnt);

@@ -134,16 +134,17 @@ class PassJudge:
 
 
 def _count_mlp_init(seed: int) -> np.ndarray:
-    """FP32 weights of a cost MLP that starts out ordering tiles by its
-    feature 0 (a log count): hidden unit 0 passes it to the output, the
-    others start small, and training moves it from there."""
+    """FP32 weights of a cost MLP that starts out ordering tiles exactly by
+    its feature 0 (a log count): hidden unit 0 passes it to the output, the
+    other hidden units get random input weights but zero output weights, so
+    they add nothing until training gives them a share (their output weights
+    get gradient at once, their input weights from then on)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     w = np.zeros(MLP_W, np.float32)
     w[:256] = rng.normal(0, math.sqrt(2.0 / 8), 256)
     w[0:8] = 0.0
     w[0] = 1.0
     w[288] = 1.0
-    w[289:320] = rng.normal(0, 0.05, 31)
     w[320] = 10.0                      # log(ns) of a typical tile
     return w
 
