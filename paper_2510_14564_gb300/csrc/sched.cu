@@ -306,17 +306,33 @@ __global__ void __launch_bounds__(kOrderThreads) k_order_small(const float *__re
     uint32_t *wh = rank + kSmallOrder;               // [32 warps][256]
     __shared__ uint32_t s_dstart[256];
     __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_or[32], s_and[32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    uint32_t kor = 0u, kand = 0xffffffffu;
     for (int i = threadIdx.x; i < n; i += kOrderThreads) {
         uint32_t b = __float_as_uint(cost[i]);
         uint32_t asc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);   // order-preserving map
         K0[i] = ~asc;                                                 // descending cost
         V0[i] = (uint32_t)i;
+        kor |= ~asc;
+        kand &= ~asc;
     }
+    // a digit every key shares (OR and AND agree on it) needs no pass: whole
+    // bytes are common when the costs span few binades or are small integers
+    kor = __reduce_or_sync(0xffffffffu, kor);
+    kand = __reduce_and_sync(0xffffffffu, kand);
+    if (l == 0) { s_or[w] = kor; s_and[w] = kand; }
+    __syncthreads();
+    kor = 0u;
+    kand = 0xffffffffu;
+#pragma unroll
+    for (int q = 0; q < kOrderThreads / 32; ++q) { kor |= s_or[q]; kand &= s_and[q]; }
+    const uint32_t varying = kor ^ kand;
     const int seg = ((n + 31) / 32 + 31) / 32 * 32;  // items per warp segment (multiple of 32)
     uint32_t *ka = K0, *va = V0, *kb = K1, *vb = V1;
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;
+        if (((varying >> shift) & 255u) == 0u) continue;             // every key has this digit
         for (int k = threadIdx.x; k < 32 * 256; k += kOrderThreads) wh[k] = 0;
         __syncthreads();
         for (int j = 0; j < seg; j += 32) {

@@ -60,7 +60,7 @@ class Schedule:
     order by measured duration."""
     mode: str = "raster"
     feature_cap: int = 128
-    mlp_lr: float = 3e-3
+    mlp_lr: float = 1e-3
     train_every: int = 4
     bwd_order: str = "forward"
     seed: int = 0
@@ -480,8 +480,31 @@ class Frame:
             return
         self.mlp_t += 1
         m = self.mlp["bwd"]
+        if self.mlp_t == 1:
+            self._fit_line(m)
         L.gs_mlp_train_step(m["w32"], m["w16"], m["m"], m["v"], self.mlp_t, self.sched.mlp_lr, self.feats_b,
                             self.tile_ns_b, None, self.T, m["g"], m["loss"])
+
+    def _fit_line(self, m: dict) -> None:
+        """Once, before the first training step: set the MLP's output to the
+        least-squares line of log(reverse-pass tile time) on its feature 0
+        (log1p of the processed count), fitted on the tile times just
+        measured (one read-back).  The MLP then starts as the processed-count
+        order at the right scale, and training refines it instead of first
+        spending its steps on the offset."""
+        f0 = self.feats_b.view(-1, 8)[:, 0].cpu().numpy().astype(np.float64)
+        ns = self.tile_ns_b.cpu().numpy().astype(np.float64)
+        live = ns > 0
+        if live.sum() < 2 or np.ptp(f0[live]) <= 0:
+            return
+        a, b = np.polyfit(f0[live], np.log(ns[live]), 1)
+        if not (a > 0 and np.isfinite(a) and np.isfinite(b)):
+            return
+        w = m["w32"].cpu().numpy()
+        w[288] = a                     # hidden unit 0 passes feature 0 with weight 1
+        w[320] = b
+        m["w32"].copy_(torch.from_numpy(w))
+        m["w16"].copy_(torch.from_numpy(w.astype(np.float16)))
 
     def schedule_report(self) -> dict:
         """The orders in use and the measured pass durations behind them."""
