@@ -186,9 +186,9 @@ def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1) -> dict:
 # (smsp__inst_executed.sum of k_render_bwd over the sum of the per-pixel
 # processed counts).  Valid only while the kernel sources hash as captured.
 RENDER_BWD_INSTR = {
-    "warp_instr_per_pair": 385020601 / 306789136,
+    "warp_instr_per_pair": 339131212 / 306789136,
     "sources": {
-        "paper_2510_14564_gb300/csrc/render.cu": "d4537a82c71026b7380089782431322aaa5640c7231c8379dd7a341443d096b0",
+        "paper_2510_14564_gb300/csrc/render.cu": "be4556c130316a28575e6988cf1c5c579890a1d5b8ead5151de229e243080117",
         "paper_2510_14564_gb300/csrc/gs_common.cuh": "0030d55b8fab3ccb7ca6285c29977af8f502d986272319b6f97e525d5ed769b4",
     },
 }

@@ -214,18 +214,25 @@ __global__ void __launch_bounds__(256) k_onesweep_hist(uint32_t *__restrict__ ke
 }
 
 // One digit pass.  status [nb][256] and *tile_counter are zeroed by the
-// caller; ghist is this digit's global histogram.  If every key has the same
-// digit the pass is the identity and copies (the keys only if keys_needed).
-// With touched != NULL (the last pass of a one-view sort) it also writes,
-// beside each record's final position g, cnt[g] = max(0, touched[record])
-// and rs[g] = its tile rectangle (empty for a culled record): the later
-// passes then read both in depth order, coalesced, without a gather.
+// caller; ghist[4][256] holds the global histograms of the four digits, this
+// pass sorting on digit `pass`.  If every key has the same digit the pass is
+// the identity and copies (the keys only if keys_needed).
+// With touched != NULL the final pass also writes, beside each record's final
+// position g, cnt[g] = max(0, touched[record]) and rs[g] = its tile rectangle
+// (empty for a culled record): the later stages then read both in depth
+// order, coalesced, without a gather.  Which pass is final: with vfin == NULL
+// the one given touched (the host passes it to the last); with vfin every
+// pass is given touched and the final one is the last whose digit varies
+// (the digits above it are one value for every key, so the passes for them
+// would be copies): it writes the sorted values to vfin instead of vout, and
+// the passes after it return at once.
+constexpr int kLbWindow = 4;                     // status words of earlier tiles read per look-back round
 __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, uint32_t n, int shift, const uint32_t *__restrict__ ghist,
+    uint32_t *__restrict__ vout, uint32_t n, int pass, const uint32_t *__restrict__ ghist_all,
     uint32_t *status, uint32_t *tile_counter, long long wait_limit, int keys_needed,
     const int32_t *__restrict__ touched, uint32_t *__restrict__ cnt, const short4 *__restrict__ rect,
-    short4 *__restrict__ rs, int *err_word) {
+    short4 *__restrict__ rs, uint32_t *__restrict__ vfin, uint32_t *done, int *err_word) {
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_wh[8][kRadix];
@@ -233,15 +240,34 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     __shared__ uint32_t s_goff[kRadix];
     __shared__ uint32_t s_warp[8], s_warp2[8];
     __shared__ uint32_t s_bid;
-    __shared__ int s_copy;
+    __shared__ int s_copy, s_const[4], s_last;
+    const int shift = 8 * pass;
+    const uint32_t *ghist = ghist_all + kRadix * pass;
     if (threadIdx.x == 0) {
         s_bid = atomicAdd(tile_counter, 1u);
         s_copy = 0;
     }
+    if (threadIdx.x < 4) s_const[threadIdx.x] = 0;
     for (int k = threadIdx.x; k < 8 * kRadix; k += kSortThreads) (&s_wh[0][0])[k] = 0;
     __syncthreads();
     if (__ldg(ghist + threadIdx.x) == n) s_copy = 1;       // one digit for every key
+    if (vfin) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (__ldg(ghist_all + kRadix * e + threadIdx.x) == n) s_const[e] = 1;
+    }
     __syncthreads();
+    bool final_pass = touched != nullptr;
+    if (vfin) {
+        int F = 0;                                          // the last digit that varies
+#pragma unroll
+        for (int e = 1; e < 4; ++e)
+            if (!s_const[e]) F = e;
+        if (pass > F) return;                               // uniform over the CTA
+        final_pass = pass == F;
+        if (final_pass) vout = vfin;
+    }
+    const int32_t *gtouch = final_pass ? touched : nullptr;
     const uint32_t bid = s_bid;
     const long long bbase = (long long)bid * kSortTile;
     if (s_copy) {
@@ -261,17 +287,17 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
                 const long long i = i0 + u * kSortThreads;
                 if (i >= end) continue;
                 vout[i] = v[u];
-                if (keys_needed) kout[i] = __ldg(kin + i);
-                if (touched) {
+                if (keys_needed && !final_pass) kout[i] = __ldg(kin + i);
+                if (gtouch) {
                     if (rs) {                       // the count is the rectangle's area
                         rc[u] = __ldg(rect + v[u]);
                         t[u] = rect_area(rc[u]);
                     } else {
-                        t[u] = __ldg(touched + v[u]);
+                        t[u] = __ldg(gtouch + v[u]);
                     }
                 }
             }
-            if (!touched) continue;
+            if (!gtouch) continue;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const long long i = i0 + u * kSortThreads;
@@ -307,73 +333,111 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
         loc[it] = valid ? before + rank : 0xffffffffu;
     }
     __syncthreads();
-    {
-        const int d = threadIdx.x;
-        uint32_t c = 0;
+    // thread d: this tile's count of digit d (and the warps' offsets within
+    // it), published at once; the tile-local and global digit starts
+    const int d = threadIdx.x;
+    uint32_t c = 0;
 #pragma unroll
-        for (int ww = 0; ww < 8; ++ww) {
-            const uint32_t x = s_wh[ww][d];
-            s_wh[ww][d] = c;
-            c += x;
-        }
-        // publish this tile's count of digit d, then look back for the counts
-        // of all earlier tiles
-        uint32_t *my = status + (size_t)bid * kRadix + d;
-        st_relaxed(my, (bid == 0 ? kLbPre : kLbAgg) | c);
-        s_dstart[d] = block_excl_scan_256(c, s_warp);
-        const uint32_t gbase = block_excl_scan_256(__ldg(ghist + d), s_warp2);
-        uint32_t excl = 0;
-        if (bid > 0) {
-            long long j = (long long)bid - 1, reads = 0;
-            while (j >= 0) {
-                // bounded: after wait_limit reads the tile goes on with the
-                // counts it has (an unspecified order, still a set of valid
-                // record indices) and reports GS_EW_TIMEOUT
-                if (++reads > wait_limit) { set_err(err_word, GS_EW_TIMEOUT); break; }
-                const uint32_t v = ld_relaxed(status + (size_t)j * kRadix + d);
-                const uint32_t f = v & ~kLbVal;
-                if (f == 0u) continue;
-                excl += v & kLbVal;
-                if (f == kLbPre) break;
-                --j;
-            }
-            st_relaxed(my, kLbPre | (excl + c));
-        }
-        s_goff[d] = gbase + excl;
+    for (int ww = 0; ww < 8; ++ww) {
+        const uint32_t x = s_wh[ww][d];
+        s_wh[ww][d] = c;
+        c += x;
     }
+    uint32_t *my = status + (size_t)bid * kRadix + d;
+    st_relaxed(my, (bid == 0 ? kLbPre : kLbAgg) | c);
+    s_dstart[d] = block_excl_scan_256(c, s_warp);
+    const uint32_t gbase = block_excl_scan_256(__ldg(ghist + d), s_warp2);
     __syncthreads();
+    // the tile in digit order in shared memory (before the look-back, so
+    // that the keys' registers are free while it polls)
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         if (loc[it] != 0xffffffffu) {
-            const uint32_t d = (key[it] >> shift) & 255u;
-            const uint32_t pos = s_dstart[d] + s_wh[w][d] + loc[it];
+            const uint32_t dd = (key[it] >> shift) & 255u;
+            const uint32_t pos = s_dstart[dd] + s_wh[w][dd] + loc[it];
             s_keys[pos] = key[it];
             s_vals[pos] = val[it];
         }
     }
+    // look back for the counts of digit d in all earlier tiles
+    uint32_t excl = 0;
+    if (bid > 0) {
+        // rounds of kLbWindow reads in flight (tiles j, j-1, ...), taken in
+        // order until a tile not yet published or an inclusive prefix
+        long long j = (long long)bid - 1, rounds = 0;
+        bool found = false;
+        while (!found) {
+            // bounded: after wait_limit rounds the tile goes on with the
+            // counts it has (an unspecified order, still a set of valid
+            // record indices) and reports GS_EW_TIMEOUT
+            if (++rounds > wait_limit) { set_err(err_word, GS_EW_TIMEOUT); break; }
+            uint32_t v[kLbWindow];
+#pragma unroll
+            for (int q = 0; q < kLbWindow; ++q)
+                v[q] = j - q >= 0 ? ld_relaxed(status + (size_t)(j - q) * kRadix + d) : 0u;
+            int q = 0;
+#pragma unroll
+            for (; q < kLbWindow; ++q) {
+                const uint32_t f = v[q] & ~kLbVal;
+                if (f == 0u) break;                         // not published yet: poll again from here
+                excl += v[q] & kLbVal;
+                if (f == kLbPre) { found = true; break; }
+            }
+            j -= q;                                         // tile 0 publishes a prefix: j stays >= 0
+        }
+        st_relaxed(my, kLbPre | (excl + c));
+    }
+    s_goff[d] = gbase + excl;
     __syncthreads();
     const int n_local = (int)min((long long)kSortTile, (long long)n - bbase);
     for (int q = threadIdx.x; q < n_local; q += kSortThreads) {
         const uint32_t k = s_keys[q];
-        const uint32_t d = (k >> shift) & 255u;
-        const uint32_t g = s_goff[d] + (uint32_t)(q - s_dstart[d]);
+        const uint32_t dq = (k >> shift) & 255u;
+        const uint32_t g = s_goff[dq] + (uint32_t)(q - s_dstart[dq]);
         const uint32_t v = s_vals[q];
-        if (keys_needed) kout[g] = k;
+        if (keys_needed && !final_pass) kout[g] = k;
         vout[g] = v;
-        if (touched) {
+        if (gtouch) {
             const short4 rc = rs ? __ldg(rect + v) : make_short4(0, 0, 0, 0);
-            const int t = rs ? rect_area(rc) : __ldg(touched + v);             // the count is the area
+            const int t = rs ? rect_area(rc) : __ldg(gtouch + v);              // the count is the area
             cnt[g] = t > 0 ? (uint32_t)t : 0u;
             if (rs) rs[g] = t > 0 ? rc : make_short4(0, 0, 0, 0);
+        }
+    }
+    if (!final_pass || !done) return;
+    // A look-back that gave up scatters by partial counts: positions of the
+    // final outputs may collide and leave slots unwritten.  The last tile to
+    // finish checks the error word and, after a timeout, rewrites the final
+    // outputs as the identity of this pass's input (whose every slot holds a
+    // record index: the earlier passes' buffers start as 0..n-1), so the
+    // later stages read record indices and rectangles only.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (!err_word || !(ld_relaxed(reinterpret_cast<const uint32_t *>(err_word)) & GS_EW_TIMEOUT)) return;
+    for (long long i = threadIdx.x; i < (long long)n; i += kSortThreads) {
+        const uint32_t v = vin[i];
+        vout[i] = v;
+        if (gtouch) {
+            const short4 rc = rs ? __ldg(rect + v) : make_short4(0, 0, 0, 0);
+            const int t = rs ? rect_area(rc) : __ldg(gtouch + v);
+            cnt[i] = t > 0 ? (uint32_t)t : 0u;
+            if (rs) rs[i] = t > 0 ? rc : make_short4(0, 0, 0, 0);
         }
     }
 }
 
 // Scratch of the onesweep depth sort of n keys (status words of four passes,
-// four digit histograms, four tile counters).
+// four digit histograms, four tile counters, the key range, and the count of
+// final-pass tiles done).
 static size_t onesweep_scratch_bytes(long long n) {
     const long long nb = (n + kSortTile - 1) / kSortTile;
-    return 4 * (size_t)(4 * kRadix * nb + 4 * kRadix + 4 + 2);
+    return 4 * (size_t)(4 * kRadix * nb + 4 * kRadix + 4 + 2 + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -604,8 +668,10 @@ __global__ void __launch_bounds__(256) k_depth_keys(const float *__restrict__ de
             inv = max(inv, s_inv[w]);
             mx = max(mx, s_max[w]);
         }
-        if (inv) atomicMax(range, inv);
-        if (mx) atomicMax(range + 1, mx);
+        // most tiles find the running maxima above their own: a read
+        // instead of an atomic on the same two words
+        if (inv && inv > ld_relaxed(range)) atomicMax(range, inv);
+        if (mx && mx > ld_relaxed(range + 1)) atomicMax(range + 1, mx);
     }
 }
 
@@ -1129,7 +1195,8 @@ static void radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
 static const uint32_t *depth_order(const float *d_depth, const int32_t *d_touched, long long VN, int N,
                                    int n_views, uint32_t *dk0, uint32_t *dk1, uint32_t *dv0, uint32_t *dv1,
                                    uint32_t *hist, void *part, int *err_word, cudaStream_t st,
-                                   uint32_t *cnt = nullptr, const short4 *rect = nullptr, short4 *rs = nullptr) {
+                                   uint32_t *cnt = nullptr, const short4 *rect = nullptr, short4 *rs = nullptr,
+                                   uint32_t *vfin = nullptr) {
     uint32_t *ka = dk0, *kb = dk1, *va = dv0, *vb = dv1;
     if (VN < (long long)kLbVal) {
         // onesweep: status words of the four passes, the four histograms, the
@@ -1142,18 +1209,24 @@ static const uint32_t *depth_order(const float *d_depth, const int32_t *d_touche
         if (VN > 0) {
             const int hb = (int)(VN / 4096 + 1 < 1024 ? VN / 4096 + 1 : 1024);
             { k_onesweep_hist<<<hb, 256, 0, st>>>(ka, (uint32_t)VN, range, ghist); count_launches(1); }
+            // one view with counts: the final pass also gathers each record's
+            // tile count and rectangle; with vfin it is the last pass whose
+            // digit varies, and it leaves the order in vfin
+            const bool gather = n_views == 1 && cnt;
+            const bool early = gather && vfin;
             for (int pass = 0; pass < 4; ++pass) {
-                // the last pass of a one-view sort also gathers each record's tile count
-                const bool last = pass == 3 && n_views == 1 && cnt;
-                { k_onesweep_pass<<<(int)nb, kSortThreads, 0, st>>>(ka, va, kb, vb, (uint32_t)VN, 8 * pass, ghist + kRadix * pass,
+                const bool give = early || (gather && pass == 3);
+                { k_onesweep_pass<<<(int)nb, kSortThreads, 0, st>>>(ka, va, kb, vb, (uint32_t)VN, pass, ghist,
                                                                    status + (size_t)kRadix * nb * pass, counters + pass,
                                                                    g_wait_limit.load(), pass < 3 ? 1 : 0,
-                                                                   last ? d_touched : nullptr, cnt, rect, rs, err_word);
+                                                                   give ? d_touched : nullptr, cnt, rect, rs,
+                                                                   early ? vfin : nullptr, counters + 6, err_word);
                   count_launches(1); }
                 uint32_t *t = ka; ka = kb; kb = t;
                 t = va; va = vb; vb = t;
             }
-            if (n_views == 1 && cnt) return va;
+            if (early) return vfin;
+            if (gather) return va;
         }
     } else {
         { k_depth_keys<<<cdiv(cdiv(VN, 4), 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0, dv1, nullptr); count_launches(1); }
@@ -1379,7 +1452,7 @@ extern "C" int gs_bin_sort(const gs_camera *cams, int n_views, int N, const floa
 // prefixes of gs_bin_sort's lists, long enough that blending never reaches
 // their end, so images and gradients are those of the full lists.
 // ---------------------------------------------------------------------------
-constexpr int kPreChunks = 608;
+constexpr int kPreChunks = 456;
 constexpr int kPreMinChunksPerView = 152;
 constexpr int kPreMaxTiles = 16384;               // cursor row of at most 64 KB
 constexpr float kCovScale = 4096.0f;              // fixed-point units of -ln(1 - alpha)
@@ -1414,9 +1487,11 @@ __device__ __forceinline__ uint32_t core_rect(const void *splats, uint32_t g, sh
 // of the view.  Placement work is in the part of the lists that is kept; with
 // per-tile limits (the previous step's processed counts) the kept share s of a
 // view's instances is estimated as sum(2 limit + 64) / instances (an overestimate
-// where lists are cut), and the first half of the chunks splits the first s
-// of the instances evenly, the second half the rest with quadratic growth
-// (starting small, so an underestimate costs little).  Without limits the chunks grow cubically
+// where lists are cut), and the first quarter of the chunks splits the first s
+// of the instances evenly (each a few hundred records: a tile's kept prefix
+// overshoots its limit by little), the rest the remaining instances with
+// quadratic growth (starting small, so an underestimate costs little; the
+// later chunks are kept by few tiles and mostly skipped).  Without limits the chunks grow cubically
 // (fine at the front of the depth order, where lists are cut).  One CTA.
 constexpr int kBoundThreads = 1024;
 
@@ -1449,8 +1524,10 @@ __device__ __forceinline__ long long warp_lower_bound(const unsigned long long *
 __global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(TileBatch tb, int Cv, int N,
                                                                 const unsigned long long *__restrict__ offs,
                                                                 const int32_t *__restrict__ limit,
-                                                                long long *__restrict__ bounds) {
+                                                                long long *__restrict__ bounds,
+                                                                uint32_t *__restrict__ max_last) {
     __shared__ long long s_part[kBoundThreads / 32];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *max_last = 0u;   // k_pre_colscan raises it
     __shared__ double s_share[2];
     const int n_views = tb.n;
     const int jw0 = blockIdx.x * (kBoundThreads / 32);
@@ -1500,7 +1577,7 @@ __global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(TileBatch tb, in
         const double total = (double)(offs[s0 + N] - offs[s0]);
         if (total > 0.0) share = fmin(0.5, fmax(0.01, (double)est / total));
     }
-    const int half = Cv / 2;
+    const int half = Cv / 4;
     const long long s0 = (long long)v * N, s1 = s0 + N;
     const unsigned long long i0 = offs[s0], span = offs[s1] - i0;
     unsigned long long b;
@@ -1596,8 +1673,10 @@ __global__ void __launch_bounds__(256) k_pre_count(TileBatch tb, int N, int Cv, 
 // its chunks up to the first one where either the coverage bound passes the
 // target, or the kept count reaches the tile's limit (limit[t] > 0:
 // 2 limit + 64 entries; no limit otherwise); both running sums only grow, so
-// that chunk is the first where the inclusive sums meet the rule.  One CTA
-// per 32 tiles of a view (lane = tile: coalesced rows), its 8 warps taking 8
+// that chunk is the first where the inclusive sums meet the rule.  A tile
+// that never meets it keeps all its entries, up to the last chunk holding
+// one (so that the placement of later chunks can skip it).  One CTA
+// per 32 tiles of a view (lane = tile: coalesced rows), its kColWarps warps taking
 // contiguous chunk ranges: each warp sums its range, the CTA adds up the
 // warps before it, and each warp writes its range's prefixes and finds the
 // first chunk of its range that meets the rule; the first warp that found
@@ -1609,10 +1688,12 @@ __global__ void __launch_bounds__(32 * kColWarps) k_pre_colscan(TileBatch tb, in
                                                                const int32_t *__restrict__ limit,
                                                                uint32_t *__restrict__ full,
                                                                uint32_t *__restrict__ last_chunk,
-                                                               uint32_t *__restrict__ kept) {
+                                                               uint32_t *__restrict__ kept,
+                                                               uint32_t *__restrict__ max_last) {
     __shared__ uint32_t s_c[kColWarps][32];
     __shared__ unsigned long long s_v[kColWarps][32];
     __shared__ uint32_t s_fk[kColWarps][32], s_keep[kColWarps][32];
+    __shared__ int s_lnz[kColWarps][32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     int b = blockIdx.x, v = 0;
     for (; v < tb.n; ++v) {                        // blocks of 32 tiles, view by view
@@ -1659,6 +1740,7 @@ __global__ void __launch_bounds__(32 * kColWarps) k_pre_colscan(TileBatch tb, in
     const uint32_t want = lim > 0 ? (uint32_t)min(2ll * lim + 64, 0x7fffffffll) : 0xffffffffu;
     // 2. exclusive prefixes of this range; the first chunk meeting the rule
     uint32_t fk = 0xffffffffu, fkeep = 0;
+    int lnz = -1;                                  // the last chunk of this range holding an entry
     if (live) {
         for (int k = k0; k < k1; k += 8) {
             uint32_t a[8], c[8];
@@ -1674,21 +1756,32 @@ __global__ void __launch_bounds__(32 * kColWarps) k_pre_colscan(TileBatch tb, in
                 col[(long long)(k + j) * Tmax] = run;
                 run += a[j];
                 rcov += c[j];
+                if (a[j] > 0u) lnz = k + j;
                 if (fk == 0xffffffffu && (rcov >= kCovTarget || run >= want)) { fk = (uint32_t)(k + j); fkeep = run; }
             }
         }
     }
     s_fk[w][l] = fk;
     s_keep[w][l] = fkeep;
+    s_lnz[w][l] = lnz;
     __syncthreads();
     if (w == 0 && live) {
-        uint32_t lastc = (uint32_t)(Cv - 1), keep = total;
+        // a tile that never meets the rule keeps its whole list: up to the last
+        // chunk holding one of its entries (the chunks after it add nothing)
+        int last_nz = 0;
+#pragma unroll
+        for (int q = 0; q < kColWarps; ++q) last_nz = max(last_nz, s_lnz[q][l]);
+        uint32_t lastc = (uint32_t)last_nz, keep = total;
 #pragma unroll
         for (int q = kColWarps - 1; q >= 0; --q)
             if (s_fk[q][l] != 0xffffffffu) { lastc = s_fk[q][l]; keep = s_keep[q][l]; }
         full[g] = total;
         last_chunk[g] = lastc;
         kept[g] = keep;
+    }
+    if (w == 0) {                                  // the last chunk any tile keeps
+        const uint32_t mx = __reduce_max_sync(0xffffffffu, live ? last_chunk[g] : 0u);
+        if (l == 0 && mx > ld_relaxed(max_last)) atomicMax(max_last, mx);
     }
 }
 
@@ -1718,7 +1811,7 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     const uint32_t *__restrict__ Mc, const uint32_t *__restrict__ last_chunk,
     const unsigned long long *__restrict__ tstart, const unsigned long long *__restrict__ total,
     long long cap, uint32_t *__restrict__ vals, const float *__restrict__ depth,
-    unsigned long long *__restrict__ keys) {
+    unsigned long long *__restrict__ keys, const uint32_t *__restrict__ max_last) {
     extern __shared__ uint32_t s_cur[];
     __shared__ int s_any;
     __shared__ uint32_t s_g[kPlaceBatch];
@@ -1726,6 +1819,7 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     __shared__ int s_wc[kPlaceRounds * kPlaceWarps];
     if ((long long)*total > cap) return;
     const int v = blockIdx.x / Cv, k = blockIdx.x % Cv;
+    if ((uint32_t)k > *max_last) return;            // no tile of any view keeps this chunk
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int TX = tb.v[v].TX, TY = tb.v[v].TY, Tv = TX * TY, tbase = tb.v[v].tile_base;
     const int GX = TX + 1;
@@ -1881,7 +1975,7 @@ __global__ void k_range_counts(const uint2 *__restrict__ ranges, int T, uint32_t
 }
 
 struct PrePlan {
-    size_t dk0, dk1, dv0, dv1, cnt, rs, offs, mc, mv, full, lastc, kept, tstart, bnd, hist, part, misc, bytes;
+    size_t dk0, dk1, dv0, dv1, vfin, cnt, rs, offs, mc, mv, full, lastc, kept, tstart, bnd, hist, part, misc, bytes;
     int Cv, Tmax;
     bool ok;
 };
@@ -1896,6 +1990,7 @@ static PrePlan make_pre_plan(long long VN, const TileBatch &tb) {
     p.Cv = (kPreChunks + tb.n - 1) / tb.n;
     if (p.Cv < kPreMinChunksPerView) p.Cv = kPreMinChunksPerView;   // several views: at least this many each
     p.dk0 = take(4 * VN); p.dk1 = take(4 * VN); p.dv0 = take(4 * VN); p.dv1 = take(4 * VN);
+    p.vfin = take(4 * VN);
     p.cnt = take(4 * VN);
     p.rs = take(8 * VN);
     p.offs = take(8 * (VN + 1));
@@ -2031,7 +2126,8 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     }
     short4 *rs = (short4 *)(ws + p.rs);                 // rectangles in sorted order
     const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, d_err_word, st,
-                                        cnt, reinterpret_cast<const short4 *>(d_rect), rs);
+                                        cnt, reinterpret_cast<const short4 *>(d_rect), rs,
+                                        (uint32_t *)(ws + p.vfin));
     exclusive_scan<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, offs + VN, st);
     size_t gmax = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -2040,7 +2136,8 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     }
     const int nchunks = n_views * p.Cv;
     long long *bnd = (long long *)(ws + p.bnd);
-    { k_chunk_bounds<<<cdiv(n_views * (p.Cv + 1), kBoundThreads / 32), kBoundThreads, 0, st>>>(tb, p.Cv, N, offs, d_tile_limit, bnd); count_launches(1); }
+    uint32_t *max_last = count + 1;                     // the last chunk any tile keeps
+    { k_chunk_bounds<<<cdiv(n_views * (p.Cv + 1), kBoundThreads / 32), kBoundThreads, 0, st>>>(tb, p.Cv, N, offs, d_tile_limit, bnd, max_last); count_launches(1); }
     const void *kc = rgb_dtype == GS_F32 ? (const void *)k_pre_count<GS_F32>
                      : rgb_dtype == GS_BF16 ? (const void *)k_pre_count<GS_BF16> : (const void *)k_pre_count<GS_F16>;
     allow_dynamic_smem(kc, gmax);
@@ -2057,7 +2154,8 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     {
         int nblk = 0;
         for (int v = 0; v < n_views; ++v) nblk += cdiv(tb.v[v].TX * tb.v[v].TY, 32);
-        k_pre_colscan<<<nblk, 32 * kColWarps, 0, st>>>(tb, p.Cv, p.Tmax, Mc, Mv_used, d_tile_limit, full, lastc, kept);
+        k_pre_colscan<<<nblk, 32 * kColWarps, 0, st>>>(tb, p.Cv, p.Tmax, Mc, Mv_used, d_tile_limit, full, lastc, kept,
+                                                       max_last);
         count_launches(1);
     }
     exclusive_scan<uint32_t, unsigned long long>(kept, tstart, T, (unsigned long long *)part, tstart + T, st);
@@ -2074,7 +2172,7 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
         allow_dynamic_smem((const void *)k_pre_place, smem);      // 25 KB of its own static arrays
         { k_pre_place<<<nchunks, kPlaceThreads, smem, st>>>(tb, N, p.Cv, p.Tmax, order, rs, bnd, Mc, lastc, tstart,
                                                  tstart + T, capacity, d_vals, d_depth,
-                                                 reinterpret_cast<unsigned long long *>(d_keys)); count_launches(1); }
+                                                 reinterpret_cast<unsigned long long *>(d_keys), max_last); count_launches(1); }
     }
     return launch_status();
 }
@@ -2327,8 +2425,10 @@ extern "C" int gs_bin_sort_prefix_repair(const gs_camera *cams, int n_views, int
     if (workspace_bytes < p.bytes) return GS_ERR_CAPACITY;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char *ws = reinterpret_cast<char *>(d_workspace);
-    // the record order left by the last gs_bin_sort_prefix call (see depth_order)
-    const uint32_t *order = (const uint32_t *)(ws + (n_views > 1 ? p.dv1 : p.dv0));
+    // the record order left by the last gs_bin_sort_prefix call (see
+    // depth_order: one view sorted by the onesweep leaves it in vfin)
+    const size_t at = n_views > 1 ? p.dv1 : VN < (long long)kLbVal ? p.vfin : p.dv0;
+    const uint32_t *order = (const uint32_t *)(ws + at);
     const uint32_t *full = (const uint32_t *)(ws + p.full);
     uint32_t *rep_start = (uint32_t *)(ws + p.kept);  // kept counts are no longer needed
     const short4 *rect = reinterpret_cast<const short4 *>(d_rect);

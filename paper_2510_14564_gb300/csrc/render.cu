@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_render_fwd(TileBatch tb, con
 }
 
 template <int DT, int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 8) k_render_bwd(
+__global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 10) k_render_bwd(
     TileBatch tb, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
     const void *__restrict__ splats, SchedArgs sa, const float *__restrict__ dimg,
     const float *__restrict__ T_final, const int *__restrict__ n_proc, const int *__restrict__ tile_nproc,
@@ -368,7 +368,10 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 
         const TileCtx<PPT> c = tile_ctx<PPT>(tb, ranges, tile, part);
         const ViewTiles &vt = tb.v[c.view];
         const float pcx = (float)c.px + 0.5f;
-        float pcy[PPT], T[PPT], G0[PPT], G1[PPT], G2[PPT], bgdot[PPT], R0[PPT], R1[PPT], R2[PPT];
+        // per pixel: G = dL/dC, and GR = G . R with R the colour blended
+        // behind the current entry (the whole recursion of R is needed only
+        // through its dot with G, so one scalar replaces three)
+        float pcy[PPT], T[PPT], G0[PPT], G1[PPT], G2[PPT], bgdot[PPT], GR[PPT];
         int last[PPT];
         const long long HW = (long long)vt.W * vt.H;
         const float *di = dimg + 3 * vt.pix_base;
@@ -386,8 +389,12 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 
             }
             bgdot[p] = Tf * (vt.bg[0] * G0[p] + vt.bg[1] * G1[p] + vt.bg[2] * G2[p]);
             T[p] = Tf;
-            R0[p] = R1[p] = R2[p] = 0.0f;
+            GR[p] = 0.0f;
         }
+        // the reduced values of lane group l >> 2 are scaled on the way out:
+        // -ln2 (u, v), -1/2 (A, C), -1 (B), 1/o (opacity, per entry), 1 (colour)
+        const int vj = (threadIdx.x & 31) >> 2;
+        const float vscale = vj < 2 ? -kLn2 : (vj == 2 || vj == 4) ? -0.5f : vj == 3 ? -1.0f : 1.0f;
         const int jend = (int)c.range.x + __ldg(tile_nproc + tile);
         for (int j1 = jend; j1 > (int)c.range.x; j1 -= kBatch) {
             const int j0 = max((int)c.range.x, j1 - kBatch);
@@ -398,12 +405,16 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 
                 const float4 b = s_b[k];
                 const float4 cc = s_c[k];
                 const int e = __float_as_int(cc.y);
-                float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
+                const float dx = pcx - a.x;
+                // per thread (one column, dx fixed): moments of the power
+                // gradient dpow over its pixels, sum dpow dy^k for k = 0, 1, 2;
+                // the conic and mean gradients are linear in them
+                float M0 = 0.f, M1 = 0.f, M2 = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
                 bool contrib = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     if (e >= last[p]) continue;
-                    const float dx = pcx - a.x, dy = pcy[p] - a.y;
+                    const float dy = pcy[p] - a.y;
                     float q;
                     const float araw = pair_alpha_raw(a.z, a.w, b.x, b.y, dx, dy, &q);
                     const float alpha = fminf(kAlphaMax, araw);
@@ -414,28 +425,29 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 
                     const float Tb = T[p] * rom;
                     const float w = alpha * Tb;
                     gr = fmaf(G0[p], w, gr); gg = fmaf(G1[p], w, gg); gb = fmaf(G2[p], w, gb);
-                    const float dal = Tb * (G0[p] * (b.z - R0[p]) + G1[p] * (b.w - R1[p]) + G2[p] * (cc.x - R2[p])) -
-                                      bgdot[p] * rom;
-                    R0[p] = fmaf(b.z, alpha, om * R0[p]);
-                    R1[p] = fmaf(b.w, alpha, om * R1[p]);
-                    R2[p] = fmaf(cc.x, alpha, om * R2[p]);
+                    // dL/dalpha = T (G.c - G.R) - T_final (bg.G) / (1 - alpha)
+                    const float D = fmaf(G0[p], b.z, fmaf(G1[p], b.w, G2[p] * cc.x)) - GR[p];
+                    const float dal = fmaf(Tb, D, -bgdot[p] * rom);
+                    GR[p] = fmaf(alpha, D, GR[p]);             // R <- alpha c + (1 - alpha) R
                     T[p] = Tb;
                     if (araw <= kAlphaMax) {
                         const float dpow = dal * alpha;
-                        go = fmaf(dpow, cc.w, go);                     // dal * G, G = alpha / o
-                        gA = fmaf(-0.5f * dpow, dx * dx, gA);
-                        gB = fmaf(-dpow, dx * dy, gB);
-                        gC = fmaf(-0.5f * dpow, dy * dy, gC);
-                        // A dx + B dy = -ln2 (2 Ap dx + Bp dy); B dx + C dy = -ln2 (Bp dx + 2 Cp dy)
-                        gu = fmaf(-kLn2 * dpow, 2.0f * a.z * dx + a.w * dy, gu);
-                        gv = fmaf(-kLn2 * dpow, a.w * dx + 2.0f * b.x * dy, gv);
+                        const float t = dpow * dy;
+                        M0 += dpow;
+                        M1 += t;
+                        M2 = fmaf(t, dy, M2);
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
+                    // A dx + B dy = -ln2 (2 Ap dx + Bp dy); B dx + C dy = -ln2 (Bp dx + 2 Cp dy):
+                    // u: -ln2 (2 Ap dx M0 + Bp M1), v: -ln2 (Bp dx M0 + 2 Cp M1),
+                    // A: -dx^2 M0 / 2, B: -dx M1, C: -M2 / 2, opacity: M0 / o
+                    const float dxM0 = dx * M0;
                     // eight values by a halving butterfly: lane l ends with the
                     // warp sum of value (l >> 2), the ninth by a full butterfly
                     const int l = threadIdx.x & 31;
-                    float v8[8] = {gu, gv, gA, gB, gC, go, gr, gg};
+                    float v8[8] = {fmaf(2.0f * a.z, dxM0, a.w * M1), fmaf(a.w, dxM0, 2.0f * b.x * M1),
+                                   dx * dxM0, dx * M1, M2, M0, gr, gg};
                     const bool b4 = l & 16, b3 = l & 8, b2 = l & 4;
                     float h4[4];
 #pragma unroll
@@ -461,7 +473,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, PPT == 1 ? 4 : PPT == 2 ? 6 : 
                     h1 += __shfl_xor_sync(0xffffffffu, h1, 1);
                     gb = warp_sum(gb);
                     float *dst = grad2d + 12ll * __float_as_uint(cc.z);
-                    if ((l & 3) == 0) atomicAdd(dst + (l >> 2), h1);
+                    if ((l & 3) == 0) atomicAdd(dst + vj, h1 * (vj == 5 ? cc.w : vscale));
                     if (l == 0) atomicAdd(dst + 8, gb);
                 }
             }

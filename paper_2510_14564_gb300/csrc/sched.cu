@@ -286,101 +286,76 @@ __global__ void k_cost_keys(const float *__restrict__ cost, int n, uint32_t *__r
     vals[i] = (uint32_t)i;
 }
 
-// Work orders of at most kSmallOrder tiles: one CTA sorts the whole array in
-// shared memory, stable LSD radix (4 x 8 bits), each warp owning a
-// contiguous segment so that per-warp digit counts give stable ranks.
+// Work orders of at most kSmallOrder tiles by direct ranking: the position
+// of tile i in the descending order is the number of tiles j that precede it,
+// cost_j > cost_i, or cost_j == cost_i and j < i (the stable order).  Each CTA
+// ranks 32 tiles (one per lane) against every tile, its 8 warps taking 8
+// slices of the j range out of shared memory, and writes order[rank] = i:
+// n^2 comparisons spread over n / 32 CTAs in one launch, a few microseconds
+// at the tile counts of one view.  The comparison runs on the same
+// order-preserving key map as the radix path, so both give one order.
 constexpr int kSmallOrder = 8192;
-constexpr int kOrderThreads = 1024;
+constexpr int kRankWarps = 8;
 
-__device__ __forceinline__ unsigned lanemask_lt_s() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
+__device__ __forceinline__ uint32_t order_key(float c) {
+    const uint32_t b = __float_as_uint(c);
+    const uint32_t asc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);   // order-preserving map
+    return ~asc;                                                      // ascending = descending cost
 }
 
-__global__ void __launch_bounds__(kOrderThreads) k_order_small(const float *__restrict__ cost, int n,
+__global__ void __launch_bounds__(32 * kRankWarps) k_order_rank(const float *__restrict__ cost, int n,
                                                                int32_t *__restrict__ order) {
-    extern __shared__ uint32_t s_mem[];
-    uint32_t *K0 = s_mem, *V0 = K0 + kSmallOrder, *K1 = V0 + kSmallOrder, *V1 = K1 + kSmallOrder;
-    uint32_t *rank = V1 + kSmallOrder;               // [kSmallOrder]
-    uint32_t *wh = rank + kSmallOrder;               // [32 warps][256]
-    __shared__ uint32_t s_dstart[256];
-    __shared__ uint32_t s_tot[256];
-    __shared__ uint32_t s_or[32], s_and[32];
+    extern __shared__ __align__(16) uint32_t s_key[];   // [n rounded up to 4]
+    __shared__ uint32_t s_cnt[kRankWarps][32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    uint32_t kor = 0u, kand = 0xffffffffu;
-    for (int i = threadIdx.x; i < n; i += kOrderThreads) {
-        uint32_t b = __float_as_uint(cost[i]);
-        uint32_t asc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);   // order-preserving map
-        K0[i] = ~asc;                                                 // descending cost
-        V0[i] = (uint32_t)i;
-        kor |= ~asc;
-        kand &= ~asc;
-    }
-    // a digit every key shares (OR and AND agree on it) needs no pass: whole
-    // bytes are common when the costs span few binades or are small integers
-    kor = __reduce_or_sync(0xffffffffu, kor);
-    kand = __reduce_and_sync(0xffffffffu, kand);
-    if (l == 0) { s_or[w] = kor; s_and[w] = kand; }
-    __syncthreads();
-    kor = 0u;
-    kand = 0xffffffffu;
+    const int n4 = (n + 3) & ~3;
+    constexpr int U = 8;                            // loads in flight per thread
+    for (int j0 = threadIdx.x; j0 < n4; j0 += U * 32 * kRankWarps) {
+        uint32_t k[U];
 #pragma unroll
-    for (int q = 0; q < kOrderThreads / 32; ++q) { kor |= s_or[q]; kand &= s_and[q]; }
-    const uint32_t varying = kor ^ kand;
-    const int seg = ((n + 31) / 32 + 31) / 32 * 32;  // items per warp segment (multiple of 32)
-    uint32_t *ka = K0, *va = V0, *kb = K1, *vb = V1;
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 8 * pass;
-        if (((varying >> shift) & 255u) == 0u) continue;             // every key has this digit
-        for (int k = threadIdx.x; k < 32 * 256; k += kOrderThreads) wh[k] = 0;
-        __syncthreads();
-        for (int j = 0; j < seg; j += 32) {
-            const int i = w * seg + j + l;
-            const bool valid = i < n;
-            const uint32_t d = valid ? (ka[i] >> shift) & 255u : 256u;
-            const unsigned peers = warp_peers(d, 8);
-            const uint32_t before = valid ? wh[w * 256 + d] : 0u;
-            __syncwarp();
-            if (valid && (peers & lanemask_lt_s()) == 0) wh[w * 256 + d] = before + __popc(peers);
-            __syncwarp();
-            if (valid) rank[i] = before + __popc(peers & lanemask_lt_s());
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * 32 * kRankWarps;
+            k[u] = j < n ? order_key(__ldg(cost + j)) : 0xffffffffu;
         }
-        __syncthreads();
-        if (threadIdx.x < 256) {
-            const int d = threadIdx.x;
-            uint32_t run = 0;
-            for (int ww = 0; ww < 32; ++ww) {
-                uint32_t c = wh[ww * 256 + d];
-                wh[ww * 256 + d] = run;
-                run += c;
-            }
-            s_tot[d] = run;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * 32 * kRankWarps;
+            if (j < n4) s_key[j] = k[u];
         }
-        __syncthreads();
-        if (threadIdx.x < 32) {                      // exclusive scan of 256 totals, 8 per lane
-            uint32_t loc[8], sum = 0;
-            for (int q = 0; q < 8; ++q) { loc[q] = s_tot[8 * l + q]; sum += loc[q]; }
-            uint32_t inc = sum;
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-                if (l >= o) inc += t;
-            }
-            uint32_t run = inc - sum;
-            for (int q = 0; q < 8; ++q) { s_dstart[8 * l + q] = run; run += loc[q]; }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += kOrderThreads) {
-            const uint32_t d = (ka[i] >> shift) & 255u;
-            const uint32_t pos = s_dstart[d] + wh[(i / seg) * 256 + d] + rank[i];
-            kb[pos] = ka[i];
-            vb[pos] = va[i];
-        }
-        __syncthreads();
-        uint32_t *t = ka; ka = kb; kb = t;
-        t = va; va = vb; vb = t;
     }
-    for (int i = threadIdx.x; i < n; i += kOrderThreads) order[i] = (int32_t)va[i];
+    __syncthreads();
+    const int base = 32 * blockIdx.x;
+    const int i = base + l;
+    const uint32_t mi = i < n ? s_key[i] : 0u;
+    // warp w: j in [j0, j1), bounds multiples of 4 (padded keys); j < base
+    // counts keys <= mi, j >= base + 32 keys < mi, the CTA's own 32 the full rule
+    const int per = ((n4 / 4 + kRankWarps - 1) / kRankWarps) * 4;
+    const int j0 = min(n4, w * per), j1 = min(n4, j0 + per);
+    uint32_t c = 0;
+    const int a0 = j0, a1 = max(j0, min(j1, base));                  // before the CTA's tiles
+    const int b0 = max(j0, min(j1, base + 32));                      // after them
+    for (int j = a0; j < a1; j += 4) {                               // a0, a1 multiples of 4 (base is)
+        const uint4 k4 = *reinterpret_cast<const uint4 *>(s_key + j);
+        c += (k4.x <= mi) + (k4.y <= mi) + (k4.z <= mi) + (k4.w <= mi);
+    }
+    for (int j = a1; j < b0; ++j) {
+        const uint32_t kj = s_key[j];
+        c += (kj < mi) || (kj == mi && j < i);
+    }
+    for (int j = b0; j < j1; j += 4) {                               // b0 a multiple of 4
+        const uint4 k4 = *reinterpret_cast<const uint4 *>(s_key + j);
+        c += (k4.x < mi) + (k4.y < mi) + (k4.z < mi) + (k4.w < mi);
+    }
+    s_cnt[w][l] = c;
+    __syncthreads();
+    if (w == 0 && i < n) {
+        uint32_t r = 0;
+#pragma unroll
+        for (int q = 0; q < kRankWarps; ++q) r += s_cnt[q][l];
+        // the padding keys (j >= n > i) are never below mi and never before
+        // the CTA's tiles, so they count for no tile
+        order[r] = (int32_t)i;
+    }
 }
 
 // Seeded pair of tiles k of a judge round (counter-based: a 32-bit mix of the
@@ -544,9 +519,8 @@ extern "C" int gs_sched_order(const float *d_cost, int n, int32_t *d_order, void
     if (n == 0) return GS_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (n <= kSmallOrder) {
-        const size_t smem = sizeof(uint32_t) * (5 * (size_t)kSmallOrder + 32 * 256);
-        allow_dynamic_smem((const void *)k_order_small, smem);
-        { k_order_small<<<1, kOrderThreads, smem, st>>>(d_cost, n, d_order); count_launches(1); }
+        const size_t smem = sizeof(uint32_t) * (size_t)((n + 3) & ~3);
+        { k_order_rank<<<cdiv(n, 32), 32 * kRankWarps, smem, st>>>(d_cost, n, d_order); count_launches(1); }
         return launch_status();
     }
     char *ws = reinterpret_cast<char *>(d_workspace);

@@ -80,10 +80,14 @@ def test_mlp_predict_and_grad_match_oracle():
     assert np.allclose(g.cpu().numpy(), gr, rtol=1e-3, atol=1e-4 * np.abs(gr).max())
 
 
-def test_order_is_a_stable_descending_permutation():
-    rng = np.random.default_rng(5)
-    n = 5000
+@pytest.mark.parametrize("n", [1, 31, 33, 100, 5000, 8192, 8193, 20000])
+def test_order_is_a_stable_descending_permutation(n):
+    # n <= 8192: direct ranking in one launch; above: the radix sort
+    rng = np.random.default_rng(5 + n)
     cost = rng.integers(0, 50, n).astype(np.float32) - 20.0     # ties and negatives
+    cost[rng.integers(0, n, max(1, n // 50))] = rng.normal(0, 1e30, max(1, n // 50)).astype(np.float32)
+    if n > 40:
+        cost[:3] = (np.inf, -np.inf, 3.5)
     c = torch.from_numpy(cost).cuda()
     order = torch.empty(n, dtype=torch.int32, device="cuda")
     ws = torch.empty(L.gs_sched_order_workspace(n) // 4 + 64, device="cuda")
