@@ -41,12 +41,12 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # captured.
 MEASURED_TRAFFIC = {
     "project_bwd_adam": {
-        "bytes_per_gaussian": (0.843597 + 0.649045 + 1.872040 + 1.952119) * 1e9 / 3e6,
+        "bytes_per_gaussian": (0.840275968 + 0.535303424 + 1.872146944 + 1.953029376) * 1e9 / 3e6,
         "sources": {
             "paper_2510_14564_gb300/csrc/project.cu":
-                "e14e6ad10839e7a22e6dcf6326919d18f9c950c58a9907b898aaa7f6e1954adb",
+                "e5f197897e2bd32408cd9e3c8881c4c448f118aa24e1fbbbf7b66e34a40d00d3",
             "paper_2510_14564_gb300/csrc/gs_common.cuh":
-                "0030d55b8fab3ccb7ca6285c29977af8f502d986272319b6f97e525d5ed769b4",
+                "8f7d0bfb7a35c475775f8adef83c7e3b96d9a905d18100f831e0c9437a2b9690",
         },
     },
 }
@@ -189,7 +189,7 @@ RENDER_BWD_INSTR = {
     "warp_instr_per_pair": 339131212 / 306789136,
     "sources": {
         "paper_2510_14564_gb300/csrc/render.cu": "be4556c130316a28575e6988cf1c5c579890a1d5b8ead5151de229e243080117",
-        "paper_2510_14564_gb300/csrc/gs_common.cuh": "0030d55b8fab3ccb7ca6285c29977af8f502d986272319b6f97e525d5ed769b4",
+        "paper_2510_14564_gb300/csrc/gs_common.cuh": "8f7d0bfb7a35c475775f8adef83c7e3b96d9a905d18100f831e0c9437a2b9690",
     },
 }
 

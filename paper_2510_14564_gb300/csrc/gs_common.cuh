@@ -189,14 +189,30 @@ __device__ __forceinline__ unsigned warp_peers(uint32_t d, int bits) {
     return peers;
 }
 
+// sqrt(x) and 1/x on the SM's special-function unit (PTX sqrt.approx and
+// rcp.approx, flush-to-zero; a few ulp of relative error), where a result
+// only feeds an optimiser step or a gradient.
+__device__ __forceinline__ float sqrt_mufu(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_mufu(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // One Adam step (Kingma & Ba, Algorithm 1) on one entry, bias corrections
 // passed as 1/(1 - b1^t) and 1/(1 - b2^t); shared by every Adam kernel so the
-// fused and separate paths apply the same arithmetic.
+// fused and separate paths apply the same arithmetic.  The step's square
+// root and division run on the special-function unit (eps > 0 keeps the
+// denominator normal).
 __device__ __forceinline__ void adam_core(float &p, float g, float &m, float &v, float lr, float b1, float b2,
                                           float inv_c1, float inv_c2, float eps) {
     m = b1 * m + (1.0f - b1) * g;
     v = b2 * v + (1.0f - b2) * g * g;
-    p -= lr * (m * inv_c1) / (sqrtf(v * inv_c2) + eps);
+    p -= lr * (m * inv_c1) * rcp_mufu(sqrt_mufu(v * inv_c2) + eps);
 }
 
 // Warp helpers

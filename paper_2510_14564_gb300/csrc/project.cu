@@ -415,14 +415,78 @@ __global__ void __launch_bounds__(128) k_project(GeomBatch views, int N, const f
 // Reverse mode of the projection for one view, geometric part: chains the
 // 2D gradient g (u, v, A, B, C, opacity) to the mean, log-scales,
 // quaternion and opacity logit (accumulated into dmean, dls, dq, dlog).
+// The forward quantities the backward needs -- camera-space mean, rotation,
+// scales and the entries of Sigma' -- recomputed with contracted FP32
+// arithmetic and the special-function unit.  The backward is held to a
+// relative tolerance; only the forward's discrete path (tile keys and
+// counts) has to reproduce IEEE-rounded values.
+struct FwdQ {
+    float x, y, z, ca, cb, cc;
+    float Rq[9], s[3];
+    float w, qa, qb, qc, iq;                   // the unit quaternion and 1/|q|
+};
+
+__device__ __forceinline__ void fwd_quantities(const ViewGeom &cam, float mx, float my, float mz,
+                                               const float ls[3], const float q[4], FwdQ &o) {
+    const float *R = cam.R;
+    o.x = fmaf(R[0], mx, fmaf(R[1], my, fmaf(R[2], mz, cam.t[0])));
+    o.y = fmaf(R[3], mx, fmaf(R[4], my, fmaf(R[5], mz, cam.t[1])));
+    o.z = fmaf(R[6], mx, fmaf(R[7], my, fmaf(R[8], mz, cam.t[2])));
+    o.iq = rsqrtf(fmaf(q[0], q[0], fmaf(q[1], q[1], fmaf(q[2], q[2], q[3] * q[3]))));
+    const float w = q[0] * o.iq, qa = q[1] * o.iq, qb = q[2] * o.iq, qc = q[3] * o.iq;
+    o.w = w; o.qa = qa; o.qb = qb; o.qc = qc;
+    float *Rq = o.Rq;
+    Rq[0] = 1.0f - 2.0f * (qb * qb + qc * qc);
+    Rq[1] = 2.0f * (qa * qb - w * qc);
+    Rq[2] = 2.0f * (qa * qc + w * qb);
+    Rq[3] = 2.0f * (qa * qb + w * qc);
+    Rq[4] = 1.0f - 2.0f * (qa * qa + qc * qc);
+    Rq[5] = 2.0f * (qb * qc - w * qa);
+    Rq[6] = 2.0f * (qa * qc - w * qb);
+    Rq[7] = 2.0f * (qb * qc + w * qa);
+    Rq[8] = 1.0f - 2.0f * (qa * qa + qb * qb);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o.s[k] = __expf(ls[k]);
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) M[3 * r + k] = Rq[3 * r + k] * o.s[k];
+    float S[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = r; c < 3; ++c) {
+            S[3 * r + c] = fmaf(M[3 * r], M[3 * c], fmaf(M[3 * r + 1], M[3 * c + 1], M[3 * r + 2] * M[3 * c + 2]));
+            S[3 * c + r] = S[3 * r + c];
+        }
+    const float iz = rcp_mufu(o.z);
+    const float j00 = cam.fx * iz, j11 = cam.fy * iz;
+    const float j02 = -cam.fx * o.x * iz * iz, j12 = -cam.fy * o.y * iz * iz;
+    float T[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T[k] = fmaf(j00, R[k], j02 * R[6 + k]);
+        T[3 + k] = fmaf(j11, R[3 + k], j12 * R[6 + k]);
+    }
+    float U[6];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            U[3 * r + k] = fmaf(T[3 * r], S[k], fmaf(T[3 * r + 1], S[3 + k], T[3 * r + 2] * S[6 + k]));
+    o.ca = fmaf(U[0], T[0], fmaf(U[1], T[1], U[2] * T[2])) + 0.3f;
+    o.cb = fmaf(U[0], T[3], fmaf(U[1], T[4], U[2] * T[5]));
+    o.cc = fmaf(U[3], T[3], fmaf(U[4], T[4], U[5] * T[5])) + 0.3f;
+}
+
 __device__ __forceinline__ void geom_bwd(const ViewGeom &cam, float mx, float my, float mz, const float ls[3],
                                          const float q[4], float lg, const float g[9], float dmean[3],
                                          float dls[3], float dq[4], float &dlog) {
     const float *R = cam.R;
     const float fx = cam.fx, fy = cam.fy;
-    // forward quantities (same values as k_project)
-    Discrete d;
-    discrete_path(cam, mx, my, mz, ls, q, d);
+    FwdQ d;
+    fwd_quantities(cam, mx, my, mz, ls, q, d);
     const float x = d.x, y = d.y, z = d.z;
     float M[9], Sg[9];
 #pragma unroll
@@ -434,7 +498,7 @@ __device__ __forceinline__ void geom_bwd(const ViewGeom &cam, float mx, float my
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc)
             Sg[3 * rr + cc] = M[3 * rr] * M[3 * cc] + M[3 * rr + 1] * M[3 * cc + 1] + M[3 * rr + 2] * M[3 * cc + 2];
-    float iz = 1.0f / z, iz2 = iz * iz;
+    float iz = rcp_mufu(z), iz2 = iz * iz;
     float J[6] = {fx * iz, 0.0f, -fx * x * iz2, 0.0f, fy * iz, -fy * y * iz2};
     float T[6];
 #pragma unroll
@@ -443,7 +507,7 @@ __device__ __forceinline__ void geom_bwd(const ViewGeom &cam, float mx, float my
         for (int kk = 0; kk < 3; ++kk)
             T[3 * rr + kk] = J[3 * rr] * R[kk] + J[3 * rr + 1] * R[3 + kk] + J[3 * rr + 2] * R[6 + kk];
     const float a = d.ca, b = d.cb, c = d.cc;
-    float D = a * c - b * b, iD = 1.0f / D, iD2 = iD * iD;
+    float D = a * c - b * b, iD = rcp_mufu(D), iD2 = iD * iD;
     // conic (A, B, C) = (c, -b, a) / D
     float gA = g[2], gB = g[3], gC = g[4];
     float ga_ = gA * (-c * c * iD2) + gB * (b * c * iD2) + gC * (iD - a * c * iD2);
@@ -502,9 +566,8 @@ __device__ __forceinline__ void geom_bwd(const ViewGeom &cam, float mx, float my
         dls[kk] += ds * d.s[kk];
     }
     // rotation from the unit quaternion
-    float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    float iq = 1.0f / qn;
-    float w = q[0] * iq, qx = q[1] * iq, qy = q[2] * iq, qz = q[3] * iq;
+    const float iq = d.iq;
+    const float w = d.w, qx = d.qa, qy = d.qb, qz = d.qc;
     float dqh[4];
     dqh[0] = 2.0f * (-qz * G[1] + qy * G[2] + qz * G[3] - qx * G[5] - qy * G[6] + qx * G[7]);
     dqh[1] = 2.0f * (qy * G[1] + qz * G[2] + qy * G[3] - 2.0f * qx * G[4] - w * G[5] + qz * G[6] + w * G[7] - 2.0f * qx * G[8]);
@@ -516,7 +579,7 @@ __device__ __forceinline__ void geom_bwd(const ViewGeom &cam, float mx, float my
     dq[2] += (dqh[2] - qy * dot) * iq;
     dq[3] += (dqh[3] - qz * dot) * iq;
     // opacity
-    float o = 1.0f / (1.0f + expf(-lg));
+    const float o = rcp_mufu(1.0f + __expf(-lg));
     dlog += g[5] * o * (1.0f - o);
 }
 
@@ -531,9 +594,8 @@ struct AdamArgs {
 
 __device__ __forceinline__ float adam_update(float *p, float *m, float *v, long long idx, float g, float lr,
                                              const AdamArgs &a) {
-    float mm = a.b1 * m[idx] + (1.0f - a.b1) * g;
-    float vv = a.b2 * v[idx] + (1.0f - a.b2) * g * g;
-    float pp = p[idx] - lr * (mm * a.inv_c1) / (sqrtf(vv * a.inv_c2) + a.eps);
+    float pp = p[idx], mm = m[idx], vv = v[idx];
+    adam_core(pp, g, mm, vv, lr, a.b1, a.b2, a.inv_c1, a.inv_c2, a.eps);
     m[idx] = mm;
     v[idx] = vv;
     p[idx] = pp;
@@ -671,9 +733,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(GeomBatch views, int N, con
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (!ok[u]) continue;
-                const float m1 = adam.b1 * mm[u] + (1.0f - adam.b1) * gv[u];
-                const float v1 = adam.b2 * vv[u] + (1.0f - adam.b2) * gv[u] * gv[u];
-                const float p1 = pp[u] - lrv[u] * (m1 * adam.inv_c1) / (sqrtf(v1 * adam.inv_c2) + adam.eps);
+                float p1 = pp[u], m1 = mm[u], v1 = vv[u];
+                adam_core(p1, gv[u], m1, v1, lrv[u], adam.b1, adam.b2, adam.inv_c1, adam.inv_c2, adam.eps);
                 adam.m[id[u]] = m1;
                 adam.v[id[u]] = v1;
                 adam.p[id[u]] = p1;
