@@ -433,11 +433,19 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
 }
 
 // Scratch of the onesweep depth sort of n keys (status words of four passes,
-// four digit histograms, four tile counters, the key range, and the count of
-// final-pass tiles done).
+// four digit histograms, four tile counters, the key range, the count of
+// final-pass tiles done) and of the single-pass scan that follows it.
 static size_t onesweep_scratch_bytes(long long n) {
     const long long nb = (n + kSortTile - 1) / kSortTile;
-    return 4 * (size_t)(4 * kRadix * nb + 4 * kRadix + 4 + 2 + 1);
+    const size_t words = (size_t)(4 * kRadix * nb + 4 * kRadix + 4 + 2 + 1 + 1);   // even: the scan state is 8-B aligned
+    return 4 * words + 8 * (size_t)(nb + 1);
+}
+
+// The single-pass scan's state inside the onesweep scratch (zeroed with
+// it): one 64-bit status word per 4096-item tile and the tile counter.
+static unsigned long long *onesweep_scan_state(uint32_t *hist, long long n) {
+    const long long nb = (n + kSortTile - 1) / kSortTile;
+    return reinterpret_cast<unsigned long long *>(hist + 4 * kRadix * nb + 4 * kRadix + 4 + 2 + 1 + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -605,6 +613,152 @@ static void exclusive_scan(const Tin *in, Tout *out, long long n, Tout *partials
     { k_scan_apply<Tin, Tout><<<nbk, kScanThreads, 0, st>>>(in, n, partials, out); count_launches(1); }
 }
 
+// Exclusive scan of n 32-bit counts into 64-bit offsets in one pass
+// (decoupled look-back): each 4096-item tile, numbered in the order the
+// tiles start, publishes its sum, then warp 0 reads the status words of the
+// 32 tiles before it at once, adds the sums back to the nearest tile that
+// has published its inclusive prefix, and publishes its own.  status
+// [ceil(n/4096)] and *counter are zeroed by the caller; out[n] = the total.
+// A look-back that runs out of rounds (wait_limit) reports GS_EW_TIMEOUT and
+// goes on with the sums it has: the offsets are then wrong but monotone.
+constexpr unsigned long long kScanAgg = 1ull << 62, kScanPre = 2ull << 62;
+constexpr unsigned long long kScanVal = (1ull << 62) - 1ull;
+__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__global__ void __launch_bounds__(kScanThreads) k_scan_lookback(const uint32_t *__restrict__ in, long long n,
+                                                                unsigned long long *__restrict__ out,
+                                                                unsigned long long *status, uint32_t *counter,
+                                                                long long wait_limit, int *err_word) {
+    __shared__ unsigned long long s_w[kScanThreads / 32];
+    __shared__ unsigned long long s_excl;
+    __shared__ uint32_t s_bid;
+    if (threadIdx.x == 0) s_bid = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t bid = s_bid;
+    const long long i0 = (long long)bid * kScanChunk + (long long)threadIdx.x * kScanItems;
+    uint32_t vin[kScanItems];
+    load_items<uint32_t>(in, i0, n, vin);
+    unsigned long long loc[kScanItems], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        loc[k] = vin[k];
+        sum += loc[k];
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned long long inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += t;
+    }
+    if (l == 31) s_w[w] = inc;
+    __syncthreads();
+    unsigned long long off = 0, tile_sum = 0;
+#pragma unroll
+    for (int ww = 0; ww < kScanThreads / 32; ++ww) {
+        off += (ww < w) ? s_w[ww] : 0ull;
+        tile_sum += s_w[ww];
+    }
+    if (w == 0) {
+        unsigned long long *my = status + bid;
+        if (l == 0) st_relaxed64(my, (bid == 0 ? kScanPre : kScanAgg) | tile_sum);
+        unsigned long long excl = 0;
+        if (bid > 0) {
+            long long j = (long long)bid - 1, rounds = 0;
+            while (true) {
+                if (++rounds > wait_limit) { if (l == 0) set_err(err_word, GS_EW_TIMEOUT); break; }
+                const long long idx = j - l;
+                const unsigned long long v = idx >= 0 ? ld_relaxed64(status + idx) : kScanPre;
+                const unsigned long long f = v & ~kScanVal;
+                const unsigned pre = __ballot_sync(0xffffffffu, f == kScanPre);
+                const unsigned none = __ballot_sync(0xffffffffu, f == 0ull);
+                // lanes up to the nearest prefix (or all 32) must all have published
+                const unsigned upto = pre ? (pre & (~pre + 1u)) * 2u - 1u : 0xffffffffu;
+                if (none & upto) continue;                        // a tile in the window is not ready yet
+                unsigned long long add = (upto >> l) & 1u ? (v & kScanVal) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+                excl += add;
+                if (pre) break;
+                j -= 32;
+            }
+            if (l == 0) st_relaxed64(my, kScanPre | (excl + tile_sum));
+        }
+        if (l == 0) {
+            s_excl = excl;
+            if ((long long)(bid + 1) * kScanChunk >= n) out[n] = excl + tile_sum;   // the last tile: the total
+        }
+    }
+    __syncthreads();
+    unsigned long long run = s_excl + off + inc - sum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const unsigned long long c = loc[k];
+        loc[k] = run;
+        run += c;
+    }
+    store_items<unsigned long long>(out, i0, n, loc);
+}
+
+// The kept counts of T tiles in one CTA: exclusive offsets tstart[0..T)
+// with the total at tstart[T], the instance count and its capacity check
+// (*n_inst = total; more than cap sets GS_EW_CAPACITY and *count = cap, else
+// *count = total), and each tile's range [tstart, tstart + kept) (0, 0 when
+// it keeps nothing).  Each thread owns a contiguous run of tiles.
+constexpr int kTileScanThreads = 1024;
+__global__ void __launch_bounds__(kTileScanThreads) k_tile_scan_finish(int T, const uint32_t *__restrict__ kept,
+                                                                       unsigned long long *__restrict__ tstart,
+                                                                       long long cap, long long *n_inst,
+                                                                       uint32_t *count, uint2 *__restrict__ ranges,
+                                                                       int *err_word) {
+    __shared__ unsigned long long s_w[kTileScanThreads / 32];
+    const int per = (T + kTileScanThreads - 1) / kTileScanThreads;
+    const int b = threadIdx.x * per;
+    unsigned long long sum = 0;
+    for (int k = 0; k < per; ++k)
+        if (b + k < T) sum += __ldg(kept + b + k);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned long long inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += t;
+    }
+    if (l == 31) s_w[w] = inc;
+    __syncthreads();
+    unsigned long long run = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < kTileScanThreads / 32; ++q) {
+        run += q < w ? s_w[q] : 0ull;
+        total += s_w[q];
+    }
+    run += inc - sum;
+    for (int k = 0; k < per; ++k) {
+        const int t = b + k;
+        if (t >= T) break;
+        const uint32_t c = __ldg(kept + t);
+        tstart[t] = run;
+        ranges[t] = c > 0 ? make_uint2((uint32_t)run, (uint32_t)run + c) : make_uint2(0u, 0u);
+        run += c;
+    }
+    if (threadIdx.x == 0) {
+        tstart[T] = total;
+        if (n_inst) *n_inst = (long long)total;
+        if ((long long)total > cap) {
+            set_err(err_word, GS_EW_CAPACITY);
+            *count = (uint32_t)cap;
+        } else {
+            *count = (uint32_t)total;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Binning kernels
 // ---------------------------------------------------------------------------
@@ -612,8 +766,8 @@ static void exclusive_scan(const Tin *in, Tout *out, long long n, Tout *partials
 // value buffers of the sort's ping-pong, so that every value buffer holds
 // record indices only, whatever a sort cut short by a timeout leaves there.
 // With range != NULL also range[0] = ~(smallest visible key) and range[1] =
-// the largest (both zeroed by the caller): reduced per CTA, one atomic per
-// CTA and word.  Four records per thread, with 16-byte accesses where the
+// the largest (both zeroed by the caller): reduced per CTA; a CTA whose
+// extreme does not beat the running one (read first) makes no atomic.  Four records per thread, with 16-byte accesses where the
 // four are whole and aligned.
 __global__ void __launch_bounds__(256) k_depth_keys(const float *__restrict__ depth, const int *__restrict__ touched,
                                                     long long n, uint32_t *__restrict__ keys,
@@ -1785,15 +1939,6 @@ __global__ void __launch_bounds__(32 * kColWarps) k_pre_colscan(TileBatch tb, in
     }
 }
 
-__global__ void k_pre_ranges(int T, const uint32_t *__restrict__ kept,
-                             const unsigned long long *__restrict__ tstart, uint2 *__restrict__ ranges) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    const uint32_t c = kept[t];
-    const uint32_t s0 = (uint32_t)tstart[t];
-    ranges[t] = c > 0 ? make_uint2(s0, s0 + c) : make_uint2(0u, 0u);
-}
-
 // Place the kept instances: one CTA of 16 warps per chunk, per-tile cursors in
 // shared memory (a skip mark for tiles that keep no entry of this chunk) and a
 // summed-area table of the tiles still active in this chunk.  The CTA reads
@@ -2128,7 +2273,15 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, d_err_word, st,
                                         cnt, reinterpret_cast<const short4 *>(d_rect), rs,
                                         (uint32_t *)(ws + p.vfin));
-    exclusive_scan<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, offs + VN, st);
+    if (VN < (long long)kLbVal) {                       // the onesweep ran: its scratch holds the scan state
+        unsigned long long *sst = onesweep_scan_state(hist, VN);
+        const long long nbs = (VN + kScanChunk - 1) / kScanChunk;
+        { k_scan_lookback<<<(int)nbs, kScanThreads, 0, st>>>(cnt, VN, offs, sst,
+                                                            reinterpret_cast<uint32_t *>(sst + nbs),
+                                                            g_wait_limit.load(), d_err_word); count_launches(1); }
+    } else {
+        exclusive_scan<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, offs + VN, st);
+    }
     size_t gmax = 0;
     for (int v = 0; v < n_views; ++v) {
         size_t g = 2 * sizeof(int) * (size_t)(tb.v[v].TX + 1) * (tb.v[v].TY + 1);
@@ -2158,9 +2311,9 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
                                                        max_last);
         count_launches(1);
     }
-    exclusive_scan<uint32_t, unsigned long long>(kept, tstart, T, (unsigned long long *)part, tstart + T, st);
-    { k_finish_count<<<1, 1, 0, st>>>(tstart + T, capacity, d_n_instances, count, d_err_word); count_launches(1); }
-    { k_pre_ranges<<<cdiv(T, 256), 256, 0, st>>>(T, kept, tstart, reinterpret_cast<uint2 *>(d_tile_ranges)); count_launches(1); }
+    { k_tile_scan_finish<<<1, kTileScanThreads, 0, st>>>(T, kept, tstart, capacity, d_n_instances, count,
+                                                          reinterpret_cast<uint2 *>(d_tile_ranges), d_err_word);
+      count_launches(1); }
     if (d_tile_count) cudaMemcpyAsync(d_tile_count, full, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToDevice, st);
     if (capacity > 0) {
         size_t gmax1 = 0;

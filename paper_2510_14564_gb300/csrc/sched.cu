@@ -331,22 +331,26 @@ __global__ void __launch_bounds__(32 * kRankWarps) k_order_rank(const float *__r
     // counts keys <= mi, j >= base + 32 keys < mi, the CTA's own 32 the full rule
     const int per = ((n4 / 4 + kRankWarps - 1) / kRankWarps) * 4;
     const int j0 = min(n4, w * per), j1 = min(n4, j0 + per);
-    uint32_t c = 0;
+    // four independent counts (one per vector component) and four vector
+    // loads in flight per round: the loop is bound by issue, not latency
+    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
     const int a0 = j0, a1 = max(j0, min(j1, base));                  // before the CTA's tiles
     const int b0 = max(j0, min(j1, base + 32));                      // after them
+#pragma unroll 4
     for (int j = a0; j < a1; j += 4) {                               // a0, a1 multiples of 4 (base is)
         const uint4 k4 = *reinterpret_cast<const uint4 *>(s_key + j);
-        c += (k4.x <= mi) + (k4.y <= mi) + (k4.z <= mi) + (k4.w <= mi);
+        c0 += k4.x <= mi; c1 += k4.y <= mi; c2 += k4.z <= mi; c3 += k4.w <= mi;
     }
     for (int j = a1; j < b0; ++j) {
         const uint32_t kj = s_key[j];
-        c += (kj < mi) || (kj == mi && j < i);
+        c0 += (kj < mi) || (kj == mi && j < i);
     }
+#pragma unroll 4
     for (int j = b0; j < j1; j += 4) {                               // b0 a multiple of 4
         const uint4 k4 = *reinterpret_cast<const uint4 *>(s_key + j);
-        c += (k4.x < mi) + (k4.y < mi) + (k4.z < mi) + (k4.w < mi);
+        c0 += k4.x < mi; c1 += k4.y < mi; c2 += k4.z < mi; c3 += k4.w < mi;
     }
-    s_cnt[w][l] = c;
+    s_cnt[w][l] = c0 + c1 + c2 + c3;
     __syncthreads();
     if (w == 0 && i < n) {
         uint32_t r = 0;
