@@ -238,6 +238,8 @@ def run_ours(args):
     tgt_host = torch.from_numpy(np.concatenate([S.random_image(c.W, c.H, seed=1 + v).ravel()
                                                 for v, c in enumerate(cams)])).pin_memory()
     tgt = tgt_host.cuda()
+    tgt_bufs = [torch.empty_like(tgt), torch.empty_like(tgt)]      # the e2e steps' targets, in turn
+    cs = torch.cuda.Stream()                                        # their host-to-device copies
     flat0 = torch.from_numpy(scene.flat())
 
     # Learning rates scaled by --lr-scale: every step runs the full Adam update
@@ -275,11 +277,27 @@ def run_ours(args):
         if profile:                     # a profiler started with --profile-from-start off sees only this
             torch.cuda.profiler.start()
         t0.record(st)
-        for _ in range(steps):
+        if e2e:
+            # each step's targets come from pinned host memory on a copy
+            # stream (two device buffers in turn), overlapping the step's
+            # projection, binning and forward; the L1 waits for its copy
+            cs.wait_event(t0)
+            freed = [None, None]
+        for k in range(steps):
+            ready = None
             if e2e:
-                tgt.copy_(tgt_host, non_blocking=True)
-            tr.step(mark=mark if stage_times is not None else None, adam=adam)
+                buf = tgt_bufs[k % 2]
+                if freed[k % 2] is not None:
+                    cs.wait_event(freed[k % 2])
+                with torch.cuda.stream(cs):
+                    buf.copy_(tgt_host, non_blocking=True)
+                ready = torch.cuda.Event()
+                ready.record(cs)
+            tr.step(mark=mark if stage_times is not None else None, adam=adam,
+                    targets=buf if e2e else None, targets_ready=ready)
             if e2e:
+                freed[k % 2] = torch.cuda.Event()
+                freed[k % 2].record(st)
                 loss_host.copy_(tr.frame.loss, non_blocking=True)
         t1.record(st)
         torch.cuda.synchronize()
@@ -764,8 +782,9 @@ def run_colour_merge(args):
         if prefix:                     # a step's history: prefixes cut at twice the processed counts
             fr.render()
             fr.bin_sort()
+        tile_nproc = torch.empty(fr.T, dtype=torch.int32, device="cuda")    # leaves the history alone
         exact = lambda: L.gs_render_fwd(fr.cams, fr.ranges, fr.vals, fr.splats, fr.rgb_dtype, None, fr.img,
-                                        fr.T_final, fr.n_proc, None, None, fr.err)
+                                        fr.T_final, fr.n_proc, tile_nproc, None, fr.err)
         ms_exact = timed(exact)
         img_exact = fr.img.clone()
         ms_merged = timed(fr.render_merged)

@@ -227,6 +227,14 @@ class Frame:
         # event): an instance-capacity overflow raises, never passes silently
         self.err_host = torch.zeros(1, dtype=torch.int32).pin_memory()
         self.err_event = None
+        # a second stream for work off the critical path of a training step
+        # (zeroing the 2D gradients during the binning, the reverse pass's
+        # order during the L1, the cost MLP's training during the fused
+        # backward), joined back by events
+        self.side = None
+        self.ev_zeroed = None        # the 2D gradients zeroed on the side stream
+        self.bwd_prep = None         # (timing, schedule, event): the reverse pass's order, prepared
+        self.ev_mlp = None           # the cost MLP's training step queued on the side stream
 
     # -- buffers -----------------------------------------------------------
     def _alloc_gaussians(self, N: int) -> None:
@@ -371,6 +379,9 @@ class Frame:
         measure the reverse pass's tile times (self.tile_ns_b)."""
         if self.sched.mode == "raster":
             return None
+        if self.ev_mlp is not None:          # the cost MLP's training reads the buffers refilled below
+            torch.cuda.current_stream().wait_event(self.ev_mlp)
+            self.ev_mlp = None
         base = {"queue": self.queue, "split": self.split, "mode": L.GS_SCHED_ORDER}
         if timing:
             L.gs_zero(self.tile_ns_b)
@@ -391,6 +402,49 @@ class Frame:
         L.gs_int_cost(self.tile_nproc, self.T, self.cost)
         L.gs_sched_order(self.cost, self.T, self.order_b, self.order_ws)
         return dict(base, order=self.order_b)
+
+    # -- side stream ---------------------------------------------------------
+    def _fork(self):
+        """The side stream, ordered after everything queued so far on the
+        current stream."""
+        if self.side is None:
+            self.side = torch.cuda.Stream(device=self.dev)
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.current_stream())
+        self.side.wait_event(ev)
+        return self.side
+
+    @staticmethod
+    def _recorded(stream):
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        return ev
+
+    def zero_grad2d_async(self) -> None:
+        """Zero the 2D gradients on the side stream (after every reader queued
+        so far); render_bwd waits for it instead of zeroing itself."""
+        s = self._fork()
+        with torch.cuda.stream(s):
+            L.gs_zero(self.grad2d[:self.V * self.N * 12])
+        self.ev_zeroed = self._recorded(s)
+
+    def prepare_bwd_async(self, timing: bool = False) -> None:
+        """The reverse pass's order (features, cost MLP, order) on the side
+        stream, after the forward queued so far and overlapping what the
+        current stream does next (the L1); render_bwd with the same timing
+        waits for it and uses it."""
+        s = self._fork()
+        with torch.cuda.stream(s):
+            sched = self._sched_bwd(timing=timing)
+        self.bwd_prep = (timing, sched, self._recorded(s))
+
+    def train_scheduler_async(self) -> None:
+        """train_scheduler on the side stream, overlapping what the current
+        stream does next; the next reverse-pass order waits for it."""
+        s = self._fork()
+        with torch.cuda.stream(s):
+            self.train_scheduler()
+        self.ev_mlp = self._recorded(s)
 
     def render(self, timing: bool = False, mark=None) -> None:
         s = self._sched_fwd()
@@ -444,8 +498,18 @@ class Frame:
     def render_bwd(self, dimg: torch.Tensor, timing: bool = False, mark=None) -> None:
         """The reverse pass into self.grad2d (zeroed first) in the schedule's
         order; timing: also measure its per-tile times (self.tile_ns_b)."""
-        L.gs_zero(self.grad2d[:self.V * self.N * 12])
-        s = self._sched_bwd(timing=timing)
+        cur = torch.cuda.current_stream()
+        if self.ev_zeroed is not None:
+            cur.wait_event(self.ev_zeroed)
+            self.ev_zeroed = None
+        else:
+            L.gs_zero(self.grad2d[:self.V * self.N * 12])
+        if self.bwd_prep is not None and self.bwd_prep[0] == timing:
+            s = self.bwd_prep[1]
+            cur.wait_event(self.bwd_prep[2])
+        else:
+            s = self._sched_bwd(timing=timing)
+        self.bwd_prep = None
         if mark:
             mark("render_bwd")
         judged = self.sched.mode == "learned" and self.force_order is None
@@ -620,10 +684,14 @@ class Trainer:
         step every train_every-th iteration."""
         return self.step(mark=mark, targets=targets, adam=False)
 
-    def step(self, mark=None, targets: torch.Tensor | None = None, adam: bool = True) -> torch.Tensor:
+    def step(self, mark=None, targets: torch.Tensor | None = None, adam: bool = True,
+             targets_ready=None) -> torch.Tensor:
         """One training step (adam=False: without the parameter update, see
         iteration()).  `mark(name)`, if given, is called before each stage
-        (and with "end" after the last) so a caller can time stages."""
+        (and with "end" after the last) so a caller can time stages.
+        targets_ready: a CUDA event the L1 waits for (e.g. the end of the
+        targets' copy from the host on another stream, which then overlaps
+        the projection, binning and forward)."""
         mk = mark or (lambda name: None)
         f = self.frame
         pk = self.params_for_kernels()
@@ -631,14 +699,20 @@ class Trainer:
         train_now = timing and (f.step_count % max(1, f.sched.train_every) == 0)
         mk("project")
         f.project(pk)
+        f.zero_grad2d_async()                  # overlaps the binning (latency-bound, SM slots to spare)
         mk("bin_sort")
         f.bin_sort()
         mk("sched_fwd")
         f.render(timing=timing, mark=mark)
+        f.prepare_bwd_async(timing=train_now)  # overlaps the L1
         mk("l1")
+        if targets_ready is not None:
+            torch.cuda.current_stream().wait_event(targets_ready)
         f.l1(self.targets if targets is None else targets)
         mk("sched_bwd")
         f.render_bwd(f.dimg, timing=train_now, mark=mark)
+        if train_now:
+            f.train_scheduler_async()          # overlaps the fused backward
         if self.grad_norm is not None:
             mk("grad_stat")
             L.gs_grad2d_norm(len(f.cams), self.N, f.grad2d, self.grad_norm)
@@ -664,9 +738,6 @@ class Trainer:
             mk("adam")
             L.gs_adam_step(self.N, self.p, f.dparams, self.m, self.v, self.lr, ADAM_B1, ADAM_B2, ADAM_EPS,
                            self.t, self.sh_shadow, self.sh_storage)
-        if train_now:
-            mk("mlp_train")
-            f.train_scheduler()
         mk("end")
         f.step_count += 1
         return f.loss
