@@ -313,14 +313,19 @@ def run_ours(args):
         return ms, launches
 
     # plain FP32 path, tile order by instance count: the training step, then
-    # the fwd+bwd iteration (no Adam)
+    # the fwd+bwd iteration (no Adam).  Its steps follow the learned path's
+    # sequence (calibration + warm-up, timed steps, the end-to-end steps,
+    # the iterations), so that at real learning rates, where the scene
+    # changes from step to step, both paths are timed on the same steps of
+    # the same training run.
     plain = make("count", False)
-    for _ in range(args.warmup):
+    for _ in range(args.calib + args.warmup):
         plain.step()
-    plain_ms, _ = timed(plain, args.steps)
-    plain_ips = replica_throughput(args.steps, plain_ms, 1)
     plain_stages = {}
-    timed(plain, args.steps, stage_times=plain_stages)
+    plain_ms, _ = timed(plain, args.steps, stage_times=plain_stages)
+    plain_ips = replica_throughput(args.steps, plain_ms, 1)
+    for _ in range(args.steps):             # where the learned path runs its end-to-end steps
+        plain.step()
     for _ in range(3):
         plain.iteration()
     plain_it_ms, _ = timed(plain, args.steps, adam=False)

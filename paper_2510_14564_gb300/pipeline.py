@@ -74,34 +74,36 @@ class Schedule:
 
 
 class PassJudge:
-    """Chooses the tile order of one render pass between the learned cost
-    model's and the instance count's by measured duration: every `every`-th
-    pass runs the count order, the pass half-way between runs the learned
-    order, and the others the order with the lower mean duration (an
-    exponential average over its measured passes; the count order until both
-    have been measured).  Durations are CUDA events around the pass's
-    kernel, read back without waiting."""
+    """Chooses the tile order of one render pass between two by measured
+    duration: a candidate (by default the learned cost model's order) and a
+    fallback (by default the instance count's).  Every `every`-th pass runs
+    the fallback, the pass half-way between runs the candidate, and the
+    others the order with the lower mean duration (an exponential average
+    over its measured passes; the fallback until both have been measured).
+    Durations are CUDA events around the pass's kernel, read back without
+    waiting."""
 
-    def __init__(self, every: int = 8, weight: float = 0.25):
+    def __init__(self, every: int = 8, weight: float = 0.25, arms=("learned", "count")):
         self.every = max(2, int(every))
         self.weight = weight
-        self.mean = {"learned": None, "count": None}
-        self.passes = {"learned": 0, "count": 0}
+        self.cand, self.fallback = arms
+        self.mean = {self.cand: None, self.fallback: None}
+        self.passes = {self.cand: 0, self.fallback: 0}
         self.pending = []
         self.k = 0
 
     def winner(self) -> str:
-        l, c = self.mean["learned"], self.mean["count"]
-        return "learned" if l is not None and c is not None and l < c else "count"
+        l, c = self.mean[self.cand], self.mean[self.fallback]
+        return self.cand if l is not None and c is not None and l < c else self.fallback
 
     def pick(self) -> str:
         self.poll()
         r = self.k % self.every
         self.k += 1
         if r == 0:
-            return "count"
+            return self.fallback
         if r == self.every // 2:
-            return "learned"
+            return self.cand
         return self.winner()
 
     def start(self, which: str):
@@ -222,6 +224,12 @@ class Frame:
         self.force_order = "learned" if self.sched.mode == "learned" and not self.sched.judge else None
         self.judge_b = PassJudge(self.sched.judge_every)
         self.pick_b = "count"
+        # the forward of the learned schedule: raster order (one CTA per tile),
+        # judged against the order of the previous step's processed counts,
+        # which the side stream computes while the step projects and bins
+        self.judge_f = PassJudge(self.sched.judge_every, arms=("processed", "raster"))
+        self.fwd_prep = None         # (pick, event): the forward's order, prepared
+        self.cost_f = torch.zeros(self.T, dtype=torch.float32, device=d)
         self.step_count = 0
         # the error word, read back each step without waiting (pinned copy +
         # event): an instance-capacity overflow raises, never passes silently
@@ -363,8 +371,14 @@ class Frame:
         L.gs_sched_order(self.cost, self.T, out, self.order_ws)
 
     def _sched_fwd(self):
-        """The forward's schedule: None (raster) for the raster and learned
-        schedules, the instance-count order for the plain one."""
+        """The forward's schedule: None (raster) for the raster schedule, the
+        instance-count order for the plain one; for the learned one raster,
+        or the order prepare_fwd_async made when its judge picked it."""
+        if self.sched.mode == "learned":
+            if self.fwd_prep is None or self.fwd_prep[0] != "processed":
+                return None
+            torch.cuda.current_stream().wait_event(self.fwd_prep[1])
+            return {"mode": L.GS_SCHED_ORDER, "order": self.order_f, "queue": self.queue}
         if self.sched.mode != "count":
             return None
         self._count_order(self.order_f)
@@ -438,6 +452,24 @@ class Frame:
             sched = self._sched_bwd(timing=timing)
         self.bwd_prep = (timing, sched, self._recorded(s))
 
+    def prepare_fwd_async(self) -> None:
+        """The learned schedule's forward order for this step: the judge
+        picks raster or the previous step's processed-count order, and the
+        latter is computed on the side stream (from the per-tile counts the
+        previous forward left), overlapping the projection and binning."""
+        if self.sched.mode != "learned" or self.force_order is not None:
+            self.fwd_prep = None
+            return
+        pick = self.judge_f.pick()
+        ev = None
+        if pick == "processed":
+            s = self._fork()
+            with torch.cuda.stream(s):
+                L.gs_int_cost(self.tile_nproc, self.T, self.cost_f)
+                L.gs_sched_order(self.cost_f, self.T, self.order_f, self.order_ws)
+            ev = self._recorded(s)
+        self.fwd_prep = (pick, ev)
+
     def train_scheduler_async(self) -> None:
         """train_scheduler on the side stream, overlapping what the current
         stream does next; the next reverse-pass order waits for it."""
@@ -452,14 +484,22 @@ class Frame:
             mark("render_fwd")
         tns = self.tile_ns if timing else None
         if not self.prefix:
+            tok = self.judge_f.start(self.fwd_prep[0]) if self.fwd_prep is not None else None
+            self.fwd_prep = None
             L.gs_render_fwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, s, self.img,
                             self.T_final, self.n_proc, self.tile_nproc, tns, self.err)
+            if tok:
+                self.judge_f.stop(tok)
             return
         # kept prefixes: check that no pixel ran past one, rebuild and re-render any that did
         L.gs_zero(self.flag_count)
+        tok = self.judge_f.start(self.fwd_prep[0]) if self.fwd_prep is not None else None
+        self.fwd_prep = None
         L.gs_render_fwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, s, self.img,
                         self.T_final, self.n_proc, self.tile_nproc, tns, self.err,
                         tile_count=self.tile_count, flag_tiles=self.flag_tiles, flag_count=self.flag_count)
+        if tok:
+            self.judge_f.stop(tok)
         L.gs_bin_sort_prefix_repair(self.cams, self.N, self.rect, self.touched, self.flag_tiles,
                                     self.flag_count, self.capacity, self.vals, self.ranges, self.n_inst,
                                     self.ws, self.err)
@@ -576,7 +616,7 @@ class Frame:
             return {"forward": self.sched.mode, "backward": self.sched.mode}
         if self.force_order is not None:
             return {"forward": "raster", "backward": self.force_order, "judged": False}
-        return {"forward": "raster", "backward": self.judge_b.report(), "judged": True}
+        return {"forward": self.judge_f.report(), "backward": self.judge_b.report(), "judged": True}
 
     def check_errors(self) -> int:
         return int(self.err.item())
@@ -697,6 +737,7 @@ class Trainer:
         pk = self.params_for_kernels()
         timing = f.sched.mode == "learned"
         train_now = timing and (f.step_count % max(1, f.sched.train_every) == 0)
+        f.prepare_fwd_async()                  # the forward's order, if judged, overlaps the projection
         mk("project")
         f.project(pk)
         f.zero_grad2d_async()                  # overlaps the binning (latency-bound, SM slots to spare)

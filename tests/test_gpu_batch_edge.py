@@ -214,6 +214,45 @@ def test_depth_sort_wait_limit_sets_error_and_returns():
         L.gs_set_wait_limit(-1)
 
 
+def test_prefix_binning_wait_limit_leaves_valid_lists():
+    """The kept-prefix binning has two bounded look-backs (the depth sort's
+    and the single-pass scan of the records' tile counts).  At limit 0 both
+    give up: GS_EW_TIMEOUT is set, the final sort pass rewrites its outputs
+    as an identity, and the lists left hold record indices only, inside
+    their ranges.  With the default limit the same call is exact again."""
+    scene = S.uniform_scene(20_000, 3)           # five 4096-record tiles in the sort and the scan
+    cam = S.front_camera(256, 256)
+    params = P.to_device_params(scene)
+    views = dict(P.param_views(params, scene.n))
+    fr = P.Frame([cam], scene.n, prefix=True)
+    fr.project(views)
+    fr.bin_sort()
+    fr.render()                                  # the history the kept prefixes are cut by
+    fr.bin_sort()
+    torch.cuda.synchronize()
+    assert fr.check_errors() == 0
+    I = int(fr.n_inst.item())
+    want_vals, want_ranges = fr.vals[:I].clone(), fr.ranges.clone()
+    try:
+        L.gs_set_wait_limit(0)
+        fr.err.zero_()
+        fr.bin_sort()
+        torch.cuda.synchronize()
+        assert fr.check_errors() & L.GS_EW_TIMEOUT
+        n = min(int(fr.n_inst.item()), fr.capacity)
+        got = fr.vals[:n]
+        assert n == 0 or (int(got.min()) >= 0 and int(got.max()) < scene.n)
+        r = fr.ranges.view(-1, 2).long()
+        assert bool((r[:, 0] <= r[:, 1]).all()) and int(r[:, 1].max()) <= n
+    finally:
+        L.gs_set_wait_limit(1 << 20)
+    fr.err.zero_()
+    fr.bin_sort()
+    torch.cuda.synchronize()
+    assert fr.check_errors() == 0
+    assert torch.equal(fr.ranges, want_ranges) and torch.equal(fr.vals[:I], want_vals)
+
+
 def test_argument_errors_are_reported():
     cam = S.front_camera(64, 64)
     fr = P.Frame([cam], 8)
