@@ -188,7 +188,7 @@ def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1) -> dict:
 RENDER_BWD_INSTR = {
     "warp_instr_per_pair": 339131212 / 306789136,
     "sources": {
-        "paper_2510_14564_gb300/csrc/render.cu": "be4556c130316a28575e6988cf1c5c579890a1d5b8ead5151de229e243080117",
+        "paper_2510_14564_gb300/csrc/render.cu": "db548d8484e4c08ba09f4f09652b36166792a331993a4a6b5523a6acf7395b17",
         "paper_2510_14564_gb300/csrc/gs_common.cuh": "8f7d0bfb7a35c475775f8adef83c7e3b96d9a905d18100f831e0c9437a2b9690",
     },
 }

@@ -112,10 +112,9 @@ int gs_zero(void *d_ptr, size_t n_bytes, gs_stream_t stream);
  * The depth sort inside gs_bin_sort, gs_bin_sort_noalloc and
  * gs_bin_sort_prefix is a onesweep radix sort: each 4096-key tile of a digit
  * pass reads the digit counts of earlier tiles from status words those tiles
- * publish (decoupled look-back); the scan of the records' tile counts in
- * gs_bin_sort_prefix does the same with its tiles' sums.  A tile makes at
- * most `reads` rounds of status-word reads (each round reads the words of a
- * few earlier tiles at once) per digit or scan; past that it gives up, sets
+ * publish (decoupled look-back).  A tile makes at most `reads` rounds of
+ * status-word reads (each round reads the words of four earlier tiles at
+ * once) per digit; past that it gives up, sets
  * GS_EW_TIMEOUT in *err_word and goes on with the counts it has.  The call then completes with an unspecified
  * instance order, but every buffer it leaves still holds record indices in
  * [0, V*N), and the counts the lists are placed by are taken from that same

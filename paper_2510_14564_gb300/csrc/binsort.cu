@@ -433,19 +433,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
 }
 
 // Scratch of the onesweep depth sort of n keys (status words of four passes,
-// four digit histograms, four tile counters, the key range, the count of
-// final-pass tiles done) and of the single-pass scan that follows it.
+// four digit histograms, four tile counters, the key range, and the count of
+// final-pass tiles done).
 static size_t onesweep_scratch_bytes(long long n) {
     const long long nb = (n + kSortTile - 1) / kSortTile;
-    const size_t words = (size_t)(4 * kRadix * nb + 4 * kRadix + 4 + 2 + 1 + 1);   // even: the scan state is 8-B aligned
-    return 4 * words + 8 * (size_t)(nb + 1);
-}
-
-// The single-pass scan's state inside the onesweep scratch (zeroed with
-// it): one 64-bit status word per 4096-item tile and the tile counter.
-static unsigned long long *onesweep_scan_state(uint32_t *hist, long long n) {
-    const long long nb = (n + kSortTile - 1) / kSortTile;
-    return reinterpret_cast<unsigned long long *>(hist + 4 * kRadix * nb + 4 * kRadix + 4 + 2 + 1 + 1);
+    return 4 * (size_t)(4 * kRadix * nb + 4 * kRadix + 4 + 2 + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -604,6 +596,74 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const Tin *__restri
     store_items<Tout>(out, i0, n, loc);
 }
 
+// The second half of a two-launch exclusive scan: each CTA adds up the
+// partial sums of the chunks before it itself (a few thousand at most, read
+// by the whole CTA from L2) instead of a third launch scanning them; the CTA
+// of the last chunk writes the total.
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply_sum(const Tin *__restrict__ in, long long n,
+                                                                 const Tout *__restrict__ partials,
+                                                                 Tout *__restrict__ out, Tout *__restrict__ total) {
+    __shared__ Tout s_w[kScanThreads / 32];
+    __shared__ Tout s_base;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    {
+        Tout b = 0;
+        for (int j = threadIdx.x; j < (int)blockIdx.x; j += kScanThreads) b += __ldg(partials + j);
+        b = warp_sum(b);
+        if (l == 0) s_w[w] = b;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Tout t = 0;
+#pragma unroll
+            for (int q = 0; q < kScanThreads / 32; ++q) t += s_w[q];
+            s_base = t;
+        }
+        __syncthreads();
+    }
+    const long long i0 = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+    Tin vin[kScanItems];
+    load_items<Tin>(in, i0, n, vin);
+    Tout loc[kScanItems];
+    Tout sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        loc[k] = (Tout)vin[k];
+        sum += loc[k];
+    }
+    Tout inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Tout t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += t;
+    }
+    if (l == 31) s_w[w] = inc;
+    __syncthreads();
+    Tout off = s_base, tile = 0;
+#pragma unroll
+    for (int ww = 0; ww < kScanThreads / 32; ++ww) {
+        off += (ww < w) ? s_w[ww] : (Tout)0;
+        tile += s_w[ww];
+    }
+    Tout run = off + inc - sum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const Tout c = loc[k];
+        loc[k] = run;
+        run += c;
+    }
+    store_items<Tout>(out, i0, n, loc);
+    if (total && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) *total = s_base + tile;
+}
+
+// Exclusive scan in two launches: chunk sums, then each chunk's offsets.
+template <typename Tin, typename Tout>
+static void exclusive_scan2(const Tin *in, Tout *out, long long n, Tout *partials, Tout *total, cudaStream_t st) {
+    const int nbk = cdiv(n, kScanChunk);
+    { k_scan_partials<Tin, Tout><<<nbk, kScanThreads, 0, st>>>(in, n, partials); count_launches(1); }
+    { k_scan_apply_sum<Tin, Tout><<<nbk, kScanThreads, 0, st>>>(in, n, partials, out, total); count_launches(1); }
+}
+
 template <typename Tin, typename Tout>
 static void exclusive_scan(const Tin *in, Tout *out, long long n, Tout *partials, Tout *total,
                            cudaStream_t st) {
@@ -611,99 +671,6 @@ static void exclusive_scan(const Tin *in, Tout *out, long long n, Tout *partials
     { k_scan_partials<Tin, Tout><<<nbk, kScanThreads, 0, st>>>(in, n, partials); count_launches(1); }
     { k_scan_top<Tout><<<1, 1024, 0, st>>>(partials, nbk, total); count_launches(1); }
     { k_scan_apply<Tin, Tout><<<nbk, kScanThreads, 0, st>>>(in, n, partials, out); count_launches(1); }
-}
-
-// Exclusive scan of n 32-bit counts into 64-bit offsets in one pass
-// (decoupled look-back): each 4096-item tile, numbered in the order the
-// tiles start, publishes its sum, then warp 0 reads the status words of the
-// 32 tiles before it at once, adds the sums back to the nearest tile that
-// has published its inclusive prefix, and publishes its own.  status
-// [ceil(n/4096)] and *counter are zeroed by the caller; out[n] = the total.
-// A look-back that runs out of rounds (wait_limit) reports GS_EW_TIMEOUT and
-// goes on with the sums it has: the offsets are then wrong but monotone.
-constexpr unsigned long long kScanAgg = 1ull << 62, kScanPre = 2ull << 62;
-constexpr unsigned long long kScanVal = (1ull << 62) - 1ull;
-__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__global__ void __launch_bounds__(kScanThreads) k_scan_lookback(const uint32_t *__restrict__ in, long long n,
-                                                                unsigned long long *__restrict__ out,
-                                                                unsigned long long *status, uint32_t *counter,
-                                                                long long wait_limit, int *err_word) {
-    __shared__ unsigned long long s_w[kScanThreads / 32];
-    __shared__ unsigned long long s_excl;
-    __shared__ uint32_t s_bid;
-    if (threadIdx.x == 0) s_bid = atomicAdd(counter, 1u);
-    __syncthreads();
-    const uint32_t bid = s_bid;
-    const long long i0 = (long long)bid * kScanChunk + (long long)threadIdx.x * kScanItems;
-    uint32_t vin[kScanItems];
-    load_items<uint32_t>(in, i0, n, vin);
-    unsigned long long loc[kScanItems], sum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        loc[k] = vin[k];
-        sum += loc[k];
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    unsigned long long inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (l >= o) inc += t;
-    }
-    if (l == 31) s_w[w] = inc;
-    __syncthreads();
-    unsigned long long off = 0, tile_sum = 0;
-#pragma unroll
-    for (int ww = 0; ww < kScanThreads / 32; ++ww) {
-        off += (ww < w) ? s_w[ww] : 0ull;
-        tile_sum += s_w[ww];
-    }
-    if (w == 0) {
-        unsigned long long *my = status + bid;
-        if (l == 0) st_relaxed64(my, (bid == 0 ? kScanPre : kScanAgg) | tile_sum);
-        unsigned long long excl = 0;
-        if (bid > 0) {
-            long long j = (long long)bid - 1, rounds = 0;
-            while (true) {
-                if (++rounds > wait_limit) { if (l == 0) set_err(err_word, GS_EW_TIMEOUT); break; }
-                const long long idx = j - l;
-                const unsigned long long v = idx >= 0 ? ld_relaxed64(status + idx) : kScanPre;
-                const unsigned long long f = v & ~kScanVal;
-                const unsigned pre = __ballot_sync(0xffffffffu, f == kScanPre);
-                const unsigned none = __ballot_sync(0xffffffffu, f == 0ull);
-                // lanes up to the nearest prefix (or all 32) must all have published
-                const unsigned upto = pre ? (pre & (~pre + 1u)) * 2u - 1u : 0xffffffffu;
-                if (none & upto) continue;                        // a tile in the window is not ready yet
-                unsigned long long add = (upto >> l) & 1u ? (v & kScanVal) : 0ull;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
-                excl += add;
-                if (pre) break;
-                j -= 32;
-            }
-            if (l == 0) st_relaxed64(my, kScanPre | (excl + tile_sum));
-        }
-        if (l == 0) {
-            s_excl = excl;
-            if ((long long)(bid + 1) * kScanChunk >= n) out[n] = excl + tile_sum;   // the last tile: the total
-        }
-    }
-    __syncthreads();
-    unsigned long long run = s_excl + off + inc - sum;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const unsigned long long c = loc[k];
-        loc[k] = run;
-        run += c;
-    }
-    store_items<unsigned long long>(out, i0, n, loc);
 }
 
 // The kept counts of T tiles in one CTA: exclusive offsets tstart[0..T)
@@ -2273,15 +2240,7 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     const uint32_t *order = depth_order(d_depth, d_touched, VN, N, n_views, dk0, dk1, dv0, dv1, hist, part, d_err_word, st,
                                         cnt, reinterpret_cast<const short4 *>(d_rect), rs,
                                         (uint32_t *)(ws + p.vfin));
-    if (VN < (long long)kLbVal) {                       // the onesweep ran: its scratch holds the scan state
-        unsigned long long *sst = onesweep_scan_state(hist, VN);
-        const long long nbs = (VN + kScanChunk - 1) / kScanChunk;
-        { k_scan_lookback<<<(int)nbs, kScanThreads, 0, st>>>(cnt, VN, offs, sst,
-                                                            reinterpret_cast<uint32_t *>(sst + nbs),
-                                                            g_wait_limit.load(), d_err_word); count_launches(1); }
-    } else {
-        exclusive_scan<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, offs + VN, st);
-    }
+    exclusive_scan2<uint32_t, unsigned long long>(cnt, offs, VN, (unsigned long long *)part, offs + VN, st);
     size_t gmax = 0;
     for (int v = 0; v < n_views; ++v) {
         size_t g = 2 * sizeof(int) * (size_t)(tb.v[v].TX + 1) * (tb.v[v].TY + 1);

@@ -500,6 +500,7 @@ __global__ void __launch_bounds__(1024) k_split_head(const int *__restrict__ til
     __shared__ int s_cnt[32];
     __shared__ float s_total;
     float sum = 0;
+#pragma unroll 8
     for (int t = threadIdx.x; t < T; t += 1024) sum += split_cost(tile_nproc, log_cost, t);
     sum = warp_sum(sum);
     if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
@@ -512,6 +513,7 @@ __global__ void __launch_bounds__(1024) k_split_head(const int *__restrict__ til
     __syncthreads();
     const float per_cta = s_total / (float)max(1, n_cta);
     int cnt = 0;
+#pragma unroll 8
     for (int t = threadIdx.x; t < T; t += 1024) cnt += split_cost(tile_nproc, log_cost, t) > per_cta;
     cnt = warp_sum(cnt);
     if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = cnt;

@@ -141,14 +141,23 @@ __global__ void __launch_bounds__(256) k_bwd_features(TileBatch tb, const uint2 
     const int inx = min(kTile, vt.W - tx * kTile), iny = min(kTile, vt.H - ty * kTile);
     long long sum = 0;
     int mx0 = 0, mx1 = 0, active = 0;
-    for (int k = l; k < kTilePix; k += 32) {
-        const int px = k & (kTile - 1), py = k / kTile;
-        if (px < inx && py < iny) {
-            const int c = max(0, __ldg(n_proc + vt.pix_base + (long long)(ty * kTile + py) * vt.W + tx * kTile + px));
-            sum += c;
-            active += c > 0;
-            if (py < kTile / 2) mx0 = max(mx0, c); else mx1 = max(mx1, c);
-        }
+    // the tile's 256 counts, 8 per lane, every load issued before any use
+    constexpr int kPer = kTilePix / 32;
+    int cv[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int k = l + 32 * j, px = k & (kTile - 1), py = k / kTile;
+        cv[j] = (px < inx && py < iny)
+                    ? __ldg(n_proc + vt.pix_base + (long long)(ty * kTile + py) * vt.W + tx * kTile + px)
+                    : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int c = max(0, cv[j]);
+        const int py = (l + 32 * j) / kTile;
+        sum += c;
+        active += c > 0;
+        if (py < kTile / 2) mx0 = max(mx0, c); else mx1 = max(mx1, c);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

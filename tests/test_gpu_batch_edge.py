@@ -215,12 +215,12 @@ def test_depth_sort_wait_limit_sets_error_and_returns():
 
 
 def test_prefix_binning_wait_limit_leaves_valid_lists():
-    """The kept-prefix binning has two bounded look-backs (the depth sort's
-    and the single-pass scan of the records' tile counts).  At limit 0 both
-    give up: GS_EW_TIMEOUT is set, the final sort pass rewrites its outputs
-    as an identity, and the lists left hold record indices only, inside
-    their ranges.  With the default limit the same call is exact again."""
-    scene = S.uniform_scene(20_000, 3)           # five 4096-record tiles in the sort and the scan
+    """The kept-prefix binning's depth sort at look-back limit 0: every tile
+    but the first gives up, GS_EW_TIMEOUT is set, the final sort pass
+    rewrites its outputs as an identity, and the lists left hold record
+    indices only, inside their ranges.  With the default limit the same call
+    is exact again."""
+    scene = S.uniform_scene(20_000, 3)           # five 4096-record tiles per digit pass
     cam = S.front_camera(256, 256)
     params = P.to_device_params(scene)
     views = dict(P.param_views(params, scene.n))
