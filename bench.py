@@ -41,10 +41,10 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # captured.
 MEASURED_TRAFFIC = {
     "project_bwd_adam": {
-        "bytes_per_gaussian": (0.840275968 + 0.535303424 + 1.872146944 + 1.953029376) * 1e9 / 3e6,
+        "bytes_per_gaussian": (0.840355200 + 0.536993920 + 1.872078848 + 1.953295232) * 1e9 / 3e6,
         "sources": {
             "paper_2510_14564_gb300/csrc/project.cu":
-                "e5f197897e2bd32408cd9e3c8881c4c448f118aa24e1fbbbf7b66e34a40d00d3",
+                "55c9225b91d375a10d8d47bbc2aa26c016ef14bb73e3d956bb3583dad1207138",
             "paper_2510_14564_gb300/csrc/gs_common.cuh":
                 "8f7d0bfb7a35c475775f8adef83c7e3b96d9a905d18100f831e0c9437a2b9690",
         },

@@ -194,28 +194,6 @@ __device__ __forceinline__ void sh_eval_words(const uint32_t (&w)[NB][12], float
     }
 }
 
-// The SH gradient of one Gaussian, [16][3] as 12 float4: value (j, ch) is
-// w[ch] Y_j(u) (w = upstream colour gradient, zero on clamped channels).
-template <int Q>
-__device__ __forceinline__ void write_dsh(float4 *ps, float ux, float uy, float uz, const float w[3]) {
-    if constexpr (Q < 12) {
-        float v[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) v[e] = 0.0f;
-        auto term = [&](auto jc, int e, int ch) {
-            float Y, a, b, c;
-            sh_term<decltype(jc)::value>(ux, uy, uz, Y, a, b, c);
-            v[e] = w[ch] * Y;
-        };
-        term(std::integral_constant<int, (4 * Q + 0) / 3>{}, 0, (4 * Q + 0) % 3);
-        term(std::integral_constant<int, (4 * Q + 1) / 3>{}, 1, (4 * Q + 1) % 3);
-        term(std::integral_constant<int, (4 * Q + 2) / 3>{}, 2, (4 * Q + 2) % 3);
-        term(std::integral_constant<int, (4 * Q + 3) / 3>{}, 3, (4 * Q + 3) % 3);
-        ps[Q] = make_float4(v[0], v[1], v[2], v[3]);
-        write_dsh<Q + 1>(ps, ux, uy, uz, w);
-    }
-}
-
 // SH coefficients of one Gaussian as FP32 [16][3].
 template <int SDT>
 __device__ __forceinline__ void load_sh(const void *sh, long long i, float k[48]) {
@@ -761,50 +739,78 @@ __global__ void __launch_bounds__(128) k_project_bwd1(ViewGeom cam, int N, const
                                                       const int *__restrict__ touched,
                                                       const float *__restrict__ grad2d,
                                                       float *__restrict__ dparams) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    // the SH gradient (48 floats a Gaussian, the bulk of the output) leaves
+    // through shared memory: each warp stages its Gaussians' two factors,
+    // the basis values Y_j(u) and w_ch, and writes their 32 blocks of 192
+    // contiguous bytes with coalesced float4 stores
+    __shared__ float s_y[4][32 * 17];
+    __shared__ float s_w[4][32 * 3];
+    const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
     const long long n = N;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long wfirst = (long long)blockIdx.x * blockDim.x + 32 * wp;
+    if (wfirst >= n) return;                                        // uniform over the warp
     float *pm = dparams, *pls = dparams + 3 * n, *pq = dparams + 6 * n, *plg = dparams + 10 * n;
-    float4 *ps = reinterpret_cast<float4 *>(dparams + 11 * n) + 12 * i;
-    if (__ldg(touched + i) <= 0) {
+    float w[3] = {0.0f, 0.0f, 0.0f};
+    float ux = 0.0f, uy = 0.0f, uz = 1.0f;
+    if (i < n) {
+        float dmean[3] = {0, 0, 0}, dls[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dlog = 0.0f;
+        if (__ldg(touched + i) > 0) {
+            const float mx = __ldg(means + 3 * i), my = __ldg(means + 3 * i + 1), mz = __ldg(means + 3 * i + 2);
+            const float ls[3] = {__ldg(log_scales + 3 * i), __ldg(log_scales + 3 * i + 1),
+                                 __ldg(log_scales + 3 * i + 2)};
+            const float4 q4 = __ldg(reinterpret_cast<const float4 *>(quats) + i);
+            const float q[4] = {q4.x, q4.y, q4.z, q4.w};
+            const float lg = __ldg(logits + i);
+            const float4 *gp = reinterpret_cast<const float4 *>(grad2d + 12 * i);
+            const float4 ga = __ldg(gp), gb = __ldg(gp + 1), gc = __ldg(gp + 2);
+            const float g[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
+            geom_bwd(cam, mx, my, mz, ls, q, lg, g, dmean, dls, dq, dlog);
+            // colour: max(0, 0.5 + sum_j Y_j(u) k_j), u = (mu - campos) / |mu - campos|
+            const float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
+            const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+            ux = vx * inv; uy = vy * inv; uz = vz * inv;
+            float pre[3] = {0.5f, 0.5f, 0.5f};
+            float acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+            sh_stream<SDT>(sh, i, ux, uy, uz, pre, acc);
 #pragma unroll
-        for (int kk = 0; kk < 3; ++kk) { pm[3 * i + kk] = 0.0f; pls[3 * i + kk] = 0.0f; }
-        reinterpret_cast<float4 *>(pq)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        plg[i] = 0.0f;
+            for (int ch = 0; ch < 3; ++ch) w[ch] = pre[ch] > 0.0f ? g[6 + ch] : 0.0f;
+            float gd[3];
 #pragma unroll
-        for (int j = 0; j < 12; ++j) ps[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
+            for (int a = 0; a < 3; ++a) gd[a] = w[0] * acc[0][a] + w[1] * acc[1][a] + w[2] * acc[2][a];
+            const float gdd = gd[0] * ux + gd[1] * uy + gd[2] * uz;
+            dmean[0] += (gd[0] - ux * gdd) * inv;
+            dmean[1] += (gd[1] - uy * gdd) * inv;
+            dmean[2] += (gd[2] - uz * gdd) * inv;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) { pm[3 * i + kk] = dmean[kk]; pls[3 * i + kk] = dls[kk]; }
+        reinterpret_cast<float4 *>(pq)[i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+        plg[i] = dlog;
     }
-    const float mx = __ldg(means + 3 * i), my = __ldg(means + 3 * i + 1), mz = __ldg(means + 3 * i + 2);
-    const float ls[3] = {__ldg(log_scales + 3 * i), __ldg(log_scales + 3 * i + 1), __ldg(log_scales + 3 * i + 2)};
-    const float4 q4 = __ldg(reinterpret_cast<const float4 *>(quats) + i);
-    const float q[4] = {q4.x, q4.y, q4.z, q4.w};
-    const float lg = __ldg(logits + i);
-    const float4 *gp = reinterpret_cast<const float4 *>(grad2d + 12 * i);
-    const float4 ga = __ldg(gp), gb = __ldg(gp + 1), gc = __ldg(gp + 2);
-    const float g[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
-    float dmean[3] = {0, 0, 0}, dls[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dlog = 0.0f;
-    geom_bwd(cam, mx, my, mz, ls, q, lg, g, dmean, dls, dq, dlog);
-    // colour: max(0, 0.5 + sum_j Y_j(u) k_j), u = (mu - campos) / |mu - campos|
-    const float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
-    const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
-    const float ux = vx * inv, uy = vy * inv, uz = vz * inv;
-    float pre[3] = {0.5f, 0.5f, 0.5f};
-    float acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    sh_stream<SDT>(sh, i, ux, uy, uz, pre, acc);
-    const float w[3] = {pre[0] > 0.0f ? g[6] : 0.0f, pre[1] > 0.0f ? g[7] : 0.0f, pre[2] > 0.0f ? g[8] : 0.0f};
-    float gd[3];
+    {
+        float Y[16];
+        sh_basis(ux, uy, uz, Y);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) gd[a] = w[0] * acc[0][a] + w[1] * acc[1][a] + w[2] * acc[2][a];
-    const float gdd = gd[0] * ux + gd[1] * uy + gd[2] * uz;
-    dmean[0] += (gd[0] - ux * gdd) * inv;
-    dmean[1] += (gd[1] - uy * gdd) * inv;
-    dmean[2] += (gd[2] - uz * gdd) * inv;
+        for (int j = 0; j < 16; ++j) s_y[wp][17 * l + j] = Y[j];
+        s_w[wp][3 * l] = w[0]; s_w[wp][3 * l + 1] = w[1]; s_w[wp][3 * l + 2] = w[2];
+    }
+    __syncwarp();
+    const long long left = n - wfirst;
+    const int total4 = 12 * (int)(left < 32 ? left : 32);
+    float4 *G4 = reinterpret_cast<float4 *>(dparams) + ((11 * n + 48 * wfirst) >> 2);   // N % 4 == 0
+    const float *sy = s_y[wp], *sw = s_w[wp];
+    for (int qq = l; qq < total4; qq += 32) {
+        const int gl = qq / 12;
+        const int r = 4 * (qq - 12 * gl);                           // entries r..r+3, (j, ch) = divmod(e, 3)
+        float v[4];
 #pragma unroll
-    for (int kk = 0; kk < 3; ++kk) { pm[3 * i + kk] = dmean[kk]; pls[3 * i + kk] = dls[kk]; }
-    reinterpret_cast<float4 *>(pq)[i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
-    plg[i] = dlog;
-    write_dsh<0>(ps, ux, uy, uz, w);
+        for (int k = 0; k < 4; ++k) {
+            const int e = r + k, j = e / 3, ch = e - 3 * j;
+            v[k] = sw[3 * gl + ch] * sy[17 * gl + j];
+        }
+        G4[qq] = make_float4(v[0], v[1], v[2], v[3]);
+    }
 }
 
 // One view, fused with Adam, in two launches.  Part 1, one lane per
