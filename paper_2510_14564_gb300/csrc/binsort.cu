@@ -23,6 +23,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys per CTA
 constexpr int kRadix = 256;
+constexpr int kSortDigitsMax = 5;                      // four 8-bit depth digits, then (several views) the view
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -187,7 +188,8 @@ __device__ __forceinline__ int rect_area(short4 r) {
 // Range reduction and the global histograms of the four 8-bit digits of n
 // keys.  range[0] holds ~min and range[1] the max of the visible keys (raw
 // FP32 depth bits; 0xffffffff marks a culled record), as k_depth_keys left
-// them.  Each key is rewritten in place as its offset from the smallest
+// them (with view_n != 0 also the histogram of the view digit, view_n per
+// view).  Each key is rewritten in place as its offset from the smallest
 // visible key, culled records as the largest visible offset + 1: an
 // order-preserving map, so the stable sort is unchanged, whose top digits are
 // zero for every key when the depths span few binades (a digit pass in
@@ -195,8 +197,11 @@ __device__ __forceinline__ int rect_area(short4 r) {
 // zeroed by the caller.
 __global__ void __launch_bounds__(256) k_onesweep_hist(uint32_t *__restrict__ keys, uint32_t n,
                                                        const uint32_t *__restrict__ range,
-                                                       uint32_t *__restrict__ ghist) {
+                                                       uint32_t *__restrict__ ghist, int n_views,
+                                                       uint32_t view_n) {
     __shared__ uint32_t s_h[4 * kRadix];
+    // the fifth digit (several views): every view holds view_n records
+    if (view_n && blockIdx.x == 0 && (int)threadIdx.x < n_views) ghist[4 * kRadix + threadIdx.x] = view_n;
     for (int k = threadIdx.x; k < 4 * kRadix; k += 256) s_h[k] = 0;
     __syncthreads();
     const uint32_t kmin = ~__ldg(range), kmax = __ldg(range + 1);
@@ -227,12 +232,14 @@ __global__ void __launch_bounds__(256) k_onesweep_hist(uint32_t *__restrict__ ke
 // would be copies): it writes the sorted values to vfin instead of vout, and
 // the passes after it return at once.
 constexpr int kLbWindow = 4;                     // status words of earlier tiles read per look-back round
+template <bool VIEW>
 __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, uint32_t n, int pass, const uint32_t *__restrict__ ghist_all,
     uint32_t *status, uint32_t *tile_counter, long long wait_limit, int keys_needed,
     const int32_t *__restrict__ touched, uint32_t *__restrict__ cnt, const short4 *__restrict__ rect,
-    short4 *__restrict__ rs, uint32_t *__restrict__ vfin, uint32_t *done, int *err_word) {
+    short4 *__restrict__ rs, uint32_t *__restrict__ vfin, uint32_t *done, int npasses, uint32_t view_n,
+    int *err_word) {
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_wh[8][kRadix];
@@ -240,32 +247,46 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     __shared__ uint32_t s_goff[kRadix];
     __shared__ uint32_t s_warp[8], s_warp2[8];
     __shared__ uint32_t s_bid;
-    __shared__ int s_copy, s_const[4], s_last;
-    const int shift = 8 * pass;
+    __shared__ int s_copy, s_const[kSortDigitsMax], s_last;
+    // VIEW: the fifth pass, whose digit is the record's view, value / view_n
+    const int shift = VIEW ? 0 : 8 * pass;
     const uint32_t *ghist = ghist_all + kRadix * pass;
     if (threadIdx.x == 0) {
         s_bid = atomicAdd(tile_counter, 1u);
         s_copy = 0;
     }
-    if (threadIdx.x < 4) s_const[threadIdx.x] = 0;
+    if (threadIdx.x < kSortDigitsMax) s_const[threadIdx.x] = 0;
     for (int k = threadIdx.x; k < 8 * kRadix; k += kSortThreads) (&s_wh[0][0])[k] = 0;
     __syncthreads();
     if (__ldg(ghist + threadIdx.x) == n) s_copy = 1;       // one digit for every key
     if (vfin) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
+        for (int e = 0; e < npasses; ++e)
             if (__ldg(ghist_all + kRadix * e + threadIdx.x) == n) s_const[e] = 1;
     }
     __syncthreads();
     bool final_pass = touched != nullptr;
+    int keys_out = keys_needed;
     if (vfin) {
-        int F = 0;                                          // the last digit that varies
-#pragma unroll
-        for (int e = 1; e < 4; ++e)
+        // Passes over digits every key shares move nothing, so none runs:
+        // the data sits in buffer 0 or 1 by the parity of the passes before
+        // that moved it (both given as kin/vin and kout/vout), and the final
+        // pass -- the last whose digit varies -- writes the order to vfin.
+        int F = 0, moved = 0;
+        bool later_depth = false;
+        for (int e = 1; e < npasses; ++e)
             if (!s_const[e]) F = e;
+        for (int e = 0; e < pass; ++e) moved += !s_const[e];
+        for (int e = pass + 1; e < npasses && e < 4; ++e) later_depth = later_depth || !s_const[e];
         if (pass > F) return;                               // uniform over the CTA
         final_pass = pass == F;
+        if (!final_pass && s_copy) return;                  // this digit is one value: nothing moves
+        if (moved & 1) {
+            const uint32_t *tk = kin, *tv = vin;
+            kin = kout; vin = vout;
+            kout = const_cast<uint32_t *>(tk); vout = const_cast<uint32_t *>(tv);
+        }
         if (final_pass) vout = vfin;
+        keys_out = later_depth;                             // the keys only a later depth pass reads
     }
     const int32_t *gtouch = final_pass ? touched : nullptr;
     const uint32_t bid = s_bid;
@@ -287,7 +308,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
                 const long long i = i0 + u * kSortThreads;
                 if (i >= end) continue;
                 vout[i] = v[u];
-                if (keys_needed && !final_pass) kout[i] = __ldg(kin + i);
+                if (keys_out && !final_pass) kout[i] = __ldg(kin + i);
                 if (gtouch) {
                     if (rs) {                       // the count is the rectangle's area
                         rc[u] = __ldg(rect + v[u]);
@@ -316,8 +337,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     for (int it = 0; it < kSortItems; ++it) {
         const long long idx = base + it * 32 + l;
         const bool valid = idx < (long long)n;
-        key[it] = valid ? __ldg(kin + idx) : 0u;
         val[it] = valid ? __ldg(vin + idx) : 0u;
+        if constexpr (VIEW)
+            key[it] = valid ? val[it] / view_n : 0u;
+        else
+            key[it] = valid ? __ldg(kin + idx) : 0u;
     }
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
@@ -395,7 +419,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
         const uint32_t dq = (k >> shift) & 255u;
         const uint32_t g = s_goff[dq] + (uint32_t)(q - s_dstart[dq]);
         const uint32_t v = s_vals[q];
-        if (keys_needed && !final_pass) kout[g] = k;
+        if (keys_out && !final_pass) kout[g] = k;
         vout[g] = v;
         if (gtouch) {
             const short4 rc = rs ? __ldg(rect + v) : make_short4(0, 0, 0, 0);
@@ -432,12 +456,12 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     }
 }
 
-// Scratch of the onesweep depth sort of n keys (status words of four passes,
-// four digit histograms, four tile counters, the key range, and the count of
-// final-pass tiles done).
+// Scratch of the onesweep depth sort of n keys (status words of up to five
+// passes, their digit histograms and tile counters, the key range, and the
+// count of final-pass tiles done).
 static size_t onesweep_scratch_bytes(long long n) {
     const long long nb = (n + kSortTile - 1) / kSortTile;
-    return 4 * (size_t)(4 * kRadix * nb + 4 * kRadix + 4 + 2 + 1);
+    return 4 * (size_t)(kSortDigitsMax * kRadix * nb + kSortDigitsMax * kRadix + kSortDigitsMax + 2 + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -688,6 +712,7 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tile_scan_finish(int T, co
     const int per = (T + kTileScanThreads - 1) / kTileScanThreads;
     const int b = threadIdx.x * per;
     unsigned long long sum = 0;
+#pragma unroll 8
     for (int k = 0; k < per; ++k)
         if (b + k < T) sum += __ldg(kept + b + k);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -725,6 +750,31 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tile_scan_finish(int T, co
         }
     }
 }
+
+// The same finish for many tiles (several views), after a multi-CTA scan
+// left the offsets and the total (tstart[T]): one thread per tile.
+__global__ void __launch_bounds__(256) k_tile_ranges_finish(int T, const uint32_t *__restrict__ kept,
+                                                            const unsigned long long *__restrict__ tstart,
+                                                            long long cap, long long *n_inst, uint32_t *count,
+                                                            uint2 *__restrict__ ranges, int *err_word) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T) {
+        const uint32_t c = __ldg(kept + t);
+        const uint32_t s0 = (uint32_t)__ldg(tstart + t);
+        ranges[t] = c > 0 ? make_uint2(s0, s0 + c) : make_uint2(0u, 0u);
+    }
+    if (t == 0) {
+        const unsigned long long total = tstart[T];
+        if (n_inst) *n_inst = (long long)total;
+        if ((long long)total > cap) {
+            set_err(err_word, GS_EW_CAPACITY);
+            *count = (uint32_t)cap;
+        } else {
+            *count = (uint32_t)total;
+        }
+    }
+}
+constexpr int kTileScanOneCta = 16384;             // up to this many tiles, k_tile_scan_finish alone
 
 // ---------------------------------------------------------------------------
 // Binning kernels
@@ -1320,34 +1370,41 @@ static const uint32_t *depth_order(const float *d_depth, const int32_t *d_touche
                                    uint32_t *vfin = nullptr) {
     uint32_t *ka = dk0, *kb = dk1, *va = dv0, *vb = dv1;
     if (VN < (long long)kLbVal) {
-        // onesweep: status words of the four passes, the four histograms, the
-        // four tile counters and the key range, zeroed together
+        // onesweep: status words of the passes, the histograms, the tile
+        // counters and the key range, zeroed together
         const long long nb = (VN + kSortTile - 1) / kSortTile;
-        uint32_t *status = hist, *ghist = hist + 4 * kRadix * nb, *counters = ghist + 4 * kRadix;
-        uint32_t *range = counters + 4;
+        uint32_t *status = hist, *ghist = hist + kSortDigitsMax * kRadix * nb;
+        uint32_t *counters = ghist + kSortDigitsMax * kRadix;
+        uint32_t *range = counters + kSortDigitsMax, *done = range + 2;
+        // with vfin (and counts): passes over constant digits are skipped, the
+        // final pass -- the last varying digit, after the four depth digits
+        // the view for several views -- gathers each record's tile count and
+        // rectangle and leaves the order in vfin.  Without: one view with
+        // counts gathers in the fourth pass.
+        const bool early = vfin && cnt;
+        const bool gather1 = !early && n_views == 1 && cnt;
+        const int npasses = early && n_views > 1 ? 5 : 4;
+        const uint32_t view_n = npasses == 5 ? (uint32_t)N : 0u;
         cudaMemsetAsync(hist, 0, onesweep_scratch_bytes(VN), st);
         { k_depth_keys<<<cdiv(cdiv(VN, 4), 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0, dv1, range); count_launches(1); }
         if (VN > 0) {
             const int hb = (int)(VN / 4096 + 1 < 1024 ? VN / 4096 + 1 : 1024);
-            { k_onesweep_hist<<<hb, 256, 0, st>>>(ka, (uint32_t)VN, range, ghist); count_launches(1); }
-            // one view with counts: the final pass also gathers each record's
-            // tile count and rectangle; with vfin it is the last pass whose
-            // digit varies, and it leaves the order in vfin
-            const bool gather = n_views == 1 && cnt;
-            const bool early = gather && vfin;
-            for (int pass = 0; pass < 4; ++pass) {
-                const bool give = early || (gather && pass == 3);
-                { k_onesweep_pass<<<(int)nb, kSortThreads, 0, st>>>(ka, va, kb, vb, (uint32_t)VN, pass, ghist,
-                                                                   status + (size_t)kRadix * nb * pass, counters + pass,
-                                                                   g_wait_limit.load(), pass < 3 ? 1 : 0,
-                                                                   give ? d_touched : nullptr, cnt, rect, rs,
-                                                                   early ? vfin : nullptr, counters + 6, err_word);
+            { k_onesweep_hist<<<hb, 256, 0, st>>>(ka, (uint32_t)VN, range, ghist, n_views, view_n); count_launches(1); }
+            for (int pass = 0; pass < npasses; ++pass) {
+                const bool give = early || (gather1 && pass == 3);
+                auto *kern = pass == 4 ? k_onesweep_pass<true> : k_onesweep_pass<false>;
+                { kern<<<(int)nb, kSortThreads, 0, st>>>(ka, va, kb, vb, (uint32_t)VN, pass, ghist,
+                                                         status + (size_t)kRadix * nb * pass, counters + pass,
+                                                         g_wait_limit.load(), pass < 3 ? 1 : 0,
+                                                         give ? d_touched : nullptr, cnt, rect, rs,
+                                                         early ? vfin : nullptr, done, npasses, view_n, err_word);
                   count_launches(1); }
+                if (early) continue;                    // the kernels find their buffers by parity
                 uint32_t *t = ka; ka = kb; kb = t;
                 t = va; va = vb; vb = t;
             }
             if (early) return vfin;
-            if (gather) return va;
+            if (gather1) return va;
         }
     } else {
         { k_depth_keys<<<cdiv(cdiv(VN, 4), 256), 256, 0, st>>>(d_depth, d_touched, VN, dk0, dv0, dv1, nullptr); count_launches(1); }
@@ -1648,7 +1705,7 @@ __global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(TileBatch tb, in
                                                                 long long *__restrict__ bounds,
                                                                 uint32_t *__restrict__ max_last) {
     __shared__ long long s_part[kBoundThreads / 32];
-    if (blockIdx.x == 0 && threadIdx.x == 0) *max_last = 0u;   // k_pre_colscan raises it
+    if (blockIdx.x == 0 && threadIdx.x < tb.n) max_last[threadIdx.x] = 0u;   // k_pre_colscan raises them
     __shared__ double s_share[2];
     const int n_views = tb.n;
     const int jw0 = blockIdx.x * (kBoundThreads / 32);
@@ -1662,6 +1719,7 @@ __global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(TileBatch tb, in
             long long est = 0;
             if (limit) {
                 const int Tv = tb.v[vv].TX * tb.v[vv].TY, tbase = tb.v[vv].tile_base;
+#pragma unroll 8
                 for (int t = threadIdx.x; t < Tv; t += kBoundThreads) {
                     const int lm = __ldg(limit + tbase + t);
                     if (lm > 0) est += 2ll * lm + 64;
@@ -1900,9 +1958,9 @@ __global__ void __launch_bounds__(32 * kColWarps) k_pre_colscan(TileBatch tb, in
         last_chunk[g] = lastc;
         kept[g] = keep;
     }
-    if (w == 0) {                                  // the last chunk any tile keeps
+    if (w == 0) {                                  // the last chunk any tile of the view keeps
         const uint32_t mx = __reduce_max_sync(0xffffffffu, live ? last_chunk[g] : 0u);
-        if (l == 0 && mx > ld_relaxed(max_last)) atomicMax(max_last, mx);
+        if (l == 0 && mx > ld_relaxed(max_last + v)) atomicMax(max_last + v, mx);
     }
 }
 
@@ -1931,7 +1989,7 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     __shared__ int s_wc[kPlaceRounds * kPlaceWarps];
     if ((long long)*total > cap) return;
     const int v = blockIdx.x / Cv, k = blockIdx.x % Cv;
-    if ((uint32_t)k > *max_last) return;            // no tile of any view keeps this chunk
+    if ((uint32_t)k > max_last[v]) return;          // no tile of this view keeps this chunk
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int TX = tb.v[v].TX, TY = tb.v[v].TY, Tv = TX * TY, tbase = tb.v[v].tile_base;
     const int GX = TX + 1;
@@ -2087,7 +2145,8 @@ __global__ void k_range_counts(const uint2 *__restrict__ ranges, int T, uint32_t
 }
 
 struct PrePlan {
-    size_t dk0, dk1, dv0, dv1, vfin, cnt, rs, offs, mc, mv, full, lastc, kept, tstart, bnd, hist, part, misc, bytes;
+    size_t dk0, dk1, dv0, dv1, vfin, cnt, rs, offs, mc, mv, full, lastc, kept, tstart, bnd, maxlast, hist, part, misc,
+        bytes;
     int Cv, Tmax;
     bool ok;
 };
@@ -2113,6 +2172,7 @@ static PrePlan make_pre_plan(long long VN, const TileBatch &tb) {
     p.kept = take(4 * (size_t)tb.total_tiles);
     p.tstart = take(8 * (size_t)(tb.total_tiles + 1));
     p.bnd = take(8 * (size_t)tb.n * (p.Cv + 1));
+    p.maxlast = take(4 * (size_t)tb.n);
     long long nb = (VN + kSortTile - 1) / kSortTile;
     if (nb < 1) nb = 1;
     {
@@ -2248,7 +2308,7 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     }
     const int nchunks = n_views * p.Cv;
     long long *bnd = (long long *)(ws + p.bnd);
-    uint32_t *max_last = count + 1;                     // the last chunk any tile keeps
+    uint32_t *max_last = (uint32_t *)(ws + p.maxlast);  // per view: the last chunk any of its tiles keeps
     { k_chunk_bounds<<<cdiv(n_views * (p.Cv + 1), kBoundThreads / 32), kBoundThreads, 0, st>>>(tb, p.Cv, N, offs, d_tile_limit, bnd, max_last); count_launches(1); }
     const void *kc = rgb_dtype == GS_F32 ? (const void *)k_pre_count<GS_F32>
                      : rgb_dtype == GS_BF16 ? (const void *)k_pre_count<GS_BF16> : (const void *)k_pre_count<GS_F16>;
@@ -2270,9 +2330,16 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
                                                        max_last);
         count_launches(1);
     }
-    { k_tile_scan_finish<<<1, kTileScanThreads, 0, st>>>(T, kept, tstart, capacity, d_n_instances, count,
-                                                          reinterpret_cast<uint2 *>(d_tile_ranges), d_err_word);
-      count_launches(1); }
+    if (T <= kTileScanOneCta) {
+        { k_tile_scan_finish<<<1, kTileScanThreads, 0, st>>>(T, kept, tstart, capacity, d_n_instances, count,
+                                                              reinterpret_cast<uint2 *>(d_tile_ranges), d_err_word);
+          count_launches(1); }
+    } else {                                           // many views: the scan across CTAs
+        exclusive_scan2<uint32_t, unsigned long long>(kept, tstart, T, (unsigned long long *)part, tstart + T, st);
+        { k_tile_ranges_finish<<<cdiv(T, 256), 256, 0, st>>>(T, kept, tstart, capacity, d_n_instances, count,
+                                                             reinterpret_cast<uint2 *>(d_tile_ranges), d_err_word);
+          count_launches(1); }
+    }
     if (d_tile_count) cudaMemcpyAsync(d_tile_count, full, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToDevice, st);
     if (capacity > 0) {
         size_t gmax1 = 0;
@@ -2538,8 +2605,8 @@ extern "C" int gs_bin_sort_prefix_repair(const gs_camera *cams, int n_views, int
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char *ws = reinterpret_cast<char *>(d_workspace);
     // the record order left by the last gs_bin_sort_prefix call (see
-    // depth_order: one view sorted by the onesweep leaves it in vfin)
-    const size_t at = n_views > 1 ? p.dv1 : VN < (long long)kLbVal ? p.vfin : p.dv0;
+    // depth_order: the onesweep leaves it in vfin)
+    const size_t at = VN < (long long)kLbVal ? p.vfin : n_views > 1 ? p.dv1 : p.dv0;
     const uint32_t *order = (const uint32_t *)(ws + at);
     const uint32_t *full = (const uint32_t *)(ws + p.full);
     uint32_t *rep_start = (uint32_t *)(ws + p.kept);  // kept counts are no longer needed

@@ -75,11 +75,16 @@ def test_prefix_binning_is_exact(name, rgb):
     assert (g0 - g1).abs().max() <= 1e-5 * g0.abs().max()
 
 
-def test_prefix_repair_restores_exact_results():
+@pytest.mark.parametrize("views_case", ["one-view", "three-views"])
+def test_prefix_repair_restores_exact_results(views_case):
     """Limits far too short: the forward lists the tiles that ran out, the
-    repair rebuilds their full lists, the re-render makes every output equal
-    to the full-list path."""
-    scene, cams = S.skewed_scene(200_000, 0), [S.front_camera(640, 480)]
+    repair rebuilds their full lists (from the record order the binning left,
+    for one view or a batch of views), the re-render makes every output
+    equal to the full-list path."""
+    if views_case == "one-view":
+        scene, cams = S.skewed_scene(200_000, 0), [S.front_camera(640, 480)]
+    else:
+        scene, cams = S.skewed_scene(60_000, 3), S.ring_cameras(3, [(320, 240), (200, 300), (256, 256)])
     params = P.to_device_params(scene)
     views = P.param_views(params, scene.n)
     full = P.Frame(cams, scene.n)
