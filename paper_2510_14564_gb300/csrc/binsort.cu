@@ -1868,7 +1868,8 @@ __global__ void __launch_bounds__(32 * kColWarps) k_pre_colscan(TileBatch tb, in
                                                                uint32_t *__restrict__ full,
                                                                uint32_t *__restrict__ last_chunk,
                                                                uint32_t *__restrict__ kept,
-                                                               uint32_t *__restrict__ max_last) {
+                                                               uint32_t *__restrict__ max_last,
+                                                               uint32_t *__restrict__ tile_count) {
     __shared__ uint32_t s_c[kColWarps][32];
     __shared__ unsigned long long s_v[kColWarps][32];
     __shared__ uint32_t s_fk[kColWarps][32], s_keep[kColWarps][32];
@@ -1955,6 +1956,7 @@ __global__ void __launch_bounds__(32 * kColWarps) k_pre_colscan(TileBatch tb, in
         for (int q = kColWarps - 1; q >= 0; --q)
             if (s_fk[q][l] != 0xffffffffu) { lastc = s_fk[q][l]; keep = s_keep[q][l]; }
         full[g] = total;
+        if (tile_count) tile_count[g] = total;      // the caller's copy of the full counts
         last_chunk[g] = lastc;
         kept[g] = keep;
     }
@@ -2327,7 +2329,7 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
         int nblk = 0;
         for (int v = 0; v < n_views; ++v) nblk += cdiv(tb.v[v].TX * tb.v[v].TY, 32);
         k_pre_colscan<<<nblk, 32 * kColWarps, 0, st>>>(tb, p.Cv, p.Tmax, Mc, Mv_used, d_tile_limit, full, lastc, kept,
-                                                       max_last);
+                                                       max_last, d_tile_count);
         count_launches(1);
     }
     if (T <= kTileScanOneCta) {
@@ -2340,7 +2342,6 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
                                                              reinterpret_cast<uint2 *>(d_tile_ranges), d_err_word);
           count_launches(1); }
     }
-    if (d_tile_count) cudaMemcpyAsync(d_tile_count, full, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToDevice, st);
     if (capacity > 0) {
         size_t gmax1 = 0;
         for (int v = 0; v < n_views; ++v) {
