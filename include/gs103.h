@@ -114,15 +114,17 @@ int gs_zero(void *d_ptr, size_t n_bytes, gs_stream_t stream);
  * pass reads the digit counts of earlier tiles from status words those tiles
  * publish (decoupled look-back).  A tile makes at most `reads` rounds of
  * status-word reads (each round reads the words of four earlier tiles at
- * once) per digit; past that it gives up, sets
- * GS_EW_TIMEOUT in *err_word and goes on with the counts it has.  The call then completes with an unspecified
- * instance order, but every buffer it leaves still holds record indices in
- * [0, V*N), and the counts the lists are placed by are taken from that same
- * order, so no later kernel reads or writes out of bounds.  A healthy look-back makes a few hundred reads at
- * most; 0 makes every tile but the first give up at once (how the tests
- * reach this path without a stuck GPU).  The limit is process-wide and
- * applies to calls made after gs_set_wait_limit returns; reads < 0 returns
- * GS_ERR_ARG.  gs_get_wait_limit returns the limit in force. */
+ * once) per digit; past that it gives up, sets GS_EW_TIMEOUT in *err_word
+ * and goes on with the counts it has.  The call then completes with an
+ * unspecified instance order, but every buffer it leaves still holds record
+ * indices in [0, V*N) (the sort's last pass rewrites its outputs as an
+ * identity when any look-back gave up), and the counts the lists are placed
+ * by are taken from that same order, so no later kernel reads or writes out
+ * of bounds.  A healthy look-back makes a few hundred rounds at most; 0
+ * makes every tile but the first give up at once (how the tests reach this
+ * path without a stuck GPU).  The limit is process-wide and applies to calls
+ * made after gs_set_wait_limit returns; reads < 0 returns GS_ERR_ARG.
+ * gs_get_wait_limit returns the limit in force. */
 #define GS_WAIT_LIMIT_DEFAULT (1LL << 20)
 int gs_set_wait_limit(long long reads);
 long long gs_get_wait_limit(void);
