@@ -257,6 +257,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     }
     if (threadIdx.x < kSortDigitsMax) s_const[threadIdx.x] = 0;
     for (int k = threadIdx.x; k < 8 * kRadix; k += kSortThreads) (&s_wh[0][0])[k] = 0;
+    s_goff[threadIdx.x] = 0u;                               // the tile's digit counts, then global starts
     __syncthreads();
     if (__ldg(ghist + threadIdx.x) == n) s_copy = 1;       // one digit for every key
     if (vfin) {
@@ -343,6 +344,17 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
         else
             key[it] = valid ? __ldg(kin + idx) : 0u;
     }
+    // The tile's digit counts come first, by shared atomics, and are
+    // published before the ranking, so that later tiles' look-backs find
+    // them without waiting for this tile's ranking.
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it)
+        if (base + it * 32 + l < (long long)n) atomicAdd(&s_goff[(key[it] >> shift) & 255u], 1u);
+    __syncthreads();
+    const int d = threadIdx.x;
+    const uint32_t c = s_goff[d];
+    uint32_t *my = status + (size_t)bid * kRadix + d;
+    st_relaxed(my, (bid == 0 ? kLbPre : kLbAgg) | c);
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const long long idx = base + it * 32 + l;
@@ -350,25 +362,27 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
         const uint32_t d = valid ? ((key[it] >> shift) & 255u) : kRadix;
         const unsigned peers = warp_peers(d, 8);
         const unsigned rank = __popc(peers & lanemask_lt());
-        const uint32_t before = valid ? s_wh[w][d] : 0u;
+        // the first lane of each digit adds the digit's lanes to the warp's
+        // count and hands the count before them to its peers; the warp
+        // barrier orders the next item's additions after this one's
+        uint32_t old = 0u;
+        if (valid && rank == 0) old = atomicAdd(&s_wh[w][d], (uint32_t)__popc(peers));
         __syncwarp();
-        if (valid && rank == 0) s_wh[w][d] = before + __popc(peers);
-        __syncwarp();
+        const uint32_t before = __shfl_sync(0xffffffffu, old, __ffs(peers) - 1);
         loc[it] = valid ? before + rank : 0xffffffffu;
     }
     __syncthreads();
-    // thread d: this tile's count of digit d (and the warps' offsets within
-    // it), published at once; the tile-local and global digit starts
-    const int d = threadIdx.x;
-    uint32_t c = 0;
+    // thread d: the warps' offsets within digit d; the tile-local and
+    // global digit starts
+    {
+        uint32_t run = 0;
 #pragma unroll
-    for (int ww = 0; ww < 8; ++ww) {
-        const uint32_t x = s_wh[ww][d];
-        s_wh[ww][d] = c;
-        c += x;
+        for (int ww = 0; ww < 8; ++ww) {
+            const uint32_t x = s_wh[ww][d];
+            s_wh[ww][d] = run;
+            run += x;
+        }
     }
-    uint32_t *my = status + (size_t)bid * kRadix + d;
-    st_relaxed(my, (bid == 0 ? kLbPre : kLbAgg) | c);
     s_dstart[d] = block_excl_scan_256(c, s_warp);
     const uint32_t gbase = block_excl_scan_256(__ldg(ghist + d), s_warp2);
     __syncthreads();
@@ -414,18 +428,41 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     s_goff[d] = gbase + excl;
     __syncthreads();
     const int n_local = (int)min((long long)kSortTile, (long long)n - bbase);
-    for (int q = threadIdx.x; q < n_local; q += kSortThreads) {
-        const uint32_t k = s_keys[q];
-        const uint32_t dq = (k >> shift) & 255u;
-        const uint32_t g = s_goff[dq] + (uint32_t)(q - s_dstart[dq]);
-        const uint32_t v = s_vals[q];
-        if (keys_out && !final_pass) kout[g] = k;
-        vout[g] = v;
-        if (gtouch) {
-            const short4 rc = rs ? __ldg(rect + v) : make_short4(0, 0, 0, 0);
-            const int t = rs ? rect_area(rc) : __ldg(gtouch + v);              // the count is the area
-            cnt[g] = t > 0 ? (uint32_t)t : 0u;
-            if (rs) rs[g] = t > 0 ? rc : make_short4(0, 0, 0, 0);
+    if (gtouch) {
+        // the final pass gathers each record's rectangle (or count): groups of
+        // kGatherItems records per thread, every gather issued before any store
+        constexpr int kGatherItems = 8;
+        for (int q0 = threadIdx.x; q0 < n_local; q0 += kGatherItems * kSortThreads) {
+            uint32_t gpos[kGatherItems], vv[kGatherItems];
+            short4 rc[kGatherItems];
+            int t[kGatherItems];
+#pragma unroll
+            for (int u = 0; u < kGatherItems; ++u) {
+                const int q = q0 + u * kSortThreads;
+                if (q >= n_local) continue;
+                const uint32_t dq = (s_keys[q] >> shift) & 255u;
+                gpos[u] = s_goff[dq] + (uint32_t)(q - s_dstart[dq]);
+                vv[u] = s_vals[q];
+                if (rs) rc[u] = __ldg(rect + vv[u]);
+                else t[u] = __ldg(gtouch + vv[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < kGatherItems; ++u) {
+                const int q = q0 + u * kSortThreads;
+                if (q >= n_local) continue;
+                if (rs) t[u] = rect_area(rc[u]);                         // the count is the area
+                vout[gpos[u]] = vv[u];
+                cnt[gpos[u]] = t[u] > 0 ? (uint32_t)t[u] : 0u;
+                if (rs) rs[gpos[u]] = t[u] > 0 ? rc[u] : make_short4(0, 0, 0, 0);
+            }
+        }
+    } else {
+        for (int q = threadIdx.x; q < n_local; q += kSortThreads) {
+            const uint32_t k = s_keys[q];
+            const uint32_t dq = (k >> shift) & 255u;
+            const uint32_t g = s_goff[dq] + (uint32_t)(q - s_dstart[dq]);
+            if (keys_out) kout[g] = k;
+            vout[g] = s_vals[q];
         }
     }
     if (!final_pass || !done) return;
@@ -2315,7 +2352,6 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     const void *kc = rgb_dtype == GS_F32 ? (const void *)k_pre_count<GS_F32>
                      : rgb_dtype == GS_BF16 ? (const void *)k_pre_count<GS_BF16> : (const void *)k_pre_count<GS_F16>;
     allow_dynamic_smem(kc, gmax);
-    const short4 *rect = reinterpret_cast<const short4 *>(d_rect);
     // the coverage bound needs no history; with per-tile limits it is not computed
     const void *cov_splats = d_tile_limit ? nullptr : d_splats;
     uint32_t *Mv_used = d_tile_limit ? nullptr : Mv;

@@ -177,8 +177,8 @@ size_t radix_sort_workspace(long long n);
 void radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *vout, long long n, int bits, void *scratch,
                       cudaStream_t st);
 
-// Lanes of the warp whose digit equals this lane's: one ballot per digit bit
-// (bits <= 9; the sentinel digit 1 << bits marks an invalid lane).
+// Lanes of the warp whose value d (< 2^bits) equals this lane's: one ballot
+// per bit, bits + 1 in all (the sentinel 1 << bits marks an invalid lane).
 __device__ __forceinline__ unsigned warp_peers(uint32_t d, int bits) {
     unsigned peers = 0xffffffffu;
     for (int b = 0; b <= bits; ++b) {
