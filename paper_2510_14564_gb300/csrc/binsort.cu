@@ -1793,9 +1793,9 @@ __global__ void __launch_bounds__(kBoundThreads) k_chunk_bounds(TileBatch tb, in
         const double total = (double)(offs[s0 + N] - offs[s0]);
         if (total > 0.0) share = fmin(0.5, fmax(0.01, (double)est / total));
     }
-    const int half = Cv / 4;
     const long long s0 = (long long)v * N, s1 = s0 + N;
     const unsigned long long i0 = offs[s0], span = offs[s1] - i0;
+    const int half = Cv / 4;
     unsigned long long b;
     if (k >= Cv) {
         b = i0 + span;
@@ -2003,14 +2003,16 @@ __global__ void __launch_bounds__(32 * kColWarps) k_pre_colscan(TileBatch tb, in
     }
 }
 
-// Place the kept instances: one CTA of 16 warps per chunk, per-tile cursors in
+// Place the kept instances: CTAs of 16 warps per chunk, per-tile cursors in
 // shared memory (a skip mark for tiles that keep no entry of this chunk) and a
 // summed-area table of the tiles still active in this chunk.  The CTA reads
 // the chunk's records 2048 at a time, keeps those whose rectangle holds an
-// active tile (in order), and then warp w hands out slots in the tile rows
-// y = w (mod 16): every warp walks the kept records in order, so each tile's
-// slots follow record order.
-constexpr int kPlaceWarps = 16;
+// active tile (in order; every record with a tile when all tiles are active,
+// as in the front chunks, whose table is then not built), and then warp w
+// hands out slots in the tile rows y = w (mod 16): every warp walks the kept
+// records in order, so each tile's slots follow record order.
+constexpr int kPlaceRowLog = 4;
+constexpr int kPlaceWarps = 1 << kPlaceRowLog;           // warp w: tile rows y = w (mod kPlaceWarps)
 constexpr int kPlaceThreads = 32 * kPlaceWarps;
 constexpr int kPlaceRounds = 4;                        // records staged per thread per batch
 constexpr int kPlaceBatch = kPlaceRounds * kPlaceThreads;
@@ -2022,7 +2024,8 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     long long cap, uint32_t *__restrict__ vals, const float *__restrict__ depth,
     unsigned long long *__restrict__ keys, const uint32_t *__restrict__ max_last) {
     extern __shared__ uint32_t s_cur[];
-    __shared__ int s_any;
+    __shared__ int s_nact;                          // tiles that keep entries of this chunk
+    __shared__ int s_box[4];                        // the active tiles' bounding box [x0, x1) x [y0, y1)
     __shared__ uint32_t s_g[kPlaceBatch];
     __shared__ short4 s_rc[kPlaceBatch];
     __shared__ int s_wc[kPlaceRounds * kPlaceWarps];
@@ -2034,9 +2037,14 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     const int GX = TX + 1;
     uint32_t *sat = s_cur + Tmax;                   // [(TY + 1) x (TX + 1)]
     const uint32_t *row = Mc + ((long long)v * Cv + k) * Tmax;
-    if (threadIdx.x == 0) s_any = 0;
+    if (threadIdx.x == 0) {
+        s_nact = 0;
+        s_box[0] = s_box[2] = 0x7fffffff;
+        s_box[1] = s_box[3] = 0;
+    }
     __syncthreads();
-    bool any = false;
+    int nact = 0;
+    int bx0 = 0x7fffffff, bx1 = 0, by0 = 0x7fffffff, by1 = 0;
     for (int t0 = threadIdx.x; t0 < Tv; t0 += 4 * kPlaceThreads) {
         uint32_t lc[4], rw[4];
         unsigned long long ts[4];
@@ -2052,26 +2060,43 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
             const int t = t0 + r * kPlaceThreads;
             if (t >= Tv) continue;
             const bool act = (uint32_t)k <= lc[r];
+            const int ty = t / TX, tx = t - ty * TX;
             s_cur[t] = act ? (uint32_t)ts[r] + rw[r] : 0xffffffffu;
-            sat[(t / TX + 1) * GX + t % TX + 1] = act ? 1u : 0u;
-            any |= act;
+            sat[(ty + 1) * GX + tx + 1] = act ? 1u : 0u;
+            nact += act;
+            if (act) {
+                bx0 = min(bx0, tx); bx1 = max(bx1, tx + 1);
+                by0 = min(by0, ty); by1 = max(by1, ty + 1);
+            }
         }
+    }
+    bx0 = __reduce_min_sync(0xffffffffu, bx0); bx1 = __reduce_max_sync(0xffffffffu, bx1);
+    by0 = __reduce_min_sync(0xffffffffu, by0); by1 = __reduce_max_sync(0xffffffffu, by1);
+    nact = __reduce_add_sync(0xffffffffu, nact);
+    if (l == 0 && nact > 0) atomicAdd(&s_nact, nact);
+    if (l == 0 && bx1 > 0) {
+        atomicMin(&s_box[0], bx0); atomicMax(&s_box[1], bx1);
+        atomicMin(&s_box[2], by0); atomicMax(&s_box[3], by1);
     }
     for (int x = threadIdx.x; x < GX; x += kPlaceThreads) sat[x] = 0;
     for (int y = threadIdx.x; y <= TY; y += kPlaceThreads) sat[y * GX] = 0;
-    if (any) s_any = 1;
     __syncthreads();
-    if (!s_any) return;
-    for (int y = 1 + threadIdx.x; y <= TY; y += kPlaceThreads) {   // prefix along x
-        uint32_t run = 0;
-        for (int x = 1; x < GX; ++x) { run += sat[y * GX + x]; sat[y * GX + x] = run; }
+    if (s_nact == 0) return;
+    const bool all_active = s_nact == Tv;           // uniform over the CTA
+    if (!all_active) {
+        for (int y = 1 + threadIdx.x; y <= TY; y += kPlaceThreads) {   // prefix along x
+            uint32_t run = 0;
+            for (int x = 1; x < GX; ++x) { run += sat[y * GX + x]; sat[y * GX + x] = run; }
+        }
+        __syncthreads();
+        for (int x = 1 + threadIdx.x; x < GX; x += kPlaceThreads) {    // prefix along y
+            uint32_t run = 0;
+            for (int y = 1; y <= TY; ++y) { run += sat[y * GX + x]; sat[y * GX + x] = run; }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int x = 1 + threadIdx.x; x < GX; x += kPlaceThreads) {    // prefix along y
-        uint32_t run = 0;
-        for (int y = 1; y <= TY; ++y) { run += sat[y * GX + x]; sat[y * GX + x] = run; }
-    }
-    __syncthreads();
+    // a record's pairs are enumerated within the active tiles' bounding box only
+    const short ax0 = (short)s_box[0], ax1 = (short)s_box[1], ay0 = (short)s_box[2], ay1 = (short)s_box[3];
     ChunkGeom cg;
     cg.lo = __ldg(bounds + v * (Cv + 1) + k);
     cg.hi = __ldg(bounds + v * (Cv + 1) + k + 1);
@@ -2097,7 +2122,8 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
         for (int r = 0; r < kPlaceRounds; ++r) {
             const short4 q = rc[r];
             if (q.z > q.x && q.w > q.y)
-                keep[r] = sat[q.w * GX + q.z] - sat[q.y * GX + q.z] - sat[q.w * GX + q.x] + sat[q.y * GX + q.x] > 0;
+                keep[r] = all_active ||
+                          sat[q.w * GX + q.z] - sat[q.y * GX + q.z] - sat[q.w * GX + q.x] + sat[q.y * GX + q.x] > 0;
             bal[r] = __ballot_sync(0xffffffffu, keep[r]);
             if (l == 0) s_wc[r * kPlaceWarps + w] = __popc(bal[r]);
         }
@@ -2128,9 +2154,14 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
             const int j = j0 + l;
             uint32_t gj = 0;
             short4 r = make_short4(0, 0, 0, 0);
-            if (j < n_keep) { gj = s_g[j]; r = s_rc[j]; }
-            const int y0w = r.y + ((w - r.y) % kPlaceWarps + kPlaceWarps) % kPlaceWarps;
-            const int hw = r.w > y0w ? (r.w - y0w + kPlaceWarps - 1) / kPlaceWarps : 0;
+            if (j < n_keep) {
+                gj = s_g[j];
+                r = s_rc[j];
+                r.x = max(r.x, ax0); r.z = min(r.z, ax1);
+                r.y = max(r.y, ay0); r.w = min(r.w, ay1);
+            }
+            const int y0w = r.y + ((w - r.y) & (kPlaceWarps - 1));          // the rect's first row of warp w
+            const int hw = r.w > y0w ? (r.w - y0w + kPlaceWarps - 1) >> kPlaceRowLog : 0;
             const int wd = r.z - r.x;
             const int cnt = wd > 0 ? wd * hw : 0;
             if (!__any_sync(0xffffffffu, cnt > 0)) continue;  // none of these records reaches this warp's rows
@@ -2160,7 +2191,7 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
                 if (valid) {
                     const int loc = pidx - oex;
                     const int rr = loc / owd;
-                    t = (oyw + kPlaceWarps * rr) * TX + ox + (loc - rr * owd);
+                    t = (oyw + (rr << kPlaceRowLog)) * TX + ox + (loc - rr * owd);
                     cur = s_cur[t];
                 }
                 const bool act = cur != 0xffffffffu;
