@@ -159,9 +159,9 @@ def replica_throughput(steps: int, ms_max: float, world: int) -> float:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1) -> dict:
+def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1, n_grad: int = 0) -> dict:
     """Minimum bytes each stage must move (per step) for N Gaussians seen
-    from V views with P pixels in all."""
+    from V views with P pixels in all, n_grad of them with a 2D gradient."""
     rec = 34 if half else 40            # id + xy + conic + opacity + rgb per processed instance
     sh_read = 140 if half else 236
     return {
@@ -173,11 +173,13 @@ def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1) -> dict:
         "project_bwd": N * (sh_read + 32 + 236) + V * N * 36,
         "adam": N * (1652 + (96 if half else 0)),
         # fused, one view, two launches.  Geometry: 11 params, touched, the 2D
-        # gradient, the SH the forward read, m and v of the 11; writes p, m, v
-        # of the 11 and the 24-byte SH-gradient factors.  SH: the factors, p, m
-        # and v of the 48 SH entries read and written (+ the 16-bit shadow).
-        "project_bwd_adam": N * ((44 + 4 + 48 + (96 if half else 192) + 88 + 132 + 24)
-                                 + (24 + 576 + 576 + (96 if half else 0))),
+        # gradient record, the SH the forward read, m and v of the 11; writes
+        # p, m, v of the 11.  SH: the SH-gradient factors (24 bytes of the
+        # record), p, m and v of the 48 SH entries read and written (+ the
+        # 16-bit shadow).  A record the reverse pass wrote (n_grad of them) is
+        # also written twice: the factors over it (48 bytes), then zeros (24).
+        "project_bwd_adam": N * ((44 + 4 + 48 + (96 if half else 192) + 88 + 132)
+                                 + (24 + 576 + 576 + (96 if half else 0))) + 72 * n_grad,
     }
 
 
@@ -356,6 +358,9 @@ def run_ours(args):
     timed(tr, args.steps, stage_times=it_stages, adam=False)
     it_ips = replica_throughput(args.steps, it_ms, 1)
     assert tr.frame.check_errors() == 0, "kernel error word set (learned path)"
+    # Gaussians the reverse pass gave a 2D gradient (the iteration's projection
+    # backward leaves the records as the reverse pass wrote them)
+    n_grad = int((tr.frame.grad2d[:len(cams) * N * 12].view(-1, 12)[:, :9] != 0).any(1).sum().item())
 
     f = tr.frame
     # tiles whose kept prefix ran short and were repaired, per step (read back
@@ -370,7 +375,7 @@ def run_ours(args):
     I_proc = int(f.tile_nproc.sum().item())
     pairs = int(f.n_proc.sum().item())           # (pixel, Gaussian) pairs the blend loops walk
     Pix = sum(c.W * c.H for c in cams)
-    ab = algorithmic_bytes(N, Pix, I, I_proc, True, len(cams))
+    ab = algorithmic_bytes(N, Pix, I, I_proc, True, len(cams), n_grad)
     stage_ms = {k: statistics.mean(v) for k, v in stages.items()}
     it_stage_ms = {k: statistics.mean(v) for k, v in it_stages.items()}
     kernel_stages = {k: v for k, v in stage_ms.items() if k in ab}
@@ -410,7 +415,7 @@ def run_ours(args):
                        "hbm_frac": round(it_gbs / hbm, 4),
                        "stage_ms": {k: round(v, 4) for k, v in it_stage_ms.items()}},
                    "instances_full_lists": I_full, "instances_kept": I, "processed_instances": I_proc,
-                   "pixel_pairs_processed": pairs,
+                   "pixel_pairs_processed": pairs, "gaussians_with_2d_gradient": n_grad,
                    "flagged_tiles_per_step": {"mean": round(statistics.mean(flagged), 2), "max": max(flagged)},
                    "l2": "inputs larger than L2 (0.4-0.7 GB of parameters, 1.5+ GB of instances)",
                    "parallelism": "replicas" if world > 1 else "1 GPU",

@@ -357,9 +357,11 @@ int gs_project_bwd(const gs_camera *cams, int n_views, int N, const float *d_mea
  * refreshed in place): each Gaussian's coefficients are read before its
  * update is written.  Gradients and updates equal those of the two calls (up
  * to the last bit of the SH basis, evaluated by two code paths).  With one
- * view d_grad2d is consumed: it serves as scratch (each record's entries 0..5
- * hold the factors of its SH gradient) and its contents on return are
- * unspecified; with several views it is only read. */
+ * view d_grad2d is consumed and left all zero: a nonzero record serves as
+ * scratch (its entries 0..5 hold the factors of its SH gradient) and is
+ * zeroed after use, a zero record is neither used nor written, so a caller
+ * that zeroed the records before gs_render_bwd need not zero them again for
+ * the next step; with several views d_grad2d is only read. */
 int gs_project_bwd_adam(const gs_camera *cams, int n_views, int N, float *d_params,
                         const void *d_sh, int sh_dtype, const int32_t *d_touched,
                         float *d_grad2d, float *d_m, float *d_v, const float *lr, float b1,

@@ -817,7 +817,10 @@ __global__ void __launch_bounds__(128) k_project_bwd1(ViewGeom cam, int N, const
 // Gaussian: the backward, the Adam step of the 11 geometric entries, and the
 // SH gradient left as its two factors -- w_ch (the upstream colour gradient,
 // zero on clamped channels) and the view direction u -- written over the
-// Gaussian's consumed 2D-gradient record (entries 0..5).
+// Gaussian's consumed 2D-gradient record (entries 0..5, the rest zeroed).
+// A record that is all zero (a Gaussian no pixel's reverse pass reached: its
+// gradients are zero) is neither used nor written, and part 2 zeroes the
+// factors it read, so the records are all zero again on return.
 template <int SDT>
 __global__ void __launch_bounds__(128, SDT == GS_F32 ? 4 : 6) k_bwd_adam_geom(ViewGeom cam, int N, const void *__restrict__ sh,
                                                        const int *__restrict__ touched,
@@ -859,7 +862,9 @@ __global__ void __launch_bounds__(128, SDT == GS_F32 ? 4 : 6) k_bwd_adam_geom(Vi
     float dmean[3] = {0, 0, 0}, dls[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dlog = 0.0f;
     float w[3] = {0.0f, 0.0f, 0.0f};
     float ux = 0.0f, uy = 0.0f, uz = 1.0f;
-    if (hit > 0) {
+    const bool nz = ga.x != 0.0f || ga.y != 0.0f || ga.z != 0.0f || ga.w != 0.0f || gb.x != 0.0f ||
+                    gb.y != 0.0f || gb.z != 0.0f || gb.w != 0.0f || gc.x != 0.0f;
+    if (hit > 0 && nz) {
         const float g[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
         geom_bwd(cam, mx, my, mz, ls, q, lg, g, dmean, dls, dq, dlog);
         const float vx = mx - cam.campos[0], vy = my - cam.campos[1], vz = mz - cam.campos[2];
@@ -878,8 +883,11 @@ __global__ void __launch_bounds__(128, SDT == GS_F32 ? 4 : 6) k_bwd_adam_geom(Vi
         dmean[1] += (gd[1] - uy * gdd) * inv;
         dmean[2] += (gd[2] - uz * gdd) * inv;
     }
-    rec[0] = make_float4(w[0], w[1], w[2], ux);
-    *reinterpret_cast<float2 *>(grad2d + 12 * i + 4) = make_float2(uy, uz);
+    if (nz) {
+        rec[0] = make_float4(w[0], w[1], w[2], ux);
+        rec[1] = make_float4(uy, uz, 0.0f, 0.0f);
+        rec[2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
     if (dparams) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) { dparams[3 * i + k] = dmean[k]; dparams[3 * n + 3 * i + k] = dls[k]; }
@@ -909,7 +917,7 @@ __global__ void __launch_bounds__(128, SDT == GS_F32 ? 4 : 6) k_bwd_adam_geom(Vi
 // rebuilding each SH gradient w_ch Y_j(u) from the factors part 1 left,
 // with the 16 basis values and w of each Gaussian staged in shared memory.
 template <int SHD>
-__global__ void __launch_bounds__(256, 4) k_bwd_adam_sh(int N, const float *__restrict__ grad2d,
+__global__ void __launch_bounds__(256, 4) k_bwd_adam_sh(int N, float *__restrict__ grad2d,
                                                      float *__restrict__ dparams, AdamArgs a) {
     __shared__ float s_y[8][32 * 17];        // per warp: 16 basis values per Gaussian (stride 17)
     __shared__ float s_w[8][32 * 3];
@@ -921,10 +929,14 @@ __global__ void __launch_bounds__(256, 4) k_bwd_adam_sh(int N, const float *__re
     {
         float w0 = 0.0f, w1 = 0.0f, w2 = 0.0f, ux = 0.0f, uy = 0.0f, uz = 1.0f;
         if (l < left) {
-            const float *r = grad2d + 12 * (wfirst + l);
-            const float4 a4 = __ldg(reinterpret_cast<const float4 *>(r));
-            const float2 b2 = __ldg(reinterpret_cast<const float2 *>(r + 4));
+            float *r = grad2d + 12 * (wfirst + l);
+            const float4 a4 = *reinterpret_cast<const float4 *>(r);
+            const float2 b2 = *reinterpret_cast<const float2 *>(r + 4);
             w0 = a4.x; w1 = a4.y; w2 = a4.z; ux = a4.w; uy = b2.x; uz = b2.y;
+            if (a4.x != 0.0f || a4.y != 0.0f || a4.z != 0.0f || a4.w != 0.0f || b2.x != 0.0f || b2.y != 0.0f) {
+                *reinterpret_cast<float4 *>(r) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // the record zero again
+                *reinterpret_cast<float2 *>(r + 4) = make_float2(0.0f, 0.0f);
+            }
         }
         float Y[16];
         sh_basis(ux, uy, uz, Y);

@@ -258,6 +258,7 @@ class Frame:
         self.touched = torch.empty(VN, dtype=torch.int32, device=d)
         self.radius = torch.empty(VN, dtype=torch.int32, device=d)
         self.grad2d = torch.empty(VN * 12, dtype=torch.float32, device=d)
+        self.grad2d_zero = False     # whether the 2D-gradient records are known to be all zero
         self.dparams = torch.empty(PARAM_FLOATS * self.gcap, dtype=torch.float32, device=d)
 
     def resize(self, N: int) -> None:
@@ -273,6 +274,7 @@ class Frame:
         if N > self.gcap:
             self._alloc_gaussians(N + N // 4)
         self.N = N
+        self.grad2d_zero = False
         if self.vals is None:
             return
         need = int(self.inst_per_gaussian * N) + 65536
@@ -436,7 +438,12 @@ class Frame:
 
     def zero_grad2d_async(self) -> None:
         """Zero the 2D gradients on the side stream (after every reader queued
-        so far); render_bwd waits for it instead of zeroing itself."""
+        so far); render_bwd waits for it instead of zeroing itself.  Nothing
+        to do when the last consumer left them all zero (the fused one-view
+        backward + Adam does)."""
+        if self.grad2d_zero:
+            self.ev_zeroed = None
+            return
         s = self._fork()
         with torch.cuda.stream(s):
             L.gs_zero(self.grad2d[:self.V * self.N * 12])
@@ -542,8 +549,9 @@ class Frame:
         if self.ev_zeroed is not None:
             cur.wait_event(self.ev_zeroed)
             self.ev_zeroed = None
-        else:
+        elif not self.grad2d_zero:
             L.gs_zero(self.grad2d[:self.V * self.N * 12])
+        self.grad2d_zero = False                 # the reverse pass adds into the records
         if self.bwd_prep is not None and self.bwd_prep[0] == timing:
             s = self.bwd_prep[1]
             cur.wait_event(self.bwd_prep[2])
@@ -770,6 +778,7 @@ class Trainer:
             L.gs_project_bwd_adam(f.cams, self.N, self.p, self.sh_shadow, self.sh_storage, f.touched, f.grad2d,
                                   self.m, self.v, self.lr, ADAM_B1, ADAM_B2, ADAM_EPS, self.t,
                                   self.sh_shadow, self.sh_storage)
+            f.grad2d_zero = True                 # the call leaves the records all zero
         else:
             # several views: gradients summed over views, then Adam
             self.t += 1

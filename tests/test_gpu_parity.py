@@ -229,6 +229,7 @@ def test_fused_backward_adam_matches_separate_calls(sh_dtype):
     fr.grad2d.zero_()
     L.gs_render_bwd(fr.cams, fr.ranges, fr.vals, fr.splats, fr.rgb_dtype, None, d, fr.T_final, fr.n_proc,
                     fr.tile_nproc, fr.grad2d, fr.err)
+    fr.grad2d[:12 * n].view(n, 12)[::7] = 0.0     # Gaussians without a 2D gradient, on both paths
     rng = np.random.default_rng(2)
     m0 = torch.from_numpy(rng.normal(0, 1e-3, 59 * n).astype(np.float32)).cuda()
     v0 = torch.from_numpy(rng.random(59 * n).astype(np.float32) * 1e-6).cuda()
@@ -245,9 +246,13 @@ def test_fused_backward_adam_matches_separate_calls(sh_dtype):
     pB, mB, vB = params.clone(), m0.clone(), v0.clone()
     gB = torch.empty(59 * n, device="cuda")
     shB = torch.empty(48 * n, dtype=torch.bfloat16, device="cuda")
+    n_written = int((fr.grad2d[:12 * n].view(n, 12) != 0).any(1).sum())
+    assert 0 < n_written < n                      # records with a gradient, and zero ones
     L.gs_project_bwd_adam([cam], n, pB, shadow0, sh_dtype if shadow0 is not None else L.GS_F32, fr.touched,
                           fr.grad2d, mB, vB, lr, 0.9, 0.999, 1e-15, 3, shB, L.GS_BF16, gB)
     torch.cuda.synchronize()
+    # the call leaves every record zero (ready for the next reverse pass)
+    assert int((fr.grad2d[:12 * n] != 0).sum()) == 0
     # the same backward (two compilations of one source: last-bit differences only)
     assert (g - gB).abs().max() <= 1e-5 * g.abs().max()
     assert torch.allclose(pA, pB, rtol=1e-6, atol=1e-7)

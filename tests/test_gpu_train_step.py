@@ -151,6 +151,32 @@ def test_bf16_training_step_updates_master_and_shadow():
     assert moved.max() > 0
 
 
+def test_next_step_reuses_the_records_the_fused_call_zeroed():
+    """One view: the fused backward + Adam leaves the 2D-gradient records all
+    zero, so the next step's reverse pass adds into them without a memset;
+    two steps that way equal two steps with the records zeroed explicitly."""
+    scene = S.uniform_scene(1500, 4)
+    cams = [S.front_camera(112, 72)]
+    tgt = torch.from_numpy(S.random_image(112, 72, seed=21).ravel()).cuda()
+    trs = [P.Trainer(cams, P.to_device_params(scene), scene.n, tgt, rgb_dtype=L.GS_BF16,
+                     sh_storage=L.GS_BF16, schedule=P.Schedule("count")) for _ in range(2)]
+    n = scene.n
+    for k, tr in enumerate(trs):
+        tr.step()
+        torch.cuda.synchronize()
+        assert tr.frame.grad2d_zero
+        assert int((tr.frame.grad2d[:12 * n] != 0).sum()) == 0
+        if k == 1:
+            tr.frame.grad2d_zero = False          # the second trainer zeroes again before its reverse pass
+        tr.step()
+    torch.cuda.synchronize()
+    a, b = trs
+    assert a.frame.check_errors() == 0 and b.frame.check_errors() == 0
+    # equal up to the order of the reverse pass's atomic additions
+    assert (a.m - b.m).abs().max() <= 1e-5 * b.m.abs().max()
+    assert (a.p - b.p).abs().max() <= 1e-5 * b.p.abs().max()
+
+
 def test_target_of_the_wrong_size_is_refused():
     """The L1 target covers every view's pixels; a target for one view of a
     two-view batch is refused on the host, before the L1 kernel runs."""
