@@ -41,12 +41,12 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # captured.
 MEASURED_TRAFFIC = {
     "project_bwd_adam": {
-        "bytes_per_gaussian": (0.840355200 + 0.536993920 + 1.872078848 + 1.953295232) * 1e9 / 3e6,
+        "bytes_per_gaussian": (0.566188288 + 0.377644544 + 1.872073984 + 1.954449920) * 1e9 / 3e6,
         "sources": {
             "paper_2510_14564_gb300/csrc/project.cu":
-                "55c9225b91d375a10d8d47bbc2aa26c016ef14bb73e3d956bb3583dad1207138",
+                "23aa6bfc8cd300502707d577fafd6c5232beace1ca655c77db2e4333be8e6e5a",
             "paper_2510_14564_gb300/csrc/gs_common.cuh":
-                "8f7d0bfb7a35c475775f8adef83c7e3b96d9a905d18100f831e0c9437a2b9690",
+                "48ec94c1bce3261c8aa6f96a82c366ec0c9b5ffa9490f3f62cec3ebaa685e270",
         },
     },
 }
@@ -173,13 +173,14 @@ def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1, n_grad: int = 0) 
         "project_bwd": N * (sh_read + 32 + 236) + V * N * 36,
         "adam": N * (1652 + (96 if half else 0)),
         # fused, one view, two launches.  Geometry: 11 params, touched, the 2D
-        # gradient record, the SH the forward read, m and v of the 11; writes
-        # p, m, v of the 11.  SH: the SH-gradient factors (24 bytes of the
-        # record), p, m and v of the 48 SH entries read and written (+ the
-        # 16-bit shadow).  A record the reverse pass wrote (n_grad of them) is
-        # also written twice: the factors over it (48 bytes), then zeros (24).
-        "project_bwd_adam": N * ((44 + 4 + 48 + (96 if half else 192) + 88 + 132)
-                                 + (24 + 576 + 576 + (96 if half else 0))) + 72 * n_grad,
+        # gradient record, m and v of the 11; writes p, m, v of the 11.  SH:
+        # the SH-gradient factors (24 bytes of the record), p, m and v of the
+        # 48 SH entries read and written (+ the 16-bit shadow).  A Gaussian
+        # with a 2D gradient (n_grad of them) also has its SH read by the
+        # geometry kernel and its record written twice: the factors over it
+        # (48 bytes), then zeros (24); the others' gradients are zero.
+        "project_bwd_adam": N * ((44 + 4 + 48 + 88 + 132) + (24 + 576 + 576 + (96 if half else 0)))
+                            + n_grad * ((96 if half else 192) + 48 + 24),
     }
 
 
@@ -191,7 +192,7 @@ RENDER_BWD_INSTR = {
     "warp_instr_per_pair": 339131212 / 306789136,
     "sources": {
         "paper_2510_14564_gb300/csrc/render.cu": "db548d8484e4c08ba09f4f09652b36166792a331993a4a6b5523a6acf7395b17",
-        "paper_2510_14564_gb300/csrc/gs_common.cuh": "8f7d0bfb7a35c475775f8adef83c7e3b96d9a905d18100f831e0c9437a2b9690",
+        "paper_2510_14564_gb300/csrc/gs_common.cuh": "48ec94c1bce3261c8aa6f96a82c366ec0c9b5ffa9490f3f62cec3ebaa685e270",
     },
 }
 
