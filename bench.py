@@ -159,11 +159,15 @@ def replica_throughput(steps: int, ms_max: float, world: int) -> float:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1, n_grad: int = 0) -> dict:
+def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1, n_grad: int = 0,
+                      sh_half: bool | None = None) -> dict:
     """Minimum bytes each stage must move (per step) for N Gaussians seen
-    from V views with P pixels in all, n_grad of them with a 2D gradient."""
+    from V views with P pixels in all, n_grad of them with a 2D gradient;
+    half: 16-bit colour records, sh_half: 16-bit SH storage (default: half)."""
+    if sh_half is None:
+        sh_half = half
     rec = 34 if half else 40            # id + xy + conic + opacity + rgb per processed instance
-    sh_read = 140 if half else 236
+    sh_read = 140 if sh_half else 236
     return {
         "project": V * N * (sh_read + (46 if half else 52)),
         "bin_sort": V * N * 8 + I * (12 + 24 + 8),
@@ -171,7 +175,7 @@ def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1, n_grad: int = 0) 
         "l1": P * 36,
         "render_bwd": I_proc * rec + P * 20 + V * N * 36,
         "project_bwd": N * (sh_read + 32 + 236) + V * N * 36,
-        "adam": N * (1652 + (96 if half else 0)),
+        "adam": N * (1652 + (96 if sh_half else 0)),
         # fused, one view, two launches.  Geometry: 11 params, touched, the 2D
         # gradient record, m and v of the 11; writes p, m, v of the 11.  SH:
         # the SH-gradient factors (24 bytes of the record), p, m and v of the
@@ -179,8 +183,8 @@ def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1, n_grad: int = 0) 
         # with a 2D gradient (n_grad of them) also has its SH read by the
         # geometry kernel and its record written twice: the factors over it
         # (48 bytes), then zeros (24); the others' gradients are zero.
-        "project_bwd_adam": N * ((44 + 4 + 48 + 88 + 132) + (24 + 576 + 576 + (96 if half else 0)))
-                            + n_grad * ((96 if half else 192) + 48 + 24),
+        "project_bwd_adam": N * ((44 + 4 + 48 + 88 + 132) + (24 + 576 + 576 + (96 if sh_half else 0)))
+                            + n_grad * ((96 if sh_half else 192) + 48 + 24),
     }
 
 
@@ -252,9 +256,16 @@ def run_ours(args):
     # Gaussians step after step).
     lr = tuple(x * args.lr_scale for x in P.DEFAULT_LR)
 
+    # SH storage of the learned path: a 16-bit shadow halves the projection's
+    # SH read of every (view, Gaussian) but costs a write of it per step; with
+    # one view the fused backward + Adam reads SH only for the Gaussians with a
+    # gradient, so FP32 SH (no shadow) is the faster step there, while several
+    # views read SH once per view and in the backward, and the shadow pays.
+    learned_sh = L.GS_BF16 if len(cams) > 1 else L.GS_F32
+
     def make(mode, half):
         dt = L.GS_BF16 if half else L.GS_F32
-        tr = P.Trainer(cams, flat0.cuda(), N, tgt, rgb_dtype=dt, sh_storage=dt,
+        tr = P.Trainer(cams, flat0.cuda(), N, tgt, rgb_dtype=dt, sh_storage=learned_sh if half else L.GS_F32,
                        schedule=P.Schedule(mode=mode), lr=lr)
         return tr
 
@@ -376,7 +387,7 @@ def run_ours(args):
     I_proc = int(f.tile_nproc.sum().item())
     pairs = int(f.n_proc.sum().item())           # (pixel, Gaussian) pairs the blend loops walk
     Pix = sum(c.W * c.H for c in cams)
-    ab = algorithmic_bytes(N, Pix, I, I_proc, True, len(cams), n_grad)
+    ab = algorithmic_bytes(N, Pix, I, I_proc, True, len(cams), n_grad, learned_sh != L.GS_F32)
     stage_ms = {k: statistics.mean(v) for k, v in stages.items()}
     it_stage_ms = {k: statistics.mean(v) for k, v in it_stages.items()}
     kernel_stages = {k: v for k, v in stage_ms.items() if k in ab}
@@ -403,7 +414,8 @@ def run_ours(args):
                    "view": [cam.W, cam.H] if len(cams) == 1 else [[c.W, c.H] for c in cams],
                    "step": "training step: every hot-path row incl. Adam and the cost-MLP training",
                    "schedule": f.schedule_report(),
-                   "storage": "bf16 SH + bf16 colour, fp32 blending and gradients",
+                   "storage": ("bf16" if learned_sh == L.GS_BF16 else "fp32") + " SH + bf16 colour records, "
+                              "fp32 blending and gradients",
                    "plain_fp32_count_iters_per_s": round(plain_ips * world, 3),
                    "learned_vs_plain": round(ips / plain_ips, 4),
                    "fwd_bwd_iteration": {
