@@ -226,9 +226,9 @@ class Frame:
         self.pick_b = "count"
         # the forward of the learned schedule: raster order (one CTA per tile),
         # judged against the order of the previous step's processed counts,
-        # which the side stream computes while the step projects and bins
+        # computed at the start of the judged time
         self.judge_f = PassJudge(self.sched.judge_every, arms=("processed", "raster"))
-        self.fwd_prep = None         # (pick, event): the forward's order, prepared
+        self.fwd_prep = None         # (pick, None): the forward's arm for this step
         self.cost_f = torch.zeros(self.T, dtype=torch.float32, device=d)
         self.step_count = 0
         # the error word, read back each step without waiting (pinned copy +
@@ -372,14 +372,16 @@ class Frame:
         L.gs_range_cost(self.ranges, self.T, self.cost)
         L.gs_sched_order(self.cost, self.T, out, self.order_ws)
 
-    def _sched_fwd(self):
+    def _sched_fwd(self, pick=None):
         """The forward's schedule: None (raster) for the raster schedule, the
         instance-count order for the plain one; for the learned one raster,
-        or the order prepare_fwd_async made when its judge picked it."""
+        or, when its judge picked it, the order of the processed counts the
+        previous forward left (computed here, inside the judged time)."""
         if self.sched.mode == "learned":
-            if self.fwd_prep is None or self.fwd_prep[0] != "processed":
+            if pick != "processed":
                 return None
-            torch.cuda.current_stream().wait_event(self.fwd_prep[1])
+            L.gs_int_cost(self.tile_nproc, self.T, self.cost_f)
+            L.gs_sched_order(self.cost_f, self.T, self.order_f, self.order_ws)
             return {"mode": L.GS_SCHED_ORDER, "order": self.order_f, "queue": self.queue}
         if self.sched.mode != "count":
             return None
@@ -460,22 +462,15 @@ class Frame:
         self.bwd_prep = (timing, sched, self._recorded(s))
 
     def prepare_fwd_async(self) -> None:
-        """The learned schedule's forward order for this step: the judge
-        picks raster or the previous step's processed-count order, and the
-        latter is computed on the side stream (from the per-tile counts the
-        previous forward left), overlapping the projection and binning."""
+        """The learned schedule's forward order for this step: its judge picks
+        raster or the previous step's processed-count order.  The order is
+        computed when the forward starts, inside the time the judge measures,
+        so that its cost counts against it (computed on the side stream
+        during the binning, it slowed the binning by as much as it saved)."""
         if self.sched.mode != "learned" or self.force_order is not None:
             self.fwd_prep = None
             return
-        pick = self.judge_f.pick()
-        ev = None
-        if pick == "processed":
-            s = self._fork()
-            with torch.cuda.stream(s):
-                L.gs_int_cost(self.tile_nproc, self.T, self.cost_f)
-                L.gs_sched_order(self.cost_f, self.T, self.order_f, self.order_ws)
-            ev = self._recorded(s)
-        self.fwd_prep = (pick, ev)
+        self.fwd_prep = (self.judge_f.pick(), None)
 
     def train_scheduler_async(self) -> None:
         """train_scheduler on the side stream, overlapping what the current
@@ -486,13 +481,14 @@ class Frame:
         self.ev_mlp = self._recorded(s)
 
     def render(self, timing: bool = False, mark=None) -> None:
-        s = self._sched_fwd()
+        pick = self.fwd_prep[0] if self.fwd_prep is not None else None
+        self.fwd_prep = None
+        tok = self.judge_f.start(pick) if pick is not None else None     # the order's cost included
+        s = self._sched_fwd(pick)
         if mark:
             mark("render_fwd")
         tns = self.tile_ns if timing else None
         if not self.prefix:
-            tok = self.judge_f.start(self.fwd_prep[0]) if self.fwd_prep is not None else None
-            self.fwd_prep = None
             L.gs_render_fwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, s, self.img,
                             self.T_final, self.n_proc, self.tile_nproc, tns, self.err)
             if tok:
@@ -500,8 +496,6 @@ class Frame:
             return
         # kept prefixes: check that no pixel ran past one, rebuild and re-render any that did
         L.gs_zero(self.flag_count)
-        tok = self.judge_f.start(self.fwd_prep[0]) if self.fwd_prep is not None else None
-        self.fwd_prep = None
         L.gs_render_fwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, s, self.img,
                         self.T_final, self.n_proc, self.tile_nproc, tns, self.err,
                         tile_count=self.tile_count, flag_tiles=self.flag_tiles, flag_count=self.flag_count)
@@ -552,16 +546,20 @@ class Frame:
         elif not self.grad2d_zero:
             L.gs_zero(self.grad2d[:self.V * self.N * 12])
         self.grad2d_zero = False                 # the reverse pass adds into the records
+        judged = self.sched.mode == "learned" and self.force_order is None
         if self.bwd_prep is not None and self.bwd_prep[0] == timing:
+            # the judged time includes the wait for the order the side stream
+            # prepared (the learned order's features and MLP cost more than
+            # the count order's ranking)
+            tok = self.judge_b.start(self.pick_b) if judged else None
             s = self.bwd_prep[1]
             cur.wait_event(self.bwd_prep[2])
         else:
             s = self._sched_bwd(timing=timing)
+            tok = self.judge_b.start(self.pick_b) if judged else None
         self.bwd_prep = None
         if mark:
             mark("render_bwd")
-        judged = self.sched.mode == "learned" and self.force_order is None
-        tok = self.judge_b.start(self.pick_b) if judged else None
         L.gs_render_bwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, s, dimg,
                         self.T_final, self.n_proc, self.tile_nproc, self.grad2d, self.err)
         if tok:
