@@ -36,12 +36,13 @@ WORKLOAD = "skewed-3M-1600x1060"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 
 # DRAM bytes (read + write) per Gaussian of the dominant call, from one ncu
-# capture of the full-size workload (the summary of that capture is kept with
-# the profiles).  Valid only while the kernel sources hash as they did when
-# captured.
+# capture of the full-size workload in the configuration the bench times
+# (one view: FP32 SH, no 16-bit shadow; the summary of that capture is kept
+# with the profiles).  Valid only while the kernel sources hash as they did
+# when captured.
 MEASURED_TRAFFIC = {
     "project_bwd_adam": {
-        "bytes_per_gaussian": (0.566188288 + 0.377644544 + 1.872073984 + 1.954449920) * 1e9 / 3e6,
+        "bytes_per_gaussian": (0.558744576 + 0.338226944 + 1.872152320 + 1.666972416) * 1e9 / 3e6,
         "sources": {
             "paper_2510_14564_gb300/csrc/project.cu":
                 "23aa6bfc8cd300502707d577fafd6c5232beace1ca655c77db2e4333be8e6e5a",
