@@ -161,16 +161,19 @@ def replica_throughput(steps: int, ms_max: float, world: int) -> float:
 # our arm
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1, n_grad: int = 0,
-                      sh_half: bool | None = None) -> dict:
+                      sh_half: bool | None = None, n_col: int | None = None) -> dict:
     """Minimum bytes each stage must move (per step) for N Gaussians seen
     from V views with P pixels in all, n_grad of them with a 2D gradient;
-    half: 16-bit colour records, sh_half: 16-bit SH storage (default: half)."""
+    half: 16-bit colour records, sh_half: 16-bit SH storage (default: half);
+    n_col: the records whose colour is deferred to the colour stage (None:
+    the projection colours every record)."""
     if sh_half is None:
         sh_half = half
     rec = 34 if half else 40            # id + xy + conic + opacity + rgb per processed instance
     sh_read = 140 if sh_half else 236
-    return {
-        "project": V * N * (sh_read + (46 if half else 52)),
+    sh_b = 96 if sh_half else 192
+    out = {
+        "project": V * N * ((44 if n_col is not None else sh_read) + (46 if half else 52)),
         "bin_sort": V * N * 8 + I * (12 + 24 + 8),
         "render_fwd": I_proc * rec + P * 20,
         "l1": P * 36,
@@ -187,6 +190,10 @@ def algorithmic_bytes(N, P, I, I_proc, half: bool, V: int = 1, n_grad: int = 0,
         "project_bwd_adam": N * ((44 + 4 + 48 + 88 + 132) + (24 + 576 + 576 + (96 if sh_half else 0)))
                             + n_grad * ((96 if sh_half else 192) + 48 + 24),
     }
+    if n_col is not None:
+        # the listed records: index, mean and SH read, colour written
+        out["colour"] = n_col * (4 + 12 + sh_b + (8 if half else 12))
+    return out
 
 
 # Warp instructions the reverse pass issues per (pixel, Gaussian) pair its
@@ -374,6 +381,8 @@ def run_ours(args):
     # Gaussians the reverse pass gave a 2D gradient (the iteration's projection
     # backward leaves the records as the reverse pass wrote them)
     n_grad = int((tr.frame.grad2d[:len(cams) * N * 12].view(-1, 12)[:, :9] != 0).any(1).sum().item())
+    # records whose colour the colour stage computed (the lists' records)
+    n_col = int(tr.frame.colour_count.sum().item()) if tr.frame.defer_colour else None
 
     f = tr.frame
     # tiles whose kept prefix ran short and were repaired, per step (read back
@@ -388,7 +397,7 @@ def run_ours(args):
     I_proc = int(f.tile_nproc.sum().item())
     pairs = int(f.n_proc.sum().item())           # (pixel, Gaussian) pairs the blend loops walk
     Pix = sum(c.W * c.H for c in cams)
-    ab = algorithmic_bytes(N, Pix, I, I_proc, True, len(cams), n_grad, learned_sh != L.GS_F32)
+    ab = algorithmic_bytes(N, Pix, I, I_proc, True, len(cams), n_grad, learned_sh != L.GS_F32, n_col)
     stage_ms = {k: statistics.mean(v) for k, v in stages.items()}
     it_stage_ms = {k: statistics.mean(v) for k, v in it_stages.items()}
     kernel_stages = {k: v for k, v in stage_ms.items() if k in ab}
@@ -430,6 +439,7 @@ def run_ours(args):
                        "stage_ms": {k: round(v, 4) for k, v in it_stage_ms.items()}},
                    "instances_full_lists": I_full, "instances_kept": I, "processed_instances": I_proc,
                    "pixel_pairs_processed": pairs, "gaussians_with_2d_gradient": n_grad,
+                   "records_coloured": n_col,
                    "flagged_tiles_per_step": {"mean": round(statistics.mean(flagged), 2), "max": max(flagged)},
                    "l2": "inputs larger than L2 (0.4-0.7 GB of parameters, 1.5+ GB of instances)",
                    "parallelism": "replicas" if world > 1 else "1 GPU",

@@ -143,12 +143,38 @@ long long gs_get_wait_limit(void);
  * bit for bit by any IEEE implementation of the same order.
  * d_quats, d_sh and d_splats must be 16-byte aligned and d_rect 8-byte
  * aligned (in the grouped layout: N a multiple of 4), else GS_ERR_ARG.
+ * d_sh may be NULL: no SH is read and every record's colour is zero, to be
+ * filled in by gs_colour_records for the records the tile lists reference.
  * Non-finite parameters cull the Gaussian and set GS_EW_NONFINITE. */
 int gs_project(const gs_camera *cams, int n_views, int N, const float *d_means,
                const float *d_log_scales, const float *d_quats, const float *d_opacity_logits,
                const void *d_sh, int sh_dtype, void *d_splats, int rgb_dtype, float *d_depth,
                int16_t *d_rect, int32_t *d_touched, int32_t *d_radius, int *d_err_word,
                gs_stream_t stream);
+
+/* a1, deferred colour: only the records the tile lists reference are ever
+ * read by the blend loops, so after gs_project with d_sh NULL their colours
+ * alone are computed, as gs_project computes them (the same code, the same
+ * bits), and written into their splat records (the other fields untouched).
+ * gs_colour_records colours each record d_list[0, *d_count) (device uint32
+ * count; record indices v*N+i, those at or above V*N ignored): the list
+ * gs_bin_sort_prefix leaves (d_colour_list, the records its kept lists
+ * reference, each once, marked colour_epoch in d_colour_mark).
+ * gs_colour_repaired colours, after a repair, the records of the lists of
+ * the *d_n_tiles tiles d_tiles[] (as gs_render_fwd lists the tiles to
+ * repair; ranges from d_tile_ranges, entries clamped to capacity) whose mark
+ * in d_mark (V*N uint32) is not yet epoch, marking them epoch (one atomic
+ * exchange each: each is coloured once); with no tile it returns at once.
+ * d_sh / d_splats not 16-byte or d_tile_ranges not 8-byte aligned, or a
+ * NULL pointer: GS_ERR_ARG. */
+int gs_colour_records(const gs_camera *cams, int n_views, int N, const float *d_means,
+                      const void *d_sh, int sh_dtype, const uint32_t *d_list, const uint32_t *d_count,
+                      void *d_splats, int rgb_dtype, gs_stream_t stream);
+int gs_colour_repaired(const gs_camera *cams, int n_views, int N, const float *d_means,
+                       const void *d_sh, int sh_dtype, const uint32_t *d_vals, long long capacity,
+                       const int32_t *d_tiles, const int32_t *d_n_tiles, const uint32_t *d_tile_ranges,
+                       uint32_t *d_mark, uint32_t epoch, void *d_splats, int rgb_dtype,
+                       gs_stream_t stream);
 
 /* a2. Tile binning and the (tile, depth) sort.
  * gs_bin_sort_workspace gives the scratch bytes gs_bin_sort needs for V*N
@@ -195,6 +221,10 @@ int gs_bin_sort(const gs_camera *cams, int n_views, int N, const float *d_depth,
  * one holding entry 2 limit + 64 (a tile with limit <= 0 keeps its whole
  * list).  Such a cut is not guaranteed, so gs_render_fwd checks it
  * (d_tile_count) and gs_bin_sort_prefix_repair rebuilds the tiles it lists.
+ * d_colour_list (optional, V*N uint32): the records the lists reference,
+ * each once, in no fixed order, *d_colour_count (uint32, zeroed by the call)
+ * of them, each marked colour_epoch in d_colour_mark (V*N uint32; both
+ * needed with the list) -- the input of gs_colour_records.
  * Overflow and workspace rules as gs_bin_sort.  Views of more than 16384
  * tiles get the full lists. */
 int gs_bin_sort_prefix_workspace(int n_views, int N, long long capacity, const gs_camera *cams,
@@ -203,8 +233,9 @@ int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, const float *d
                        const int16_t *d_rect, const int32_t *d_touched, const void *d_splats,
                        int rgb_dtype, const int32_t *d_tile_limit, long long capacity,
                        uint32_t *d_vals, uint32_t *d_tile_ranges, uint32_t *d_tile_count,
-                       uint64_t *d_keys, long long *d_n_instances, void *d_workspace,
-                       size_t workspace_bytes, int *d_err_word, gs_stream_t stream);
+                       uint64_t *d_keys, long long *d_n_instances, uint32_t *d_colour_list,
+                       uint32_t *d_colour_count, uint32_t *d_colour_mark, uint32_t colour_epoch,
+                       void *d_workspace, size_t workspace_bytes, int *d_err_word, gs_stream_t stream);
 
 /* Rebuild the full lists of the *d_flag_count tiles in d_flag_tiles (as
  * listed by gs_render_fwd) after the kept entries (*d_n_instances of them),

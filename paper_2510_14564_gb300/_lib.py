@@ -27,7 +27,7 @@ GS_MAX_VIEWS = 64
 SPLAT_BYTES = {GS_F32: 48, GS_BF16: 32, GS_F16: 32}
 
 # Every symbol include/gs103.h declares.
-EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_set_wait_limit", "gs_get_wait_limit", "gs_zero", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort", "gs_bin_sort_noalloc",
+EXPORTS = ["gs_version", "gs_strerror", "gs_launch_count", "gs_set_wait_limit", "gs_get_wait_limit", "gs_zero", "gs_project", "gs_colour_records", "gs_colour_repaired", "gs_bin_sort_workspace", "gs_bin_sort", "gs_bin_sort_noalloc",
            "gs_bin_sort_prefix_workspace", "gs_bin_sort_prefix", "gs_bin_sort_prefix_repair",
            "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_project_bwd", "gs_project_bwd_adam", "gs_adam_step",
            "gs_adam_flat", "gs_tile_features", "gs_mlp_predict", "gs_mlp_grad",
@@ -87,7 +87,10 @@ def lib():
         L.gs_bin_sort.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, I64, VP, VP, VP, VP, VP, SZ, VP, VP]
         L.gs_bin_sort_prefix_workspace.argtypes = [I32, I32, I64, P(GsCamera), P(SZ)]
         L.gs_bin_sort_prefix.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, VP, I32, VP, I64, VP, VP, VP, VP,
-                                         VP, VP, SZ, VP, VP]
+                                         VP, VP, VP, VP, ctypes.c_uint32, VP, SZ, VP, VP]
+        L.gs_colour_records.argtypes = [P(GsCamera), I32, I32, VP, VP, I32, VP, VP, VP, I32, VP]
+        L.gs_colour_repaired.argtypes = [P(GsCamera), I32, I32, VP, VP, I32, VP, I64, VP, VP, VP, VP,
+                                         ctypes.c_uint32, VP, I32, VP]
         L.gs_bin_sort_prefix_repair.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, VP, I64, VP, VP, VP, VP,
                                                 SZ, VP, VP]
         L.gs_bin_sort_noalloc.argtypes = [P(GsCamera), I32, I32, VP, VP, VP, I64, VP, VP, VP, VP, VP, VP]
@@ -232,13 +235,31 @@ def gs_bin_sort_prefix_workspace(cams, N, capacity) -> int:
 
 
 def gs_bin_sort_prefix(cams, N, depth, rect, touched, splats, rgb_dtype, tile_limit, capacity, vals,
-                       tile_ranges, tile_count, keys, n_instances, workspace, err_word, stream=None):
+                       tile_ranges, tile_count, keys, n_instances, workspace, err_word, stream=None,
+                       colour_list=None, colour_count=None, colour_mark=None, colour_epoch=0):
     ca = camera_array(cams)
     check(lib().gs_bin_sort_prefix(ca, len(cams), int(N), ptr(depth), ptr(rect), ptr(touched), ptr(splats),
                                    int(rgb_dtype), ptr(tile_limit), int(capacity), ptr(vals),
                                    ptr(tile_ranges), ptr(tile_count), ptr(keys), ptr(n_instances),
+                                   ptr(colour_list), ptr(colour_count), ptr(colour_mark), int(colour_epoch),
                                    ptr(workspace), workspace.numel() * workspace.element_size(),
                                    ptr(err_word), stream_ptr(stream)), "gs_bin_sort_prefix")
+
+
+def gs_colour_records(cams, N, means, sh, sh_dtype, rec_list, count, splats, rgb_dtype, stream=None):
+    ca = camera_array(cams)
+    check(lib().gs_colour_records(ca, len(cams), int(N), ptr(means), ptr(sh), int(sh_dtype), ptr(rec_list),
+                                  ptr(count), ptr(splats), int(rgb_dtype), stream_ptr(stream)),
+          "gs_colour_records")
+
+
+def gs_colour_repaired(cams, N, means, sh, sh_dtype, vals, capacity, tiles, n_tiles, tile_ranges, mark, epoch,
+                       splats, rgb_dtype, stream=None):
+    ca = camera_array(cams)
+    check(lib().gs_colour_repaired(ca, len(cams), int(N), ptr(means), ptr(sh), int(sh_dtype), ptr(vals),
+                                   int(capacity), ptr(tiles), ptr(n_tiles), ptr(tile_ranges), ptr(mark),
+                                   int(epoch), ptr(splats), int(rgb_dtype), stream_ptr(stream)),
+          "gs_colour_repaired")
 
 
 def gs_bin_sort_prefix_repair(cams, N, rect, touched, flag_tiles, flag_count, capacity, vals,

@@ -2022,8 +2022,11 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     const uint32_t *__restrict__ Mc, const uint32_t *__restrict__ last_chunk,
     const unsigned long long *__restrict__ tstart, const unsigned long long *__restrict__ total,
     long long cap, uint32_t *__restrict__ vals, const float *__restrict__ depth,
-    unsigned long long *__restrict__ keys, const uint32_t *__restrict__ max_last) {
+    unsigned long long *__restrict__ keys, const uint32_t *__restrict__ max_last,
+    uint32_t *__restrict__ colour_list, uint32_t *__restrict__ colour_count,
+    uint32_t *__restrict__ colour_mark, uint32_t colour_epoch) {
     extern __shared__ uint32_t s_cur[];
+    __shared__ uint32_t s_cbase;
     __shared__ int s_nact;                          // tiles that keep entries of this chunk
     __shared__ int s_box[4];                        // the active tiles' bounding box [x0, x1) x [y0, y1)
     __shared__ uint32_t s_g[kPlaceBatch];
@@ -2145,7 +2148,17 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
             }
             n_keep += tot;
         }
+        // each record lies in one chunk, read once: the kept ones go to the
+        // colour list (the records the lists reference) exactly once
+        if (colour_list && threadIdx.x == 0 && n_keep > 0) s_cbase = atomicAdd(colour_count, (uint32_t)n_keep);
         __syncthreads();
+        if (colour_list) {
+            for (int j = threadIdx.x; j < n_keep; j += kPlaceThreads) {
+                const uint32_t gj = s_g[j];
+                colour_list[s_cbase + j] = gj;
+                colour_mark[gj] = colour_epoch;
+            }
+        }
         // 2. each warp places the kept records' tiles in its own rows, in order.
         //    The (record, tile) pairs of 32 records are flattened record by
         //    record and handled 32 at a time: pairs on the same tile get slots
@@ -2206,6 +2219,23 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
             }
         }
         __syncthreads();
+    }
+}
+
+// The records that cover a tile (touched > 0), appended to a colour list and
+// marked: what the full lists reference.
+__global__ void __launch_bounds__(256) k_list_touched(const int32_t *__restrict__ touched, long long VN,
+                                                      uint32_t *__restrict__ list, uint32_t *__restrict__ count,
+                                                      uint32_t *__restrict__ mark, uint32_t epoch) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool t = r < VN && __ldg(touched + r) > 0;
+    const unsigned b = __ballot_sync(0xffffffffu, t);
+    uint32_t base = 0;
+    if ((threadIdx.x & 31) == 0 && b) base = atomicAdd(count, (uint32_t)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (t) {
+        list[base + __popc(b & lanemask_lt())] = (uint32_t)r;
+        mark[r] = epoch;
     }
 }
 
@@ -2322,28 +2352,36 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
                                   const int16_t *d_rect, const int32_t *d_touched, const void *d_splats,
                                   int rgb_dtype, const int32_t *d_tile_limit, long long capacity,
                                   uint32_t *d_vals, uint32_t *d_tile_ranges, uint32_t *d_tile_count,
-                                  uint64_t *d_keys, long long *d_n_instances, void *d_workspace,
-                                  size_t workspace_bytes, int *d_err_word, gs_stream_t stream) {
+                                  uint64_t *d_keys, long long *d_n_instances, uint32_t *d_colour_list,
+                                  uint32_t *d_colour_count, uint32_t *d_colour_mark, uint32_t colour_epoch,
+                                  void *d_workspace, size_t workspace_bytes, int *d_err_word,
+                                  gs_stream_t stream) {
     TileBatch tb;
     if (make_tile_batch(cams, n_views, &tb) != GS_OK) return GS_ERR_ARG;
     if (N < 0 || capacity < 0 || capacity > 0xF0000000ll) return GS_ERR_ARG;
     if (!d_depth || !d_rect || !d_touched || !d_splats || !d_vals || !d_tile_ranges || !d_n_instances ||
         !d_workspace)
         return GS_ERR_ARG;
+    if (d_colour_list && (!d_colour_count || !d_colour_mark)) return GS_ERR_ARG;
     if (rgb_dtype < GS_F32 || rgb_dtype > GS_F16) return GS_ERR_ARG;
     if (!aligned(d_workspace, 256) || !aligned(d_rect, 8) || !aligned(d_tile_ranges, 8) || !aligned(d_splats, 16))
         return GS_ERR_ARG;
     const long long VN = (long long)n_views * N;
     if (VN > 0xF0000000ll) return GS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (d_colour_list) cudaMemsetAsync(d_colour_count, 0, sizeof(uint32_t), st);
     PrePlan p = make_pre_plan(VN, tb);
     if (!p.ok) {
-        // views too large for the shared cursor row: the full lists
+        // views too large for the shared cursor row: the full lists (which
+        // reference every record that covers a tile)
         int rc = gs_bin_sort(cams, n_views, N, d_depth, d_rect, d_touched, capacity, d_vals, d_tile_ranges,
                              d_keys, d_n_instances, d_workspace, workspace_bytes, d_err_word, stream);
         if (rc == GS_OK && d_tile_count)
             { k_range_counts<<<cdiv(tb.total_tiles, 256), 256, 0, st>>>(
                 reinterpret_cast<const uint2 *>(d_tile_ranges), tb.total_tiles, d_tile_count); count_launches(1); }
+        if (rc == GS_OK && d_colour_list && VN > 0)
+            { k_list_touched<<<cdiv(VN, 256), 256, 0, st>>>(d_touched, VN, d_colour_list, d_colour_count,
+                                                              d_colour_mark, colour_epoch); count_launches(1); }
         return rc == GS_OK ? launch_status() : rc;
     }
     if (workspace_bytes < p.bytes) return GS_ERR_CAPACITY;
@@ -2419,7 +2457,9 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
         allow_dynamic_smem((const void *)k_pre_place, smem);      // 25 KB of its own static arrays
         { k_pre_place<<<nchunks, kPlaceThreads, smem, st>>>(tb, N, p.Cv, p.Tmax, order, rs, bnd, Mc, lastc, tstart,
                                                  tstart + T, capacity, d_vals, d_depth,
-                                                 reinterpret_cast<unsigned long long *>(d_keys), max_last); count_launches(1); }
+                                                 reinterpret_cast<unsigned long long *>(d_keys), max_last,
+                                                 d_colour_list, d_colour_count, d_colour_mark, colour_epoch);
+          count_launches(1); }
     }
     return launch_status();
 }

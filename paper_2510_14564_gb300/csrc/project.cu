@@ -305,6 +305,27 @@ __device__ __forceinline__ void discrete_path(const ViewGeom &cam, float mx, flo
     o.visible = true;
 }
 
+// The colour max(0, 0.5 + sum_j Y_j(dir) k_j) of Gaussian i with mean m seen
+// from campos (dir the unit vector from the camera to the mean): the one code
+// path of the projection and of the deferred colour, so both give the same bits.
+template <int SDT>
+__device__ __forceinline__ void splat_colour(const float campos[3], float mx, float my, float mz,
+                                             const void *sh, long long i, float c[3]) {
+    const float dx = mx - campos[0], dy = my - campos[1], dz = mz - campos[2];
+    const float inv = rsqrtf(fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx))));
+    float Y[16];
+    sh_basis(dx * inv, dy * inv, dz * inv, Y);
+    float k[48];
+    load_sh<SDT>(sh, i, k);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.5f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc = fmaf(Y[j], k[3 * j + ch], acc);
+        c[ch] = fmaxf(acc, 0.0f);
+    }
+}
+
 __device__ __forceinline__ bool finite_params(float mx, float my, float mz, const float ls[3],
                                               const float q[4]) {
     bool f = isfinite(mx) && isfinite(my) && isfinite(mz);
@@ -354,21 +375,9 @@ __global__ void __launch_bounds__(128) k_project(GeomBatch views, int N, const f
         float lg = __ldg(logits + i);
         float o = 1.0f / (1.0f + expf(-lg));
         float lo = log2f(o);
-        // colour: max(0, 0.5 + sum_j Y_j(dir) k_j)
-        float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
-        float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-        float Y[16];
-        sh_basis(dx * inv, dy * inv, dz * inv, Y);
-        float k[48];
-        load_sh<SDT>(sh, i, k);
-        float c[3];
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.5f;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) acc = fmaf(Y[j], k[3 * j + ch], acc);
-            c[ch] = fmaxf(acc, 0.0f);
-        }
+        // colour (none without SH: gs_colour_records fills in the records the lists reference)
+        float c[3] = {0.0f, 0.0f, 0.0f};
+        if (sh) splat_colour<SDT>(cam.campos, mx, my, mz, sh, i, c);
         g0 = make_float4(d.u, d.v, -0.5f * kLog2e * A, -kLog2e * B);
         if (RDT == GS_F32) {
             g1 = make_float4(-0.5f * kLog2e * C, lo, c[0], c[1]);
@@ -986,6 +995,72 @@ __global__ void __launch_bounds__(256, 4) k_bwd_adam_sh(int N, float *__restrict
 }
 
 // ---------------------------------------------------------------------------
+// a1, deferred: the colours of the records the tile lists reference
+// ---------------------------------------------------------------------------
+// Record r's colour written into its splat record (the other fields
+// untouched), as k_project would have written it.
+template <int SDT, int RDT>
+__device__ __forceinline__ void colour_record(const GeomBatch &views, int N, const float *__restrict__ means,
+                                              const void *__restrict__ sh, long long r, void *__restrict__ splats) {
+    const int vi = (int)(r / N);
+    const long long i = r - (long long)vi * N;
+    const float mx = __ldg(means + 3 * i), my = __ldg(means + 3 * i + 1), mz = __ldg(means + 3 * i + 2);
+    float c[3];
+    splat_colour<SDT>(views.v[vi].campos, mx, my, mz, sh, i, c);
+    if (RDT == GS_F32) {
+        SplatF32 *p = reinterpret_cast<SplatF32 *>(splats) + r;
+        *reinterpret_cast<float2 *>(&p->g1.z) = make_float2(c[0], c[1]);
+        p->g2.x = c[2];
+    } else {
+        SplatHalf *p = reinterpret_cast<SplatHalf *>(splats) + r;
+        *reinterpret_cast<uint2 *>(&p->g1.z) = make_uint2(pack2(c[0], c[1], RDT), pack2(c[2], 0.0f, RDT));
+    }
+}
+
+// Each record list[i], i < *count, gets its colour (colour_record).
+// A grid-stride loop: the count is known on the device only.
+template <int SDT, int RDT>
+__global__ void __launch_bounds__(128) k_colour_records(GeomBatch views, int N, const float *__restrict__ means,
+                                                        const void *__restrict__ sh,
+                                                        const uint32_t *__restrict__ list,
+                                                        const uint32_t *__restrict__ count,
+                                                        void *__restrict__ splats) {
+    const long long n = *count, VN = (long long)views.n * N;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long r = __ldg(list + q);
+        if (r >= VN) continue;
+        colour_record<SDT, RDT>(views, N, means, sh, r, splats);
+    }
+}
+
+// The records of the lists of the tiles tiles[0, *n_tiles) not yet marked
+// `epoch`: marked (one atomic exchange each, so that one thread takes each)
+// and coloured by the thread that took it.  A CTA per tile in turn; with no
+// tile every CTA returns at once.
+template <int SDT, int RDT>
+__global__ void __launch_bounds__(256) k_colour_repaired(GeomBatch views, int N, const float *__restrict__ means,
+                                                         const void *__restrict__ sh,
+                                                         const uint32_t *__restrict__ vals, long long cap,
+                                                         const int32_t *__restrict__ tiles,
+                                                         const int32_t *__restrict__ n_tiles,
+                                                         const uint2 *__restrict__ ranges,
+                                                         uint32_t *__restrict__ mark, uint32_t epoch,
+                                                         void *__restrict__ splats) {
+    const int nt = *n_tiles;
+    const long long VN = (long long)views.n * N;
+    for (int f = blockIdx.x; f < nt; f += gridDim.x) {
+        const uint2 r = ranges[tiles[f]];
+        const long long hi = min((long long)r.y, cap);
+        for (long long e = (long long)r.x + threadIdx.x; e < hi; e += blockDim.x) {
+            const uint32_t g = __ldg(vals + e);
+            if ((long long)g >= VN || mark[g] == epoch) continue;
+            if (atomicExch(mark + g, epoch) != epoch) colour_record<SDT, RDT>(views, N, means, sh, g, splats);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 int make_geom_batch(const gs_camera *cams, int n_views, GeomBatch *out) {
@@ -1035,20 +1110,99 @@ extern "C" int gs_project(const gs_camera *cams, int n_views, int N, const float
     if (make_geom_batch(cams, n_views, &vb) != GS_OK) return GS_ERR_ARG;
     if (N < 0) return GS_ERR_ARG;
     if (N == 0) return GS_OK;
-    if (!d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_sh || !d_splats ||
-        !d_depth || !d_rect || !d_touched)
+    if (!d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_splats || !d_depth || !d_rect ||
+        !d_touched)
         return GS_ERR_ARG;
     if (sh_dtype < GS_F32 || sh_dtype > GS_F16 || rgb_dtype < GS_F32 || rgb_dtype > GS_F16) return GS_ERR_ARG;
-    if (!aligned(d_quats, 16) || !aligned(d_sh, 16) || !aligned(d_splats, 16) || !aligned(d_rect, 8))
+    if (!aligned(d_quats, 16) || (d_sh && !aligned(d_sh, 16)) || !aligned(d_splats, 16) || !aligned(d_rect, 8))
         return GS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     short4 *rect = reinterpret_cast<short4 *>(d_rect);
-    if (sh_dtype == GS_F32)
+    if (sh_dtype == GS_F32 || !d_sh)
         launch_project<GS_F32>(rgb_dtype, vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_splats, d_depth, rect, d_touched, d_radius, d_err_word, st);
     else if (sh_dtype == GS_BF16)
         launch_project<GS_BF16>(rgb_dtype, vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_splats, d_depth, rect, d_touched, d_radius, d_err_word, st);
     else
         launch_project<GS_F16>(rgb_dtype, vb, N, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_splats, d_depth, rect, d_touched, d_radius, d_err_word, st);
+    return launch_status();
+}
+
+template <int SDT>
+static void launch_colour_records(int rdt, const GeomBatch &vb, int N, const float *m, const void *sh,
+                                  const uint32_t *list, const uint32_t *count, void *splats, int grid,
+                                  cudaStream_t st) {
+    if (rdt == GS_F32)
+        { k_colour_records<SDT, GS_F32><<<grid, 128, 0, st>>>(vb, N, m, sh, list, count, splats); count_launches(1); }
+    else if (rdt == GS_BF16)
+        { k_colour_records<SDT, GS_BF16><<<grid, 128, 0, st>>>(vb, N, m, sh, list, count, splats); count_launches(1); }
+    else
+        { k_colour_records<SDT, GS_F16><<<grid, 128, 0, st>>>(vb, N, m, sh, list, count, splats); count_launches(1); }
+}
+
+static int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+extern "C" int gs_colour_records(const gs_camera *cams, int n_views, int N, const float *d_means,
+                                 const void *d_sh, int sh_dtype, const uint32_t *d_list, const uint32_t *d_count,
+                                 void *d_splats, int rgb_dtype, gs_stream_t stream) {
+    GeomBatch vb;
+    if (make_geom_batch(cams, n_views, &vb) != GS_OK) return GS_ERR_ARG;
+    if (N < 0) return GS_ERR_ARG;
+    if (N == 0) return GS_OK;
+    if (!d_means || !d_sh || !d_list || !d_count || !d_splats) return GS_ERR_ARG;
+    if (sh_dtype < GS_F32 || sh_dtype > GS_F16 || rgb_dtype < GS_F32 || rgb_dtype > GS_F16) return GS_ERR_ARG;
+    if (!aligned(d_sh, 16) || !aligned(d_splats, 16)) return GS_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int grid = sm_count() * 8;                // 8 CTAs of 128 per SM, grid-stride over the list
+    if (sh_dtype == GS_F32)
+        launch_colour_records<GS_F32>(rgb_dtype, vb, N, d_means, d_sh, d_list, d_count, d_splats, grid, st);
+    else if (sh_dtype == GS_BF16)
+        launch_colour_records<GS_BF16>(rgb_dtype, vb, N, d_means, d_sh, d_list, d_count, d_splats, grid, st);
+    else
+        launch_colour_records<GS_F16>(rgb_dtype, vb, N, d_means, d_sh, d_list, d_count, d_splats, grid, st);
+    return launch_status();
+}
+
+template <int SDT>
+static void launch_colour_repaired(int rdt, const GeomBatch &vb, int N, const float *m, const void *sh,
+                                   const uint32_t *vals, long long cap, const int32_t *tiles, const int32_t *nt,
+                                   const uint2 *ranges, uint32_t *mark, uint32_t epoch, void *splats, int grid,
+                                   cudaStream_t st) {
+    if (rdt == GS_F32)
+        { k_colour_repaired<SDT, GS_F32><<<grid, 256, 0, st>>>(vb, N, m, sh, vals, cap, tiles, nt, ranges, mark, epoch, splats); count_launches(1); }
+    else if (rdt == GS_BF16)
+        { k_colour_repaired<SDT, GS_BF16><<<grid, 256, 0, st>>>(vb, N, m, sh, vals, cap, tiles, nt, ranges, mark, epoch, splats); count_launches(1); }
+    else
+        { k_colour_repaired<SDT, GS_F16><<<grid, 256, 0, st>>>(vb, N, m, sh, vals, cap, tiles, nt, ranges, mark, epoch, splats); count_launches(1); }
+}
+
+extern "C" int gs_colour_repaired(const gs_camera *cams, int n_views, int N, const float *d_means,
+                                  const void *d_sh, int sh_dtype, const uint32_t *d_vals, long long capacity,
+                                  const int32_t *d_tiles, const int32_t *d_n_tiles, const uint32_t *d_tile_ranges,
+                                  uint32_t *d_mark, uint32_t epoch, void *d_splats, int rgb_dtype,
+                                  gs_stream_t stream) {
+    GeomBatch vb;
+    if (make_geom_batch(cams, n_views, &vb) != GS_OK) return GS_ERR_ARG;
+    if (N < 0 || capacity < 0) return GS_ERR_ARG;
+    if (!d_means || !d_sh || !d_tiles || !d_n_tiles || !d_tile_ranges || !d_mark || !d_splats ||
+        (capacity > 0 && !d_vals))
+        return GS_ERR_ARG;
+    if (sh_dtype < GS_F32 || sh_dtype > GS_F16 || rgb_dtype < GS_F32 || rgb_dtype > GS_F16) return GS_ERR_ARG;
+    if (!aligned(d_sh, 16) || !aligned(d_splats, 16) || !aligned(d_tile_ranges, 8)) return GS_ERR_ARG;
+    if (N == 0 || capacity == 0) return GS_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint2 *rg = reinterpret_cast<const uint2 *>(d_tile_ranges);
+    const int grid = sm_count() * 2;
+    if (sh_dtype == GS_F32)
+        launch_colour_repaired<GS_F32>(rgb_dtype, vb, N, d_means, d_sh, d_vals, capacity, d_tiles, d_n_tiles, rg, d_mark, epoch, d_splats, grid, st);
+    else if (sh_dtype == GS_BF16)
+        launch_colour_repaired<GS_BF16>(rgb_dtype, vb, N, d_means, d_sh, d_vals, capacity, d_tiles, d_n_tiles, rg, d_mark, epoch, d_splats, grid, st);
+    else
+        launch_colour_repaired<GS_F16>(rgb_dtype, vb, N, d_means, d_sh, d_vals, capacity, d_tiles, d_n_tiles, rg, d_mark, epoch, d_splats, grid, st);
     return launch_status();
 }
 

@@ -156,11 +156,17 @@ class Frame:
 
     def __init__(self, cams, N: int, rgb_dtype: int = L.GS_F32, sh_dtype: int = L.GS_F32,
                  capacity: int | None = None, schedule: Schedule | None = None, device=None,
-                 prefix: bool = False):
+                 prefix: bool = False, defer_colour: bool = True):
         """prefix: bin with gs_bin_sort_prefix (exact list prefixes that blending
-        never runs past) instead of the full lists of gs_bin_sort."""
+        never runs past) instead of the full lists of gs_bin_sort.
+        defer_colour (with prefix): project without SH and colour only the
+        records the kept lists reference (gs_colour_records), after binning
+        and after a repair."""
         self.dev = device or _dev()
         self.prefix = prefix
+        self.defer_colour = defer_colour and prefix
+        self.colour_src = None       # (means, sh) of the last projection whose colours are deferred
+        self.colour_epoch = 0        # this step's mark of the records coloured
         self.cams = list(cams)
         self.V = len(self.cams)
         self.N = int(N)
@@ -174,6 +180,7 @@ class Frame:
         self._alloc_gaussians(self.N)
         self.err = torch.zeros(1, dtype=torch.int32, device=d)
         self.n_inst = torch.zeros(1, dtype=torch.int64, device=d)
+        self.colour_count = torch.zeros(1, dtype=torch.int32, device=d)   # records the binning listed
         self.ranges = torch.empty(self.T * 2, dtype=torch.int32, device=d)
         self.tile_count = torch.zeros(self.T, dtype=torch.int32, device=d)
         self.img = torch.empty(3 * self.P, dtype=torch.float32, device=d)
@@ -259,6 +266,9 @@ class Frame:
         self.radius = torch.empty(VN, dtype=torch.int32, device=d)
         self.grad2d = torch.empty(VN * 12, dtype=torch.float32, device=d)
         self.grad2d_zero = False     # whether the 2D-gradient records are known to be all zero
+        if self.defer_colour:
+            self.colour_mark = torch.zeros(VN, dtype=torch.int32, device=d)
+            self.colour_list = torch.empty(VN, dtype=torch.int32, device=d)
         self.dparams = torch.empty(PARAM_FLOATS * self.gcap, dtype=torch.float32, device=d)
 
     def resize(self, N: int) -> None:
@@ -307,16 +317,42 @@ class Frame:
 
     # -- forward -----------------------------------------------------------
     def project(self, params: dict) -> None:
+        defer = self.defer_colour
+        self.colour_src = (params["means"], params["sh"]) if defer else None
         L.gs_project(self.cams, self.N, params["means"], params["log_scales"], params["quats"],
-                     params["opacity_logits"], params["sh"], self.sh_dtype, self.splats,
+                     params["opacity_logits"], None if defer else params["sh"], self.sh_dtype, self.splats,
                      self.rgb_dtype, self.depth, self.rect, self.touched, self.radius, self.err)
+
+    def colour_kept(self) -> None:
+        """The deferred colours of the records the kept lists reference (after
+        bin_sort with colour=False)."""
+        if self.colour_src is None:
+            return
+        means, sh = self.colour_src
+        L.gs_colour_records(self.cams, self.N, means, sh, self.sh_dtype, self.colour_list, self.colour_count,
+                            self.splats, self.rgb_dtype)
+
+    def _colour_repaired(self) -> None:
+        """The deferred colours of the records only the repaired lists reference."""
+        if self.colour_src is None:
+            return
+        means, sh = self.colour_src
+        L.gs_colour_repaired(self.cams, self.N, means, sh, self.sh_dtype, self.vals, self.capacity,
+                             self.flag_tiles, self.flag_count, self.ranges, self.colour_mark, self.colour_epoch,
+                             self.splats, self.rgb_dtype)
 
     def _bin(self, capacity: int, keys) -> None:
         if self.prefix:
             lim = self.tile_nproc if self.limit_history else None
+            col = self.colour_src is not None and capacity > 0
+            if col:
+                self.colour_epoch += 1
             L.gs_bin_sort_prefix(self.cams, self.N, self.depth, self.rect, self.touched, self.splats,
                                  self.rgb_dtype, lim, capacity, self.vals, self.ranges, self.tile_count,
-                                 keys, self.n_inst, self.ws, self.err)
+                                 keys, self.n_inst, self.ws, self.err,
+                                 colour_list=self.colour_list if col else None,
+                                 colour_count=self.colour_count if col else None,
+                                 colour_mark=self.colour_mark if col else None, colour_epoch=self.colour_epoch)
         else:
             L.gs_bin_sort(self.cams, self.N, self.depth, self.rect, self.touched, capacity, self.vals,
                           self.ranges, keys, self.n_inst, self.ws, self.err)
@@ -337,7 +373,9 @@ class Frame:
             self.err_event = torch.cuda.Event()
             self.err_event.record()
 
-    def bin_sort(self, want_keys: bool = False) -> None:
+    def bin_sort(self, want_keys: bool = False, colour: bool = True) -> None:
+        """Bin and sort; colour: then the deferred colours of the kept records
+        (else the caller calls colour_kept())."""
         self._watch_errors(issue=False)
         if self.vals is None:
             # first call: size the instance buffers from the exact count
@@ -352,6 +390,8 @@ class Frame:
         elif want_keys and self.keys is None:
             self.reserve(self.capacity, with_keys=True)
         self._bin(self.capacity, self.keys if want_keys else None)
+        if colour:
+            self.colour_kept()
 
     @property
     def use_learned(self) -> bool:
@@ -504,6 +544,7 @@ class Frame:
         L.gs_bin_sort_prefix_repair(self.cams, self.N, self.rect, self.touched, self.flag_tiles,
                                     self.flag_count, self.capacity, self.vals, self.ranges, self.n_inst,
                                     self.ws, self.err)
+        self._colour_repaired()
         rep = {"mode": L.GS_SCHED_ORDER, "order": self.flag_tiles, "queue": self.queue,
                "n_order": self.flag_count}
         L.gs_render_fwd(self.cams, self.ranges, self.vals, self.splats, self.rgb_dtype, rep, self.img,
@@ -748,7 +789,9 @@ class Trainer:
         f.project(pk)
         f.zero_grad2d_async()                  # overlaps the binning (latency-bound, SM slots to spare)
         mk("bin_sort")
-        f.bin_sort()
+        f.bin_sort(colour=False)
+        mk("colour")
+        f.colour_kept()
         mk("sched_fwd")
         f.render(timing=timing, mark=mark)
         f.prepare_bwd_async(timing=train_now)  # overlaps the L1
