@@ -685,7 +685,11 @@ class Trainer:
 
     def __init__(self, cams, params_flat: torch.Tensor, N: int, targets: torch.Tensor,
                  rgb_dtype: int = L.GS_F32, sh_storage: int = L.GS_F32,
-                 schedule: Schedule | None = None, lr=DEFAULT_LR, prefix: bool = True):
+                 schedule: Schedule | None = None, lr=DEFAULT_LR, prefix: bool = True,
+                 defer_colour: bool = True):
+        """defer_colour: colour only the records the kept lists reference (see
+        Frame); off where repairs are frequent, since a repaired full list's
+        records are coloured one by one."""
         self.N = N
         self.p = params_flat
         self.m = torch.zeros_like(params_flat)
@@ -700,7 +704,7 @@ class Trainer:
         else:
             self.sh_shadow = None
         self.frame = Frame(cams, N, rgb_dtype=rgb_dtype, sh_dtype=sh_storage, schedule=schedule,
-                           device=params_flat.device, prefix=prefix)
+                           device=params_flat.device, prefix=prefix, defer_colour=defer_colour)
         if targets.numel() != 3 * self.frame.P:
             raise ValueError(f"targets must hold 3 x {self.frame.P} values (every view's pixels, "
                              f"view after view), got {targets.numel()}")
