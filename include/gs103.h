@@ -224,7 +224,8 @@ int gs_bin_sort(const gs_camera *cams, int n_views, int N, const float *d_depth,
  * d_colour_list (optional, V*N uint32): the records the lists reference,
  * each once, in no fixed order, *d_colour_count (uint32, zeroed by the call)
  * of them, each marked colour_epoch in d_colour_mark (V*N uint32; both
- * needed with the list) -- the input of gs_colour_records.
+ * needed with the list) -- the input of gs_colour_records; refused
+ * (GS_ERR_ARG) for views that get the full lists.
  * Overflow and workspace rules as gs_bin_sort.  Views of more than 16384
  * tiles get the full lists. */
 int gs_bin_sort_prefix_workspace(int n_views, int N, long long capacity, const gs_camera *cams,

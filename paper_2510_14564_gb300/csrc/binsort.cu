@@ -2222,23 +2222,6 @@ __global__ void __launch_bounds__(kPlaceThreads) k_pre_place(
     }
 }
 
-// The records that cover a tile (touched > 0), appended to a colour list and
-// marked: what the full lists reference.
-__global__ void __launch_bounds__(256) k_list_touched(const int32_t *__restrict__ touched, long long VN,
-                                                      uint32_t *__restrict__ list, uint32_t *__restrict__ count,
-                                                      uint32_t *__restrict__ mark, uint32_t epoch) {
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool t = r < VN && __ldg(touched + r) > 0;
-    const unsigned b = __ballot_sync(0xffffffffu, t);
-    uint32_t base = 0;
-    if ((threadIdx.x & 31) == 0 && b) base = atomicAdd(count, (uint32_t)__popc(b));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (t) {
-        list[base + __popc(b & lanemask_lt())] = (uint32_t)r;
-        mark[r] = epoch;
-    }
-}
-
 __global__ void k_range_counts(const uint2 *__restrict__ ranges, int T, uint32_t *__restrict__ out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < T) out[t] = ranges[t].y - ranges[t].x;
@@ -2369,21 +2352,19 @@ extern "C" int gs_bin_sort_prefix(const gs_camera *cams, int n_views, int N, con
     const long long VN = (long long)n_views * N;
     if (VN > 0xF0000000ll) return GS_ERR_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (d_colour_list) cudaMemsetAsync(d_colour_count, 0, sizeof(uint32_t), st);
     PrePlan p = make_pre_plan(VN, tb);
     if (!p.ok) {
         // views too large for the shared cursor row: the full lists (which
-        // reference every record that covers a tile)
+        // reference every record that covers a tile: nothing to list)
+        if (d_colour_list) return GS_ERR_ARG;
         int rc = gs_bin_sort(cams, n_views, N, d_depth, d_rect, d_touched, capacity, d_vals, d_tile_ranges,
                              d_keys, d_n_instances, d_workspace, workspace_bytes, d_err_word, stream);
         if (rc == GS_OK && d_tile_count)
             { k_range_counts<<<cdiv(tb.total_tiles, 256), 256, 0, st>>>(
                 reinterpret_cast<const uint2 *>(d_tile_ranges), tb.total_tiles, d_tile_count); count_launches(1); }
-        if (rc == GS_OK && d_colour_list && VN > 0)
-            { k_list_touched<<<cdiv(VN, 256), 256, 0, st>>>(d_touched, VN, d_colour_list, d_colour_count,
-                                                              d_colour_mark, colour_epoch); count_launches(1); }
         return rc == GS_OK ? launch_status() : rc;
     }
+    if (d_colour_list) cudaMemsetAsync(d_colour_count, 0, sizeof(uint32_t), st);
     if (workspace_bytes < p.bytes) return GS_ERR_CAPACITY;
     char *ws = reinterpret_cast<char *>(d_workspace);
     uint32_t *dk0 = (uint32_t *)(ws + p.dk0), *dk1 = (uint32_t *)(ws + p.dk1);

@@ -164,10 +164,12 @@ class Frame:
         and after a repair."""
         self.dev = device or _dev()
         self.prefix = prefix
-        self.defer_colour = defer_colour and prefix
+        self.cams = list(cams)
+        # (views of more than 16384 tiles get full lists, which reference every
+        # visible record: nothing to defer)
+        self.defer_colour = defer_colour and prefix and max(c.n_tiles for c in self.cams) <= 16384
         self.colour_src = None       # (means, sh) of the last projection whose colours are deferred
         self.colour_epoch = 0        # this step's mark of the records coloured
-        self.cams = list(cams)
         self.V = len(self.cams)
         self.N = int(N)
         self.rgb_dtype = rgb_dtype
