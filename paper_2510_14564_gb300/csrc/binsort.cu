@@ -359,14 +359,14 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_pass(
     for (int it = 0; it < kSortItems; ++it) {
         const long long idx = base + it * 32 + l;
         const bool valid = idx < (long long)n;
-        const uint32_t d = valid ? ((key[it] >> shift) & 255u) : kRadix;
-        const unsigned peers = warp_peers(d, 8);
+        const uint32_t dig = valid ? ((key[it] >> shift) & 255u) : kRadix;
+        const unsigned peers = warp_peers(dig, 8);
         const unsigned rank = __popc(peers & lanemask_lt());
         // the first lane of each digit adds the digit's lanes to the warp's
         // count and hands the count before them to its peers; the warp
         // barrier orders the next item's additions after this one's
         uint32_t old = 0u;
-        if (valid && rank == 0) old = atomicAdd(&s_wh[w][d], (uint32_t)__popc(peers));
+        if (valid && rank == 0) old = atomicAdd(&s_wh[w][dig], (uint32_t)__popc(peers));
         __syncwarp();
         const uint32_t before = __shfl_sync(0xffffffffu, old, __ffs(peers) - 1);
         loc[it] = valid ? before + rank : 0xffffffffu;
